@@ -1,0 +1,152 @@
+/*
+ * CPU oracle for the LWE-style PIR of the QPADL spectrum-database query path
+ * (arxiv 2510.03631).  TEST INFRASTRUCTURE ONLY: the tests, the smoke check
+ * and the benchmark's CPU-baseline leg are the only code that may load it.
+ * It shares no code, header, table or constant generator with the CUDA path.
+ *
+ * Everything is exact integer arithmetic in Z_q with q = 2^32, i.e. uint32_t
+ * with wraparound.  Each function is the plain definition, a loop nest in the
+ * order the definition is written, with no blocking or reordering; the only
+ * concession to speed is an optional OpenMP split over independent output
+ * rows, which changes no arithmetic.
+ *
+ * What the paper fixes and what is read into it:
+ *  - Def. 1 (Sec. 3, PIR): Query(theta) -> q ; Response(q) -> rho computed
+ *    from the server's local database ; BlockReconst(rho) -> D_theta.
+ *  - Sec. 5.2 ("Parallel Chor-PIR", "Parallel Goldberg-PIR", Alg. 3/4): the
+ *    server's work is one product of the query with the whole database
+ *    matrix, accumulated "mod q" (Alg. 4).
+ *  - Sec. 5.3 (offline-online mode): query-independent work moves offline;
+ *    here that is the hint H = D * A.
+ *  - The lattice instantiation itself (public A, secret s, noise e, scale
+ *    Delta = q / p, rounding in Recover) is the standard single-server LWE
+ *    PIR; the paper states no formula for it, so the readings are:
+ *      Setup   : A[j][k] = hi32(SplitMix64 output number j*n+k, state = seed)
+ *      Hint    : H[i][k] = sum_j D[i][j] * A[j][k]                 (mod 2^32)
+ *      Query   : qu[j]  = sum_k A[j][k]*s[k] + e[j] + Delta*[j == col]
+ *      Answer  : ans[i] = sum_j D[i][j] * qu[j]                    (mod 2^32)
+ *      Recover : x = ans[i] - sum_k H[i][k]*s[k];  d = floor((x + Delta/2) / Delta) mod p
+ *    A record is a column of D; digits are unsigned in [0, p), p = 2^l.
+ */
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014): state advances by the golden gamma, the output
+ * is the state passed through the variant-13 finaliser.  Output number i
+ * (0-based) from initial state `seed` therefore uses state seed + (i+1)*gamma. */
+static uint64_t oracle_splitmix64_at(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + (i + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Exposed so the tests can check the generator against its published vectors. */
+uint64_t oracle_splitmix64(uint64_t seed, uint64_t i)
+{
+    return oracle_splitmix64_at(seed, i);
+}
+
+/* Setup: the public matrix A in Z_q^{C x n}, row-major, from its seed. */
+void oracle_gen_a(uint64_t seed, uint64_t C, uint64_t n, uint32_t *A)
+{
+    for (uint64_t j = 0; j < C; ++j)
+        for (uint64_t k = 0; k < n; ++k)
+            A[j * n + k] = (uint32_t)(oracle_splitmix64_at(seed, j * n + k) >> 32);
+}
+
+static int oracle_threads(int nthreads)
+{
+    return nthreads > 0 ? nthreads : 1;
+}
+
+/* Hint (offline, Sec. 5.3): H = D * A over Z_q.  D: R x C, A: C x n, H: R x n. */
+void oracle_hint(const uint8_t *D, uint64_t R, uint64_t C,
+                 const uint32_t *A, uint64_t n, uint32_t *H, int nthreads)
+{
+    int nt = oracle_threads(nthreads);
+    (void)nt;
+#pragma omp parallel for num_threads(nt) schedule(static)
+    for (int64_t i = 0; i < (int64_t)R; ++i) {
+        for (uint64_t k = 0; k < n; ++k) {
+            uint32_t acc = 0;
+            for (uint64_t j = 0; j < C; ++j)
+                acc += (uint32_t)D[(uint64_t)i * C + j] * A[j * n + k];
+            H[(uint64_t)i * n + k] = acc;
+        }
+    }
+}
+
+/* Query (Def. 1, Client.Query): qu = A*s + e + Delta * u_col over Z_q.
+ * e is a signed integer reduced mod 2^32. */
+void oracle_query(const uint32_t *A, uint64_t C, uint64_t n, const uint32_t *s,
+                  const int32_t *e, uint64_t col, uint32_t delta, uint32_t *qu)
+{
+    for (uint64_t j = 0; j < C; ++j) {
+        uint32_t acc = 0;
+        for (uint64_t k = 0; k < n; ++k)
+            acc += A[j * n + k] * s[k];
+        acc += (uint32_t)e[j];
+        if (j == col)
+            acc += delta;
+        qu[j] = acc;
+    }
+}
+
+/* Answer (Def. 1, DB.Query.Response; Sec. 5.2 "rho <- q . DB", accumulated
+ * mod q as in Alg. 4): ans = D * qu over Z_q, digits read unsigned. */
+void oracle_answer(const uint8_t *D, uint64_t R, uint64_t C,
+                   const uint32_t *qu, uint32_t *ans, int nthreads)
+{
+    int nt = oracle_threads(nthreads);
+    (void)nt;
+#pragma omp parallel for num_threads(nt) schedule(static)
+    for (int64_t i = 0; i < (int64_t)R; ++i) {
+        uint32_t acc = 0;
+        for (uint64_t j = 0; j < C; ++j)
+            acc += (uint32_t)D[(uint64_t)i * C + j] * qu[j];
+        ans[i] = acc;
+    }
+}
+
+/* Batched answer (Alg. 4's batch of queries): each query answered on its own.
+ * Q holds query b at Q[b*C .. b*C+C-1]; answer b goes to ans[b*R .. b*R+R-1]. */
+void oracle_answer_batch(const uint8_t *D, uint64_t R, uint64_t C,
+                         const uint32_t *Q, uint64_t B, uint32_t *ans, int nthreads)
+{
+    for (uint64_t b = 0; b < B; ++b)
+        oracle_answer(D, R, C, Q + b * C, ans + b * R, nthreads);
+}
+
+/* Recover (Def. 1, Client.BlockReconst): strip the mask H*s, then round to
+ * the nearest multiple of Delta = 2^32 / p and reduce mod p.  p = 2^l with
+ * 1 <= l <= 8, so dividing by Delta is a right shift by 32 - l and the
+ * "mod p" is implied by the 32-bit wrap. */
+void oracle_recover(const uint32_t *ans, const uint32_t *H, uint64_t R, uint64_t n,
+                    const uint32_t *s, uint32_t log2_p, uint8_t *out)
+{
+    uint32_t shift = 32u - log2_p;
+    uint32_t half = 1u << (shift - 1u);
+    for (uint64_t i = 0; i < R; ++i) {
+        uint32_t mask = 0;
+        for (uint64_t k = 0; k < n; ++k)
+            mask += H[i * n + k] * s[k];
+        uint32_t x = ans[i] - mask;
+        out[i] = (uint8_t)((uint32_t)(x + half) >> shift);
+    }
+}
+
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
