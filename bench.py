@@ -1,0 +1,408 @@
+"""Benchmark of the LWE-style PIR hot path on one GB300 (or N replicas).
+
+Workload (default): the single-query memory-bound Response on a 1 GiB
+spectrum database, 32768 x 32768 uniform digits (p = 256), LWE n = 1024,
+q = 2^32.  One timed step is one online round trip of the hot path for one
+query: Query (A s + e + Delta u_col) -> Response (D qu) -> Recover, all on the
+device, inputs resident in HBM.  The offline hint D A is computed once before
+timing (it is query independent) and timed separately.  `value` is the
+database bytes scanned per second over whole steps.
+
+Also measured in the same run and reported beside the headline:
+  - the Response kernel alone and its fraction of the measured HBM roofline;
+  - the batched Response (exact byte-limb tensor-core GEMM) over a batch
+    sweep, as queries/s against one-query-at-a-time on the same database;
+  - the hint time;
+  - the CPU oracle on a bounded sample (cpu_baseline).
+
+`--impl reference` times the CPU oracle itself as the reference arm.
+Multi-GPU (torchrun): each rank holds its own replica and answers its own
+queries (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PIR Response DB-scan GB/s and queries/s, batched vs per-query; p50/p99 latency"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def cpu_oracle_sample(D, A_np, H_np, budget_s: float = 12.0, threads: int | None = None):
+    """Time the oracle's Query -> Answer -> Recover on a bounded row sample.
+
+    The sample answers one query against `rows` rows of the database
+    (all C columns, with the full-length Query) and recovers those rows;
+    it repeats until `budget_s` seconds have passed and returns the
+    database-scan rate in GB/s (database bytes of the sampled rows / time).
+    """
+    import oracle
+    from paper_2510_03631_gb300 import inputs
+    threads = threads or (os.cpu_count() or 1)
+    R, C = D.shape
+    n = A_np.shape[1]
+    rows = min(R, 2048)
+    sub = np.ascontiguousarray(D[:rows])
+    Hs = np.ascontiguousarray(H_np[:rows])
+    reps, t0 = 0, time.perf_counter()
+    scanned = 0
+    while True:
+        s = inputs.secrets(1, n, seed=1000 + reps)[0]
+        e = inputs.noise(C, seed=2000 + reps)
+        col = int(inputs.target_columns(1, C, seed=3000 + reps)[0])
+        qu = oracle.query(A_np, s, e, col, oracle.delta_for(256))
+        ans = oracle.answer(sub, qu, threads=threads)
+        oracle.recover(ans, Hs, s)
+        scanned += rows * C
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return {"value": scanned / el / 1e9, "unit": "GB/s", "cores": threads, "kind": "oracle",
+            "sample": f"{reps} x (Query over all {C} columns, Answer of {rows} of {R} rows, Recover of those rows); "
+                      f"{el:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2510_03631_gb300 import inputs
+    w = inputs.WORKLOADS["single_1gib"]
+    R, C, n = w["rows"], w["cols"], w["n"]
+    rows = 2048
+    D = inputs.db_digits(R, C, 256, seed=1, row_start=0, row_count=rows)
+    A_np = oracle.gen_a(1, C, n)
+    threads = os.cpu_count() or 1
+    H_np = oracle.hint(D, A_np, threads=threads)
+    per_step = []
+    for i in range(args.warmup + args.steps):
+        s = inputs.secrets(1, n, seed=10 + i)[0]
+        e = inputs.noise(C, seed=20 + i)
+        col = int(inputs.target_columns(1, C, seed=30 + i)[0])
+        t0 = time.perf_counter()
+        qu = oracle.query(A_np, s, e, col, oracle.delta_for(256))
+        ans = oracle.answer(D, qu, threads=threads)
+        oracle.recover(ans, H_np, s)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            per_step.append(dt)
+    t = sum(per_step) / len(per_step)
+    gbs = rows * C / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "single_1gib", "rows": R, "cols": C, "n": n, "p": 256,
+                   "sample_rows": rows, "note": "CPU oracle, bounded row sample of the 1 GiB database"},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": threads, "kind": "oracle",
+                         "sample": f"Query over all {C} columns + Answer and Recover of {rows} of {R} rows per step"},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    from paper_2510_03631_gb300 import inputs, pir
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = inputs.WORKLOADS["single_1gib"]
+    R, C, n, p = w["rows"], w["cols"], w["n"], w["p"]
+    seed = 1 + rank
+    D_np = inputs.db_digits(R, C, p, seed=seed)
+    prm = pir.params(R, C, n, p=p, seed=seed)
+    D = torch.from_numpy(D_np).cuda()
+    db = pir.qpadl_pir_setup(prm, D)
+    A = torch.empty(C * n, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_gen_a(prm, A)
+    H = torch.empty(R * n, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+
+    # offline hint (first call also builds the tensor-core copy of D)
+    pir.qpadl_pir_hint(db, A, H)
+    torch.cuda.synchronize()
+    hint_ms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pir.qpadl_pir_hint(db, A, H)
+        e1.record()
+        torch.cuda.synchronize()
+        hint_ms.append(e0.elapsed_time(e1))
+
+    K, W = args.steps, args.warmup
+    T = K + W
+    S = pir.from_u32(inputs.secrets(T, n, seed=seed + 10).reshape(-1))
+    E = torch.from_numpy(inputs.noise_batch(T, C, seed=seed + 11).reshape(-1)).cuda()
+    cols_np = inputs.target_columns(T, C, seed=seed + 12)
+    q = torch.empty(T * C, dtype=torch.int32, device="cuda")
+    ans = torch.empty(T * R, dtype=torch.int32, device="cuda")
+    out = torch.empty(T * R, dtype=torch.uint8, device="cuda")
+
+    def step(i):
+        qi, ai, oi = q[i * C:(i + 1) * C], ans[i * R:(i + 1) * R], out[i * R:(i + 1) * R]
+        si = S[i * n:(i + 1) * n]
+        pir.qpadl_pir_query(prm, A, si, E[i * C:(i + 1) * C], int(cols_np[i]), qi)
+        pir.qpadl_pir_answer(db, qi, ai)
+        pir.qpadl_pir_recover(prm, ai, H, si, oi)
+
+    for i in range(W):
+        step(i)
+    torch.cuda.synchronize()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)   # let the sampler start
+        ev0.record()
+        for i in range(W, T):
+            step(i)
+        ev1.record()
+        torch.cuda.synchronize()
+        step_ms = ev0.elapsed_time(ev1) / K
+    barrier()
+    # correctness of what was timed: every recovered column must equal D's column
+    out_np = out.cpu().numpy().reshape(T, R)
+    ok = all(np.array_equal(out_np[i], D_np[:, cols_np[i]]) for i in range(T))
+    if not ok:
+        raise SystemExit("bench: recovered records differ from the database")
+    if pir.qpadl_pir_status(db) != 0:
+        raise SystemExit("bench: device status word set")
+
+    if dist is not None:
+        t = torch.tensor([step_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+
+    # ---- the Response kernel alone (roofline of the dominant kernel)
+    resp_ms = []
+    for i in range(W, T):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pir.qpadl_pir_answer(db, q[i * C:(i + 1) * C], ans[i * R:(i + 1) * R])
+        e1.record()
+        torch.cuda.synchronize()
+        resp_ms.append(e0.elapsed_time(e1))
+    resp_ms_avg = sum(resp_ms) / len(resp_ms)
+    alg_bytes = R * C + 4 * C + 4 * R
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / (resp_ms_avg * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "stream_answer_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # ---- batched Response sweep vs one-at-a-time on the same database
+    one_qps = 1e3 / resp_ms_avg
+    sweep = {}
+    if not args.quick:
+        for B in (1, 8, 32, 128, 256, 1024):
+            QB = torch.randint(-2**31, 2**31 - 1, (B * C,), dtype=torch.int32, device="cuda")
+            AB = torch.empty(B * R, dtype=torch.int32, device="cuda")
+            for _ in range(2):
+                pir.qpadl_pir_answer_batch(db, QB, AB)
+            torch.cuda.synchronize()
+            reps = 5
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                pir.qpadl_pir_answer_batch(db, QB, AB)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            sweep[str(B)] = {"ms": round(ms, 4), "queries_per_s": round(B / ms * 1e3, 1),
+                             "db_scan_gbs": round(B * R * C / (ms * 1e-3) / 1e9, 1),
+                             "tops_u32mac": round(B * R * C / (ms * 1e-3) / 1e12, 3),
+                             "x_vs_one_at_a_time": round(B / ms * 1e3 / one_qps, 2)}
+            del QB, AB
+
+    # ---- end to end through the public API with host buffers
+    s_h = torch.from_numpy(inputs.secrets(1, n, seed=seed + 50).reshape(-1).view(np.int32)).pin_memory()
+    e_h = torch.from_numpy(inputs.noise(C, seed=seed + 51)).pin_memory()
+    out_h = torch.empty(R, dtype=torch.uint8).pin_memory()
+    s_d = torch.empty(n, dtype=torch.int32, device="cuda")
+    e_d = torch.empty(C, dtype=torch.int32, device="cuda")
+    col_e2e = int(inputs.target_columns(1, C, seed=seed + 52)[0])
+
+    def e2e_step():
+        s_d.copy_(s_h, non_blocking=True)
+        e_d.copy_(e_h, non_blocking=True)
+        pir.qpadl_pir_query(prm, A, s_d, e_d, col_e2e, q[:C])
+        pir.qpadl_pir_answer(db, q[:C], ans[:R])
+        pir.qpadl_pir_recover(prm, ans[:R], H, s_d, out[:R])
+        out_h.copy_(out[:R], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    for _ in range(W):
+        e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t0) / K
+    if not np.array_equal(out_h.numpy(), D_np[:, col_e2e]):
+        raise SystemExit("bench: e2e recovered record differs")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        A_np = pir.as_u32(A).reshape(C, n)
+        H_np = pir.as_u32(H).reshape(R, n)
+        cpu = cpu_oracle_sample(D_np, A_np, H_np, budget_s=args.cpu_budget)
+
+    gbs = world * R * C / (step_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC,
+        "value": round(gbs, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": round(step_ms, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "single_1gib", "rows": R, "cols": C, "n": n, "p": p, "q": "2^32",
+                   "batch_per_step": 1, "step": "Query -> Response -> Recover on device",
+                   "l2": "inputs larger than L2 (1 GiB database per step)", "parallelism": f"replicas{world}"},
+        "queries_per_s": round(world * 1e3 / step_ms, 1),
+        "response_only": {"ms": round(resp_ms_avg, 4), "db_scan_gbs": round(R * C / (resp_ms_avg * 1e-3) / 1e9, 2),
+                          "queries_per_s": round(one_qps, 1)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "qpadl_pir_answer (pack_query + stream_answer)",
+                     "alg_bytes_per_launch": alg_bytes},
+        "batched": {"one_at_a_time_qps": round(one_qps, 1), "sweep": sweep},
+        "hint_ms": round(min(hint_ms), 3),
+        "gpu_launches": 4 * K,
+        "e2e": {"value": round(R * C / e2e_s / 1e9, 2), "unit": "GB/s", "ms_per_step": round(e2e_s * 1e3, 4),
+                "h2d_bytes_per_step": 4 * n + 4 * C, "d2h_bytes_per_step": R},
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    db.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip the batch sweep")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

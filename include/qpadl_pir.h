@@ -1,0 +1,201 @@
+/*
+ * qpadl_pir.h - C ABI of the GB300 (sm_103a) LWE-style PIR engine for the
+ * private spectrum-database queries of QPADL (arxiv 2510.03631).
+ *
+ * The scheme.  A database D of R x C digits in Z_p (p = 2^l, l = 1..8) is
+ * stored row-major as uint8; a record is a column of D.  All other quantities
+ * live in Z_q with q = 2^32, i.e. uint32 with wraparound.  With public
+ * A in Z_q^{C x n}, client secret s in Z_q^n, noise e in Z^C and
+ * Delta = q / p:
+ *     Setup    A       = PRG(seed)                       (C x n)
+ *     Hint     H       = D * A                           (R x n, offline)
+ *     Query    qu      = A * s + e + Delta * u_col       (C)
+ *     Answer   ans     = D * qu                          (R)
+ *     Recover  d_i     = round((ans_i - (H s)_i) / Delta) mod p  = D[i][col]
+ * The paper's Def. 1 (Sec. 3) fixes the three-call shape (Client.Query,
+ * DB.Query.Response, Client.BlockReconst); Sec. 5.2 fixes the server's work
+ * as one product of the query with the whole database matrix accumulated
+ * mod q (Alg. 3, Alg. 4); Sec. 5.3 moves query-independent work offline
+ * (here, the hint).  The lattice instantiation is the standard
+ * single-server LWE PIR, which the paper does not spell out.
+ *
+ * Conventions shared by every call:
+ *  - Return value: QPADL_OK (0) or a negative QPADL_E* code.  Nothing throws.
+ *  - Pointers named *_dev are device pointers that the CALLER allocates,
+ *    owns and frees; the library never frees them.  They must stay valid
+ *    until the work enqueued on `stream` has completed.  Pointers named
+ *    *_host are host pointers; calls taking them return after the result is
+ *    back in host memory.
+ *  - `stream` is a cudaStream_t (0 = legacy default stream).  Device calls
+ *    are asynchronous on it unless documented otherwise.
+ *  - Shapes are validated before any launch; invalid shapes or pointers
+ *    return QPADL_EINVAL and enqueue nothing.
+ *  - A handle (qpadl_db) is library-owned and freed by qpadl_pir_destroy.
+ *    Device work that fails inside a kernel (a bounded wait that ran out)
+ *    records a code in the handle's device status word; qpadl_pir_status
+ *    reads it.
+ *  - Calls on one handle must not overlap on different streams: the
+ *    handle's scratch buffers are shared by its calls.
+ */
+#ifndef QPADL_PIR_H
+#define QPADL_PIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *qpadl_stream_t; /* identical to cudaStream_t */
+
+enum {
+    QPADL_OK = 0,
+    QPADL_EINVAL = -1,   /* bad argument, shape, alignment or digit >= p */
+    QPADL_ENOMEM = -2,   /* device allocation failed / over memory budget */
+    QPADL_ECUDA = -3,    /* a CUDA runtime call or launch failed */
+    QPADL_ETIMEOUT = -4, /* a kernel's bounded wait ran out (see qpadl_pir_status) */
+    QPADL_EBUSY = -5,    /* serving admission refused the request */
+    QPADL_EAGAIN = -6    /* serving: result not ready yet */
+};
+
+/* Setup flags. */
+#define QPADL_SETUP_TENSOR_COPY 0x1u /* build the tensor-core operand copy of D
+                                        at setup (else: on first batched call) */
+
+/* Scheme parameters (Setup).  Digits of D must be < p. */
+typedef struct qpadl_params {
+    uint64_t rows;   /* R: database rows (> 0) */
+    uint64_t cols;   /* C: database columns = number of records (> 0) */
+    uint32_t n;      /* LWE dimension (> 0, <= 16384) */
+    uint32_t log_q;  /* must be 32 */
+    uint32_t p;      /* plaintext modulus, a power of two in [2, 256] */
+    uint32_t flags;  /* QPADL_SETUP_* */
+    double sigma;    /* noise standard deviation (informational: noise is an input) */
+    uint64_t seed;   /* seed of the public matrix A (qpadl_pir_gen_a) */
+} qpadl_params;
+
+typedef struct qpadl_db qpadl_db;
+
+/* Human-readable name of a QPADL_* code (static storage). */
+const char *qpadl_strerror(int code);
+
+/* Version of this ABI (major * 10000 + minor * 100 + patch). */
+int qpadl_version(void);
+
+/*
+ * Setup (server side; Def. 1's server holds D).  Validates `prm`, records
+ * the shape and binds the caller's resident database `db_dev` (R*C bytes,
+ * row-major, not copied; it must outlive the handle).  When p < 256 the
+ * digits are checked on the device (this call then synchronises `stream`)
+ * and a digit >= p returns QPADL_EINVAL.  With QPADL_SETUP_TENSOR_COPY the
+ * library also allocates and fills its tensor-core operand copy of D
+ * (2 * R * roundup(C, 8) bytes, library-owned) on `stream`.
+ * On success *out receives the handle.
+ */
+int qpadl_pir_setup(const qpadl_params *prm, const uint8_t *db_dev,
+                    qpadl_stream_t stream, qpadl_db **out);
+
+/* Frees the handle and all library-owned device memory it holds.  Waits
+ * for work the handle enqueued.  NULL is accepted. */
+int qpadl_pir_destroy(qpadl_db *db);
+
+/* Reads (synchronously, after the handle's last stream has drained) and
+ * clears the handle's device status word: QPADL_OK, or QPADL_ETIMEOUT when
+ * a kernel's bounded wait ran out since the last call. */
+int qpadl_pir_status(qpadl_db *db);
+
+/* Bytes of device memory the handle currently owns (operand copy + scratch). */
+uint64_t qpadl_pir_device_bytes(const qpadl_db *db);
+
+/*
+ * Setup, public matrix: A_dev[j*n + k] = upper 32 bits of output number
+ * j*n + k of SplitMix64 started from state prm->seed (C x n, row-major).
+ * A_dev: C*n uint32, 4-byte aligned.
+ */
+int qpadl_pir_gen_a(const qpadl_params *prm, uint32_t *A_dev, qpadl_stream_t stream);
+
+/*
+ * Hint (offline; Sec. 5.3's offline precomputation): H = D * A mod 2^32.
+ * A_dev: C x n uint32 row-major; H_dev: R x n uint32 row-major.  Runs the
+ * exact byte-limb tensor-core GEMM; allocates the handle's operand copy of
+ * D on first use and a library-owned scratch of 8 * n * roundup(C, 8) bytes
+ * (kept for reuse).
+ */
+int qpadl_pir_hint(qpadl_db *db, const uint32_t *A_dev, uint32_t *H_dev,
+                   qpadl_stream_t stream);
+
+/*
+ * Query (Def. 1, Client.Query): q_dev[j] = sum_k A[j][k] s[k] + e[j]
+ * + (j == col ? Delta : 0) mod 2^32, Delta = 2^32 / p.
+ * A_dev: C x n uint32; s_dev: n uint32; e_dev: C int32 (reduced mod 2^32);
+ * q_dev: C uint32.  col < C.
+ */
+int qpadl_pir_query(const qpadl_params *prm, const uint32_t *A_dev,
+                    const uint32_t *s_dev, const int32_t *e_dev, uint64_t col,
+                    uint32_t *q_dev, qpadl_stream_t stream);
+
+/*
+ * Batched Query: B queries.  S_dev: B x n (secret b in row b); E_dev: B x C;
+ * cols_dev: B uint32 target columns (each < C, not checked on the host);
+ * Q_dev: B x C (query b in row b).
+ */
+int qpadl_pir_query_batch(const qpadl_params *prm, const uint32_t *A_dev,
+                          const uint32_t *S_dev, const int32_t *E_dev,
+                          const uint32_t *cols_dev, uint32_t B, uint32_t *Q_dev,
+                          qpadl_stream_t stream);
+
+/*
+ * Answer (Def. 1, DB.Query.Response; Sec. 5.2's product of the query with
+ * the database, accumulated mod q as in Alg. 4): ans_dev[i] = sum_j D[i][j]
+ * q[j] mod 2^32.  q_dev: C uint32; ans_dev: R uint32.  One streaming pass
+ * over D (HBM bound).  Allocates nothing.
+ */
+int qpadl_pir_answer(qpadl_db *db, const uint32_t *q_dev, uint32_t *ans_dev,
+                     qpadl_stream_t stream);
+
+/*
+ * Batched Answer (Alg. 4's batch of q-bar queries): for b < B,
+ * ans_dev[b*R + i] = sum_j D[i][j] Q[b*C + j] mod 2^32.  Q_dev: B x C
+ * (query b in row b); ans_dev: B x R (answer b in row b).  B >= 1.
+ * Small B runs the streaming kernel; larger B the exact byte-limb
+ * tensor-core GEMM (which allocates the handle's operand copy of D on first
+ * use and a library-owned limb scratch of 8 * B * roundup(C, 8) bytes, kept
+ * and grown as needed).
+ */
+int qpadl_pir_answer_batch(qpadl_db *db, const uint32_t *Q_dev, uint32_t B,
+                           uint32_t *ans_dev, qpadl_stream_t stream);
+
+/* As qpadl_pir_answer_batch, forcing the path: 0 = streaming kernel,
+ * 1 = tensor-core GEMM.  For tests and measurement. */
+int qpadl_pir_answer_batch_path(qpadl_db *db, const uint32_t *Q_dev, uint32_t B,
+                                uint32_t *ans_dev, int path, qpadl_stream_t stream);
+
+/*
+ * Answer with host buffers (the end-to-end call): copies q_host (C uint32)
+ * to the device, answers, copies ans_host (R uint32) back and synchronises
+ * `stream`.  Uses a handle-owned device staging buffer.
+ */
+int qpadl_pir_answer_host(qpadl_db *db, const uint32_t *q_host, uint32_t *ans_host,
+                          qpadl_stream_t stream);
+
+/*
+ * Recover (Def. 1, Client.BlockReconst): out_dev[i] = ((ans[i] - sum_k
+ * H[i][k] s[k]) + Delta/2 mod 2^32) >> (32 - log2 p), i.e. the nearest
+ * multiple of Delta, reduced mod p.  ans_dev: R uint32; H_dev: R x n;
+ * s_dev: n; out_dev: R bytes.  prm gives R, n and p.
+ */
+int qpadl_pir_recover(const qpadl_params *prm, const uint32_t *ans_dev,
+                      const uint32_t *H_dev, const uint32_t *s_dev, uint8_t *out_dev,
+                      qpadl_stream_t stream);
+
+/* Batched Recover: ans_dev B x R, S_dev B x n, out_dev B x R. */
+int qpadl_pir_recover_batch(const qpadl_params *prm, const uint32_t *ans_dev,
+                            const uint32_t *H_dev, const uint32_t *S_dev, uint32_t B,
+                            uint8_t *out_dev, qpadl_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QPADL_PIR_H */

@@ -1,0 +1,400 @@
+// Exact mod-2^32 product of the database with many Z_q vectors on the
+// tcgen05 tensor cores:  OUT[i][b] = sum_j D[i][j] * X[b][j]  (mod 2^32).
+//
+// Used for the batched Response (X = a batch of queries; QPADL Alg. 4's
+// q-bar queries against one database) and for the offline hint
+// H = D * A (X = columns of A; Sec. 5.3 offline precomputation).
+//
+// Exactness.  Each X word is split into four balanced byte limbs
+// x = sum_k 2^{8k} c_k with c_k in [-128, 127] (low byte, minus 256 and a
+// carry when >= 128; the last carry is a multiple of 2^32 and is dropped).
+// Digits d in [0, 255] and limbs are small integers, exactly representable
+// in fp16, and every product d*c is an integer of magnitude <= 32640.  A run
+// of 512 such products sums to less than 2^24 in magnitude, so the fp32
+// tensor-core accumulator holds every partial sum of a 512-deep K-chunk
+// exactly.  After each chunk the epilogue converts the four limb sums to
+// int32 (exact), recombines them as sum_k 2^{8k} s_k in uint32 arithmetic
+// (that is, mod 2^32) and adds them into per-thread running sums.  No value
+// is ever rounded.  (tcgen05 has no integer kind on sm_103a, so the byte
+// limbs ride in fp16 operands.)
+//
+// Kernel shape (one CTA per SM, persistent over output tiles):
+//   warp 0      TMA producer: 128x64 tile of D16 and BNx64 tile of limbs per
+//               stage, 128-byte swizzle, 4-stage mbarrier ring.
+//   warp 1      allocates TMEM (two BN-column fp32 accumulators) and one
+//               thread issues tcgen05.mma M=128, N=BN, K=16 (4 per stage).
+//   warps 2..5  epilogue: drain one accumulator per 512-deep K-chunk while
+//               the MMA fills the other.
+// Output element (row i, vector b) goes to out[i * ld_m + b * ld_b].
+#include <cstdint>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "limb_gemm.cuh"
+#include "ptx.cuh"
+
+namespace qpadl {
+
+constexpr int kBM = 128;
+constexpr int kBK = 64;          // fp16 elements per 128-byte swizzled row
+constexpr int kGemmStages = 4;
+constexpr int kChunkKB = 8;      // 8 x 64 = 512-deep exact K-chunks
+constexpr int kGemmThreads = 192;
+
+template <int BN>
+struct GemmCfg {
+    static constexpr uint32_t kABytes = kBM * kBK * 2;
+    static constexpr uint32_t kBBytes = BN * kBK * 2;
+    static constexpr uint32_t kStageBytes = kABytes + kBBytes;
+    static constexpr uint32_t kTmemCols = (2 * BN < 32) ? 32 : 2 * BN;
+    static constexpr int kSmemBytes = kGemmStages * kStageBytes + 256 + 1024;
+    static constexpr int kQPT = BN / 4;   // vectors per tile
+};
+
+__device__ __forceinline__ bool drain_wait_g(uint64_t *bar, uint32_t parity) {
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_test(bar, parity)) {
+        if (global_ns() - t0 > QPADL_WAIT_NS) return false;
+    }
+    return true;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    limb_gemm_kernel(const __grid_constant__ CUtensorMap a_map, const __grid_constant__ CUtensorMap b_map,
+                     uint32_t *__restrict__ out, uint64_t ld_m, uint64_t ld_b, uint32_t M, uint32_t NV,
+                     uint32_t KB, int *__restrict__ status) {
+    using Cfg = GemmCfg<BN>;
+    constexpr int QPT = Cfg::kQPT;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kGemmStages * Cfg::kStageBytes);
+    uint64_t *empty = full + kGemmStages;
+    uint64_t *acc_full = empty + kGemmStages;   // [2]
+    uint64_t *acc_empty = acc_full + 2;          // [2]
+    uint64_t *mma_done = acc_empty + 2;          // [1]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kGemmStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);
+        }
+        mbar_init(mma_done, 1);
+        *abort = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, Cfg::kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    const uint32_t m_tiles = (M + kBM - 1) / kBM;
+    const uint32_t n_tiles = (NV * 4 + BN - 1) / BN;
+    const uint32_t tiles = m_tiles * n_tiles;
+    bool failed = false;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            tma_prefetch_desc(&a_map);
+            tma_prefetch_desc(&b_map);
+            uint32_t it = 0;
+            for (uint32_t t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
+                const int32_t m0 = static_cast<int32_t>((t / n_tiles) * kBM);
+                const int32_t n0 = static_cast<int32_t>((t % n_tiles) * BN);
+                for (uint32_t kb = 0; kb < KB; ++kb, ++it) {
+                    const uint32_t st = it % kGemmStages;
+                    const uint32_t ph = (it / kGemmStages) & 1u;
+                    if (!mbar_wait(&empty[st], ph ^ 1u, abort)) {
+                        failed = true;
+                        break;
+                    }
+                    uint8_t *sa = smem + st * Cfg::kStageBytes;
+                    mbar_arrive_expect_tx(&full[st], Cfg::kStageBytes);
+                    tma_load_2d(sa, &a_map, &full[st], static_cast<int32_t>(kb * kBK), m0);
+                    tma_load_2d(sa + Cfg::kABytes, &b_map, &full[st], static_cast<int32_t>(kb * kBK), n0);
+                }
+            }
+            const uint32_t inflight = it < (uint32_t)kGemmStages ? it : (uint32_t)kGemmStages;
+            for (uint32_t j = it - inflight; j < it; ++j)
+                if (!drain_wait_g(&full[j % kGemmStages], (j / kGemmStages) & 1u)) failed = true;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            constexpr uint32_t idesc = umma_idesc_f16(kBM, BN);
+            uint32_t it = 0, ci = 0;
+            bool issued = false;
+            for (uint32_t t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
+                uint32_t d_tmem = tmem_base;
+                for (uint32_t kb = 0; kb < KB; ++kb, ++it) {
+                    if (kb % kChunkKB == 0) {
+                        const uint32_t buf = ci & 1u;
+                        if (!mbar_wait(&acc_empty[buf], ((ci >> 1) & 1u) ^ 1u, abort)) {
+                            failed = true;
+                            break;
+                        }
+                        tc_fence_after();
+                        d_tmem = tmem_base + buf * BN;
+                    }
+                    const uint32_t st = it % kGemmStages;
+                    const uint32_t ph = (it / kGemmStages) & 1u;
+                    if (!mbar_wait(&full[st], ph, abort)) {
+                        failed = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_addr(smem + st * Cfg::kStageBytes);
+                    const uint64_t adesc = umma_desc_sw128(sa);
+                    const uint64_t bdesc = umma_desc_sw128(sa + Cfg::kABytes);
+#pragma unroll
+                    for (int k = 0; k < kBK / 16; ++k) {
+                        // advance the start address by 16 elements (32 bytes) inside the swizzle atom
+                        umma_f16(d_tmem, adesc + 2u * k, bdesc + 2u * k, idesc,
+                                 (kb % kChunkKB != 0 || k != 0) ? 1u : 0u);
+                    }
+                    issued = true;
+                    umma_commit(&empty[st]);
+                    if (kb % kChunkKB == kChunkKB - 1 || kb == KB - 1) {
+                        umma_commit(&acc_full[ci & 1u]);
+                        ++ci;
+                    }
+                }
+            }
+            // every MMA this thread issued must finish before TMEM is released
+            if (issued) {
+                umma_commit(mma_done);
+                if (!drain_wait_g(mma_done, 0)) failed = true;
+            }
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5; TMEM lane quarter = warp % 4)
+        const uint32_t quarter = static_cast<uint32_t>(warp & 3);
+        const uint32_t lane_addr = (quarter * 32u) << 16;
+        uint32_t ci = 0;
+        for (uint32_t t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
+            const uint32_t m0 = (t / n_tiles) * kBM;
+            const uint32_t v0 = (t % n_tiles) * QPT;
+            uint32_t run[QPT];
+#pragma unroll
+            for (int q = 0; q < QPT; ++q) run[q] = 0u;
+            const uint32_t nchunks = (KB + kChunkKB - 1) / kChunkKB;
+            for (uint32_t c = 0; c < nchunks; ++c, ++ci) {
+                const uint32_t buf = ci & 1u;
+                if (!mbar_wait(&acc_full[buf], (ci >> 1) & 1u, abort)) {
+                    failed = true;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int j = 0; j < BN / 32; ++j) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem_base + lane_addr + buf * BN + 32u * j, v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const uint32_t s0 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 0])));
+                        const uint32_t s1 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 1])));
+                        const uint32_t s2 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 2])));
+                        const uint32_t s3 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 3])));
+                        run[8 * j + q] += s0 + (s1 << 8) + (s2 << 16) + (s3 << 24);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[buf]);
+            }
+            if (failed) break;
+            const uint32_t row = m0 + quarter * 32u + static_cast<uint32_t>(lane);
+            if (row < M) {
+#pragma unroll
+                for (int q = 0; q < QPT; ++q) {
+                    const uint32_t vi = v0 + q;
+                    if (vi < NV) out[(uint64_t)row * ld_m + (uint64_t)vi * ld_b] = run[q];
+                }
+            }
+        }
+    }
+
+    if (failed) {
+        *abort = 1;
+        *status = kDevTimeout;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, Cfg::kTmemCols);
+    }
+}
+
+// D (uint8, R x C) -> D16 (fp16, R x pitch), digits as exact small integers.
+// One block per row at a time; 16 digits per thread step when rows are aligned.
+__global__ void db_to_f16_kernel(const uint8_t *__restrict__ D, uint64_t R, uint64_t C, __half *__restrict__ D16,
+                                 uint64_t pitch) {
+    const bool vec = (C % 16 == 0) && ((reinterpret_cast<uintptr_t>(D) & 15u) == 0) && (pitch % 8 == 0);
+    for (uint64_t i = blockIdx.x; i < R; i += gridDim.x) {
+        const uint8_t *src = D + i * C;
+        __half *dst = D16 + i * pitch;
+        if (vec) {
+            for (uint64_t j = 16ull * threadIdx.x; j < C; j += 16ull * blockDim.x) {
+                const uint4 w = *reinterpret_cast<const uint4 *>(src + j);
+                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+                uint32_t h[8];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const __half2 lo = __halves2half2(__ushort2half_rn(ws[t] & 255u), __ushort2half_rn((ws[t] >> 8) & 255u));
+                    const __half2 hi = __halves2half2(__ushort2half_rn((ws[t] >> 16) & 255u), __ushort2half_rn(ws[t] >> 24));
+                    h[2 * t] = *reinterpret_cast<const uint32_t *>(&lo);
+                    h[2 * t + 1] = *reinterpret_cast<const uint32_t *>(&hi);
+                }
+                uint4 *d4 = reinterpret_cast<uint4 *>(dst + j);
+                d4[0] = make_uint4(h[0], h[1], h[2], h[3]);
+                d4[1] = make_uint4(h[4], h[5], h[6], h[7]);
+            }
+        } else {
+            for (uint64_t j = threadIdx.x; j < C; j += blockDim.x)
+                dst[j] = __ushort2half_rn(static_cast<unsigned short>(src[j]));
+        }
+    }
+}
+
+__device__ __forceinline__ void balanced_limbs(uint32_t x, float (&c)[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int byte = static_cast<int>(x & 255u);
+        if (byte >= 128) {
+            c[k] = static_cast<float>(byte - 256);
+            x = (x >> 8) + 1u;
+        } else {
+            c[k] = static_cast<float>(byte);
+            x >>= 8;
+        }
+    }
+}
+
+// X (uint32, NV x C, vector v in row v) -> limbs (fp16, 4*NV x pitch),
+// limb k of vector v in row 4v + k.  One block per vector at a time.
+__global__ void vec_limbs_kernel(const uint32_t *__restrict__ X, uint64_t x_ld, uint32_t NV, uint64_t C,
+                                 __half *__restrict__ L, uint64_t pitch) {
+    for (uint32_t v = blockIdx.x; v < NV; v += gridDim.x) {
+        const uint32_t *src = X + (uint64_t)v * x_ld;
+        __half *dst = L + 4ull * v * pitch;
+        for (uint64_t j = threadIdx.x; j < C; j += blockDim.x) {
+            float c[4];
+            balanced_limbs(src[j], c);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) dst[k * pitch + j] = __float2half_rn(c[k]);
+        }
+    }
+}
+
+// A (uint32, C x n row-major) -> limbs of its columns (fp16, 4n x pitch):
+// limb l of column k (over j) in row 4k + l.  32x32 tiles through shared memory.
+__global__ void mat_col_limbs_kernel(const uint32_t *__restrict__ A, uint64_t C, uint32_t n,
+                                     __half *__restrict__ L, uint64_t pitch) {
+    __shared__ uint32_t tile[32][33];
+    const uint64_t j0 = (uint64_t)blockIdx.x * 32;
+    const uint32_t k0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const uint64_t j = j0 + r;
+        const uint32_t k = k0 + threadIdx.x;
+        tile[r][threadIdx.x] = (j < C && k < n) ? A[j * n + k] : 0u;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const uint32_t k = k0 + r;
+        const uint64_t j = j0 + threadIdx.x;
+        if (k < n && j < C) {
+            float c[4];
+            balanced_limbs(tile[threadIdx.x][r], c);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) L[(4ull * k + l) * pitch + j] = __float2half_rn(c[l]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+template <int BN>
+static cudaError_t set_gemm_attr() {
+    return cudaFuncSetAttribute(limb_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                GemmCfg<BN>::kSmemBytes);
+}
+
+cudaError_t prepare_limb_gemm_kernels() {
+    cudaError_t e;
+    if ((e = set_gemm_attr<32>()) != cudaSuccess) return e;
+    if ((e = set_gemm_attr<64>()) != cudaSuccess) return e;
+    if ((e = set_gemm_attr<128>()) != cudaSuccess) return e;
+    if ((e = set_gemm_attr<256>()) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+int limb_gemm_bn_for(uint32_t nv) {
+    const uint32_t cols = 4 * nv;
+    if (cols <= 32) return 32;
+    if (cols <= 64) return 64;
+    if (cols <= 128) return 128;
+    return 256;
+}
+
+template <int BN>
+static cudaError_t launch_bn(const CUtensorMap &a_map, const CUtensorMap &b_map, uint32_t *out, uint64_t ld_m,
+                             uint64_t ld_b, uint32_t M, uint32_t NV, uint32_t KB, int grid, int *status,
+                             cudaStream_t stream) {
+    limb_gemm_kernel<BN><<<grid, kGemmThreads, GemmCfg<BN>::kSmemBytes, stream>>>(a_map, b_map, out, ld_m, ld_b, M,
+                                                                                  NV, KB, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_limb_gemm(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, uint32_t *out,
+                             uint64_t ld_m, uint64_t ld_b, uint32_t M, uint32_t NV, uint64_t K, int num_sms,
+                             int *status, cudaStream_t stream) {
+    const uint32_t KB = static_cast<uint32_t>((K + kBK - 1) / kBK);
+    const uint64_t tiles = (uint64_t)((M + kBM - 1) / kBM) * ((4ull * NV + bn - 1) / bn);
+    const int grid = static_cast<int>(tiles < (uint64_t)num_sms ? tiles : (uint64_t)num_sms);
+    switch (bn) {
+        case 32: return launch_bn<32>(a_map, b_map, out, ld_m, ld_b, M, NV, KB, grid, status, stream);
+        case 64: return launch_bn<64>(a_map, b_map, out, ld_m, ld_b, M, NV, KB, grid, status, stream);
+        case 128: return launch_bn<128>(a_map, b_map, out, ld_m, ld_b, M, NV, KB, grid, status, stream);
+        case 256: return launch_bn<256>(a_map, b_map, out, ld_m, ld_b, M, NV, KB, grid, status, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_db_to_f16(const uint8_t *D, uint64_t R, uint64_t C, __half *D16, uint64_t pitch, int num_sms,
+                             cudaStream_t stream) {
+    const uint64_t blocks = R < (uint64_t)num_sms * 8 ? R : (uint64_t)num_sms * 8;
+    db_to_f16_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(D, R, C, D16, pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vec_limbs(const uint32_t *X, uint64_t x_ld, uint32_t NV, uint64_t C, __half *L, uint64_t pitch,
+                             int num_sms, cudaStream_t stream) {
+    const uint32_t blocks = NV < (uint32_t)(num_sms * 8) ? NV : (uint32_t)(num_sms * 8);
+    vec_limbs_kernel<<<blocks, 256, 0, stream>>>(X, x_ld, NV, C, L, pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mat_col_limbs(const uint32_t *A, uint64_t C, uint32_t n, __half *L, uint64_t pitch,
+                                 cudaStream_t stream) {
+    dim3 grid(static_cast<unsigned>((C + 31) / 32), (n + 31) / 32);
+    mat_col_limbs_kernel<<<grid, dim3(32, 8), 0, stream>>>(A, C, n, L, pitch);
+    return cudaGetLastError();
+}
+
+}  // namespace qpadl

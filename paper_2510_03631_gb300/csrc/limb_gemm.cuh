@@ -1,0 +1,31 @@
+// Launch interface of the exact byte-limb tensor-core GEMM (limb_gemm.cu).
+#pragma once
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+namespace qpadl {
+
+constexpr int kLimbBoxK = 64;    // fp16 elements per TMA box row (128 bytes, 128-byte swizzle)
+constexpr int kLimbBoxM = 128;   // database rows per tile
+
+cudaError_t prepare_limb_gemm_kernels();
+
+// Limb columns per tile (32/64/128/256) for `nv` vectors.
+int limb_gemm_bn_for(uint32_t nv);
+
+// out[i * ld_m + v * ld_b] = sum_j D[i][j] X[v][j] mod 2^32, i < M, v < NV,
+// j < K; a_map covers D16 (box 64 x 128), b_map the limbs (box 64 x bn).
+cudaError_t launch_limb_gemm(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, uint32_t *out,
+                             uint64_t ld_m, uint64_t ld_b, uint32_t M, uint32_t NV, uint64_t K, int num_sms,
+                             int *status, cudaStream_t stream);
+
+cudaError_t launch_db_to_f16(const uint8_t *D, uint64_t R, uint64_t C, __half *D16, uint64_t pitch, int num_sms,
+                             cudaStream_t stream);
+cudaError_t launch_vec_limbs(const uint32_t *X, uint64_t x_ld, uint32_t NV, uint64_t C, __half *L, uint64_t pitch,
+                             int num_sms, cudaStream_t stream);
+cudaError_t launch_mat_col_limbs(const uint32_t *A, uint64_t C, uint32_t n, __half *L, uint64_t pitch,
+                                 cudaStream_t stream);
+
+}  // namespace qpadl

@@ -1,0 +1,454 @@
+// C-ABI entry points of the LWE-style PIR engine (declared in include/qpadl_pir.h).
+//
+// This file owns validation, the per-database handle, tensor-map encoding
+// and the choice of kernel; the arithmetic lives in stream_answer.cu
+// (single/few-query Response), limb_gemm.cu (batched Response and hint) and
+// client.cu (Setup's generator, Query, Recover).
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include "client.cuh"
+#include "limb_gemm.cuh"
+#include "qpadl_pir.h"
+#include "stream_answer.cuh"
+
+using namespace qpadl;
+
+struct qpadl_db {
+    qpadl_params prm;
+    const uint8_t *db = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    int *d_status = nullptr;         // device status word (kernels' bounded waits)
+    cudaStream_t last_stream = nullptr;
+    // streaming path
+    bool stream_ok = false;          // C % 16 == 0 and D 16-byte aligned
+    CUtensorMap db_map;
+    uint32_t *qpack = nullptr;       // packed limbs of up to 4 queries
+    uint64_t pack_words = 0;         // per query
+    // tensor-core path
+    __half *d16 = nullptr;           // digits as fp16, R x pitch
+    uint64_t pitch = 0;              // roundup(C, 8)
+    CUtensorMap a_map;
+    __half *limbs = nullptr;         // limb scratch
+    uint64_t limbs_bytes = 0;
+    // host-buffer calls
+    uint32_t *stage_q = nullptr;
+    uint32_t *stage_ans = nullptr;
+    uint64_t owned_bytes = 0;
+};
+
+namespace {
+
+constexpr int kMaxN = 16384;
+
+int cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return QPADL_OK;
+    std::fprintf(stderr, "qpadl: %s: %s\n", what, cudaGetErrorString(e));
+    return QPADL_ECUDA;
+}
+
+#define QPADL_CU(call)                                        \
+    do {                                                      \
+        int rc__ = cuda_fail((call), #call);                  \
+        if (rc__ != QPADL_OK) return rc__;                    \
+    } while (0)
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 2-D map over a row-major matrix: `inner` elements per row (extent),
+// `outer` rows, `pitch_bytes` between rows, box of box_inner x box_outer.
+bool encode_2d(CUtensorMap *map, CUtensorMapDataType dt, const void *base, uint64_t inner, uint64_t outer,
+               uint64_t pitch_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swz) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {pitch_bytes};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool prepared[64];
+std::mutex prep_mu;
+
+int prepare_device(int dev) {
+    std::lock_guard<std::mutex> g(prep_mu);
+    if (dev < 0 || dev >= 64) return QPADL_EINVAL;
+    if (prepared[dev]) return QPADL_OK;
+    QPADL_CU(prepare_stream_kernels());
+    QPADL_CU(prepare_limb_gemm_kernels());
+    QPADL_CU(prepare_client_kernels());
+    prepared[dev] = true;
+    return QPADL_OK;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int log2_exact(uint32_t p) {
+    int l = 0;
+    while ((1u << l) < p) ++l;
+    return (1u << l) == p ? l : -1;
+}
+
+int validate_params(const qpadl_params *prm) {
+    if (!prm) return QPADL_EINVAL;
+    if (prm->rows == 0 || prm->cols == 0 || prm->n == 0 || prm->n > (uint32_t)kMaxN) return QPADL_EINVAL;
+    if (prm->rows >= (1ull << 31) || prm->cols >= (1ull << 31)) return QPADL_EINVAL;
+    if (prm->log_q != 32) return QPADL_EINVAL;
+    if (prm->p < 2 || prm->p > 256 || log2_exact(prm->p) < 0) return QPADL_EINVAL;
+    return QPADL_OK;
+}
+
+__global__ void max_digit_kernel(const uint8_t *D, uint64_t total, int *out) {
+    uint32_t m = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride)
+        m = D[e] > m ? D[e] : m;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint32_t v = __shfl_xor_sync(0xffffffffu, m, o);
+        m = v > m ? v : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, static_cast<int>(m));
+}
+
+int dev_alloc(qpadl_db *db, void **p, uint64_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return QPADL_ENOMEM;
+    }
+    db->owned_bytes += bytes;
+    return QPADL_OK;
+}
+
+void dev_free(qpadl_db *db, void *p, uint64_t bytes) {
+    if (p) {
+        cudaFree(p);
+        db->owned_bytes -= bytes;
+    }
+}
+
+int ensure_tensor_copy(qpadl_db *db, cudaStream_t stream) {
+    if (db->d16) return QPADL_OK;
+    const uint64_t R = db->prm.rows, C = db->prm.cols;
+    db->pitch = (C + 7) / 8 * 8;
+    const uint64_t bytes = R * db->pitch * 2;
+    int rc = dev_alloc(db, reinterpret_cast<void **>(&db->d16), bytes);
+    if (rc != QPADL_OK) return rc;
+    QPADL_CU(launch_db_to_f16(db->db, R, C, db->d16, db->pitch, db->num_sms, stream));
+    if (!encode_2d(&db->a_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, db->d16, C, R, db->pitch * 2, kLimbBoxK,
+                   kLimbBoxM, CU_TENSOR_MAP_SWIZZLE_128B))
+        return QPADL_ECUDA;
+    return QPADL_OK;
+}
+
+int ensure_limbs(qpadl_db *db, uint64_t bytes) {
+    if (db->limbs_bytes >= bytes) return QPADL_OK;
+    if (db->limbs) {
+        // the old scratch may still be read by queued work
+        if (db->last_stream) cudaStreamSynchronize(db->last_stream);
+        dev_free(db, db->limbs, db->limbs_bytes);
+        db->limbs = nullptr;
+        db->limbs_bytes = 0;
+    }
+    int rc = dev_alloc(db, reinterpret_cast<void **>(&db->limbs), bytes);
+    if (rc != QPADL_OK) return rc;
+    db->limbs_bytes = bytes;
+    return QPADL_OK;
+}
+
+int set_device(const qpadl_db *db) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return QPADL_ECUDA;
+    if (cur != db->device && cudaSetDevice(db->device) != cudaSuccess) return QPADL_ECUDA;
+    return QPADL_OK;
+}
+
+// out[i * ld_m + v * ld_b] = D * X[v] for NV vectors given as fp16 limbs in db->limbs
+int run_limb_gemm(qpadl_db *db, uint32_t NV, uint32_t *out, uint64_t ld_m, uint64_t ld_b, cudaStream_t stream) {
+    const int bn = limb_gemm_bn_for(NV);
+    CUtensorMap b_map;
+    if (!encode_2d(&b_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, db->limbs, db->prm.cols, 4ull * NV, db->pitch * 2,
+                   kLimbBoxK, static_cast<uint32_t>(bn), CU_TENSOR_MAP_SWIZZLE_128B))
+        return QPADL_ECUDA;
+    QPADL_CU(launch_limb_gemm(bn, db->a_map, b_map, out, ld_m, ld_b, static_cast<uint32_t>(db->prm.rows), NV,
+                              db->prm.cols, db->num_sms, db->d_status, stream));
+    return QPADL_OK;
+}
+
+int answer_stream_group(qpadl_db *db, const uint32_t *Q, uint32_t nq, uint32_t *ans, cudaStream_t stream) {
+    const uint64_t C = db->prm.cols, R = db->prm.rows;
+    QPADL_CU(launch_pack_query(Q, C, static_cast<uint32_t>(C), nq, db->qpack, db->pack_words, stream));
+    QPADL_CU(launch_stream_answer(static_cast<int>(nq), db->db_map, db->qpack, db->pack_words, ans, R,
+                                  static_cast<uint32_t>(R), static_cast<uint32_t>(C), db->num_sms, db->d_status,
+                                  stream));
+    return QPADL_OK;
+}
+
+int answer_streaming(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, cudaStream_t stream) {
+    const uint64_t C = db->prm.cols, R = db->prm.rows;
+    if (!db->stream_ok) {
+        QPADL_CU(launch_rowwise_answer(db->db, R, C, Q, C, B, ans, R, db->num_sms, stream));
+        return QPADL_OK;
+    }
+    uint32_t b = 0;
+    while (b < B) {
+        const uint32_t left = B - b;
+        const uint32_t nq = left >= 4 ? 4 : (left >= 2 ? 2 : 1);
+        int rc = answer_stream_group(db, Q + (uint64_t)b * C, nq, ans + (uint64_t)b * R, stream);
+        if (rc != QPADL_OK) return rc;
+        b += nq;
+    }
+    return QPADL_OK;
+}
+
+int answer_tensor(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, cudaStream_t stream) {
+    int rc = ensure_tensor_copy(db, stream);
+    if (rc != QPADL_OK) return rc;
+    rc = ensure_limbs(db, 8ull * B * db->pitch);
+    if (rc != QPADL_OK) return rc;
+    QPADL_CU(launch_vec_limbs(Q, db->prm.cols, B, db->prm.cols, db->limbs, db->pitch, db->num_sms, stream));
+    return run_limb_gemm(db, B, ans, 1, db->prm.rows, stream);
+}
+
+// Smallest batch for which the tensor-core GEMM beats the streaming kernel.
+constexpr uint32_t kTensorMinBatch = 3;
+
+}  // namespace
+
+extern "C" {
+
+const char *qpadl_strerror(int code) {
+    switch (code) {
+        case QPADL_OK: return "ok";
+        case QPADL_EINVAL: return "invalid argument";
+        case QPADL_ENOMEM: return "out of device memory";
+        case QPADL_ECUDA: return "CUDA error";
+        case QPADL_ETIMEOUT: return "device wait timed out";
+        case QPADL_EBUSY: return "busy: admission refused";
+        case QPADL_EAGAIN: return "not ready";
+        default: return "unknown error";
+    }
+}
+
+int qpadl_version(void) { return 10000; }
+
+int qpadl_pir_setup(const qpadl_params *prm, const uint8_t *db_dev, qpadl_stream_t stream, qpadl_db **out) {
+    if (!out || !db_dev) return QPADL_EINVAL;
+    *out = nullptr;
+    int rc = validate_params(prm);
+    if (rc != QPADL_OK) return rc;
+    qpadl_db *db = new (std::nothrow) qpadl_db();
+    if (!db) return QPADL_ENOMEM;
+    db->prm = *prm;
+    db->db = db_dev;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    db->last_stream = s;
+    auto fail = [&](int code) {
+        qpadl_pir_destroy(db);
+        return code;
+    };
+    if (cudaGetDevice(&db->device) != cudaSuccess) return fail(QPADL_ECUDA);
+    if (cudaDeviceGetAttribute(&db->num_sms, cudaDevAttrMultiProcessorCount, db->device) != cudaSuccess)
+        return fail(QPADL_ECUDA);
+    if ((rc = prepare_device(db->device)) != QPADL_OK) return fail(rc);
+    if ((rc = dev_alloc(db, reinterpret_cast<void **>(&db->d_status), 16)) != QPADL_OK) return fail(rc);
+    if (cudaMemsetAsync(db->d_status, 0, 16, s) != cudaSuccess) return fail(QPADL_ECUDA);
+    const uint64_t R = prm->rows, C = prm->cols;
+    if (prm->p < 256) {
+        max_digit_kernel<<<db->num_sms * 4, 256, 0, s>>>(db_dev, R * C, db->d_status + 1);
+        int mx = 0;
+        if (cudaGetLastError() != cudaSuccess) return fail(QPADL_ECUDA);
+        if (cudaMemcpyAsync(&mx, db->d_status + 1, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(QPADL_ECUDA);
+        if (mx >= static_cast<int>(prm->p)) return fail(QPADL_EINVAL);
+    }
+    db->stream_ok = (C % 16 == 0) && aligned16(db_dev);
+    if (db->stream_ok) {
+        if (!encode_2d(&db->db_map, CU_TENSOR_MAP_DATA_TYPE_UINT8, db_dev, C, R, C, kStreamChunkCols, 8,
+                       CU_TENSOR_MAP_SWIZZLE_NONE))
+            return fail(QPADL_ECUDA);
+        db->pack_words = stream_pack_words(C);
+        if ((rc = dev_alloc(db, reinterpret_cast<void **>(&db->qpack), 4 * db->pack_words * 4)) != QPADL_OK)
+            return fail(rc);
+    }
+    if ((rc = dev_alloc(db, reinterpret_cast<void **>(&db->stage_q), C * 4)) != QPADL_OK) return fail(rc);
+    if ((rc = dev_alloc(db, reinterpret_cast<void **>(&db->stage_ans), R * 4)) != QPADL_OK) return fail(rc);
+    if (prm->flags & QPADL_SETUP_TENSOR_COPY) {
+        if ((rc = ensure_tensor_copy(db, s)) != QPADL_OK) return fail(rc);
+    }
+    *out = db;
+    return QPADL_OK;
+}
+
+int qpadl_pir_destroy(qpadl_db *db) {
+    if (!db) return QPADL_OK;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (db->device != cur) cudaSetDevice(db->device);
+    if (db->last_stream) cudaStreamSynchronize(db->last_stream);
+    cudaDeviceSynchronize();
+    dev_free(db, db->d_status, 16);
+    dev_free(db, db->qpack, 4 * db->pack_words * 4);
+    dev_free(db, db->d16, db->prm.rows * db->pitch * 2);
+    dev_free(db, db->limbs, db->limbs_bytes);
+    dev_free(db, db->stage_q, db->prm.cols * 4);
+    dev_free(db, db->stage_ans, db->prm.rows * 4);
+    if (cur >= 0 && cur != db->device) cudaSetDevice(cur);
+    delete db;
+    return QPADL_OK;
+}
+
+int qpadl_pir_status(qpadl_db *db) {
+    if (!db) return QPADL_EINVAL;
+    if (set_device(db) != QPADL_OK) return QPADL_ECUDA;
+    if (db->last_stream && cudaStreamSynchronize(db->last_stream) != cudaSuccess) return QPADL_ECUDA;
+    int st = 0;
+    if (cudaMemcpy(&st, db->d_status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return QPADL_ECUDA;
+    if (st != 0) {
+        const int zero = 0;
+        cudaMemcpy(db->d_status, &zero, 4, cudaMemcpyHostToDevice);
+        return QPADL_ETIMEOUT;
+    }
+    return QPADL_OK;
+}
+
+uint64_t qpadl_pir_device_bytes(const qpadl_db *db) { return db ? db->owned_bytes : 0; }
+
+int qpadl_pir_gen_a(const qpadl_params *prm, uint32_t *A_dev, qpadl_stream_t stream) {
+    int rc = validate_params(prm);
+    if (rc != QPADL_OK) return rc;
+    if (!A_dev || (reinterpret_cast<uintptr_t>(A_dev) & 3u)) return QPADL_EINVAL;
+    int dev = 0, sms = 0;
+    QPADL_CU(cudaGetDevice(&dev));
+    QPADL_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    QPADL_CU(launch_gen_a(prm->seed, prm->cols, prm->n, A_dev, sms, reinterpret_cast<cudaStream_t>(stream)));
+    return QPADL_OK;
+}
+
+int qpadl_pir_hint(qpadl_db *db, const uint32_t *A_dev, uint32_t *H_dev, qpadl_stream_t stream) {
+    if (!db || !A_dev || !H_dev) return QPADL_EINVAL;
+    if (set_device(db) != QPADL_OK) return QPADL_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    db->last_stream = s;
+    int rc = ensure_tensor_copy(db, s);
+    if (rc != QPADL_OK) return rc;
+    const uint32_t n = db->prm.n;
+    rc = ensure_limbs(db, 8ull * n * db->pitch);
+    if (rc != QPADL_OK) return rc;
+    QPADL_CU(launch_mat_col_limbs(A_dev, db->prm.cols, n, db->limbs, db->pitch, s));
+    return run_limb_gemm(db, n, H_dev, n, 1, s);
+}
+
+int qpadl_pir_query(const qpadl_params *prm, const uint32_t *A_dev, const uint32_t *s_dev, const int32_t *e_dev,
+                    uint64_t col, uint32_t *q_dev, qpadl_stream_t stream) {
+    int rc = validate_params(prm);
+    if (rc != QPADL_OK) return rc;
+    if (!A_dev || !s_dev || !e_dev || !q_dev || col >= prm->cols) return QPADL_EINVAL;
+    int dev = 0, sms = 0;
+    QPADL_CU(cudaGetDevice(&dev));
+    QPADL_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const uint32_t delta = static_cast<uint32_t>((1ull << 32) / prm->p);
+    QPADL_CU(launch_query(A_dev, prm->cols, prm->n, s_dev, e_dev, col, delta, q_dev, sms,
+                          reinterpret_cast<cudaStream_t>(stream)));
+    return QPADL_OK;
+}
+
+int qpadl_pir_query_batch(const qpadl_params *prm, const uint32_t *A_dev, const uint32_t *S_dev,
+                          const int32_t *E_dev, const uint32_t *cols_dev, uint32_t B, uint32_t *Q_dev,
+                          qpadl_stream_t stream) {
+    int rc = validate_params(prm);
+    if (rc != QPADL_OK) return rc;
+    if (!A_dev || !S_dev || !E_dev || !cols_dev || !Q_dev || B == 0) return QPADL_EINVAL;
+    const uint32_t delta = static_cast<uint32_t>((1ull << 32) / prm->p);
+    QPADL_CU(launch_query_batch(A_dev, prm->cols, prm->n, S_dev, E_dev, cols_dev, B, delta, Q_dev,
+                                reinterpret_cast<cudaStream_t>(stream)));
+    return QPADL_OK;
+}
+
+int qpadl_pir_answer(qpadl_db *db, const uint32_t *q_dev, uint32_t *ans_dev, qpadl_stream_t stream) {
+    if (!db || !q_dev || !ans_dev) return QPADL_EINVAL;
+    if (set_device(db) != QPADL_OK) return QPADL_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    db->last_stream = s;
+    return answer_streaming(db, q_dev, 1, ans_dev, s);
+}
+
+int qpadl_pir_answer_batch_path(qpadl_db *db, const uint32_t *Q_dev, uint32_t B, uint32_t *ans_dev, int path,
+                                qpadl_stream_t stream) {
+    if (!db || !Q_dev || !ans_dev || B == 0 || (path != 0 && path != 1)) return QPADL_EINVAL;
+    if (set_device(db) != QPADL_OK) return QPADL_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    db->last_stream = s;
+    return path == 0 ? answer_streaming(db, Q_dev, B, ans_dev, s) : answer_tensor(db, Q_dev, B, ans_dev, s);
+}
+
+int qpadl_pir_answer_batch(qpadl_db *db, const uint32_t *Q_dev, uint32_t B, uint32_t *ans_dev,
+                           qpadl_stream_t stream) {
+    return qpadl_pir_answer_batch_path(db, Q_dev, B, ans_dev, B >= kTensorMinBatch ? 1 : 0, stream);
+}
+
+int qpadl_pir_answer_host(qpadl_db *db, const uint32_t *q_host, uint32_t *ans_host, qpadl_stream_t stream) {
+    if (!db || !q_host || !ans_host) return QPADL_EINVAL;
+    if (set_device(db) != QPADL_OK) return QPADL_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    db->last_stream = s;
+    const uint64_t C = db->prm.cols, R = db->prm.rows;
+    QPADL_CU(cudaMemcpyAsync(db->stage_q, q_host, C * 4, cudaMemcpyHostToDevice, s));
+    int rc = answer_streaming(db, db->stage_q, 1, db->stage_ans, s);
+    if (rc != QPADL_OK) return rc;
+    QPADL_CU(cudaMemcpyAsync(ans_host, db->stage_ans, R * 4, cudaMemcpyDeviceToHost, s));
+    QPADL_CU(cudaStreamSynchronize(s));
+    return QPADL_OK;
+}
+
+int qpadl_pir_recover(const qpadl_params *prm, const uint32_t *ans_dev, const uint32_t *H_dev,
+                      const uint32_t *s_dev, uint8_t *out_dev, qpadl_stream_t stream) {
+    int rc = validate_params(prm);
+    if (rc != QPADL_OK) return rc;
+    if (!ans_dev || !H_dev || !s_dev || !out_dev) return QPADL_EINVAL;
+    int dev = 0, sms = 0;
+    QPADL_CU(cudaGetDevice(&dev));
+    QPADL_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const uint32_t shift = 32u - static_cast<uint32_t>(log2_exact(prm->p));
+    QPADL_CU(launch_recover(ans_dev, H_dev, prm->rows, prm->n, s_dev, shift, out_dev, sms,
+                            reinterpret_cast<cudaStream_t>(stream)));
+    return QPADL_OK;
+}
+
+int qpadl_pir_recover_batch(const qpadl_params *prm, const uint32_t *ans_dev, const uint32_t *H_dev,
+                            const uint32_t *S_dev, uint32_t B, uint8_t *out_dev, qpadl_stream_t stream) {
+    int rc = validate_params(prm);
+    if (rc != QPADL_OK) return rc;
+    if (!ans_dev || !H_dev || !S_dev || !out_dev || B == 0) return QPADL_EINVAL;
+    const uint32_t shift = 32u - static_cast<uint32_t>(log2_exact(prm->p));
+    QPADL_CU(launch_recover_batch(ans_dev, H_dev, prm->rows, prm->n, S_dev, B, shift, out_dev,
+                                  reinterpret_cast<cudaStream_t>(stream)));
+    return QPADL_OK;
+}
+
+}  // extern "C"

@@ -72,6 +72,14 @@ def db_digits(rows: int, cols: int, p: int = 256, seed: int = 1,
         raise ValueError("p must be a power of two in [2, 256]")
     if row_count is None:
         row_count = rows - row_start
+    band = max(1, (64 << 20) // max(cols, 1))
+    if row_count > band:
+        # generate in 64 MiB bands to bound host memory
+        out = np.empty((row_count, cols), dtype=np.uint8)
+        for r in range(0, row_count, band):
+            k = min(band, row_count - r)
+            out[r:r + k] = db_digits(rows, cols, p, seed, row_start + r, k)
+        return out
     total = row_count * cols
     first = row_start * cols
     # eight digits per 64-bit output; regenerate the covering range of outputs

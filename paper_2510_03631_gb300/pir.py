@@ -1,0 +1,285 @@
+"""Thin Python binding of the C ABI in include/qpadl_pir.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls, takes torch
+tensors (device tensors for *_dev arguments, CPU tensors for *_host ones),
+checks dtype/shape/device, passes raw pointers and the current CUDA stream,
+and raises QpadlError on a non-zero status.  All arithmetic runs in the CUDA
+library; there is no CPU fallback: if the library cannot be loaded every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+QPADL_OK = 0
+QPADL_EINVAL = -1
+QPADL_ENOMEM = -2
+QPADL_ECUDA = -3
+QPADL_ETIMEOUT = -4
+QPADL_EBUSY = -5
+QPADL_EAGAIN = -6
+QPADL_SETUP_TENSOR_COPY = 0x1
+
+
+class QpadlError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+class qpadl_params(ctypes.Structure):
+    _fields_ = [
+        ("rows", ctypes.c_uint64),
+        ("cols", ctypes.c_uint64),
+        ("n", ctypes.c_uint32),
+        ("log_q", ctypes.c_uint32),
+        ("p", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32),
+        ("sigma", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+def params(rows: int, cols: int, n: int, p: int = 256, sigma: float = 6.4, seed: int = 1,
+           flags: int = 0) -> qpadl_params:
+    return qpadl_params(rows, cols, n, 32, p, flags, sigma, seed & (2**64 - 1))
+
+
+_lib = None
+_lock = threading.Lock()
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "qpadl_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "qpadl_version": ([], ctypes.c_int),
+    "qpadl_pir_setup": ([_P, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "qpadl_pir_destroy": ([_P], ctypes.c_int),
+    "qpadl_pir_status": ([_P], ctypes.c_int),
+    "qpadl_pir_device_bytes": ([_P], ctypes.c_uint64),
+    "qpadl_pir_gen_a": ([_P, _P, _P], ctypes.c_int),
+    "qpadl_pir_hint": ([_P, _P, _P, _P], ctypes.c_int),
+    "qpadl_pir_query": ([_P, _P, _P, _P, ctypes.c_uint64, _P, _P], ctypes.c_int),
+    "qpadl_pir_query_batch": ([_P, _P, _P, _P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
+    "qpadl_pir_answer": ([_P, _P, _P, _P], ctypes.c_int),
+    "qpadl_pir_answer_batch": ([_P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
+    "qpadl_pir_answer_batch_path": ([_P, _P, ctypes.c_uint32, _P, ctypes.c_int, _P], ctypes.c_int),
+    "qpadl_pir_answer_host": ([_P, _P, _P, _P], ctypes.c_int),
+    "qpadl_pir_recover": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "qpadl_pir_recover_batch": ([_P, _P, _P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libqpadl_pir.so (building it first if asked); raises if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing:
+                path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is not built; run __graft_entry__.build()")
+            lib = ctypes.CDLL(path)
+            for name, (argt, rest) in _SIGS.items():
+                fn = getattr(lib, name, None)
+                if fn is None:
+                    continue
+                fn.argtypes = argt
+                fn.restype = rest
+            _lib = lib
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load(build_if_missing=False).qpadl_strerror(code).decode()
+    except Exception:
+        return {0: "ok", -1: "invalid argument", -2: "out of device memory", -3: "CUDA error",
+                -4: "device wait timed out", -5: "busy", -6: "not ready"}.get(code, "unknown error")
+
+
+def _check(rc: int, what: str):
+    if rc != QPADL_OK:
+        raise QpadlError(rc, what)
+
+
+def _dev(t: torch.Tensor, dtype: torch.dtype, numel: int, name: str) -> ctypes.c_void_p:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < numel:
+        raise ValueError(f"{name} has {t.numel()} elements, needs {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(t: torch.Tensor, dtype: torch.dtype, numel: int, name: str) -> ctypes.c_void_p:
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a CPU tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() < numel:
+        raise ValueError(f"{name}: need contiguous {dtype} with >= {numel} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Database:
+    """Handle returned by qpadl_pir_setup (owns the C handle, keeps D alive)."""
+
+    def __init__(self, handle: ctypes.c_void_p, prm: qpadl_params, db: torch.Tensor):
+        self.handle = handle
+        self.prm = prm
+        self.db = db
+
+    @property
+    def rows(self) -> int:
+        return int(self.prm.rows)
+
+    @property
+    def cols(self) -> int:
+        return int(self.prm.cols)
+
+    def close(self):
+        if self.handle:
+            load().qpadl_pir_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qpadl_version() -> int:
+    return int(load().qpadl_version())
+
+
+def qpadl_pir_setup(prm: qpadl_params, db: torch.Tensor, stream=None) -> Database:
+    _dev(db, torch.uint8, int(prm.rows) * int(prm.cols), "db")
+    h = ctypes.c_void_p()
+    _check(load().qpadl_pir_setup(ctypes.byref(prm), ctypes.c_void_p(db.data_ptr()), _stream(stream),
+                                  ctypes.byref(h)), "qpadl_pir_setup")
+    return Database(h, prm, db)
+
+
+def qpadl_pir_destroy(db: Database):
+    db.close()
+
+
+def qpadl_pir_status(db: Database) -> int:
+    return int(load().qpadl_pir_status(db.handle))
+
+
+def qpadl_pir_device_bytes(db: Database) -> int:
+    return int(load().qpadl_pir_device_bytes(db.handle))
+
+
+def qpadl_pir_gen_a(prm: qpadl_params, A: torch.Tensor, stream=None) -> torch.Tensor:
+    p = _dev(A, torch.int32, int(prm.cols) * int(prm.n), "A")
+    _check(load().qpadl_pir_gen_a(ctypes.byref(prm), p, _stream(stream)), "qpadl_pir_gen_a")
+    return A
+
+
+def qpadl_pir_hint(db: Database, A: torch.Tensor, H: torch.Tensor, stream=None) -> torch.Tensor:
+    n = int(db.prm.n)
+    pa = _dev(A, torch.int32, db.cols * n, "A")
+    ph = _dev(H, torch.int32, db.rows * n, "H")
+    _check(load().qpadl_pir_hint(db.handle, pa, ph, _stream(stream)), "qpadl_pir_hint")
+    return H
+
+
+def qpadl_pir_query(prm: qpadl_params, A: torch.Tensor, s: torch.Tensor, e: torch.Tensor, col: int,
+                    q: torch.Tensor, stream=None) -> torch.Tensor:
+    C, n = int(prm.cols), int(prm.n)
+    args = (_dev(A, torch.int32, C * n, "A"), _dev(s, torch.int32, n, "s"), _dev(e, torch.int32, C, "e"))
+    _check(load().qpadl_pir_query(ctypes.byref(prm), *args, int(col), _dev(q, torch.int32, C, "q"),
+                                  _stream(stream)), "qpadl_pir_query")
+    return q
+
+
+def qpadl_pir_query_batch(prm: qpadl_params, A: torch.Tensor, S: torch.Tensor, E: torch.Tensor,
+                          cols: torch.Tensor, Q: torch.Tensor, stream=None) -> torch.Tensor:
+    C, n = int(prm.cols), int(prm.n)
+    B = int(cols.numel())
+    _check(load().qpadl_pir_query_batch(
+        ctypes.byref(prm), _dev(A, torch.int32, C * n, "A"), _dev(S, torch.int32, B * n, "S"),
+        _dev(E, torch.int32, B * C, "E"), _dev(cols, torch.int32, B, "cols"), B,
+        _dev(Q, torch.int32, B * C, "Q"), _stream(stream)), "qpadl_pir_query_batch")
+    return Q
+
+
+def qpadl_pir_answer(db: Database, q: torch.Tensor, ans: torch.Tensor, stream=None) -> torch.Tensor:
+    _check(load().qpadl_pir_answer(db.handle, _dev(q, torch.int32, db.cols, "q"),
+                                   _dev(ans, torch.int32, db.rows, "ans"), _stream(stream)),
+           "qpadl_pir_answer")
+    return ans
+
+
+def qpadl_pir_answer_batch(db: Database, Q: torch.Tensor, ans: torch.Tensor, stream=None,
+                           path: int | None = None) -> torch.Tensor:
+    B = Q.numel() // db.cols
+    if B * db.cols != Q.numel() or B == 0:
+        raise ValueError("Q must hold B x C words")
+    pq = _dev(Q, torch.int32, B * db.cols, "Q")
+    pa = _dev(ans, torch.int32, B * db.rows, "ans")
+    if path is None:
+        rc = load().qpadl_pir_answer_batch(db.handle, pq, B, pa, _stream(stream))
+    else:
+        rc = load().qpadl_pir_answer_batch_path(db.handle, pq, B, pa, int(path), _stream(stream))
+    _check(rc, "qpadl_pir_answer_batch")
+    return ans
+
+
+def qpadl_pir_answer_host(db: Database, q: torch.Tensor, ans: torch.Tensor, stream=None) -> torch.Tensor:
+    _check(load().qpadl_pir_answer_host(db.handle, _host(q, torch.int32, db.cols, "q"),
+                                        _host(ans, torch.int32, db.rows, "ans"), _stream(stream)),
+           "qpadl_pir_answer_host")
+    return ans
+
+
+def qpadl_pir_recover(prm: qpadl_params, ans: torch.Tensor, H: torch.Tensor, s: torch.Tensor,
+                      out: torch.Tensor, stream=None) -> torch.Tensor:
+    R, n = int(prm.rows), int(prm.n)
+    _check(load().qpadl_pir_recover(
+        ctypes.byref(prm), _dev(ans, torch.int32, R, "ans"), _dev(H, torch.int32, R * n, "H"),
+        _dev(s, torch.int32, n, "s"), _dev(out, torch.uint8, R, "out"), _stream(stream)), "qpadl_pir_recover")
+    return out
+
+
+def qpadl_pir_recover_batch(prm: qpadl_params, ans: torch.Tensor, H: torch.Tensor, S: torch.Tensor,
+                            out: torch.Tensor, stream=None) -> torch.Tensor:
+    R, n = int(prm.rows), int(prm.n)
+    B = S.numel() // n
+    _check(load().qpadl_pir_recover_batch(
+        ctypes.byref(prm), _dev(ans, torch.int32, B * R, "ans"), _dev(H, torch.int32, R * n, "H"),
+        _dev(S, torch.int32, B * n, "S"), B, _dev(out, torch.uint8, B * R, "out"), _stream(stream)),
+        "qpadl_pir_recover_batch")
+    return out
+
+
+def as_u32(t: torch.Tensor):
+    """View an int32 torch tensor's bits as numpy uint32 (host copy)."""
+    return t.detach().cpu().numpy().view("uint32")
+
+
+def from_u32(a, device="cuda") -> torch.Tensor:
+    """numpy uint32 -> int32 torch tensor with the same bits."""
+    import numpy as np
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(device)

@@ -1,0 +1,236 @@
+"""Bit-exact parity of every CUDA step with the CPU oracle, through the C ABI.
+
+Sizes here are small enough for the oracle to check every output element
+while still spanning several tiles and ragged tails: rows not a multiple of
+the 8-row TMA box or the 128-row MMA tile, columns not a multiple of the
+256-digit streaming chunk, the 64-element K block or the 512-deep exact
+chunk, batch sizes around every limb-tile width, C not a multiple of 16
+(the fallback kernel), and the extreme digit/limb values that push the fp32
+tensor-core accumulator to its exactness bound.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2510_03631_gb300 import inputs, pir
+
+pytestmark = pytest.mark.gpu
+
+M32 = (1 << 32) - 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pir.load()
+    torch.cuda.set_device(0)
+    yield
+
+
+def _setup(R, C, n=8, p=256, seed=1, D=None, flags=0):
+    if D is None:
+        D = inputs.db_digits(R, C, p, seed=seed)
+    prm = pir.params(R, C, n, p=p, seed=seed, flags=flags)
+    db = pir.qpadl_pir_setup(prm, torch.from_numpy(np.ascontiguousarray(D)).cuda())
+    return prm, D, db
+
+
+def _answers(db, Q_np, path=None):
+    B = Q_np.shape[0]
+    ans = torch.full((B * db.rows,), -1, dtype=torch.int32, device="cuda")
+    Q = pir.from_u32(Q_np.reshape(-1))
+    if B == 1 and path is None:
+        pir.qpadl_pir_answer(db, Q, ans)
+    else:
+        pir.qpadl_pir_answer_batch(db, Q, ans, path=path)
+    torch.cuda.synchronize()
+    assert pir.qpadl_pir_status(db) == 0
+    return pir.as_u32(ans).reshape(B, db.rows)
+
+
+# ------------------------------------------------------------------ Setup
+@pytest.mark.parametrize("C,n,seed", [(1024, 512, 1), (7, 3, 0), (1000, 33, 2**63 + 5)])
+def test_gen_a_matches_oracle(C, n, seed):
+    prm = pir.params(16, C, n, seed=seed)
+    A = torch.empty(C * n, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_gen_a(prm, A)
+    torch.cuda.synchronize()
+    assert np.array_equal(pir.as_u32(A).reshape(C, n), oracle.gen_a(seed, C, n))
+
+
+# ------------------------------------------------------------------ single-query Response
+@pytest.mark.parametrize("R,C", [
+    (1024, 1024),      # tiny workload
+    (1, 16),           # one row, one 16-digit group
+    (7, 272),          # rows < box, ragged last chunk
+    (1000, 1008),      # ragged rows (not /8) and columns (not /256)
+    (2053, 4096),      # more octets than SMs: several per CTA
+    (4100, 512),       # > 256 rows per CTA band on small grids? (band split into spans)
+    (777, 1000),       # C % 16 != 0 -> generic kernel
+    (33, 5),           # tiny ragged generic
+])
+def test_answer_single(R, C):
+    prm, D, db = _setup(R, C, seed=R + C)
+    q = inputs.uniform_u32(C, seed=R * C, tag=inputs.TAG_MISC)
+    got = _answers(db, q[None, :])
+    assert np.array_equal(got[0], oracle.answer(D, q))
+
+
+def test_answer_single_many_rows_per_cta():
+    # 40000 rows on a 152-SM grid gives each CTA > 256 rows, i.e. several spans
+    R, C = 40000, 256
+    prm, D, db = _setup(R, C, seed=5)
+    q = inputs.uniform_u32(C, seed=6, tag=inputs.TAG_MISC)
+    assert np.array_equal(_answers(db, q[None, :])[0], oracle.answer(D, q, threads=oracle.max_threads()))
+
+
+def test_answer_extreme_values():
+    # all digits 255 against the query words that give the largest limb magnitudes
+    R, C = 256, 2048
+    D = np.full((R, C), 255, dtype=np.uint8)
+    prm, D, db = _setup(R, C, D=D)
+    for word in (0x7F7F7F80, 0x7F7F7F7F, 0xFFFFFFFF, 0x80808080, 0x80000000):
+        q = np.full(C, word, dtype=np.uint32)
+        exp = np.full(R, (255 * C * word) & M32, dtype=np.uint32)
+        for path in (None, 0, 1):
+            got = _answers(db, np.stack([q, q, q]) if path is not None else q[None, :], path=path)
+            for b in range(got.shape[0]):
+                assert np.array_equal(got[b], exp), (hex(word), path)
+
+
+def test_answer_unit_queries_select_columns():
+    R, C = 300, 1024
+    prm, D, db = _setup(R, C, seed=9)
+    cols = [0, 1, 255, 256, 1023]
+    Q = np.zeros((len(cols), C), dtype=np.uint32)
+    for b, c in enumerate(cols):
+        Q[b, c] = 1 << 24
+    for path in (0, 1):
+        got = _answers(db, Q, path=path)
+        for b, c in enumerate(cols):
+            assert np.array_equal(got[b], (D[:, c].astype(np.uint64) << np.uint64(24)).astype(np.uint32))
+
+
+# ------------------------------------------------------------------ batched Response
+@pytest.mark.parametrize("B", [1, 2, 3, 4, 5, 7, 8, 9, 16, 17, 32, 33, 64, 65, 100])
+def test_answer_batch_both_paths(B):
+    R, C = 300, 1000 + 8   # ragged rows vs 128-row tile, columns vs 64/256/512
+    prm, D, db = _setup(R, C, seed=B)
+    Q = inputs.uniform_u32(B * C, seed=B + 100, tag=inputs.TAG_MISC).reshape(B, C)
+    exp = oracle.answer_batch(D, Q)
+    for path in (0, 1):
+        assert np.array_equal(_answers(db, Q, path=path), exp), f"path {path}"
+    assert np.array_equal(_answers(db, Q), exp)
+
+
+@pytest.mark.parametrize("R,C,B", [(129, 1537, 40), (128, 64, 3), (1, 8, 5), (513, 4100, 70), (1024, 1024, 256)])
+def test_answer_batch_tensor_ragged(R, C, B):
+    prm, D, db = _setup(R, C, seed=R)
+    Q = inputs.uniform_u32(B * C, seed=C, tag=inputs.TAG_MISC).reshape(B, C)
+    assert np.array_equal(_answers(db, Q, path=1), oracle.answer_batch(D, Q, threads=oracle.max_threads()))
+
+
+def test_answer_batch_linearity_on_device():
+    R, C, B = 256, 2048, 8
+    prm, D, db = _setup(R, C, seed=3)
+    Q1 = inputs.uniform_u32(B * C, seed=1, tag=inputs.TAG_MISC).reshape(B, C)
+    Q2 = inputs.uniform_u32(B * C, seed=2, tag=inputs.TAG_MISC).reshape(B, C)
+    with np.errstate(over="ignore"):
+        lhs = _answers(db, (Q1 + Q2).astype(np.uint32), path=1)
+        rhs = (_answers(db, Q1, path=1) + _answers(db, Q2, path=1)).astype(np.uint32)
+    assert np.array_equal(lhs, rhs)
+
+
+def test_small_plaintext_modulus_and_digit_check():
+    R, C = 64, 512
+    D = inputs.db_digits(R, C, 16, seed=4)
+    prm, D, db = _setup(R, C, p=16, D=D)
+    q = inputs.uniform_u32(C, seed=5, tag=inputs.TAG_MISC)
+    assert np.array_equal(_answers(db, q[None, :])[0], oracle.answer(D, q))
+    bad = D.copy()
+    bad[3, 7] = 16
+    with pytest.raises(pir.QpadlError) as ei:
+        _setup(R, C, p=16, D=bad)
+    assert ei.value.code == pir.QPADL_EINVAL
+
+
+# ------------------------------------------------------------------ Hint
+@pytest.mark.parametrize("R,C,n", [(1024, 1024, 512), (100, 1000, 17), (129, 520, 1), (300, 64, 70)])
+def test_hint_matches_oracle(R, C, n):
+    prm, D, db = _setup(R, C, n=n, seed=n)
+    A = torch.empty(C * n, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_gen_a(prm, A)
+    H = torch.full((R * n,), -1, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_hint(db, A, H)
+    torch.cuda.synchronize()
+    assert pir.qpadl_pir_status(db) == 0
+    exp = oracle.hint(D, oracle.gen_a(n, C, n), threads=oracle.max_threads())
+    assert np.array_equal(pir.as_u32(H).reshape(R, n), exp)
+
+
+# ------------------------------------------------------------------ Query / Recover
+@pytest.mark.parametrize("C,n", [(1024, 512), (1000, 33), (64, 1)])
+def test_query_single_and_batch(C, n):
+    prm = pir.params(8, C, n, seed=C)
+    A = torch.empty(C * n, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_gen_a(prm, A)
+    A_o = oracle.gen_a(C, C, n)
+    B = 19
+    S_o = inputs.secrets(B, n, seed=1)
+    E_o = inputs.noise_batch(B, C, seed=2)
+    cols = inputs.target_columns(B, C, seed=3)
+    q = torch.empty(C, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_query(prm, A, pir.from_u32(S_o[0]), torch.from_numpy(E_o[0]).cuda(), int(cols[0]), q)
+    Q = torch.empty(B * C, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_query_batch(prm, A, pir.from_u32(S_o.reshape(-1)), torch.from_numpy(E_o.reshape(-1)).cuda(),
+                              torch.from_numpy(cols.astype(np.int32)).cuda(), Q)
+    torch.cuda.synchronize()
+    exp = np.stack([oracle.query(A_o, S_o[b], E_o[b], int(cols[b]), 1 << 24) for b in range(B)])
+    assert np.array_equal(pir.as_u32(q), exp[0])
+    assert np.array_equal(pir.as_u32(Q).reshape(B, C), exp)
+
+
+@pytest.mark.parametrize("p", [256, 16, 2])
+def test_roundtrip_recover_every_column(p):
+    R, C, n = 200, 96, 64
+    prm, D, db = _setup(R, C, n=n, p=p, seed=p)
+    A = torch.empty(C * n, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_gen_a(prm, A)
+    H = torch.empty(R * n, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_hint(db, A, H)
+    B = C
+    S = pir.from_u32(inputs.secrets(B, n, seed=7).reshape(-1))
+    E = torch.from_numpy(inputs.noise_batch(B, C, seed=8).reshape(-1)).cuda()
+    cols = torch.arange(C, dtype=torch.int32, device="cuda")
+    Q = torch.empty(B * C, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_query_batch(prm, A, S, E, cols, Q)
+    ans = torch.empty(B * R, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_answer_batch(db, Q, ans)
+    out = torch.empty(B * R, dtype=torch.uint8, device="cuda")
+    pir.qpadl_pir_recover_batch(prm, ans, H, S, out)
+    out1 = torch.empty(R, dtype=torch.uint8, device="cuda")
+    pir.qpadl_pir_recover(prm, ans[:R], H, S[:n], out1)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(B, R)
+    assert np.array_equal(got, D.T)
+    assert np.array_equal(out1.cpu().numpy(), D[:, 0])
+
+
+def test_host_buffer_answer():
+    R, C = 512, 1024
+    prm, D, db = _setup(R, C, seed=12)
+    q = inputs.uniform_u32(C, seed=13, tag=inputs.TAG_MISC)
+    qh = torch.from_numpy(q.view(np.int32)).pin_memory()
+    ah = torch.empty(R, dtype=torch.int32).pin_memory()
+    pir.qpadl_pir_answer_host(db, qh, ah)
+    assert np.array_equal(ah.numpy().view(np.uint32), oracle.answer(D, q))
+
+
+def test_tensor_copy_at_setup_and_device_bytes():
+    R, C = 256, 512
+    prm, D, db = _setup(R, C, seed=14, flags=pir.QPADL_SETUP_TENSOR_COPY)
+    assert pir.qpadl_pir_device_bytes(db) >= R * C * 2
+    Q = inputs.uniform_u32(4 * C, seed=15, tag=inputs.TAG_MISC).reshape(4, C)
+    assert np.array_equal(_answers(db, Q, path=1), oracle.answer_batch(D, Q))
