@@ -83,6 +83,13 @@ const char *qpadl_strerror(int code);
 /* Version of this ABI (major * 10000 + minor * 100 + patch). */
 int qpadl_version(void);
 
+/* Tuning options of a handle (qpadl_pir_set_option / qpadl_pir_get_option).
+ * They change speed only, never results. */
+#define QPADL_OPT_STREAM_CHUNK 1     /* digits per row per pipeline stage of the streaming
+                                        Response: 512, 1024, 2048 (default) or 4096 */
+#define QPADL_OPT_TENSOR_MIN_BATCH 2 /* smallest batch that qpadl_pir_answer_batch sends to
+                                        the tensor-core GEMM (>= 1; default 3) */
+
 /*
  * Setup (server side; Def. 1's server holds D).  Validates `prm`, records
  * the shape and binds the caller's resident database `db_dev` (R*C bytes,
@@ -107,6 +114,11 @@ int qpadl_pir_status(qpadl_db *db);
 
 /* Bytes of device memory the handle currently owns (operand copy + scratch). */
 uint64_t qpadl_pir_device_bytes(const qpadl_db *db);
+
+/* Sets / reads a tuning option (QPADL_OPT_*).  QPADL_EINVAL for an unknown
+ * option or an unsupported value.  Host-only; enqueues nothing. */
+int qpadl_pir_set_option(qpadl_db *db, int option, int64_t value);
+int qpadl_pir_get_option(const qpadl_db *db, int option, int64_t *value);
 
 /*
  * Setup, public matrix: A_dev[j*n + k] = upper 32 bits of output number

@@ -30,7 +30,10 @@ struct qpadl_db {
     cudaStream_t last_stream = nullptr;
     // streaming path
     bool stream_ok = false;          // C % 16 == 0 and D 16-byte aligned
-    CUtensorMap db_map;
+    int stream_chunk = 2048;         // digits per row per stage (QPADL_OPT_STREAM_CHUNK)
+    uint32_t tensor_min_batch = 3;   // QPADL_OPT_TENSOR_MIN_BATCH
+    bool stream_maps = false;        // C % 256 == 0: 3-D tensor maps below are valid
+    CUtensorMap stream_map[4];       // box {256, cch/256, 8} for cch = 512 << i
     uint32_t *qpack = nullptr;       // packed limbs of up to 4 queries
     uint64_t pack_words = 0;         // per query
     // tensor-core path
@@ -201,10 +204,15 @@ int run_limb_gemm(qpadl_db *db, uint32_t NV, uint32_t *out, uint64_t ld_m, uint6
 
 int answer_stream_group(qpadl_db *db, const uint32_t *Q, uint32_t nq, uint32_t *ans, cudaStream_t stream) {
     const uint64_t C = db->prm.cols, R = db->prm.rows;
-    QPADL_CU(launch_pack_query(Q, C, static_cast<uint32_t>(C), nq, db->qpack, db->pack_words, stream));
-    QPADL_CU(launch_stream_answer(static_cast<int>(nq), db->db_map, db->qpack, db->pack_words, ans, R,
-                                  static_cast<uint32_t>(R), static_cast<uint32_t>(C), db->num_sms, db->d_status,
-                                  stream));
+    const int cch = nq == 1 ? db->stream_chunk : 1024;
+    QPADL_CU(launch_pack_query(Q, C, static_cast<uint32_t>(C), static_cast<uint32_t>(cch), nq, db->qpack,
+                               db->pack_words, stream));
+    int mi = 0;
+    while ((512 << mi) < cch) ++mi;
+    const CUtensorMap *map = db->stream_maps ? &db->stream_map[mi] : nullptr;
+    QPADL_CU(launch_stream_answer(static_cast<int>(nq), cch, map, db->db, static_cast<uint32_t>(R),
+                                  static_cast<uint32_t>(C), db->qpack, db->pack_words, ans, R, db->num_sms,
+                                  db->d_status, stream));
     return QPADL_OK;
 }
 
@@ -233,9 +241,6 @@ int answer_tensor(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, cu
     QPADL_CU(launch_vec_limbs(Q, db->prm.cols, B, db->prm.cols, db->limbs, db->pitch, db->num_sms, stream));
     return run_limb_gemm(db, B, ans, 1, db->prm.rows, stream);
 }
-
-// Smallest batch for which the tensor-core GEMM beats the streaming kernel.
-constexpr uint32_t kTensorMinBatch = 3;
 
 }  // namespace
 
@@ -288,10 +293,21 @@ int qpadl_pir_setup(const qpadl_params *prm, const uint8_t *db_dev, qpadl_stream
         if (mx >= static_cast<int>(prm->p)) return fail(QPADL_EINVAL);
     }
     db->stream_ok = (C % 16 == 0) && aligned16(db_dev);
+    if (db->stream_ok && C % 256 == 0) {
+        db->stream_maps = true;
+        for (int i = 0; i < 4; ++i) {
+            auto fn = encode_fn();
+            cuuint64_t dims[3] = {256, C / 256, R};
+            cuuint64_t strides[2] = {256, C};
+            cuuint32_t box[3] = {256, static_cast<cuuint32_t>((512u << i) / 256u), 8};
+            cuuint32_t estr[3] = {1, 1, 1};
+            if (!fn || fn(&db->stream_map[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(db_dev), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return fail(QPADL_ECUDA);
+        }
+    }
     if (db->stream_ok) {
-        if (!encode_2d(&db->db_map, CU_TENSOR_MAP_DATA_TYPE_UINT8, db_dev, C, R, C, kStreamChunkCols, 8,
-                       CU_TENSOR_MAP_SWIZZLE_NONE))
-            return fail(QPADL_ECUDA);
         db->pack_words = stream_pack_words(C);
         if ((rc = dev_alloc(db, reinterpret_cast<void **>(&db->qpack), 4 * db->pack_words * 4)) != QPADL_OK)
             return fail(rc);
@@ -409,7 +425,32 @@ int qpadl_pir_answer_batch_path(qpadl_db *db, const uint32_t *Q_dev, uint32_t B,
 
 int qpadl_pir_answer_batch(qpadl_db *db, const uint32_t *Q_dev, uint32_t B, uint32_t *ans_dev,
                            qpadl_stream_t stream) {
-    return qpadl_pir_answer_batch_path(db, Q_dev, B, ans_dev, B >= kTensorMinBatch ? 1 : 0, stream);
+    if (!db) return QPADL_EINVAL;
+    return qpadl_pir_answer_batch_path(db, Q_dev, B, ans_dev, B >= db->tensor_min_batch ? 1 : 0, stream);
+}
+
+int qpadl_pir_set_option(qpadl_db *db, int option, int64_t value) {
+    if (!db) return QPADL_EINVAL;
+    switch (option) {
+        case QPADL_OPT_STREAM_CHUNK:
+            if (!stream_config_valid(1, static_cast<int>(value))) return QPADL_EINVAL;
+            db->stream_chunk = static_cast<int>(value);
+            return QPADL_OK;
+        case QPADL_OPT_TENSOR_MIN_BATCH:
+            if (value < 1 || value > (1ll << 30)) return QPADL_EINVAL;
+            db->tensor_min_batch = static_cast<uint32_t>(value);
+            return QPADL_OK;
+        default: return QPADL_EINVAL;
+    }
+}
+
+int qpadl_pir_get_option(const qpadl_db *db, int option, int64_t *value) {
+    if (!db || !value) return QPADL_EINVAL;
+    switch (option) {
+        case QPADL_OPT_STREAM_CHUNK: *value = db->stream_chunk; return QPADL_OK;
+        case QPADL_OPT_TENSOR_MIN_BATCH: *value = db->tensor_min_batch; return QPADL_OK;
+        default: return QPADL_EINVAL;
+    }
 }
 
 int qpadl_pir_answer_host(qpadl_db *db, const uint32_t *q_host, uint32_t *ans_host, qpadl_stream_t stream) {

@@ -3,22 +3,28 @@
 // This is the server's product of the query with the whole database matrix
 // (QPADL Sec. 5.2; Def. 1 DB.Query.Response), accumulated mod q as in Alg. 4.
 // It reads every byte of D once and is bound by HBM bandwidth, so the design
-// is about keeping enough bytes in flight and spending few instructions per
-// byte:
-//  - Persistent grid, one CTA per SM.  Each CTA owns a contiguous band of
-//    rows (8-row granularity, so bands differ by at most 8 rows) and streams
-//    it chunk by chunk (256 columns) through a 3-stage shared-memory ring
-//    filled by TMA (one 2-D box per 8 rows) from a single producer thread.
+// is about a DRAM-friendly access pattern, enough bytes in flight, and few
+// instructions per byte:
+//  - Persistent grid, one CTA per SM.  CTA b owns rows [b R / G, (b+1) R / G)
+//    (bands differ by at most one row) and streams them in spans of up to
+//    SR rows.  A stage is SR rows x CCH contiguous digits per row (CCH =
+//    512..4096 bytes) in a shared-memory ring filled by one producer thread.
+//    The copy engine is limited by copy instructions rather than bytes
+//    (about 100 cycles per copy), so the producer moves 8 rows x CCH digits
+//    per instruction with a 3-D tensor map (256 digits x C/256 x R) and uses
+//    one plain bulk copy per row only for the rows left over below a
+//    multiple of 8, or when C is not a multiple of 256.
 //  - The query is pre-split into byte limbs: for each group of 4 columns,
 //    limb plane k holds byte k of the 4 query words.  A database word (4
 //    digits) times a limb word is one dp4a, so 16 digits x 4 limbs = 16 dp4a
-//    and no byte unpacking.  Per row the four limb sums recombine exactly
-//    as sum_k 2^{8k} acc_k (mod 2^32): D*q = sum_k 2^{8k} (D*limb_k).
-//  - 16 consumer warps: thread (row-lane rl, column group cg) covers 16
-//    digits of up to 8 rows per stage and keeps its partial sums in
-//    registers for the whole band; at the end one 16-lane shuffle reduction
-//    per row gives the row total.  No atomics, no second pass.
+//    and no byte unpacking.  Per row the four limb sums recombine exactly as
+//    sum_k 2^{8k} acc_k (mod 2^32), since D*q = sum_k 2^{8k} (D*limb_k).
+//  - 16 consumer warps: thread (row lane rl, column group cg) covers 16
+//    digits of up to RPT rows per stage and keeps its partial sums in
+//    registers for the whole span; at the end of a span a warp shuffle and
+//    a small shared-memory step reduce each row.  No atomics, no second pass.
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 #include "ptx.cuh"
@@ -26,43 +32,48 @@
 
 namespace qpadl {
 
-template <int NQ>
+template <int NQ, int CCH>
 struct StreamCfg {
+    static constexpr int kGroups = CCH / 16;                       // 16-digit groups per row chunk
+    static constexpr int kRowLanes = 32 * kStreamConsumerWarps / kGroups;
     static constexpr int kRowsPerThread = 8 / NQ;
-    static constexpr int kSpan = kStreamRowLanes * kRowsPerThread;   // rows per band span
-    static constexpr int kDbStageBytes = kSpan * kStreamChunkCols;
-    static constexpr int kQStageBytes = NQ * kStreamChunkCols * 4;
-    static constexpr int kSmemBytes = kStreamStages * (kDbStageBytes + kQStageBytes) + 256 + 1024;
+    static constexpr int kSpan = kRowLanes * kRowsPerThread;       // rows per span (= per stage)
+    static constexpr int kWarpsPerRow = kGroups / 32;
+    static constexpr int kDbStageBytes = kSpan * CCH;
+    static constexpr int kQStageBytes = NQ * CCH * 4;
+    static constexpr int kStageBytes = kDbStageBytes + kQStageBytes;
+    static constexpr int kStages = (220 * 1024) / kStageBytes > 4 ? 4 : (220 * 1024) / kStageBytes;
+    static constexpr int kRedBytes = NQ * kSpan * kWarpsPerRow * 4;
+    static constexpr int kSmemBytes = kStages * kStageBytes + kRedBytes + 256 + 1024;
+    static_assert(kGroups % 32 == 0, "a warp must cover one row lane");
+    static_assert(kStages >= 2, "need at least double buffering");
 };
 
-// byte-limb packing of the query: see the file comment
-__global__ void pack_query_kernel(const uint32_t *__restrict__ q, uint64_t q_ld, uint32_t C, uint32_t nchunks,
-                                  uint32_t *__restrict__ qpack, uint64_t pack_ld) {
+// byte-limb packing of the query: chunk c of CCH columns holds 4 planes of
+// CCH/4 words; word g of plane k = byte k of the 4 query words of columns
+// 4g..4g+3 of the chunk.  Columns >= C are packed as zero.
+__global__ void pack_query_kernel(const uint32_t *__restrict__ q, uint64_t q_ld, uint32_t C, uint32_t cch,
+                                  uint32_t nchunks, uint32_t *__restrict__ qpack, uint64_t pack_ld) {
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;   // group of 4 columns
     const uint32_t b = blockIdx.y;
-    if (g >= nchunks * (kStreamChunkCols / 4)) return;
+    const uint32_t gpc = cch / 4;                                 // groups per chunk
+    if (g >= nchunks * gpc) return;
     const uint32_t *qb = q + b * q_ld;
     const uint32_t c = 4 * g;
-    uint32_t a0 = c + 0 < C ? qb[c + 0] : 0u;
-    uint32_t a1 = c + 1 < C ? qb[c + 1] : 0u;
-    uint32_t a2 = c + 2 < C ? qb[c + 2] : 0u;
-    uint32_t a3 = c + 3 < C ? qb[c + 3] : 0u;
-    // t01 = [a.b0 b.b0 a.b1 b.b1], t23 = [c.b0 d.b0 c.b1 d.b1], ...
+    const uint32_t a0 = c + 0 < C ? qb[c + 0] : 0u;
+    const uint32_t a1 = c + 1 < C ? qb[c + 1] : 0u;
+    const uint32_t a2 = c + 2 < C ? qb[c + 2] : 0u;
+    const uint32_t a3 = c + 3 < C ? qb[c + 3] : 0u;
+    // lo01 = [a0.b0 a1.b0 a0.b1 a1.b1], lo23 likewise; hi* hold bytes 2 and 3
     const uint32_t lo01 = __byte_perm(a0, a1, 0x5140);
     const uint32_t lo23 = __byte_perm(a2, a3, 0x5140);
     const uint32_t hi01 = __byte_perm(a0, a1, 0x7362);
     const uint32_t hi23 = __byte_perm(a2, a3, 0x7362);
-    const uint32_t L0 = __byte_perm(lo01, lo23, 0x5410);
-    const uint32_t L1 = __byte_perm(lo01, lo23, 0x7632);
-    const uint32_t L2 = __byte_perm(hi01, hi23, 0x5410);
-    const uint32_t L3 = __byte_perm(hi01, hi23, 0x7632);
-    const uint32_t chunk = g / (kStreamChunkCols / 4);
-    const uint32_t gi = g % (kStreamChunkCols / 4);
-    uint32_t *dst = qpack + b * pack_ld + chunk * kStreamChunkCols + gi;
-    dst[0 * (kStreamChunkCols / 4)] = L0;
-    dst[1 * (kStreamChunkCols / 4)] = L1;
-    dst[2 * (kStreamChunkCols / 4)] = L2;
-    dst[3 * (kStreamChunkCols / 4)] = L3;
+    uint32_t *dst = qpack + b * pack_ld + (g / gpc) * cch + (g % gpc);
+    dst[0 * gpc] = __byte_perm(lo01, lo23, 0x5410);
+    dst[1 * gpc] = __byte_perm(lo01, lo23, 0x7632);
+    dst[2 * gpc] = __byte_perm(hi01, hi23, 0x5410);
+    dst[3 * gpc] = __byte_perm(hi01, hi23, 0x7632);
 }
 
 __device__ __forceinline__ bool drain_wait(uint64_t *bar, uint32_t parity) {
@@ -74,27 +85,36 @@ __device__ __forceinline__ bool drain_wait(uint64_t *bar, uint32_t parity) {
     return true;
 }
 
-template <int NQ>
+__device__ __forceinline__ void consumer_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kStreamConsumerWarps) : "memory");
+}
+
+template <int NQ, int CCH>
 __global__ void __launch_bounds__(kStreamThreads, 1)
-    stream_answer_kernel(const __grid_constant__ CUtensorMap db_map, const uint32_t *__restrict__ qpack,
-                         uint64_t pack_ld, uint32_t *__restrict__ ans, uint64_t ans_ld, uint32_t R,
-                         uint32_t nchunks, int *__restrict__ status) {
-    using Cfg = StreamCfg<NQ>;
+    stream_answer_kernel(const __grid_constant__ CUtensorMap map, int use_map, const uint8_t *__restrict__ D,
+                         uint32_t R, uint32_t C, const uint32_t *__restrict__ qpack, uint64_t pack_ld,
+                         uint32_t *__restrict__ ans, uint64_t ans_ld, int *__restrict__ status) {
+    using Cfg = StreamCfg<NQ, CCH>;
     constexpr int RPT = Cfg::kRowsPerThread;
-    constexpr int SPAN = Cfg::kSpan;
+    constexpr int SR = Cfg::kSpan;
+    constexpr int ST = Cfg::kStages;
+    constexpr int G = Cfg::kGroups;
+    constexpr int RL = Cfg::kRowLanes;
+    constexpr int WPR = Cfg::kWarpsPerRow;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *db_st = smem;                                                   // [stages][SPAN*256]
-    uint32_t *q_st = reinterpret_cast<uint32_t *>(smem + kStreamStages * Cfg::kDbStageBytes);  // [stages][NQ][256]
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStreamStages * (Cfg::kDbStageBytes + Cfg::kQStageBytes));
-    uint64_t *empty = full + kStreamStages;
-    volatile int *abort = reinterpret_cast<volatile int *>(empty + kStreamStages);
+    uint8_t *db_st = smem;                                                           // [ST][SR][CCH]
+    uint32_t *q_st = reinterpret_cast<uint32_t *>(smem + ST * Cfg::kDbStageBytes);   // [ST][NQ][CCH]
+    uint32_t *red = reinterpret_cast<uint32_t *>(smem + ST * Cfg::kStageBytes);      // [NQ][SR][WPR]
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + ST * Cfg::kStageBytes + Cfg::kRedBytes);
+    uint64_t *empty = full + ST;
+    volatile int *abort = reinterpret_cast<volatile int *>(empty + ST);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStreamStages; ++s) {
+        for (int s = 0; s < ST; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kStreamConsumerWarps);
         }
@@ -103,47 +123,50 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     }
     __syncthreads();
 
-    // this CTA's band of rows, in 8-row octets
-    const uint32_t n_oct = (R + 7) / 8;
-    const uint32_t oct0 = static_cast<uint32_t>((uint64_t)blockIdx.x * n_oct / gridDim.x);
-    const uint32_t oct1 = static_cast<uint32_t>((uint64_t)(blockIdx.x + 1) * n_oct / gridDim.x);
-    const uint32_t band_oct = oct1 - oct0;
-    const uint32_t nspan = (band_oct * 8 + SPAN - 1) / SPAN;
+    const uint32_t r0 = static_cast<uint32_t>((uint64_t)blockIdx.x * R / gridDim.x);
+    const uint32_t r1 = static_cast<uint32_t>((uint64_t)(blockIdx.x + 1) * R / gridDim.x);
+    const uint32_t band = r1 - r0;
+    const uint32_t nspan = (band + SR - 1) / SR;
+    const uint32_t nchunks = (C + CCH - 1) / CCH;
 
     if (warp == 0) {
         // ---------------- producer
         if (lane == 0) {
-            tma_prefetch_desc(&db_map);
+            if (use_map) tma_prefetch_desc(&map);
             uint32_t it = 0;
             bool ok = true;
             for (uint32_t sp = 0; sp < nspan && ok; ++sp) {
-                const uint32_t so0 = oct0 + sp * band_oct / nspan;
-                const uint32_t so1 = oct0 + (sp + 1) * band_oct / nspan;
+                const uint32_t s0 = r0 + sp * SR;
+                const uint32_t s1 = (s0 + SR < r1) ? s0 + SR : r1;
+                const uint32_t nbox = use_map ? (s1 - s0) / 8 : 0;
                 for (uint32_t c = 0; c < nchunks; ++c, ++it) {
-                    const uint32_t st = it % kStreamStages;
-                    const uint32_t ph = (it / kStreamStages) & 1u;
+                    const uint32_t st = it % ST;
+                    const uint32_t ph = (it / ST) & 1u;
                     if (!mbar_wait(&empty[st], ph ^ 1u, abort)) {
                         ok = false;
                         break;
                     }
-                    const uint32_t bytes = (so1 - so0) * 8u * kStreamChunkCols + NQ * kStreamChunkCols * 4u;
-                    mbar_arrive_expect_tx(&full[st], bytes);
+                    const uint32_t c0 = c * CCH;
+                    const uint32_t bytes = (C - c0) < (uint32_t)CCH ? (C - c0) : (uint32_t)CCH;
+                    mbar_arrive_expect_tx(&full[st],
+                                          nbox * 8u * CCH + (s1 - s0 - 8u * nbox) * bytes + NQ * CCH * 4u);
                     uint8_t *dst = db_st + st * Cfg::kDbStageBytes;
-                    for (uint32_t o = so0; o < so1; ++o)
-                        tma_load_2d(dst + (o - so0) * 8 * kStreamChunkCols, &db_map, &full[st],
-                                    static_cast<int32_t>(c * kStreamChunkCols), static_cast<int32_t>(o * 8));
-                    uint32_t *qdst = q_st + st * (Cfg::kQStageBytes / 4);
+                    for (uint32_t b = 0; b < nbox; ++b)
+                        tma_load_3d(dst + b * 8 * CCH, &map, &full[st], 0, static_cast<int32_t>(c0 / 256),
+                                    static_cast<int32_t>(s0 + 8 * b));
+                    const uint8_t *src = D + (uint64_t)s0 * C + c0;
+                    for (uint32_t r = 8 * nbox; r < s1 - s0; ++r)
+                        bulk_load(dst + r * CCH, src + (uint64_t)r * C, bytes, &full[st]);
+                    uint32_t *qdst = q_st + st * NQ * CCH;
 #pragma unroll
                     for (int b = 0; b < NQ; ++b)
-                        bulk_load(qdst + b * kStreamChunkCols, qpack + b * pack_ld + (uint64_t)c * kStreamChunkCols,
-                                  kStreamChunkCols * 4u, &full[st]);
+                        bulk_load(qdst + b * CCH, qpack + b * pack_ld + (uint64_t)c * CCH, CCH * 4u, &full[st]);
                 }
             }
             // never leave while copies issued by this thread are still landing
-            const uint32_t inflight = it < (uint32_t)kStreamStages ? it : (uint32_t)kStreamStages;
-            for (uint32_t j = it - inflight; j < it; ++j) {
-                if (!drain_wait(&full[j % kStreamStages], (j / kStreamStages) & 1u)) ok = false;
-            }
+            const uint32_t inflight = it < (uint32_t)ST ? it : (uint32_t)ST;
+            for (uint32_t j = it - inflight; j < it; ++j)
+                if (!drain_wait(&full[j % ST], (j / ST) & 1u)) ok = false;
             if (!ok) *status = kDevTimeout;
         }
         return;
@@ -151,13 +174,13 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
 
     // ---------------- consumers
     const int ct = threadIdx.x - 32;
-    const int cg = ct % kStreamColGroups;   // 16-digit column group within the chunk
-    const int rl = ct / kStreamColGroups;   // row lane
+    const int cg = ct % G;           // 16-digit column group within the chunk
+    const int rl = ct / G;           // row lane
+    const int wir = cg / 32;         // warp index within its row lane
     uint32_t it = 0;
     for (uint32_t sp = 0; sp < nspan; ++sp) {
-        const uint32_t so0 = oct0 + sp * band_oct / nspan;
-        const uint32_t so1 = oct0 + (sp + 1) * band_oct / nspan;
-        const uint32_t span_rows = (so1 - so0) * 8;
+        const uint32_t s0 = r0 + sp * SR;
+        const uint32_t span_rows = (s0 + SR < r1) ? SR : r1 - s0;
         uint32_t acc[RPT][NQ][4];
 #pragma unroll
         for (int r = 0; r < RPT; ++r)
@@ -167,26 +190,25 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                 for (int k = 0; k < 4; ++k) acc[r][b][k] = 0u;
 
         for (uint32_t c = 0; c < nchunks; ++c, ++it) {
-            const uint32_t st = it % kStreamStages;
-            const uint32_t ph = (it / kStreamStages) & 1u;
+            const uint32_t st = it % ST;
+            const uint32_t ph = (it / ST) & 1u;
             if (!mbar_wait(&full[st], ph, abort)) {
                 *status = kDevTimeout;
                 return;
             }
-            const uint32_t *qs = q_st + st * (Cfg::kQStageBytes / 4);
+            const uint32_t *qs = q_st + st * NQ * CCH;
             const uint8_t *ds = db_st + st * Cfg::kDbStageBytes + cg * 16;
 #pragma unroll
             for (int b = 0; b < NQ; ++b) {
                 uint4 L[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    L[k] = *reinterpret_cast<const uint4 *>(qs + b * kStreamChunkCols + k * (kStreamChunkCols / 4) +
-                                                            cg * 4);
+                    L[k] = *reinterpret_cast<const uint4 *>(qs + b * CCH + k * (CCH / 4) + cg * 4);
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
-                    const uint32_t row = rl + r * kStreamRowLanes;
+                    const uint32_t row = rl + r * RL;
                     if (row < span_rows) {
-                        const uint4 w = *reinterpret_cast<const uint4 *>(ds + row * kStreamChunkCols);
+                        const uint4 w = *reinterpret_cast<const uint4 *>(ds + row * CCH);
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
                             uint32_t a = acc[r][b][k];
@@ -203,26 +225,33 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
             if (lane == 0) mbar_arrive(&empty[st]);
         }
 
-        // recombine limbs, reduce over the 16 column groups of each row, store
-        const uint32_t row_base = so0 * 8;
+        // recombine limbs, reduce each row over its column groups, store
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
 #pragma unroll
             for (int b = 0; b < NQ; ++b) {
                 uint32_t v = acc[r][b][0] + (acc[r][b][1] << 8) + (acc[r][b][2] << 16) + (acc[r][b][3] << 24);
-                v += __shfl_xor_sync(0xffffffffu, v, 8, 16);
-                v += __shfl_xor_sync(0xffffffffu, v, 4, 16);
-                v += __shfl_xor_sync(0xffffffffu, v, 2, 16);
-                v += __shfl_xor_sync(0xffffffffu, v, 1, 16);
-                const uint32_t row = row_base + rl + r * kStreamRowLanes;
-                if (cg == 0 && rl + r * kStreamRowLanes < span_rows && row < R) ans[b * ans_ld + row] = v;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) red[(b * SR + rl + r * RL) * WPR + wir] = v;
             }
         }
+        consumer_sync();
+        for (int t = ct; t < NQ * SR; t += 32 * kStreamConsumerWarps) {
+            const int b = t / SR, row = t % SR;
+            if (row < (int)span_rows) {
+                uint32_t v = 0;
+#pragma unroll
+                for (int w = 0; w < WPR; ++w) v += red[t * WPR + w];
+                ans[b * ans_ld + s0 + row] = v;
+            }
+        }
+        consumer_sync();
     }
 }
 
-// Generic fallback for shapes/alignments the TMA path cannot take (C not a
-// multiple of 16, unaligned pointers): one warp per row, plain loads.
+// Generic fallback for shapes the bulk-copy path cannot take (C not a
+// multiple of 16 or an unaligned database): one warp per row, plain loads.
 __global__ void rowwise_answer_kernel(const uint8_t *__restrict__ D, uint64_t R, uint64_t C,
                                       const uint32_t *__restrict__ Q, uint64_t q_ld, uint32_t B,
                                       uint32_t *__restrict__ ans, uint64_t ans_ld) {
@@ -242,58 +271,65 @@ __global__ void rowwise_answer_kernel(const uint8_t *__restrict__ D, uint64_t R,
 }
 
 // ------------------------------------------------------------------ host side
-int stream_smem_bytes(int nq) {
-    switch (nq) {
-        case 1: return StreamCfg<1>::kSmemBytes;
-        case 2: return StreamCfg<2>::kSmemBytes;
-        case 4: return StreamCfg<4>::kSmemBytes;
-        default: return -1;
-    }
-}
-
-cudaError_t launch_pack_query(const uint32_t *q, uint64_t q_ld, uint32_t C, uint32_t nq, uint32_t *qpack,
-                              uint64_t pack_ld, cudaStream_t stream) {
-    const uint32_t nchunks = (C + kStreamChunkCols - 1) / kStreamChunkCols;
-    const uint32_t groups = nchunks * (kStreamChunkCols / 4);
-    dim3 grid((groups + 255) / 256, nq);
-    pack_query_kernel<<<grid, 256, 0, stream>>>(q, q_ld, C, nchunks, qpack, pack_ld);
-    return cudaGetLastError();
-}
-
-template <int NQ>
+template <int NQ, int CCH>
 static cudaError_t set_stream_attr() {
-    return cudaFuncSetAttribute(stream_answer_kernel<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                StreamCfg<NQ>::kSmemBytes);
+    return cudaFuncSetAttribute(stream_answer_kernel<NQ, CCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                StreamCfg<NQ, CCH>::kSmemBytes);
 }
 
 cudaError_t prepare_stream_kernels() {
     cudaError_t e;
-    if ((e = set_stream_attr<1>()) != cudaSuccess) return e;
-    if ((e = set_stream_attr<2>()) != cudaSuccess) return e;
-    return set_stream_attr<4>();
+    if ((e = set_stream_attr<1, 512>()) != cudaSuccess) return e;
+    if ((e = set_stream_attr<1, 1024>()) != cudaSuccess) return e;
+    if ((e = set_stream_attr<1, 2048>()) != cudaSuccess) return e;
+    if ((e = set_stream_attr<1, 4096>()) != cudaSuccess) return e;
+    if ((e = set_stream_attr<2, 1024>()) != cudaSuccess) return e;
+    return set_stream_attr<4, 1024>();
 }
 
-template <int NQ>
-static cudaError_t launch_stream_nq(const CUtensorMap &map, const uint32_t *qpack, uint64_t pack_ld, uint32_t *ans,
-                                    uint64_t ans_ld, uint32_t R, uint32_t C, int grid, int *status,
-                                    cudaStream_t stream) {
-    const uint32_t nchunks = (C + kStreamChunkCols - 1) / kStreamChunkCols;
-    stream_answer_kernel<NQ><<<grid, kStreamThreads, StreamCfg<NQ>::kSmemBytes, stream>>>(
-        map, qpack, pack_ld, ans, ans_ld, R, nchunks, status);
+bool stream_config_valid(int nq, int cch) {
+    if (nq == 1) return cch == 512 || cch == 1024 || cch == 2048 || cch == 4096;
+    return (nq == 2 || nq == 4) && cch == 1024;
+}
+
+cudaError_t launch_pack_query(const uint32_t *q, uint64_t q_ld, uint32_t C, uint32_t cch, uint32_t nq,
+                              uint32_t *qpack, uint64_t pack_ld, cudaStream_t stream) {
+    const uint32_t nchunks = (C + cch - 1) / cch;
+    const uint32_t groups = nchunks * (cch / 4);
+    dim3 grid((groups + 255) / 256, nq);
+    pack_query_kernel<<<grid, 256, 0, stream>>>(q, q_ld, C, cch, nchunks, qpack, pack_ld);
     return cudaGetLastError();
 }
 
-cudaError_t launch_stream_answer(int nq, const CUtensorMap &map, const uint32_t *qpack, uint64_t pack_ld,
-                                 uint32_t *ans, uint64_t ans_ld, uint32_t R, uint32_t C, int num_sms, int *status,
-                                 cudaStream_t stream) {
-    const uint32_t n_oct = (R + 7) / 8;
-    const int grid = static_cast<int>(n_oct < (uint32_t)num_sms ? n_oct : (uint32_t)num_sms);
-    switch (nq) {
-        case 1: return launch_stream_nq<1>(map, qpack, pack_ld, ans, ans_ld, R, C, grid, status, stream);
-        case 2: return launch_stream_nq<2>(map, qpack, pack_ld, ans, ans_ld, R, C, grid, status, stream);
-        case 4: return launch_stream_nq<4>(map, qpack, pack_ld, ans, ans_ld, R, C, grid, status, stream);
-        default: return cudaErrorInvalidValue;
+template <int NQ, int CCH>
+static cudaError_t launch_cfg(const CUtensorMap *map, const uint8_t *D, uint32_t R, uint32_t C,
+                              const uint32_t *qpack, uint64_t pack_ld, uint32_t *ans, uint64_t ans_ld, int grid,
+                              int *status, cudaStream_t stream) {
+    CUtensorMap m;
+    if (map) m = *map;
+    else std::memset(&m, 0, sizeof(m));
+    stream_answer_kernel<NQ, CCH><<<grid, kStreamThreads, StreamCfg<NQ, CCH>::kSmemBytes, stream>>>(
+        m, map ? 1 : 0, D, R, C, qpack, pack_ld, ans, ans_ld, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_answer(int nq, int cch, const CUtensorMap *map, const uint8_t *D, uint32_t R, uint32_t C,
+                                 const uint32_t *qpack, uint64_t pack_ld, uint32_t *ans, uint64_t ans_ld,
+                                 int num_sms, int *status, cudaStream_t stream) {
+    const int grid = static_cast<int>(R < (uint32_t)num_sms ? R : (uint32_t)num_sms);
+    if (nq == 1) {
+        switch (cch) {
+            case 512: return launch_cfg<1, 512>(map, D, R, C, qpack, pack_ld, ans, ans_ld, grid, status, stream);
+            case 1024: return launch_cfg<1, 1024>(map, D, R, C, qpack, pack_ld, ans, ans_ld, grid, status, stream);
+            case 2048: return launch_cfg<1, 2048>(map, D, R, C, qpack, pack_ld, ans, ans_ld, grid, status, stream);
+            case 4096: return launch_cfg<1, 4096>(map, D, R, C, qpack, pack_ld, ans, ans_ld, grid, status, stream);
+            default: return cudaErrorInvalidValue;
+        }
     }
+    if (cch != 1024) return cudaErrorInvalidValue;
+    if (nq == 2) return launch_cfg<2, 1024>(map, D, R, C, qpack, pack_ld, ans, ans_ld, grid, status, stream);
+    if (nq == 4) return launch_cfg<4, 1024>(map, D, R, C, qpack, pack_ld, ans, ans_ld, grid, status, stream);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_rowwise_answer(const uint8_t *D, uint64_t R, uint64_t C, const uint32_t *Q, uint64_t q_ld,

@@ -25,6 +25,8 @@ QPADL_ETIMEOUT = -4
 QPADL_EBUSY = -5
 QPADL_EAGAIN = -6
 QPADL_SETUP_TENSOR_COPY = 0x1
+QPADL_OPT_STREAM_CHUNK = 1
+QPADL_OPT_TENSOR_MIN_BATCH = 2
 
 
 class QpadlError(RuntimeError):
@@ -62,6 +64,8 @@ _SIGS = {
     "qpadl_pir_destroy": ([_P], ctypes.c_int),
     "qpadl_pir_status": ([_P], ctypes.c_int),
     "qpadl_pir_device_bytes": ([_P], ctypes.c_uint64),
+    "qpadl_pir_set_option": ([_P, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
+    "qpadl_pir_get_option": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "qpadl_pir_gen_a": ([_P, _P, _P], ctypes.c_int),
     "qpadl_pir_hint": ([_P, _P, _P, _P], ctypes.c_int),
     "qpadl_pir_query": ([_P, _P, _P, _P, ctypes.c_uint64, _P, _P], ctypes.c_int),
@@ -189,6 +193,16 @@ def qpadl_pir_status(db: Database) -> int:
 
 def qpadl_pir_device_bytes(db: Database) -> int:
     return int(load().qpadl_pir_device_bytes(db.handle))
+
+
+def qpadl_pir_set_option(db: Database, option: int, value: int):
+    _check(load().qpadl_pir_set_option(db.handle, int(option), int(value)), "qpadl_pir_set_option")
+
+
+def qpadl_pir_get_option(db: Database, option: int) -> int:
+    v = ctypes.c_int64()
+    _check(load().qpadl_pir_get_option(db.handle, int(option), ctypes.byref(v)), "qpadl_pir_get_option")
+    return int(v.value)
 
 
 def qpadl_pir_gen_a(prm: qpadl_params, A: torch.Tensor, stream=None) -> torch.Tensor:

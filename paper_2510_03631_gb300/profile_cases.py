@@ -1,0 +1,101 @@
+"""Small, self-checking launch cases for profiling one kernel at a time.
+
+    python -m paper_2510_03631_gb300.profile_cases stream --rows 8192 --cols 32768 --reps 3
+    python -m paper_2510_03631_gb300.profile_cases gemm   --rows 8192 --cols 32768 --batch 256 --reps 2
+    python -m paper_2510_03631_gb300.profile_cases hint   --rows 8192 --cols 32768 --n 1024 --reps 1
+
+Each case builds one database of the given size on cuda:0 (uniform digits,
+seed 1), runs the chosen entry point `reps` times after one warm-up call,
+prints the CUDA-event time per call and the bytes/flops it implies, and
+checks one output row against a plain host recomputation so a profile is
+never taken of a wrong kernel.  Sizes default to inputs larger than L2
+(129 MB) with a few GB on the device at most.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import inputs, pir
+
+
+def _row_check(D_row: np.ndarray, X: np.ndarray, got: np.ndarray):
+    exp = (X.astype(np.uint64) * D_row.astype(np.uint64)[None, :]).sum(axis=1) & np.uint64(0xFFFFFFFF)
+    if not np.array_equal(exp.astype(np.uint32), got):
+        raise SystemExit("profile case: output row differs from the host recomputation")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["stream", "gemm", "hint"])
+    ap.add_argument("--rows", type=int, default=8192)
+    ap.add_argument("--cols", type=int, default=32768)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--chunk", type=int, default=0, help="streaming chunk width (0 = library default)")
+    a = ap.parse_args()
+    torch.cuda.set_device(0)
+    R, C = a.rows, a.cols
+    D_np = inputs.db_digits(R, C, 256, seed=1)
+    prm = pir.params(R, C, a.n, seed=1)
+    db = pir.qpadl_pir_setup(prm, torch.from_numpy(D_np).cuda())
+    if a.chunk:
+        pir.qpadl_pir_set_option(db, pir.QPADL_OPT_STREAM_CHUNK, a.chunk)
+    res = {"case": a.case, "rows": R, "cols": C, "chunk": pir.qpadl_pir_get_option(db, pir.QPADL_OPT_STREAM_CHUNK)}
+    if a.case == "stream":
+        X_np = inputs.uniform_u32(C, seed=2, tag=inputs.TAG_MISC)
+        q = pir.from_u32(X_np)
+        ans = torch.empty(R, dtype=torch.int32, device="cuda")
+        fn = lambda: pir.qpadl_pir_answer(db, q, ans)
+        out_row = lambda: pir.as_u32(ans)[R // 2:R // 2 + 1]
+        X_chk = X_np[None, :]
+        res["alg_bytes"] = R * C + 4 * C + 4 * R
+    elif a.case == "gemm":
+        B = a.batch
+        X_np = inputs.uniform_u32(B * C, seed=3, tag=inputs.TAG_MISC).reshape(B, C)
+        Q = pir.from_u32(X_np.reshape(-1))
+        ans = torch.empty(B * R, dtype=torch.int32, device="cuda")
+        fn = lambda: pir.qpadl_pir_answer_batch(db, Q, ans, path=1)
+        out_row = lambda: pir.as_u32(ans).reshape(B, R)[:, R // 2]
+        X_chk = X_np
+        res["batch"] = B
+        res["fp16_mma_flops"] = 2 * R * C * 4 * B
+    else:
+        n = a.n
+        A = torch.empty(C * n, dtype=torch.int32, device="cuda")
+        pir.qpadl_pir_gen_a(prm, A)
+        H = torch.empty(R * n, dtype=torch.int32, device="cuda")
+        fn = lambda: pir.qpadl_pir_hint(db, A, H)
+        out_row = lambda: pir.as_u32(H).reshape(R, n)[R // 2]
+        X_chk = pir.as_u32(A).reshape(C, n).T.copy()
+        res["n"] = n
+        res["fp16_mma_flops"] = 2 * R * C * 4 * n
+    fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(a.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    if pir.qpadl_pir_status(db) != 0:
+        raise SystemExit("profile case: device status word set")
+    _row_check(D_np[R // 2], X_chk, out_row())
+    res["ms"] = times
+    ms = min(times)
+    if "alg_bytes" in res:
+        res["gbs"] = res["alg_bytes"] / (ms * 1e-3) / 1e9
+    if "fp16_mma_flops" in res:
+        res["tflops"] = res["fp16_mma_flops"] / (ms * 1e-3) / 1e12
+    print(json.dumps(res))
+    db.close()
+
+
+if __name__ == "__main__":
+    main()

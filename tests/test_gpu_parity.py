@@ -67,7 +67,7 @@ def test_gen_a_matches_oracle(C, n, seed):
     (7, 272),          # rows < box, ragged last chunk
     (1000, 1008),      # ragged rows (not /8) and columns (not /256)
     (2053, 4096),      # more octets than SMs: several per CTA
-    (4100, 512),       # > 256 rows per CTA band on small grids? (band split into spans)
+    (4100, 512),       # several spans per CTA band
     (777, 1000),       # C % 16 != 0 -> generic kernel
     (33, 5),           # tiny ragged generic
 ])
@@ -76,6 +76,27 @@ def test_answer_single(R, C):
     q = inputs.uniform_u32(C, seed=R * C, tag=inputs.TAG_MISC)
     got = _answers(db, q[None, :])
     assert np.array_equal(got[0], oracle.answer(D, q))
+
+
+@pytest.mark.parametrize("chunk", [512, 1024, 2048, 4096])
+@pytest.mark.parametrize("R,C", [
+    (1000, 1008), (153, 4096 + 16), (2, 9000 - 8),     # C % 256 != 0: per-row bulk copies
+    (640, 512), (1000, 4096), (157, 2304), (9, 33024),  # 3-D boxes, remainder rows, partial last chunk
+])
+def test_answer_single_every_chunk_width(R, C, chunk):
+    prm, D, db = _setup(R, C, seed=chunk + R)
+    pir.qpadl_pir_set_option(db, pir.QPADL_OPT_STREAM_CHUNK, chunk)
+    assert pir.qpadl_pir_get_option(db, pir.QPADL_OPT_STREAM_CHUNK) == chunk
+    q = inputs.uniform_u32(C, seed=chunk, tag=inputs.TAG_MISC)
+    assert np.array_equal(_answers(db, q[None, :])[0], oracle.answer(D, q))
+
+
+def test_options_reject_bad_values():
+    prm, D, db = _setup(64, 64, seed=1)
+    for opt, val in ((pir.QPADL_OPT_STREAM_CHUNK, 256), (pir.QPADL_OPT_STREAM_CHUNK, 3000),
+                     (pir.QPADL_OPT_TENSOR_MIN_BATCH, 0), (99, 1)):
+        with pytest.raises(pir.QpadlError):
+            pir.qpadl_pir_set_option(db, opt, val)
 
 
 def test_answer_single_many_rows_per_cta():
