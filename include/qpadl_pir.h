@@ -192,6 +192,35 @@ int qpadl_pir_answer_host(qpadl_db *db, const uint32_t *q_host, uint32_t *ans_ho
                           qpadl_stream_t stream);
 
 /*
+ * Allocation-free Response.  The paper has no counterpart: this is a
+ * deployment variant of qpadl_pir_answer for callers that cannot allocate
+ * device memory at the moment they answer - a stream being captured into a
+ * CUDA graph (allocation cannot be recorded in a capture), a runtime whose
+ * own allocator owns all device memory, or a serving loop that must not take
+ * the device-wide synchronisation that cudaMalloc/cudaFree imply.
+ *
+ * Computes ans_dev[i] = sum_j D[i][j] q_dev[j] mod 2^32 for the caller's
+ * resident database db_dev (rows x cols digits, row-major uint8) with no
+ * handle and no allocation of any kind.  Its scratch (the packed query limbs
+ * and a status word) is one fixed file-scope device array of 1 MiB + 256
+ * bytes, which every GPU that loads this library holds until process exit.
+ *  - cols > QPADL_NOALLOC_MAX_COLS returns QPADL_EINVAL (and says why on
+ *    stderr); nothing is enqueued.
+ *  - The first call on each device does a one-time host-side set-up with
+ *    that device current (resolving the array's device address, setting
+ *    kernel attributes).  Make that first call before any stream capture.
+ *  - All calls on a device share the array and it keeps the last call's
+ *    contents: calls whose work overlaps on the GPU (e.g. on two streams)
+ *    race and can return wrong answers.  Serialise them.
+ *  - Asynchronous on `stream`.  If a kernel's bounded wait runs out, ans_dev
+ *    is incomplete and the failure is recorded only in the array's status
+ *    word (cleared by the next call).
+ */
+#define QPADL_NOALLOC_MAX_COLS 262144u
+int qpadl_pir_answer_noalloc(const uint8_t *db_dev, uint64_t rows, uint64_t cols,
+                             const uint32_t *q_dev, uint32_t *ans_dev, qpadl_stream_t stream);
+
+/*
  * Recover (Def. 1, Client.BlockReconst): out_dev[i] = ((ans[i] - sum_k
  * H[i][k] s[k]) + Delta/2 mod 2^32) >> (32 - log2 p), i.e. the nearest
  * multiple of Delta, reduced mod p.  ans_dev: R uint32; H_dev: R x n;

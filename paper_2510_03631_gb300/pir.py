@@ -74,6 +74,7 @@ _SIGS = {
     "qpadl_pir_answer_batch": ([_P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
     "qpadl_pir_answer_batch_path": ([_P, _P, ctypes.c_uint32, _P, ctypes.c_int, _P], ctypes.c_int),
     "qpadl_pir_answer_host": ([_P, _P, _P, _P], ctypes.c_int),
+    "qpadl_pir_answer_noalloc": ([_P, ctypes.c_uint64, ctypes.c_uint64, _P, _P, _P], ctypes.c_int),
     "qpadl_pir_recover": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
     "qpadl_pir_recover_batch": ([_P, _P, _P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
 }
@@ -265,6 +266,15 @@ def qpadl_pir_answer_host(db: Database, q: torch.Tensor, ans: torch.Tensor, stre
     _check(load().qpadl_pir_answer_host(db.handle, _host(q, torch.int32, db.cols, "q"),
                                         _host(ans, torch.int32, db.rows, "ans"), _stream(stream)),
            "qpadl_pir_answer_host")
+    return ans
+
+
+def qpadl_pir_answer_noalloc(db: torch.Tensor, rows: int, cols: int, q: torch.Tensor, ans: torch.Tensor,
+                             stream=None) -> torch.Tensor:
+    """Allocation-free single-query Response on a caller-resident database (no handle)."""
+    _check(load().qpadl_pir_answer_noalloc(_dev(db, torch.uint8, rows * cols, "db"), rows, cols,
+                                           _dev(q, torch.int32, cols, "q"), _dev(ans, torch.int32, rows, "ans"),
+                                           _stream(stream)), "qpadl_pir_answer_noalloc")
     return ans
 
 
