@@ -102,6 +102,20 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _captured_traffic():
+    """DRAM bytes per Response launch from the committed ncu capture, or None
+    when the kernel source has changed since the counters were taken."""
+    import hashlib
+    tfile = os.path.join(ROOT, "profiles", "stream_answer_traffic.json")
+    src = os.path.join(ROOT, "paper_2510_03631_gb300", "csrc", "stream_answer.cu")
+    try:
+        rec = json.load(open(tfile))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return rec["bytes_per_launch"] if rec.get("source_sha256_16") == sha else None
+    except Exception:
+        return None
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -145,7 +159,13 @@ def cpu_oracle_sample(D, A_np, H_np, budget_s: float = 12.0, threads: int | None
                       f"{el:.1f} s"}
 
 
-def run_reference(args):
+def run_reference(args, budget_s: float = 150.0):
+    """The CPU oracle as the reference arm, on the same workload and metric.
+
+    Each step is the oracle's Query over all C columns, then Answer and
+    Recover of a row sample of the 1 GiB database; the sample size is set
+    from a calibration step so that warm-up plus timed steps fit `budget_s`.
+    """
     rank, world, _ = _dist()
     if rank != 0:
         return
@@ -153,11 +173,30 @@ def run_reference(args):
     from paper_2510_03631_gb300 import inputs
     w = inputs.WORKLOADS["single_1gib"]
     R, C, n = w["rows"], w["cols"], w["n"]
-    rows = 2048
-    D = inputs.db_digits(R, C, 256, seed=1, row_start=0, row_count=rows)
+    max_rows = 2048
+    D = inputs.db_digits(R, C, 256, seed=1, row_start=0, row_count=max_rows)
     A_np = oracle.gen_a(1, C, n)
     threads = os.cpu_count() or 1
     H_np = oracle.hint(D, A_np, threads=threads)
+
+    def one(i, rows):
+        s = inputs.secrets(1, n, seed=10 + i)[0]
+        e = inputs.noise(C, seed=20 + i)
+        col = int(inputs.target_columns(1, C, seed=30 + i)[0])
+        t0 = time.perf_counter()
+        qu = oracle.query(A_np, s, e, col, oracle.delta_for(256))
+        ans = oracle.answer(D[:rows], qu, threads=threads)
+        oracle.recover(ans, H_np[:rows], s)
+        return time.perf_counter() - t0
+
+    # calibration: fixed cost (Query) + cost per answered row
+    t_small, t_big = one(0, 64), one(1, 512)
+    per_row = max((t_big - t_small) / 448, 1e-9)
+    fixed = max(t_small - 64 * per_row, 0.0)
+    per_step_budget = budget_s / (args.steps + args.warmup)
+    rows = int((per_step_budget - fixed) / per_row) // 64 * 64
+    rows = max(64, min(max_rows, rows))
+    D_s = np.ascontiguousarray(D[:rows])
     per_step = []
     for i in range(args.warmup + args.steps):
         s = inputs.secrets(1, n, seed=10 + i)[0]
@@ -165,21 +204,22 @@ def run_reference(args):
         col = int(inputs.target_columns(1, C, seed=30 + i)[0])
         t0 = time.perf_counter()
         qu = oracle.query(A_np, s, e, col, oracle.delta_for(256))
-        ans = oracle.answer(D, qu, threads=threads)
-        oracle.recover(ans, H_np, s)
+        ans = oracle.answer(D_s, qu, threads=threads)
+        oracle.recover(ans, H_np[:rows], s)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             per_step.append(dt)
     t = sum(per_step) / len(per_step)
     gbs = rows * C / t / 1e9
+    sample = (f"per step: oracle Query over all {C} columns, Answer and Recover of {rows} of {R} rows "
+              f"(row count sized so {args.warmup}+{args.steps} steps fit ~{budget_s:.0f} s)")
     line = {
         "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": "single_1gib", "rows": R, "cols": C, "n": n, "p": 256,
-                   "sample_rows": rows, "note": "CPU oracle, bounded row sample of the 1 GiB database"},
-        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": threads, "kind": "oracle",
-                         "sample": f"Query over all {C} columns + Answer and Recover of {rows} of {R} rows per step"},
+                   "sample_rows": rows, "note": "CPU oracle on the host cores, bounded row sample"},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -227,13 +267,13 @@ def run_ours(args):
         hint_ms.append(e0.elapsed_time(e1))
 
     K, W = args.steps, args.warmup
-    T = K + W
-    S = pir.from_u32(inputs.secrets(T, n, seed=seed + 10).reshape(-1))
-    E = torch.from_numpy(inputs.noise_batch(T, C, seed=seed + 11).reshape(-1)).cuda()
-    cols_np = inputs.target_columns(T, C, seed=seed + 12)
-    q = torch.empty(T * C, dtype=torch.int32, device="cuda")
-    ans = torch.empty(T * R, dtype=torch.int32, device="cuda")
-    out = torch.empty(T * R, dtype=torch.uint8, device="cuda")
+    P = 64   # pool of distinct queries; step i uses slot i % P
+    S = pir.from_u32(inputs.secrets(P, n, seed=seed + 10).reshape(-1))
+    E = torch.from_numpy(inputs.noise_batch(P, C, seed=seed + 11).reshape(-1)).cuda()
+    cols_np = inputs.target_columns(P, C, seed=seed + 12)
+    q = torch.empty(P * C, dtype=torch.int32, device="cuda")
+    ans = torch.empty(P * R, dtype=torch.int32, device="cuda")
+    out = torch.empty(P * R, dtype=torch.uint8, device="cuda")
 
     def step(i):
         qi, ai, oi = q[i * C:(i + 1) * C], ans[i * R:(i + 1) * R], out[i * R:(i + 1) * R]
@@ -242,24 +282,53 @@ def run_ours(args):
         pir.qpadl_pir_answer(db, qi, ai)
         pir.qpadl_pir_recover(prm, ai, H, si, oi)
 
-    for i in range(W):
-        step(i)
+    def capture(fn):
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            fn()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        return g
+
+    # one graph per pool slot: the timed loop replays them, so host launch
+    # overhead does not leak into the device-side step time
+    graphs = [capture(lambda i=i: step(i)) for i in range(P)]
     torch.cuda.synchronize()
-    barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
-        time.sleep(0.3)   # let the sampler start
+        time.sleep(0.25)
+        for i in range(W):
+            graphs[i % P].replay()
+        torch.cuda.synchronize()
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
-        for i in range(W, T):
-            step(i)
+        for i in range(W, W + K):
+            graphs[i % P].replay()
         ev1.record()
         torch.cuda.synchronize()
         step_ms = ev0.elapsed_time(ev1) / K
-    barrier()
-    # correctness of what was timed: every recovered column must equal D's column
-    out_np = out.cpu().numpy().reshape(T, R)
-    ok = all(np.array_equal(out_np[i], D_np[:, cols_np[i]]) for i in range(T))
-    if not ok:
+        barrier()
+
+        # ---- the Response alone (dominant kernel), back-to-back launches on the
+        # launching stream, for the roofline
+        resp_graph = capture(lambda: pir.qpadl_pir_answer(db, q[:C], ans[:R]))
+        NR = max(50, min(2000, K))
+        for _ in range(5):
+            resp_graph.replay()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(NR):
+            resp_graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        resp_ms_avg = e0.elapsed_time(e1) / NR
+    # correctness of what was timed: every recovered record must equal D's column
+    out_np = out.cpu().numpy().reshape(P, R)
+    if not all(np.array_equal(out_np[i], D_np[:, cols_np[i]]) for i in range(P)):
         raise SystemExit("bench: recovered records differ from the database")
     if pir.qpadl_pir_status(db) != 0:
         raise SystemExit("bench: device status word set")
@@ -269,26 +338,10 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         step_ms = float(t.item())
 
-    # ---- the Response kernel alone (roofline of the dominant kernel)
-    resp_ms = []
-    for i in range(W, T):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        pir.qpadl_pir_answer(db, q[i * C:(i + 1) * C], ans[i * R:(i + 1) * R])
-        e1.record()
-        torch.cuda.synchronize()
-        resp_ms.append(e0.elapsed_time(e1))
-    resp_ms_avg = sum(resp_ms) / len(resp_ms)
     alg_bytes = R * C + 4 * C + 4 * R
     peak, peak_kind = _peaks()
     achieved = alg_bytes / (resp_ms_avg * 1e-3) / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "stream_answer_traffic.json")
-    if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = _captured_traffic()
 
     # ---- batched Response sweep vs one-at-a-time on the same database
     one_qps = 1e3 / resp_ms_avg
@@ -297,22 +350,25 @@ def run_ours(args):
         for B in (1, 8, 32, 128, 256, 1024):
             QB = torch.randint(-2**31, 2**31 - 1, (B * C,), dtype=torch.int32, device="cuda")
             AB = torch.empty(B * R, dtype=torch.int32, device="cuda")
-            for _ in range(2):
-                pir.qpadl_pir_answer_batch(db, QB, AB)
+            gB = capture(lambda: pir.qpadl_pir_answer_batch(db, QB, AB))
+            gB.replay()
             torch.cuda.synchronize()
-            reps = 5
+            reps = 10 if B <= 256 else 4
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(reps):
-                pir.qpadl_pir_answer_batch(db, QB, AB)
+                gB.replay()
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
-            sweep[str(B)] = {"ms": round(ms, 4), "queries_per_s": round(B / ms * 1e3, 1),
-                             "db_scan_gbs": round(B * R * C / (ms * 1e-3) / 1e9, 1),
-                             "tops_u32mac": round(B * R * C / (ms * 1e-3) / 1e12, 3),
-                             "x_vs_one_at_a_time": round(B / ms * 1e3 / one_qps, 2)}
-            del QB, AB
+            ent = {"ms": round(ms, 4), "queries_per_s": round(B / ms * 1e3, 1),
+                   "db_scan_gbs": round(B * R * C / (ms * 1e-3) / 1e9, 1),
+                   "x_vs_one_at_a_time": round(B / ms * 1e3 / one_qps, 2),
+                   "path": "tensor" if B >= pir.qpadl_pir_get_option(db, pir.QPADL_OPT_TENSOR_MIN_BATCH) else "stream"}
+            if ent["path"] == "tensor":
+                ent["fp16_tflops"] = round(2 * R * C * 4 * B / (ms * 1e-3) / 1e12, 1)
+            sweep[str(B)] = ent
+            del gB, QB, AB
 
     # ---- end to end through the public API with host buffers
     s_h = torch.from_numpy(inputs.secrets(1, n, seed=seed + 50).reshape(-1).view(np.int32)).pin_memory()
@@ -331,12 +387,13 @@ def run_ours(args):
         out_h.copy_(out[:R], non_blocking=True)
         torch.cuda.current_stream().synchronize()
 
+    KE = min(K, 500)
     for _ in range(W):
         e2e_step()
     t0 = time.perf_counter()
-    for _ in range(K):
+    for _ in range(KE):
         e2e_step()
-    e2e_s = (time.perf_counter() - t0) / K
+    e2e_s = (time.perf_counter() - t0) / KE
     if not np.array_equal(out_h.numpy(), D_np[:, col_e2e]):
         raise SystemExit("bench: e2e recovered record differs")
 
@@ -374,7 +431,9 @@ def run_ours(args):
         "batched": {"one_at_a_time_qps": round(one_qps, 1), "sweep": sweep},
         "hint_ms": round(min(hint_ms), 3),
         "gpu_launches": 4 * K,
+        "timing": "CUDA events around K replays of per-step CUDA graphs (64-query pool)",
         "e2e": {"value": round(R * C / e2e_s / 1e9, 2), "unit": "GB/s", "ms_per_step": round(e2e_s * 1e3, 4),
+                "steps": KE, "api": "pinned H2D (s, e) -> qpadl_pir_query -> qpadl_pir_answer -> qpadl_pir_recover -> D2H digits, synchronised each step",
                 "h2d_bytes_per_step": 4 * n + 4 * C, "d2h_bytes_per_step": R},
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
@@ -389,8 +448,8 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip the batch sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
