@@ -103,17 +103,26 @@ int qpadl_version(void);
 int qpadl_pir_setup(const qpadl_params *prm, const uint8_t *db_dev,
                     qpadl_stream_t stream, qpadl_db **out);
 
-/* Frees the handle and all library-owned device memory it holds.  Waits
- * for work the handle enqueued.  NULL is accepted. */
+/* Synchronises the device, then frees the handle and all library-owned
+ * device memory it holds.  NULL is accepted. */
 int qpadl_pir_destroy(qpadl_db *db);
 
-/* Reads (synchronously, after the handle's last stream has drained) and
- * clears the handle's device status word: QPADL_OK, or QPADL_ETIMEOUT when
- * a kernel's bounded wait ran out since the last call. */
+/* Synchronises the device, then reads and clears the handle's device
+ * status word: QPADL_OK, or QPADL_ETIMEOUT when a kernel's bounded wait ran
+ * out since the last call. */
 int qpadl_pir_status(qpadl_db *db);
 
 /* Bytes of device memory the handle currently owns (operand copy + scratch). */
 uint64_t qpadl_pir_device_bytes(const qpadl_db *db);
+
+/* Shape of a handle's database: *rows = R, *cols = C. */
+int qpadl_pir_shape(const qpadl_db *db, uint64_t *rows, uint64_t *cols);
+
+/* Pre-sizes the handle's scratch so that later Response calls with batches
+ * of up to max_batch queries allocate nothing (tensor-core operand copy of D
+ * and limb scratch when max_batch reaches the tensor-core threshold).  May
+ * call cudaMalloc; synchronises the device.  Use before a stream capture. */
+int qpadl_pir_reserve(qpadl_db *db, uint32_t max_batch, qpadl_stream_t stream);
 
 /* Sets / reads a tuning option (QPADL_OPT_*).  QPADL_EINVAL for an unknown
  * option or an unsupported value.  Host-only; enqueues nothing. */
@@ -234,6 +243,81 @@ int qpadl_pir_recover(const qpadl_params *prm, const uint32_t *ans_dev,
 int qpadl_pir_recover_batch(const qpadl_params *prm, const uint32_t *ans_dev,
                             const uint32_t *H_dev, const uint32_t *S_dev, uint32_t B,
                             uint8_t *out_dev, qpadl_stream_t stream);
+
+/* ======================================================================
+ * Serving: a continuous-batching request loop over several resident
+ * databases (the paper's server answering q-bar queries per database,
+ * Sec. 5.2, run as a long-lived service).  Requests arrive from any host
+ * thread; one loop thread forms a launch for a database whenever a launch
+ * stream is free, from up to max_batch of its queued requests (oldest
+ * database first), so new arrivals start while earlier launches are still
+ * on the GPU.  Admission is by memory: each request's query and answer live
+ * in a mapped pinned host arena of host_budget_bytes; batch buffers come
+ * from a device arena of device_budget_bytes.
+ * ==================================================================== */
+typedef struct qpadl_server qpadl_server;
+
+typedef struct qpadl_server_config {
+    uint64_t host_budget_bytes;   /* pinned host arena for queued/in-flight requests (admission) */
+    uint64_t device_budget_bytes; /* device arena for per-launch batch buffers */
+    uint32_t max_inflight;        /* requests admitted and not yet polled */
+    uint32_t max_batch;           /* requests of one database per launch (1..65535) */
+    uint32_t num_streams;         /* launches in flight at once (1..8) */
+    uint32_t test_drop_completion_launch; /* test hook: 0 = off; k = the k-th launch's completion
+                                             is not reported, so its requests run into the watchdog */
+    double hold_us;               /* a lone request may wait this long for company while other
+                                     launches run (0 = launch as soon as a stream is free) */
+    double watchdog_ms;           /* requests whose launch has not completed after this fail
+                                     with QPADL_ETIMEOUT (<= 0: 10000) */
+} qpadl_server_config;
+
+typedef struct qpadl_request_times {
+    double submit_s, launch_s, done_s; /* steady-clock seconds */
+} qpadl_request_times;
+
+typedef struct qpadl_server_stats_t {
+    uint64_t launches, completed, failed, refused;
+    uint32_t inflight, queued;
+    double mean_launch_requests;
+    uint64_t host_bytes_used, device_bytes_used;
+} qpadl_server_stats_t;
+
+/* Creates a server on the current device (allocates both arenas and the
+ * launch streams).  QPADL_EINVAL for a bad config, QPADL_ENOMEM if an arena
+ * cannot be allocated. */
+int qpadl_server_create(const qpadl_server_config *cfg, qpadl_server **out);
+
+/* Registers a database handle (before qpadl_server_start); reserves the
+ * handle's scratch for max_batch.  The handle must outlive the server. */
+int qpadl_server_add_db(qpadl_server *srv, qpadl_db *db, int *db_id);
+
+/* Starts the request loop thread. */
+int qpadl_server_start(qpadl_server *srv);
+
+/* Admits one query (C uint32 words in host memory, copied before return)
+ * for database db_id.  QPADL_EBUSY if admission refuses (in-flight limit or
+ * host arena full): retry later.  *ticket identifies the request. */
+int qpadl_server_submit(qpadl_server *srv, int db_id, const uint32_t *q_host, uint64_t *ticket);
+
+/* QPADL_EAGAIN while the request is queued or running; otherwise copies the
+ * answer (R words) to ans_host (may be NULL), fills *times (may be NULL),
+ * forgets the ticket and returns QPADL_OK, QPADL_ETIMEOUT (watchdog) or
+ * QPADL_ECUDA.  Unknown ticket: QPADL_EINVAL. */
+int qpadl_server_poll(qpadl_server *srv, uint64_t ticket, uint32_t *ans_host,
+                      qpadl_request_times *times);
+
+int qpadl_server_stats(qpadl_server *srv, qpadl_server_stats_t *st);
+
+/* Stops the loop, waits for launches in flight, frees everything. */
+int qpadl_server_destroy(qpadl_server *srv);
+
+/* Open-loop load replay: submits request i at arrival_s[i] seconds after
+ * the call starts (retrying while admission refuses), waits for all, and
+ * writes latency_s[i] = completion - scheduled arrival (-1 on failure) and
+ * status[i].  ans_host may be NULL (answers discarded). */
+int qpadl_server_replay(qpadl_server *srv, uint64_t n, const double *arrival_s,
+                        const int32_t *db_ids, const uint32_t *const *q_host,
+                        uint32_t *const *ans_host, double *latency_s, int32_t *status);
 
 #ifdef __cplusplus
 }

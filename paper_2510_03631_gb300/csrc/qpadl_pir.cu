@@ -27,7 +27,6 @@ struct qpadl_db {
     int device = 0;
     int num_sms = 0;
     int *d_status = nullptr;         // device status word (kernels' bounded waits)
-    cudaStream_t last_stream = nullptr;
     // streaming path
     bool stream_ok = false;          // C % 16 == 0 and D 16-byte aligned
     int stream_chunk = 2048;         // digits per row per stage (QPADL_OPT_STREAM_CHUNK)
@@ -171,8 +170,8 @@ int ensure_tensor_copy(qpadl_db *db, cudaStream_t stream) {
 int ensure_limbs(qpadl_db *db, uint64_t bytes) {
     if (db->limbs_bytes >= bytes) return QPADL_OK;
     if (db->limbs) {
-        // the old scratch may still be read by queued work
-        if (db->last_stream) cudaStreamSynchronize(db->last_stream);
+        // the old scratch may still be read by queued work on any stream
+        cudaDeviceSynchronize();
         dev_free(db, db->limbs, db->limbs_bytes);
         db->limbs = nullptr;
         db->limbs_bytes = 0;
@@ -271,7 +270,6 @@ int qpadl_pir_setup(const qpadl_params *prm, const uint8_t *db_dev, qpadl_stream
     db->prm = *prm;
     db->db = db_dev;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    db->last_stream = s;
     auto fail = [&](int code) {
         qpadl_pir_destroy(db);
         return code;
@@ -326,7 +324,6 @@ int qpadl_pir_destroy(qpadl_db *db) {
     int cur = -1;
     cudaGetDevice(&cur);
     if (db->device != cur) cudaSetDevice(db->device);
-    if (db->last_stream) cudaStreamSynchronize(db->last_stream);
     cudaDeviceSynchronize();
     dev_free(db, db->d_status, 16);
     dev_free(db, db->qpack, 4 * db->pack_words * 4);
@@ -342,7 +339,7 @@ int qpadl_pir_destroy(qpadl_db *db) {
 int qpadl_pir_status(qpadl_db *db) {
     if (!db) return QPADL_EINVAL;
     if (set_device(db) != QPADL_OK) return QPADL_ECUDA;
-    if (db->last_stream && cudaStreamSynchronize(db->last_stream) != cudaSuccess) return QPADL_ECUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return QPADL_ECUDA;
     int st = 0;
     if (cudaMemcpy(&st, db->d_status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return QPADL_ECUDA;
     if (st != 0) {
@@ -354,6 +351,27 @@ int qpadl_pir_status(qpadl_db *db) {
 }
 
 uint64_t qpadl_pir_device_bytes(const qpadl_db *db) { return db ? db->owned_bytes : 0; }
+
+int qpadl_pir_shape(const qpadl_db *db, uint64_t *rows, uint64_t *cols) {
+    if (!db || !rows || !cols) return QPADL_EINVAL;
+    *rows = db->prm.rows;
+    *cols = db->prm.cols;
+    return QPADL_OK;
+}
+
+int qpadl_pir_reserve(qpadl_db *db, uint32_t max_batch, qpadl_stream_t stream) {
+    if (!db || max_batch == 0) return QPADL_EINVAL;
+    if (set_device(db) != QPADL_OK) return QPADL_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (max_batch >= db->tensor_min_batch) {
+        int rc = ensure_tensor_copy(db, s);
+        if (rc != QPADL_OK) return rc;
+        rc = ensure_limbs(db, 8ull * max_batch * db->pitch);
+        if (rc != QPADL_OK) return rc;
+    }
+    QPADL_CU(cudaStreamSynchronize(s));
+    return QPADL_OK;
+}
 
 int qpadl_pir_gen_a(const qpadl_params *prm, uint32_t *A_dev, qpadl_stream_t stream) {
     int rc = validate_params(prm);
@@ -370,7 +388,6 @@ int qpadl_pir_hint(qpadl_db *db, const uint32_t *A_dev, uint32_t *H_dev, qpadl_s
     if (!db || !A_dev || !H_dev) return QPADL_EINVAL;
     if (set_device(db) != QPADL_OK) return QPADL_ECUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    db->last_stream = s;
     int rc = ensure_tensor_copy(db, s);
     if (rc != QPADL_OK) return rc;
     const uint32_t n = db->prm.n;
@@ -410,7 +427,6 @@ int qpadl_pir_answer(qpadl_db *db, const uint32_t *q_dev, uint32_t *ans_dev, qpa
     if (!db || !q_dev || !ans_dev) return QPADL_EINVAL;
     if (set_device(db) != QPADL_OK) return QPADL_ECUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    db->last_stream = s;
     return answer_streaming(db, q_dev, 1, ans_dev, s);
 }
 
@@ -419,7 +435,6 @@ int qpadl_pir_answer_batch_path(qpadl_db *db, const uint32_t *Q_dev, uint32_t B,
     if (!db || !Q_dev || !ans_dev || B == 0 || (path != 0 && path != 1)) return QPADL_EINVAL;
     if (set_device(db) != QPADL_OK) return QPADL_ECUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    db->last_stream = s;
     return path == 0 ? answer_streaming(db, Q_dev, B, ans_dev, s) : answer_tensor(db, Q_dev, B, ans_dev, s);
 }
 
@@ -457,7 +472,6 @@ int qpadl_pir_answer_host(qpadl_db *db, const uint32_t *q_host, uint32_t *ans_ho
     if (!db || !q_host || !ans_host) return QPADL_EINVAL;
     if (set_device(db) != QPADL_OK) return QPADL_ECUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    db->last_stream = s;
     const uint64_t C = db->prm.cols, R = db->prm.rows;
     QPADL_CU(cudaMemcpyAsync(db->stage_q, q_host, C * 4, cudaMemcpyHostToDevice, s));
     int rc = answer_streaming(db, db->stage_q, 1, db->stage_ans, s);

@@ -76,6 +76,16 @@ _SIGS = {
     "qpadl_pir_answer_host": ([_P, _P, _P, _P], ctypes.c_int),
     "qpadl_pir_answer_noalloc": ([_P, ctypes.c_uint64, ctypes.c_uint64, _P, _P, _P], ctypes.c_int),
     "qpadl_pir_recover": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "qpadl_pir_shape": ([_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "qpadl_pir_reserve": ([_P, ctypes.c_uint32, _P], ctypes.c_int),
+    "qpadl_server_create": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
+    "qpadl_server_add_db": ([_P, _P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "qpadl_server_start": ([_P], ctypes.c_int),
+    "qpadl_server_submit": ([_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "qpadl_server_poll": ([_P, ctypes.c_uint64, _P, _P], ctypes.c_int),
+    "qpadl_server_stats": ([_P, _P], ctypes.c_int),
+    "qpadl_server_destroy": ([_P], ctypes.c_int),
+    "qpadl_server_replay": ([_P, ctypes.c_uint64, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "qpadl_pir_recover_batch": ([_P, _P, _P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
 }
 
@@ -307,3 +317,128 @@ def from_u32(a, device="cuda") -> torch.Tensor:
     """numpy uint32 -> int32 torch tensor with the same bits."""
     import numpy as np
     return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(device)
+
+
+# ----------------------------------------------------------------------------- serving
+class qpadl_server_config(ctypes.Structure):
+    _fields_ = [
+        ("host_budget_bytes", ctypes.c_uint64),
+        ("device_budget_bytes", ctypes.c_uint64),
+        ("max_inflight", ctypes.c_uint32),
+        ("max_batch", ctypes.c_uint32),
+        ("num_streams", ctypes.c_uint32),
+        ("test_drop_completion_launch", ctypes.c_uint32),
+        ("hold_us", ctypes.c_double),
+        ("watchdog_ms", ctypes.c_double),
+    ]
+
+
+class qpadl_request_times(ctypes.Structure):
+    _fields_ = [("submit_s", ctypes.c_double), ("launch_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+
+
+class qpadl_server_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("launches", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+        ("refused", ctypes.c_uint64), ("inflight", ctypes.c_uint32), ("queued", ctypes.c_uint32),
+        ("mean_launch_requests", ctypes.c_double), ("host_bytes_used", ctypes.c_uint64),
+        ("device_bytes_used", ctypes.c_uint64),
+    ]
+
+
+def server_config(host_budget_bytes=1 << 30, device_budget_bytes=1 << 30, max_inflight=4096, max_batch=256,
+                  num_streams=4, hold_us=0.0, watchdog_ms=10000.0, test_drop_completion_launch=0):
+    return qpadl_server_config(host_budget_bytes, device_budget_bytes, max_inflight, max_batch, num_streams,
+                               test_drop_completion_launch, hold_us, watchdog_ms)
+
+
+def qpadl_pir_shape(db: Database):
+    r, c = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().qpadl_pir_shape(db.handle, ctypes.byref(r), ctypes.byref(c)), "qpadl_pir_shape")
+    return int(r.value), int(c.value)
+
+
+def qpadl_pir_reserve(db: Database, max_batch: int, stream=None):
+    _check(load().qpadl_pir_reserve(db.handle, int(max_batch), _stream(stream)), "qpadl_pir_reserve")
+
+
+class Server:
+    """Handle of a qpadl_server (keeps its databases alive)."""
+
+    def __init__(self, handle, dbs):
+        self.handle = handle
+        self.dbs = dbs
+
+    def close(self):
+        if self.handle:
+            load().qpadl_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qpadl_server_create(cfg: qpadl_server_config) -> Server:
+    h = ctypes.c_void_p()
+    _check(load().qpadl_server_create(ctypes.byref(cfg), ctypes.byref(h)), "qpadl_server_create")
+    return Server(h, [])
+
+
+def qpadl_server_add_db(srv: Server, db: Database) -> int:
+    i = ctypes.c_int()
+    _check(load().qpadl_server_add_db(srv.handle, db.handle, ctypes.byref(i)), "qpadl_server_add_db")
+    srv.dbs.append(db)
+    return int(i.value)
+
+
+def qpadl_server_start(srv: Server):
+    _check(load().qpadl_server_start(srv.handle), "qpadl_server_start")
+
+
+def qpadl_server_submit(srv: Server, db_id: int, q_host) -> int:
+    """Returns the ticket; raises QpadlError (code QPADL_EBUSY) when admission refuses.
+    q_host: numpy uint32 array (C words)."""
+    import numpy as np
+    q = np.ascontiguousarray(q_host, dtype=np.uint32)
+    t = ctypes.c_uint64()
+    _check(load().qpadl_server_submit(srv.handle, int(db_id), ctypes.c_void_p(q.ctypes.data), ctypes.byref(t)),
+           "qpadl_server_submit")
+    return int(t.value)
+
+
+def qpadl_server_poll(srv: Server, ticket: int, ans_host=None):
+    """Returns (status, times); status QPADL_EAGAIN while pending.  ans_host: numpy uint32 (R words) or None."""
+    tm = qpadl_request_times()
+    p = ctypes.c_void_p(ans_host.ctypes.data) if ans_host is not None else None
+    rc = load().qpadl_server_poll(srv.handle, ctypes.c_uint64(ticket), p, ctypes.byref(tm))
+    return int(rc), (tm.submit_s, tm.launch_s, tm.done_s)
+
+
+def qpadl_server_stats(srv: Server) -> dict:
+    st = qpadl_server_stats_t()
+    _check(load().qpadl_server_stats(srv.handle, ctypes.byref(st)), "qpadl_server_stats")
+    return {f: getattr(st, f) for f, _ in qpadl_server_stats_t._fields_}
+
+
+def qpadl_server_destroy(srv: Server):
+    srv.close()
+
+
+def qpadl_server_replay(srv: Server, arrival_s, db_ids, queries, answers=None):
+    """Open-loop replay (native): returns (latency_s, status) numpy arrays.
+    queries / answers: lists of numpy uint32 arrays (kept alive by the caller)."""
+    import numpy as np
+    n = len(arrival_s)
+    arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    ids = np.ascontiguousarray(db_ids, dtype=np.int32)
+    qp = (ctypes.c_void_p * n)(*[q.ctypes.data for q in queries])
+    ap = (ctypes.c_void_p * n)(*[a.ctypes.data for a in answers]) if answers is not None else None
+    lat = np.zeros(n, dtype=np.float64)
+    st = np.zeros(n, dtype=np.int32)
+    _check(load().qpadl_server_replay(srv.handle, n, ctypes.c_void_p(arr.ctypes.data),
+                                      ctypes.c_void_p(ids.ctypes.data), qp, ap, ctypes.c_void_p(lat.ctypes.data),
+                                      ctypes.c_void_p(st.ctypes.data)), "qpadl_server_replay")
+    return lat, st

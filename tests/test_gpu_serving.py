@@ -1,0 +1,175 @@
+"""Serving: the continuous-batching request loop over several resident
+databases gives every request the same answer it gets alone, refuses
+admission when memory or slots run out, and fails (rather than hangs)
+requests whose completion never arrives (host-side fault injection).
+"""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2510_03631_gb300 import inputs, pir
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(512, 1024), (1000, 2048), (300, 4096 + 48)]   # ragged; the last one is not a multiple of 256
+
+
+@pytest.fixture(scope="module")
+def dbs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    out = []
+    for k, (R, C) in enumerate(SHAPES):
+        D = inputs.db_digits(R, C, 256, seed=50 + k)
+        h = pir.qpadl_pir_setup(pir.params(R, C, 16, seed=50 + k), torch.from_numpy(D).cuda())
+        out.append((D, h))
+    yield out
+    for _, h in out:
+        h.close()
+
+
+def _wait(srv, ticket, R, timeout=30.0):
+    ans = np.zeros(R, dtype=np.uint32)
+    t0 = time.time()
+    while True:
+        rc, times = pir.qpadl_server_poll(srv, ticket, ans)
+        if rc != pir.QPADL_EAGAIN:
+            return rc, ans, times
+        if time.time() - t0 > timeout:
+            raise AssertionError("request did not complete")
+        time.sleep(0.0005)
+
+
+def _server(dbs, **kw):
+    srv = pir.qpadl_server_create(pir.server_config(**kw))
+    ids = [pir.qpadl_server_add_db(srv, h) for _, h in dbs]
+    pir.qpadl_server_start(srv)
+    return srv, ids
+
+
+def test_mixed_traffic_answers_equal_standalone(dbs):
+    srv, ids = _server(dbs, max_batch=64, num_streams=3)
+    rng = np.random.default_rng(7)
+    reqs = []
+    for i in range(240):
+        d = int(rng.choice(len(dbs), p=[0.6, 0.3, 0.1]))
+        C = SHAPES[d][1]
+        q = inputs.uniform_u32(C, seed=1000 + i, tag=inputs.TAG_MISC)
+        reqs.append((d, q, pir.qpadl_server_submit(srv, ids[d], q)))
+        if i % 37 == 0:
+            time.sleep(0.002)   # let launches start while more requests arrive
+    for d, q, t in reqs:
+        D, h = dbs[d]
+        rc, ans, times = _wait(srv, t, SHAPES[d][0])
+        assert rc == pir.QPADL_OK
+        # the same query answered alone, through the single-query entry point
+        alone = torch.empty(SHAPES[d][0], dtype=torch.int32, device="cuda")
+        pir.qpadl_pir_answer(h, pir.from_u32(q), alone)
+        torch.cuda.synchronize()
+        assert np.array_equal(ans, pir.as_u32(alone))
+        assert times[0] <= times[1] <= times[2]
+    st = pir.qpadl_server_stats(srv)
+    assert st["completed"] == 240 and st["failed"] == 0 and st["inflight"] == 0
+    assert st["launches"] < 240   # requests were batched
+    srv.close()
+
+
+def test_answers_match_oracle(dbs):
+    srv, ids = _server(dbs, max_batch=8, num_streams=2)
+    tickets = []
+    for d in range(len(dbs)):
+        C = SHAPES[d][1]
+        for i in range(5):
+            q = inputs.uniform_u32(C, seed=77 + 10 * d + i, tag=inputs.TAG_MISC)
+            tickets.append((d, q, pir.qpadl_server_submit(srv, ids[d], q)))
+    for d, q, t in tickets:
+        rc, ans, _ = _wait(srv, t, SHAPES[d][0])
+        assert rc == pir.QPADL_OK
+        assert np.array_equal(ans, oracle.answer(dbs[d][0], q))
+    srv.close()
+
+
+def test_admission_refuses_when_slots_run_out(dbs):
+    # a long hold keeps requests queued so the in-flight limit is reached
+    srv, ids = _server(dbs, max_inflight=4, max_batch=4, num_streams=1)
+    C = SHAPES[0][1]
+    tickets, refused = [], 0
+    for i in range(12):
+        try:
+            tickets.append(pir.qpadl_server_submit(srv, ids[0], inputs.uniform_u32(C, seed=i, tag=7)))
+        except pir.QpadlError as e:
+            assert e.code == pir.QPADL_EBUSY
+            refused += 1
+    assert len(tickets) <= 4 and refused >= 8
+    for t in tickets:
+        assert _wait(srv, t, SHAPES[0][0])[0] == pir.QPADL_OK
+    # slots free again after polling
+    t = pir.qpadl_server_submit(srv, ids[0], inputs.uniform_u32(C, seed=99, tag=7))
+    assert _wait(srv, t, SHAPES[0][0])[0] == pir.QPADL_OK
+    assert pir.qpadl_server_stats(srv)["refused"] >= 8
+    srv.close()
+
+
+def test_admission_refuses_when_host_memory_runs_out(dbs):
+    R, C = SHAPES[1]
+    per_request = 4 * (R + C) + 512
+    srv, ids = _server(dbs, host_budget_bytes=3 * per_request, max_inflight=100, num_streams=1)
+    ok, busy = [], 0
+    for i in range(10):
+        try:
+            ok.append(pir.qpadl_server_submit(srv, ids[1], inputs.uniform_u32(C, seed=i, tag=7)))
+        except pir.QpadlError as e:
+            assert e.code == pir.QPADL_EBUSY
+            busy += 1
+    assert 1 <= len(ok) <= 3 and busy >= 7
+    for t in ok:
+        assert _wait(srv, t, R)[0] == pir.QPADL_OK
+    srv.close()
+
+
+def test_bad_arguments(dbs):
+    srv, ids = _server(dbs)
+    with pytest.raises(pir.QpadlError) as e:
+        pir.qpadl_server_submit(srv, 17, np.zeros(16, np.uint32))
+    assert e.value.code == pir.QPADL_EINVAL
+    rc, _ = pir.qpadl_server_poll(srv, 123456789)
+    assert rc == pir.QPADL_EINVAL
+    srv.close()
+    with pytest.raises(pir.QpadlError):
+        pir.qpadl_server_create(pir.server_config(max_batch=0))
+
+
+def test_watchdog_fails_a_launch_whose_completion_never_arrives(dbs):
+    # host-side fault injection: the first launch's completion is dropped
+    srv, ids = _server(dbs, max_batch=4, num_streams=2, watchdog_ms=200.0, test_drop_completion_launch=1)
+    R, C = SHAPES[0]
+    t1 = pir.qpadl_server_submit(srv, ids[0], inputs.uniform_u32(C, seed=1, tag=7))
+    rc, _, _ = _wait(srv, t1, R, timeout=10)
+    assert rc == pir.QPADL_ETIMEOUT
+    # later launches are unaffected
+    q = inputs.uniform_u32(C, seed=2, tag=7)
+    t2 = pir.qpadl_server_submit(srv, ids[0], q)
+    rc, ans, _ = _wait(srv, t2, R)
+    assert rc == pir.QPADL_OK and np.array_equal(ans, oracle.answer(dbs[0][0], q))
+    assert pir.qpadl_server_stats(srv)["failed"] == 1
+    srv.close()
+
+
+def test_replay_open_loop(dbs):
+    srv, ids = _server(dbs, max_batch=64, num_streams=4)
+    n = 400
+    arr = inputs.poisson_arrivals(20000.0, n, seed=3)
+    which = inputs.skewed_choice(n, (0.6, 0.3, 0.1), seed=4)
+    queries = [inputs.uniform_u32(SHAPES[d][1], seed=500 + i, tag=7) for i, d in enumerate(which)]
+    answers = [np.zeros(SHAPES[d][0], dtype=np.uint32) for d in which]
+    lat, st = pir.qpadl_server_replay(srv, arr, [ids[d] for d in which], queries, answers)
+    assert (st == pir.QPADL_OK).all()
+    assert (lat > 0).all()
+    for i in range(0, n, 17):
+        d = which[i]
+        assert np.array_equal(answers[i], oracle.answer(dbs[d][0], queries[i]))
+    srv.close()
