@@ -225,6 +225,100 @@ def run_reference(args, budget_s: float = 150.0):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- serving
+def _pct(a, q):
+    return float(np.percentile(a, q)) if len(a) else None
+
+
+def serving_measure(torch, pir, inputs, rates, duration_s, single_db_one_ms, seed=5):
+    """Open-loop Poisson replay through the serving loop.
+
+    Part 1: the four resident spectrum databases (4096^2, 16384^2, 32768^2,
+    65536 x 32768) with a 60/25/10/5 query skew, one run per offered rate.
+    Part 2: the 1 GiB database alone, offered far above one-at-a-time
+    capacity, to compare batched serving with one-query-at-a-time.
+    Queries come from a pool of 32 distinct queries per database.
+    """
+    w = inputs.WORKLOADS["serving"]
+    shapes, skew, n_lwe = w["dbs"], w["skew"], w["n"]
+    handles, pools = [], []
+    for k, (R, C) in enumerate(shapes):
+        D = torch.from_numpy(inputs.db_digits(R, C, 256, seed=seed + k)).cuda()
+        h = pir.qpadl_pir_setup(pir.params(R, C, n_lwe, seed=seed + k, flags=pir.QPADL_SETUP_TENSOR_COPY), D)
+        handles.append(h)
+        pools.append([inputs.uniform_u32(C, seed=1000 * k + i, tag=inputs.TAG_MISC) for i in range(32)])
+    torch.cuda.synchronize()
+
+    def make_server(dbs, max_batch):
+        srv = pir.qpadl_server_create(pir.server_config(host_budget_bytes=2 << 30, device_budget_bytes=2 << 30,
+                                                        max_inflight=16384, max_batch=max_batch, num_streams=4))
+        ids = [pir.qpadl_server_add_db(srv, h) for h in dbs]
+        pir.qpadl_server_start(srv)
+        return srv, ids
+
+    # correctness in the mix: a short replay with answers kept
+    srv, ids = make_server(handles, 256)
+    n0 = 64
+    which0 = inputs.skewed_choice(n0, skew, seed=seed)
+    qs0 = [pools[d][i % 32] for i, d in enumerate(which0)]
+    ans0 = [np.zeros(shapes[d][0], dtype=np.uint32) for d in which0]
+    lat0, st0 = pir.qpadl_server_replay(srv, inputs.poisson_arrivals(2000.0, n0, seed=seed), [ids[d] for d in which0],
+                                       qs0, ans0)
+    ok = bool((st0 == 0).all())
+    for i in range(n0):
+        d = int(which0[i])
+        alone = torch.empty(shapes[d][0], dtype=torch.int32, device="cuda")
+        pir.qpadl_pir_answer(handles[d], pir.from_u32(qs0[i]), alone)
+        torch.cuda.synchronize()
+        ok = ok and np.array_equal(ans0[i], pir.as_u32(alone))
+    if not ok:
+        raise SystemExit("bench: serving answers differ from single-query answers")
+
+    runs = []
+    for rate in rates:
+        n = max(200, int(rate * duration_s))
+        arr = inputs.poisson_arrivals(float(rate), n, seed=seed + rate)
+        which = inputs.skewed_choice(n, skew, seed=seed + 2 * rate)
+        qs = [pools[d][i % 32] for i, d in enumerate(which)]
+        st_before = pir.qpadl_server_stats(srv)
+        t0 = time.perf_counter()
+        lat, st = pir.qpadl_server_replay(srv, arr, [ids[d] for d in which], qs, None)
+        wall = time.perf_counter() - t0
+        st_after = pir.qpadl_server_stats(srv)
+        good = lat[st == 0] * 1e3
+        launches = st_after["launches"] - st_before["launches"]
+        runs.append({"offered_qps": rate, "requests": n, "completed": int((st == 0).sum()),
+                     "achieved_qps": round(n / wall, 1), "p50_ms": round(_pct(good, 50), 3),
+                     "p99_ms": round(_pct(good, 99), 3), "mean_requests_per_launch": round(n / max(launches, 1), 2)})
+    srv.close()
+
+    # the 1 GiB database alone: batched serving vs one query at a time
+    srv1, ids1 = make_server([handles[2]], 1024)
+    n1 = 20000
+    arr1 = inputs.poisson_arrivals(200000.0, n1, seed=seed + 9)
+    qs1 = [pools[2][i % 32] for i in range(n1)]
+    t0 = time.perf_counter()
+    lat1, st1 = pir.qpadl_server_replay(srv1, arr1, [ids1[0]] * n1, qs1, None)
+    wall1 = time.perf_counter() - t0
+    st1s = pir.qpadl_server_stats(srv1)
+    srv1.close()
+    good1 = lat1[st1 == 0] * 1e3
+    qps1 = n1 / wall1
+    one_qps = 1e3 / single_db_one_ms
+    for h in handles:
+        h.close()
+    return {
+        "databases": [f"{R}x{C}" for R, C in shapes], "skew": list(skew), "n_lwe": n_lwe,
+        "answers_checked_in_mix": n0, "streams": 4, "max_batch": 256,
+        "rates": runs,
+        "single_1gib_saturation": {
+            "offered_qps": 200000, "requests": n1, "achieved_qps": round(qps1, 1),
+            "p50_ms": round(_pct(good1, 50), 3), "p99_ms": round(_pct(good1, 99), 3),
+            "mean_requests_per_launch": round(st1s["mean_launch_requests"], 1),
+            "one_at_a_time_qps": round(one_qps, 1), "x_vs_one_at_a_time": round(qps1 / one_qps, 2)},
+    }
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_ours(args):
     import torch
@@ -397,6 +491,14 @@ def run_ours(args):
     if not np.array_equal(out_h.numpy(), D_np[:, col_e2e]):
         raise SystemExit("bench: e2e recovered record differs")
 
+    serving = None
+    if not args.quick:
+        db.close()
+        del D
+        torch.cuda.empty_cache()
+        serving = serving_measure(torch, pir, inputs, rates=(1000, 5000, 10000, 20000, 50000),
+                                  duration_s=1.0, single_db_one_ms=resp_ms_avg)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -430,6 +532,7 @@ def run_ours(args):
                      "alg_bytes_per_launch": alg_bytes},
         "batched": {"one_at_a_time_qps": round(one_qps, 1), "sweep": sweep},
         "hint_ms": round(min(hint_ms), 3),
+        "serving": serving,
         "gpu_launches": 4 * K,
         "timing": "CUDA events around K replays of per-step CUDA graphs (64-query pool)",
         "e2e": {"value": round(R * C / e2e_s / 1e9, 2), "unit": "GB/s", "ms_per_step": round(e2e_s * 1e3, 4),
@@ -438,7 +541,8 @@ def run_ours(args):
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
-    db.close()
+    if args.quick:
+        db.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
