@@ -89,6 +89,9 @@ int qpadl_version(void);
                                         Response: 512, 1024, 2048 (default) or 4096 */
 #define QPADL_OPT_TENSOR_MIN_BATCH 2 /* smallest batch that qpadl_pir_answer_batch sends to
                                         the tensor-core GEMM (>= 1; default 3) */
+#define QPADL_OPT_STREAM_RAW 3       /* 1: a single query is packed inside the streaming kernel
+                                        (one launch, no scratch); 0 (default): a separate
+                                        packing launch first */
 
 /*
  * Setup (server side; Def. 1's server holds D).  Validates `prm`, records

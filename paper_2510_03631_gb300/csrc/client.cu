@@ -7,9 +7,12 @@
 //  Query    (Def. 1 Client.Query)      qu = A s + e + Delta * u_col   mod 2^32
 //  Recover  (Def. 1 Client.BlockReconst) d = round((ans - H s) / Delta) mod p
 //
-// Single queries are HBM-bound matrix-vector products (one warp per row of A
-// or H, the secret staged in shared memory); batches are u32 GEMMs
-// (Y = X * W^T over Z_{2^32}) on the CUDA cores with 8x8 register blocking.
+// Single queries are HBM-bound matrix-vector products: one warp per row of A
+// or H; for n in {512, 1024, 2048} each lane keeps its slice of the secret
+// in registers and issues all of a row's 16-byte loads (two rows at a time)
+// before using them; other n use a shared-memory copy of the secret.
+// Batches are u32 GEMMs (Y = X * W^T over Z_{2^32}) on the CUDA cores with
+// 8x8 register blocking.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -86,6 +89,79 @@ __global__ void matvec_kernel(const uint32_t *__restrict__ X, uint64_t rows, uin
     }
 }
 
+// Same product for n = 128 * NK: warp w owns rows [w rows / W, (w+1) rows / W).
+template <int NK, class Epi>
+__global__ void __launch_bounds__(256) matvec_reg_kernel(const uint32_t *__restrict__ X, uint64_t rows,
+                                                         const uint32_t *__restrict__ w, Epi epi) {
+    constexpr uint32_t n = 128 * NK;
+    const int lane = threadIdx.x & 31;
+    uint4 sw[NK];
+#pragma unroll
+    for (int m = 0; m < NK; ++m) sw[m] = *reinterpret_cast<const uint4 *>(w + 4 * lane + 128 * m);
+    const uint64_t W = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const uint64_t wid = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint64_t r0 = wid * rows / W, r1 = (wid + 1) * rows / W;
+    auto dot = [&](const uint4 (&a)[NK]) {
+        uint32_t acc = 0;
+#pragma unroll
+        for (int m = 0; m < NK; ++m) acc += a[m].x * sw[m].x + a[m].y * sw[m].y + a[m].z * sw[m].z + a[m].w * sw[m].w;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        return acc;
+    };
+    uint64_t i = r0;
+    for (; i + 1 < r1; i += 2) {
+        const uint4 *x0 = reinterpret_cast<const uint4 *>(X + i * n) + lane;
+        const uint4 *x1 = reinterpret_cast<const uint4 *>(X + (i + 1) * n) + lane;
+        uint4 a[NK], b[NK];
+#pragma unroll
+        for (int m = 0; m < NK; ++m) a[m] = __ldg(x0 + 32 * m);
+#pragma unroll
+        for (int m = 0; m < NK; ++m) b[m] = __ldg(x1 + 32 * m);
+        const uint32_t da = dot(a), db = dot(b);
+        if (lane == 0) {
+            epi(i, 0u, da);
+            epi(i + 1, 0u, db);
+        }
+    }
+    if (i < r1) {
+        const uint4 *x0 = reinterpret_cast<const uint4 *>(X + i * n) + lane;
+        uint4 a[NK];
+#pragma unroll
+        for (int m = 0; m < NK; ++m) a[m] = __ldg(x0 + 32 * m);
+        const uint32_t da = dot(a);
+        if (lane == 0) epi(i, 0u, da);
+    }
+}
+
+template <class Epi>
+static cudaError_t launch_matvec(const uint32_t *X, uint64_t rows, uint32_t n, const uint32_t *w, const Epi &epi,
+                                 int num_sms, cudaStream_t stream) {
+    const bool aligned = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(w)) & 15u) == 0;
+    if (aligned && (n == 512 || n == 1024 || n == 2048)) {
+        // one resident wave: blocks per SM from the kernel's occupancy
+        auto launch = [&](auto kernel) -> cudaError_t {
+            int occ = 0;
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 256, 0);
+            if (e != cudaSuccess) return e;
+            const uint64_t blocks = (uint64_t)num_sms * (occ > 0 ? occ : 1);
+            if (rows < 8 * blocks) return cudaErrorNotReady;   // too few rows: generic kernel
+            kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(X, rows, w, epi);
+            return cudaGetLastError();
+        };
+        cudaError_t e = cudaErrorNotReady;
+        if (n == 512) e = launch(matvec_reg_kernel<4, Epi>);
+        else if (n == 1024) e = launch(matvec_reg_kernel<8, Epi>);
+        else e = launch(matvec_reg_kernel<16, Epi>);
+        if (e != cudaErrorNotReady) return e;
+    }
+    const uint64_t want = (rows + 7) / 8;
+    const uint64_t cap = (uint64_t)num_sms * 8;
+    const int grid = static_cast<int>(want < cap ? (want ? want : 1) : cap);
+    matvec_kernel<Epi><<<grid, 256, n * 4u, stream>>>(X, rows, n, w, epi);
+    return cudaGetLastError();
+}
+
 // Y[i][b] = sum_k X[i][k] * W[b][k]  (mod 2^32), X: M x K, W: N x K, both
 // row-major; 128 x 128 output tile per block, 8 x 8 per thread.
 constexpr int kGT = 128, kGK = 8;
@@ -148,17 +224,10 @@ cudaError_t launch_gen_a(uint64_t seed, uint64_t C, uint32_t n, uint32_t *A, int
     return cudaGetLastError();
 }
 
-static int matvec_grid(uint64_t rows, int num_sms) {
-    const uint64_t want = (rows + 7) / 8;
-    const uint64_t cap = (uint64_t)num_sms * 8;
-    return static_cast<int>(want < cap ? (want ? want : 1) : cap);
-}
-
 cudaError_t launch_query(const uint32_t *A, uint64_t C, uint32_t n, const uint32_t *s, const int32_t *e,
                          uint64_t col, uint32_t delta, uint32_t *q, int num_sms, cudaStream_t stream) {
-    QueryEpi epi{e, 0, nullptr, col, delta, q, 0};
-    matvec_kernel<QueryEpi><<<matvec_grid(C, num_sms), 256, n * 4u, stream>>>(A, C, n, s, epi);
-    return cudaGetLastError();
+    const QueryEpi epi{e, 0, nullptr, col, delta, q, 0};
+    return launch_matvec(A, C, n, s, epi, num_sms, stream);
 }
 
 cudaError_t launch_query_batch(const uint32_t *A, uint64_t C, uint32_t n, const uint32_t *S, const int32_t *E,
@@ -171,9 +240,8 @@ cudaError_t launch_query_batch(const uint32_t *A, uint64_t C, uint32_t n, const 
 
 cudaError_t launch_recover(const uint32_t *ans, const uint32_t *H, uint64_t R, uint32_t n, const uint32_t *s,
                            uint32_t shift, uint8_t *out, int num_sms, cudaStream_t stream) {
-    RecoverEpi epi{ans, 0, shift, out, 0};
-    matvec_kernel<RecoverEpi><<<matvec_grid(R, num_sms), 256, n * 4u, stream>>>(H, R, n, s, epi);
-    return cudaGetLastError();
+    const RecoverEpi epi{ans, 0, shift, out, 0};
+    return launch_matvec(H, R, n, s, epi, num_sms, stream);
 }
 
 cudaError_t launch_recover_batch(const uint32_t *ans, const uint32_t *H, uint64_t R, uint32_t n, const uint32_t *S,

@@ -30,6 +30,7 @@ struct qpadl_db {
     // streaming path
     bool stream_ok = false;          // C % 16 == 0 and D 16-byte aligned
     int stream_chunk = 2048;         // digits per row per stage (QPADL_OPT_STREAM_CHUNK)
+    int stream_raw = 0;              // QPADL_OPT_STREAM_RAW
     uint32_t tensor_min_batch = 3;   // QPADL_OPT_TENSOR_MIN_BATCH
     bool stream_maps = false;        // C % 256 == 0: 3-D tensor maps below are valid
     CUtensorMap stream_map[4];       // box {256, cch/256, 8} for cch = 512 << i
@@ -217,6 +218,15 @@ int answer_stream_group(qpadl_db *db, const uint32_t *Q, uint32_t nq, uint32_t *
 
 int answer_streaming(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, cudaStream_t stream) {
     const uint64_t C = db->prm.cols, R = db->prm.rows;
+    if (db->stream_ok && B == 1 && db->stream_raw && aligned16(Q)) {
+        // one query: the streaming kernel packs its limbs itself (one launch, no scratch)
+        int mi = 0;
+        while ((512 << mi) < db->stream_chunk) ++mi;
+        const CUtensorMap *map = db->stream_maps ? &db->stream_map[mi] : nullptr;
+        QPADL_CU(launch_stream_answer_raw(db->stream_chunk, map, db->db, static_cast<uint32_t>(R),
+                                          static_cast<uint32_t>(C), Q, ans, db->num_sms, db->d_status, stream));
+        return QPADL_OK;
+    }
     if (!db->stream_ok) {
         QPADL_CU(launch_rowwise_answer(db->db, R, C, Q, C, B, ans, R, db->num_sms, stream));
         return QPADL_OK;
@@ -297,7 +307,8 @@ int qpadl_pir_setup(const qpadl_params *prm, const uint8_t *db_dev, qpadl_stream
             auto fn = encode_fn();
             cuuint64_t dims[3] = {256, C / 256, R};
             cuuint64_t strides[2] = {256, C};
-            cuuint32_t box[3] = {256, static_cast<cuuint32_t>((512u << i) / 256u), 8};
+            cuuint32_t box[3] = {256, static_cast<cuuint32_t>((512u << i) / 256u),
+                                 static_cast<cuuint32_t>(16384u / (512u << i))};
             cuuint32_t estr[3] = {1, 1, 1};
             if (!fn || fn(&db->stream_map[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(db_dev), dims,
                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -455,6 +466,10 @@ int qpadl_pir_set_option(qpadl_db *db, int option, int64_t value) {
             if (value < 1 || value > (1ll << 30)) return QPADL_EINVAL;
             db->tensor_min_batch = static_cast<uint32_t>(value);
             return QPADL_OK;
+        case QPADL_OPT_STREAM_RAW:
+            if (value != 0 && value != 1) return QPADL_EINVAL;
+            db->stream_raw = static_cast<int>(value);
+            return QPADL_OK;
         default: return QPADL_EINVAL;
     }
 }
@@ -464,6 +479,7 @@ int qpadl_pir_get_option(const qpadl_db *db, int option, int64_t *value) {
     switch (option) {
         case QPADL_OPT_STREAM_CHUNK: *value = db->stream_chunk; return QPADL_OK;
         case QPADL_OPT_TENSOR_MIN_BATCH: *value = db->tensor_min_batch; return QPADL_OK;
+        case QPADL_OPT_STREAM_RAW: *value = db->stream_raw; return QPADL_OK;
         default: return QPADL_EINVAL;
     }
 }

@@ -10,10 +10,10 @@
 //    SR rows.  A stage is SR rows x CCH contiguous digits per row (CCH =
 //    512..4096 bytes) in a shared-memory ring filled by one producer thread.
 //    The copy engine is limited by copy instructions rather than bytes
-//    (about 100 cycles per copy), so the producer moves 8 rows x CCH digits
-//    per instruction with a 3-D tensor map (256 digits x C/256 x R) and uses
-//    one plain bulk copy per row only for the rows left over below a
-//    multiple of 8, or when C is not a multiple of 256.
+//    (about 100 cycles per copy), so the producer moves 16 KB per
+//    instruction (16384/CCH rows x CCH digits) with a 3-D tensor map
+//    (256 digits x C/256 x R) and uses one plain bulk copy per row only for
+//    rows left over below a whole box, or when C is not a multiple of 256.
 //  - The query is pre-split into byte limbs: for each group of 4 columns,
 //    limb plane k holds byte k of the 4 query words.  A database word (4
 //    digits) times a limb word is one dp4a, so 16 digits x 4 limbs = 16 dp4a
@@ -25,27 +25,36 @@
 //    a small shared-memory step reduce each row.  No atomics, no second pass.
 #include <cstdint>
 #include <cstring>
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include "ptx.cuh"
 #include "stream_answer.cuh"
 
 namespace qpadl {
 
-template <int NQ, int CCH>
+// Where a stage's query operand comes from.
+constexpr int kQPacked = 0;   // NQ queries pre-packed into byte-limb planes (pack_query_kernel)
+constexpr int kQRaw = 1;      // one raw query (uint32 words); limbs are packed per thread
+
+template <int NQ, int CCH, int QM = kQPacked>
 struct StreamCfg {
     static constexpr int kGroups = CCH / 16;                       // 16-digit groups per row chunk
     static constexpr int kRowLanes = 32 * kStreamConsumerWarps / kGroups;
     static constexpr int kRowsPerThread = 8 / NQ;
     static constexpr int kSpan = kRowLanes * kRowsPerThread;       // rows per span (= per stage)
     static constexpr int kWarpsPerRow = kGroups / 32;
+    static constexpr int kBoxRows = 16384 / CCH;                   // every 3-D box moves 16 KB
     static constexpr int kDbStageBytes = kSpan * CCH;
+    // packed limbs of NQ queries (4 bytes per digit), or the raw secret slice (1 byte per digit)
     static constexpr int kQStageBytes = NQ * CCH * 4;
     static constexpr int kStageBytes = kDbStageBytes + kQStageBytes;
     static constexpr int kStages = (220 * 1024) / kStageBytes > 4 ? 4 : (220 * 1024) / kStageBytes;
     static constexpr int kRedBytes = NQ * kSpan * kWarpsPerRow * 4;
     static constexpr int kSmemBytes = kStages * kStageBytes + kRedBytes + 256 + 1024;
     static_assert(kGroups % 32 == 0, "a warp must cover one row lane");
+    static_assert(kSpan % kBoxRows == 0, "spans hold whole boxes");
     static_assert(kStages >= 2, "need at least double buffering");
 };
 
@@ -85,26 +94,43 @@ __device__ __forceinline__ bool drain_wait(uint64_t *bar, uint32_t parity) {
     return true;
 }
 
+// Epilogues: what happens to the finished row total v of row `row` (vector b).
+struct AnswerEpi {   // Response: store the answer word
+    uint32_t *ans;
+    uint64_t ld;
+    __device__ __forceinline__ void operator()(uint32_t row, int b, uint32_t v) const { ans[b * ld + row] = v; }
+};
 __device__ __forceinline__ void consumer_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(32 * kStreamConsumerWarps) : "memory");
 }
 
-template <int NQ, int CCH>
+// D: R rows of C digits.
+//  kQPacked: NQ packed queries (pack_ld words apart).
+//  kQRaw:    one raw query; each thread byte-permutes its 16 query words into
+//            the 4 limb words of each 4-digit group.
+// Launched with programmatic dependent launch: the kernel lets its successor
+// be scheduled at once and waits (griddepcontrol.wait) for its predecessor
+// before it reads anything the predecessor may have written.  The database
+// of a Response is immutable while bound to a handle, so the Response
+// producer issues its first stages of database loads before that wait.
+template <int NQ, int CCH, int QM, class Epi>
 __global__ void __launch_bounds__(kStreamThreads, 1)
     stream_answer_kernel(const __grid_constant__ CUtensorMap map, int use_map, const uint8_t *__restrict__ D,
-                         uint32_t R, uint32_t C, const uint32_t *__restrict__ qpack, uint64_t pack_ld,
-                         uint32_t *__restrict__ ans, uint64_t ans_ld, int *__restrict__ status) {
-    using Cfg = StreamCfg<NQ, CCH>;
+                         uint32_t R, uint32_t C, const uint32_t *__restrict__ qsrc, uint64_t pack_ld, Epi epi,
+                         int *__restrict__ status) {
+    using Cfg = StreamCfg<NQ, CCH, QM>;
+    static_assert(QM == kQPacked || NQ == 1, "the raw form serves one query");
     constexpr int RPT = Cfg::kRowsPerThread;
     constexpr int SR = Cfg::kSpan;
     constexpr int ST = Cfg::kStages;
     constexpr int G = Cfg::kGroups;
     constexpr int RL = Cfg::kRowLanes;
     constexpr int WPR = Cfg::kWarpsPerRow;
+    constexpr uint32_t BR = Cfg::kBoxRows;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *db_st = smem;                                                           // [ST][SR][CCH]
-    uint32_t *q_st = reinterpret_cast<uint32_t *>(smem + ST * Cfg::kDbStageBytes);   // [ST][NQ][CCH]
+    uint32_t *q_st = reinterpret_cast<uint32_t *>(smem + ST * Cfg::kDbStageBytes);   // [ST][kQStageBytes]
     uint32_t *red = reinterpret_cast<uint32_t *>(smem + ST * Cfg::kStageBytes);      // [NQ][SR][WPR]
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + ST * Cfg::kStageBytes + Cfg::kRedBytes);
     uint64_t *empty = full + ST;
@@ -120,6 +146,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
         }
         *abort = 0;
         fence_barrier_init();
+        griddep_launch_dependents();
     }
     __syncthreads();
 
@@ -133,12 +160,27 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
         // ---------------- producer
         if (lane == 0) {
             if (use_map) tma_prefetch_desc(&map);
+            bool waited = false;
+            uint32_t pend_st[ST], pend_c[ST], npend = 0;   // stages whose query load waits for the dependency
+            const uint32_t total = nspan * nchunks;
             uint32_t it = 0;
             bool ok = true;
+            auto load_query = [&](uint32_t st, uint32_t c) {
+                const uint32_t c0 = c * CCH;
+                const uint32_t bytes = (C - c0) < (uint32_t)CCH ? (C - c0) : (uint32_t)CCH;
+                uint32_t *qdst = q_st + st * (Cfg::kQStageBytes / 4);
+                if (QM == kQRaw) {
+                    bulk_load(qdst, qsrc + c0, bytes * 4u, &full[st]);
+                } else {
+#pragma unroll
+                    for (int b = 0; b < NQ; ++b)
+                        bulk_load(qdst + b * CCH, qsrc + b * pack_ld + (uint64_t)c * CCH, CCH * 4u, &full[st]);
+                }
+            };
             for (uint32_t sp = 0; sp < nspan && ok; ++sp) {
                 const uint32_t s0 = r0 + sp * SR;
                 const uint32_t s1 = (s0 + SR < r1) ? s0 + SR : r1;
-                const uint32_t nbox = use_map ? (s1 - s0) / 8 : 0;
+                const uint32_t nbox = use_map ? (s1 - s0) / BR : 0;
                 for (uint32_t c = 0; c < nchunks; ++c, ++it) {
                     const uint32_t st = it % ST;
                     const uint32_t ph = (it / ST) & 1u;
@@ -148,31 +190,45 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                     }
                     const uint32_t c0 = c * CCH;
                     const uint32_t bytes = (C - c0) < (uint32_t)CCH ? (C - c0) : (uint32_t)CCH;
-                    mbar_arrive_expect_tx(&full[st],
-                                          nbox * 8u * CCH + (s1 - s0 - 8u * nbox) * bytes + NQ * CCH * 4u);
+                    const uint32_t qbytes = QM == kQRaw ? bytes * 4u : NQ * CCH * 4u;
+                    mbar_arrive_expect_tx(&full[st], nbox * BR * CCH + (s1 - s0 - BR * nbox) * bytes + qbytes);
                     uint8_t *dst = db_st + st * Cfg::kDbStageBytes;
                     for (uint32_t b = 0; b < nbox; ++b)
-                        tma_load_3d(dst + b * 8 * CCH, &map, &full[st], 0, static_cast<int32_t>(c0 / 256),
-                                    static_cast<int32_t>(s0 + 8 * b));
+                        tma_load_3d(dst + b * BR * CCH, &map, &full[st], 0, static_cast<int32_t>(c0 / 256),
+                                    static_cast<int32_t>(s0 + BR * b));
                     const uint8_t *src = D + (uint64_t)s0 * C + c0;
-                    for (uint32_t r = 8 * nbox; r < s1 - s0; ++r)
+                    for (uint32_t r = BR * nbox; r < s1 - s0; ++r)
                         bulk_load(dst + r * CCH, src + (uint64_t)r * C, bytes, &full[st]);
-                    uint32_t *qdst = q_st + st * NQ * CCH;
-#pragma unroll
-                    for (int b = 0; b < NQ; ++b)
-                        bulk_load(qdst + b * CCH, qpack + b * pack_ld + (uint64_t)c * CCH, CCH * 4u, &full[st]);
+                    if (waited) {
+                        load_query(st, c);
+                    } else {
+                        pend_st[npend] = st;
+                        pend_c[npend] = c;
+                        ++npend;
+                        if (npend == (uint32_t)ST || it + 1 == total) {
+                            griddep_wait();
+                            waited = true;
+                            for (uint32_t j = 0; j < npend; ++j) load_query(pend_st[j], pend_c[j]);
+                            npend = 0;
+                        }
+                    }
                 }
+            }
+            if (!waited) {   // aborted before the first query loads: their stages are owed bytes
+                griddep_wait();
+                for (uint32_t j = 0; j < npend; ++j) load_query(pend_st[j], pend_c[j]);
             }
             // never leave while copies issued by this thread are still landing
             const uint32_t inflight = it < (uint32_t)ST ? it : (uint32_t)ST;
             for (uint32_t j = it - inflight; j < it; ++j)
                 if (!drain_wait(&full[j % ST], (j / ST) & 1u)) ok = false;
-            if (!ok) *status = kDevTimeout;
+            if (!ok && status) *status = kDevTimeout;
         }
         return;
     }
 
     // ---------------- consumers
+    griddep_wait();
     const int ct = threadIdx.x - 32;
     const int cg = ct % G;           // 16-digit column group within the chunk
     const int rl = ct / G;           // row lane
@@ -193,17 +249,39 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
             const uint32_t st = it % ST;
             const uint32_t ph = (it / ST) & 1u;
             if (!mbar_wait(&full[st], ph, abort)) {
-                *status = kDevTimeout;
+                if (status) *status = kDevTimeout;
                 return;
             }
-            const uint32_t *qs = q_st + st * NQ * CCH;
+            const uint32_t *qs = q_st + st * (Cfg::kQStageBytes / 4);
             const uint8_t *ds = db_st + st * Cfg::kDbStageBytes + cg * 16;
 #pragma unroll
             for (int b = 0; b < NQ; ++b) {
                 uint4 L[4];
+                if (QM == kQRaw) {
+                    // 16 query words of this thread's digits -> limb word k of each 4-digit group
+                    // (groups past column C hold stale words: use zero limbs there)
+                    const bool valid = c * CCH + cg * 16 < C;
+                    uint32_t l[4][4];   // [group][limb]
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    L[k] = *reinterpret_cast<const uint4 *>(qs + b * CCH + k * (CCH / 4) + cg * 4);
+                    for (int i = 0; i < 4; ++i) {
+                        uint4 a = make_uint4(0u, 0u, 0u, 0u);
+                        if (valid) a = *reinterpret_cast<const uint4 *>(qs + cg * 16 + 4 * i);
+                        const uint32_t lo01 = __byte_perm(a.x, a.y, 0x5140);
+                        const uint32_t lo23 = __byte_perm(a.z, a.w, 0x5140);
+                        const uint32_t hi01 = __byte_perm(a.x, a.y, 0x7362);
+                        const uint32_t hi23 = __byte_perm(a.z, a.w, 0x7362);
+                        l[i][0] = __byte_perm(lo01, lo23, 0x5410);
+                        l[i][1] = __byte_perm(lo01, lo23, 0x7632);
+                        l[i][2] = __byte_perm(hi01, hi23, 0x5410);
+                        l[i][3] = __byte_perm(hi01, hi23, 0x7632);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) L[k] = make_uint4(l[0][k], l[1][k], l[2][k], l[3][k]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        L[k] = *reinterpret_cast<const uint4 *>(qs + b * CCH + k * (CCH / 4) + cg * 4);
+                }
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
                     const uint32_t row = rl + r * RL;
@@ -233,9 +311,16 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                 uint32_t v = acc[r][b][0] + (acc[r][b][1] << 8) + (acc[r][b][2] << 16) + (acc[r][b][3] << 24);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) red[(b * SR + rl + r * RL) * WPR + wir] = v;
+                if (WPR == 1) {
+                    // one warp covers the whole chunk: the row total is complete
+                    const uint32_t row = rl + r * RL;
+                    if (lane == 0 && row < span_rows) epi(s0 + row, b, v);
+                } else if (lane == 0) {
+                    red[(b * SR + rl + r * RL) * WPR + wir] = v;
+                }
             }
         }
+        if (WPR == 1) continue;
         consumer_sync();
         for (int t = ct; t < NQ * SR; t += 32 * kStreamConsumerWarps) {
             const int b = t / SR, row = t % SR;
@@ -243,7 +328,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                 uint32_t v = 0;
 #pragma unroll
                 for (int w = 0; w < WPR; ++w) v += red[t * WPR + w];
-                ans[b * ans_ld + s0 + row] = v;
+                epi(s0 + row, b, v);
             }
         }
         consumer_sync();
@@ -271,20 +356,24 @@ __global__ void rowwise_answer_kernel(const uint8_t *__restrict__ D, uint64_t R,
 }
 
 // ------------------------------------------------------------------ host side
-template <int NQ, int CCH>
+template <int NQ, int CCH, int QM, class Epi>
 static cudaError_t set_stream_attr() {
-    return cudaFuncSetAttribute(stream_answer_kernel<NQ, CCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                StreamCfg<NQ, CCH>::kSmemBytes);
+    return cudaFuncSetAttribute(stream_answer_kernel<NQ, CCH, QM, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                StreamCfg<NQ, CCH, QM>::kSmemBytes);
 }
 
 cudaError_t prepare_stream_kernels() {
     cudaError_t e;
-    if ((e = set_stream_attr<1, 512>()) != cudaSuccess) return e;
-    if ((e = set_stream_attr<1, 1024>()) != cudaSuccess) return e;
-    if ((e = set_stream_attr<1, 2048>()) != cudaSuccess) return e;
-    if ((e = set_stream_attr<1, 4096>()) != cudaSuccess) return e;
-    if ((e = set_stream_attr<2, 1024>()) != cudaSuccess) return e;
-    return set_stream_attr<4, 1024>();
+    if ((e = set_stream_attr<1, 512, kQPacked, AnswerEpi>()) != cudaSuccess) return e;
+    if ((e = set_stream_attr<1, 1024, kQPacked, AnswerEpi>()) != cudaSuccess) return e;
+    if ((e = set_stream_attr<1, 2048, kQPacked, AnswerEpi>()) != cudaSuccess) return e;
+    if ((e = set_stream_attr<1, 4096, kQPacked, AnswerEpi>()) != cudaSuccess) return e;
+    if ((e = set_stream_attr<2, 1024, kQPacked, AnswerEpi>()) != cudaSuccess) return e;
+    if ((e = set_stream_attr<4, 1024, kQPacked, AnswerEpi>()) != cudaSuccess) return e;
+    if ((e = set_stream_attr<1, 512, kQRaw, AnswerEpi>()) != cudaSuccess) return e;
+    if ((e = set_stream_attr<1, 1024, kQRaw, AnswerEpi>()) != cudaSuccess) return e;
+    if ((e = set_stream_attr<1, 2048, kQRaw, AnswerEpi>()) != cudaSuccess) return e;
+    return set_stream_attr<1, 4096, kQRaw, AnswerEpi>();
 }
 
 bool stream_config_valid(int nq, int cch) {
@@ -301,35 +390,62 @@ cudaError_t launch_pack_query(const uint32_t *q, uint64_t q_ld, uint32_t C, uint
     return cudaGetLastError();
 }
 
-template <int NQ, int CCH>
+// Launch with programmatic dependent launch allowed (see the kernel comment).
+template <int NQ, int CCH, int QM, class Epi>
 static cudaError_t launch_cfg(const CUtensorMap *map, const uint8_t *D, uint32_t R, uint32_t C,
-                              const uint32_t *qpack, uint64_t pack_ld, uint32_t *ans, uint64_t ans_ld, int grid,
-                              int *status, cudaStream_t stream) {
+                              const uint32_t *qsrc, uint64_t pack_ld, const Epi &epi, int grid, int *status,
+                              cudaStream_t stream) {
     CUtensorMap m;
     if (map) m = *map;
     else std::memset(&m, 0, sizeof(m));
-    stream_answer_kernel<NQ, CCH><<<grid, kStreamThreads, StreamCfg<NQ, CCH>::kSmemBytes, stream>>>(
-        m, map ? 1 : 0, D, R, C, qpack, pack_ld, ans, ans_ld, status);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kStreamThreads);
+    cfg.dynamicSmemBytes = StreamCfg<NQ, CCH, QM>::kSmemBytes;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, stream_answer_kernel<NQ, CCH, QM, Epi>, m, map ? 1 : 0, D, R, C, qsrc, pack_ld,
+                              epi, status);
 }
+
+static int stream_grid(uint32_t R, int num_sms) { return static_cast<int>(R < (uint32_t)num_sms ? R : (uint32_t)num_sms); }
 
 cudaError_t launch_stream_answer(int nq, int cch, const CUtensorMap *map, const uint8_t *D, uint32_t R, uint32_t C,
                                  const uint32_t *qpack, uint64_t pack_ld, uint32_t *ans, uint64_t ans_ld,
                                  int num_sms, int *status, cudaStream_t stream) {
-    const int grid = static_cast<int>(R < (uint32_t)num_sms ? R : (uint32_t)num_sms);
+    const int grid = stream_grid(R, num_sms);
+    const AnswerEpi epi{ans, ans_ld};
     if (nq == 1) {
         switch (cch) {
-            case 512: return launch_cfg<1, 512>(map, D, R, C, qpack, pack_ld, ans, ans_ld, grid, status, stream);
-            case 1024: return launch_cfg<1, 1024>(map, D, R, C, qpack, pack_ld, ans, ans_ld, grid, status, stream);
-            case 2048: return launch_cfg<1, 2048>(map, D, R, C, qpack, pack_ld, ans, ans_ld, grid, status, stream);
-            case 4096: return launch_cfg<1, 4096>(map, D, R, C, qpack, pack_ld, ans, ans_ld, grid, status, stream);
+            case 512: return launch_cfg<1, 512, kQPacked>(map, D, R, C, qpack, pack_ld, epi, grid, status, stream);
+            case 1024: return launch_cfg<1, 1024, kQPacked>(map, D, R, C, qpack, pack_ld, epi, grid, status, stream);
+            case 2048: return launch_cfg<1, 2048, kQPacked>(map, D, R, C, qpack, pack_ld, epi, grid, status, stream);
+            case 4096: return launch_cfg<1, 4096, kQPacked>(map, D, R, C, qpack, pack_ld, epi, grid, status, stream);
             default: return cudaErrorInvalidValue;
         }
     }
     if (cch != 1024) return cudaErrorInvalidValue;
-    if (nq == 2) return launch_cfg<2, 1024>(map, D, R, C, qpack, pack_ld, ans, ans_ld, grid, status, stream);
-    if (nq == 4) return launch_cfg<4, 1024>(map, D, R, C, qpack, pack_ld, ans, ans_ld, grid, status, stream);
+    if (nq == 2) return launch_cfg<2, 1024, kQPacked>(map, D, R, C, qpack, pack_ld, epi, grid, status, stream);
+    if (nq == 4) return launch_cfg<4, 1024, kQPacked>(map, D, R, C, qpack, pack_ld, epi, grid, status, stream);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_stream_answer_raw(int cch, const CUtensorMap *map, const uint8_t *D, uint32_t R, uint32_t C,
+                                     const uint32_t *q, uint32_t *ans, int num_sms, int *status,
+                                     cudaStream_t stream) {
+    const int grid = stream_grid(R, num_sms);
+    const AnswerEpi epi{ans, 0};
+    switch (cch) {
+        case 512: return launch_cfg<1, 512, kQRaw>(map, D, R, C, q, 0, epi, grid, status, stream);
+        case 1024: return launch_cfg<1, 1024, kQRaw>(map, D, R, C, q, 0, epi, grid, status, stream);
+        case 2048: return launch_cfg<1, 2048, kQRaw>(map, D, R, C, q, 0, epi, grid, status, stream);
+        case 4096: return launch_cfg<1, 4096, kQRaw>(map, D, R, C, q, 0, epi, grid, status, stream);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_rowwise_answer(const uint8_t *D, uint64_t R, uint64_t C, const uint32_t *Q, uint64_t q_ld,

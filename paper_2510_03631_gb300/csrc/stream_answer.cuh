@@ -29,6 +29,12 @@ cudaError_t launch_stream_answer(int nq, int cch, const CUtensorMap *map, const 
                                  const uint32_t *qpack, uint64_t pack_ld, uint32_t *ans, uint64_t ans_ld,
                                  int num_sms, int *status, cudaStream_t stream);
 
+// One query, raw (no packing pass): the kernel packs the query limbs itself.
+// q must be 16-byte aligned.  Answer to ans[i].
+cudaError_t launch_stream_answer_raw(int cch, const CUtensorMap *map, const uint8_t *D, uint32_t R, uint32_t C,
+                                     const uint32_t *q, uint32_t *ans, int num_sms, int *status,
+                                     cudaStream_t stream);
+
 cudaError_t launch_rowwise_answer(const uint8_t *D, uint64_t R, uint64_t C, const uint32_t *Q, uint64_t q_ld,
                                   uint32_t B, uint32_t *ans, uint64_t ans_ld, int num_sms, cudaStream_t stream);
 

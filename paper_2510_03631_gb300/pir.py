@@ -27,6 +27,7 @@ QPADL_EAGAIN = -6
 QPADL_SETUP_TENSOR_COPY = 0x1
 QPADL_OPT_STREAM_CHUNK = 1
 QPADL_OPT_TENSOR_MIN_BATCH = 2
+QPADL_OPT_STREAM_RAW = 3
 
 
 class QpadlError(RuntimeError):

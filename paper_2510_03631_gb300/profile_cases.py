@@ -30,13 +30,14 @@ def _row_check(D_row: np.ndarray, X: np.ndarray, got: np.ndarray):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["stream", "gemm", "hint"])
+    ap.add_argument("case", choices=["stream", "gemm", "hint", "query", "recover"])
     ap.add_argument("--rows", type=int, default=8192)
     ap.add_argument("--cols", type=int, default=32768)
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--chunk", type=int, default=0, help="streaming chunk width (0 = library default)")
+    ap.add_argument("--raw", type=int, default=-1, help="1: single query packed inside the kernel")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     R, C = a.rows, a.cols
@@ -45,6 +46,8 @@ def main():
     db = pir.qpadl_pir_setup(prm, torch.from_numpy(D_np).cuda())
     if a.chunk:
         pir.qpadl_pir_set_option(db, pir.QPADL_OPT_STREAM_CHUNK, a.chunk)
+    if a.raw >= 0:
+        pir.qpadl_pir_set_option(db, pir.QPADL_OPT_STREAM_RAW, a.raw)
     res = {"case": a.case, "rows": R, "cols": C, "chunk": pir.qpadl_pir_get_option(db, pir.QPADL_OPT_STREAM_CHUNK)}
     if a.case == "stream":
         X_np = inputs.uniform_u32(C, seed=2, tag=inputs.TAG_MISC)
@@ -64,6 +67,25 @@ def main():
         X_chk = X_np
         res["batch"] = B
         res["fp16_mma_flops"] = 2 * R * C * 4 * B
+    elif a.case in ("query", "recover"):
+        # Query over A (C x n) or Recover over H (R x n): rows of a uint32 matrix against the secret
+        n = a.n
+        rows = C if a.case == "query" else R
+        X = torch.empty(rows * n, dtype=torch.int32, device="cuda")
+        pir.qpadl_pir_gen_a(pir.params(R, rows, n, seed=3), X)
+        s_np = inputs.secrets(1, n, seed=4)[0]
+        s_t = pir.from_u32(s_np)
+        if a.case == "query":
+            e = torch.from_numpy(inputs.noise(rows, seed=5)).cuda()
+            q = torch.empty(rows, dtype=torch.int32, device="cuda")
+            fn = lambda: pir.qpadl_pir_query(prm, X, s_t, e, 7, q)
+        else:
+            ans = pir.from_u32(inputs.uniform_u32(rows, seed=6, tag=inputs.TAG_MISC))
+            out = torch.empty(rows, dtype=torch.uint8, device="cuda")
+            fn = lambda: pir.qpadl_pir_recover(pir.params(rows, C, n), ans, X, s_t, out)
+        out_row = None
+        res["alg_bytes"] = rows * n * 4 + 4 * n + 8 * rows
+        res["n"] = n
     else:
         n = a.n
         A = torch.empty(C * n, dtype=torch.int32, device="cuda")
@@ -86,7 +108,8 @@ def main():
         times.append(e0.elapsed_time(e1))
     if pir.qpadl_pir_status(db) != 0:
         raise SystemExit("profile case: device status word set")
-    _row_check(D_np[R // 2], X_chk, out_row())
+    if out_row is not None:
+        _row_check(D_np[R // 2], X_chk, out_row())
     res["ms"] = times
     ms = min(times)
     if "alg_bytes" in res:

@@ -82,13 +82,17 @@ def test_answer_single(R, C):
 @pytest.mark.parametrize("R,C", [
     (1000, 1008), (153, 4096 + 16), (2, 9000 - 8),     # C % 256 != 0: per-row bulk copies
     (640, 512), (1000, 4096), (157, 2304), (9, 33024),  # 3-D boxes, remainder rows, partial last chunk
+    (300, 2048 + 48), (17, 4096 + 4080),                 # partial last chunk by row copies
 ])
 def test_answer_single_every_chunk_width(R, C, chunk):
     prm, D, db = _setup(R, C, seed=chunk + R)
     pir.qpadl_pir_set_option(db, pir.QPADL_OPT_STREAM_CHUNK, chunk)
     assert pir.qpadl_pir_get_option(db, pir.QPADL_OPT_STREAM_CHUNK) == chunk
     q = inputs.uniform_u32(C, seed=chunk, tag=inputs.TAG_MISC)
-    assert np.array_equal(_answers(db, q[None, :])[0], oracle.answer(D, q))
+    exp = oracle.answer(D, q)
+    for raw in (0, 1):
+        pir.qpadl_pir_set_option(db, pir.QPADL_OPT_STREAM_RAW, raw)
+        assert np.array_equal(_answers(db, q[None, :])[0], exp), f"raw={raw}"
 
 
 def test_options_reject_bad_values():
@@ -211,6 +215,29 @@ def test_query_single_and_batch(C, n):
     exp = np.stack([oracle.query(A_o, S_o[b], E_o[b], int(cols[b]), 1 << 24) for b in range(B)])
     assert np.array_equal(pir.as_u32(q), exp[0])
     assert np.array_equal(pir.as_u32(Q).reshape(B, C), exp)
+
+
+@pytest.mark.parametrize("C,n", [(1000, 128), (777, 132), (4096, 1024), (1, 256), (300, 4000), (9000, 512),
+                                 (5000, 2048), (4867, 1024)])
+def test_query_and_recover_matvec_shapes(C, n):
+    # n in {512, 1024, 2048} with enough rows takes the register-resident kernel; others the generic one
+    prm = pir.params(C, C, n, seed=n + C)
+    A = torch.empty(C * n, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_gen_a(prm, A)
+    A_o = oracle.gen_a(n + C, C, n)
+    s_o = inputs.secrets(1, n, seed=C)[0]
+    e_o = inputs.noise(C, seed=n)
+    col = C // 3
+    q = torch.empty(C, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_query(prm, A, pir.from_u32(s_o), torch.from_numpy(e_o).cuda(), col, q)
+    torch.cuda.synchronize()
+    assert np.array_equal(pir.as_u32(q), oracle.query(A_o, s_o, e_o, col, 1 << 24))
+    # Recover over H = A (any R x n matrix) with arbitrary answers
+    ans_o = inputs.uniform_u32(C, seed=3, tag=inputs.TAG_MISC)
+    out = torch.empty(C, dtype=torch.uint8, device="cuda")
+    pir.qpadl_pir_recover(prm, pir.from_u32(ans_o), A, pir.from_u32(s_o), out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), oracle.recover(ans_o, A_o, s_o))
 
 
 @pytest.mark.parametrize("p", [256, 16, 2])
