@@ -92,6 +92,9 @@ int qpadl_version(void);
 #define QPADL_OPT_STREAM_RAW 3       /* 1: a single query is packed inside the streaming kernel
                                         (one launch, no scratch); 0 (default): a separate
                                         packing launch first */
+#define QPADL_OPT_U8_MAX_BATCH 4     /* batches of up to this many queries (0..32, default 32)
+                                        run the tensor-core GEMM on the uint8 digits as stored;
+                                        larger ones use the handle's fp16 operand copy */
 
 /*
  * Setup (server side; Def. 1's server holds D).  Validates `prm`, records
@@ -183,9 +186,10 @@ int qpadl_pir_answer(qpadl_db *db, const uint32_t *q_dev, uint32_t *ans_dev,
  * ans_dev[b*R + i] = sum_j D[i][j] Q[b*C + j] mod 2^32.  Q_dev: B x C
  * (query b in row b); ans_dev: B x R (answer b in row b).  B >= 1.
  * Small B runs the streaming kernel; larger B the exact byte-limb
- * tensor-core GEMM (which allocates the handle's operand copy of D on first
- * use and a library-owned limb scratch of 8 * B * roundup(C, 8) bytes, kept
- * and grown as needed).
+ * tensor-core GEMM: on the uint8 digits as stored for B <= 32
+ * (QPADL_OPT_U8_MAX_BATCH), otherwise on the handle's fp16 operand copy of D
+ * (allocated on first use).  Both use a library-owned limb scratch of
+ * 8 * B * roundup(C, 8) bytes, kept and grown as needed.
  */
 int qpadl_pir_answer_batch(qpadl_db *db, const uint32_t *Q_dev, uint32_t B,
                            uint32_t *ans_dev, qpadl_stream_t stream);

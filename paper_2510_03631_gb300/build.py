@@ -19,7 +19,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqpadl_pir.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["qpadl_pir.cu", "stream_answer.cu", "limb_gemm.cu", "client.cu", "noalloc.cu", "server.cu"]
+SOURCES = ["qpadl_pir.cu", "stream_answer.cu", "limb_gemm.cu", "limb_gemm_u8.cu", "client.cu", "noalloc.cu",
+           "server.cu"]
 
 
 def _nvcc() -> str:

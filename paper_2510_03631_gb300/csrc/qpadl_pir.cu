@@ -16,6 +16,7 @@
 
 #include "client.cuh"
 #include "limb_gemm.cuh"
+#include "limb_gemm_u8.cuh"
 #include "qpadl_pir.h"
 #include "stream_answer.cuh"
 
@@ -36,7 +37,10 @@ struct qpadl_db {
     CUtensorMap stream_map[4];       // box {256, cch/256, 8} for cch = 512 << i
     uint32_t *qpack = nullptr;       // packed limbs of up to 4 queries
     uint64_t pack_words = 0;         // per query
-    // tensor-core path
+    // tensor-core paths
+    bool u8_ok = false;              // digits can feed the u8 GEMM directly (C % 16 == 0, aligned)
+    CUtensorMap u8_map;              // uint8 digits, box {64, 128}
+    uint32_t u8_max_batch = 32;      // QPADL_OPT_U8_MAX_BATCH
     __half *d16 = nullptr;           // digits as fp16, R x pitch
     uint64_t pitch = 0;              // roundup(C, 8)
     CUtensorMap a_map;
@@ -102,6 +106,7 @@ int prepare_device(int dev) {
     if (prepared[dev]) return QPADL_OK;
     QPADL_CU(prepare_stream_kernels());
     QPADL_CU(prepare_limb_gemm_kernels());
+    QPADL_CU(prepare_limb_gemm_u8_kernels());
     QPADL_CU(prepare_client_kernels());
     prepared[dev] = true;
     return QPADL_OK;
@@ -157,7 +162,6 @@ void dev_free(qpadl_db *db, void *p, uint64_t bytes) {
 int ensure_tensor_copy(qpadl_db *db, cudaStream_t stream) {
     if (db->d16) return QPADL_OK;
     const uint64_t R = db->prm.rows, C = db->prm.cols;
-    db->pitch = (C + 7) / 8 * 8;
     const uint64_t bytes = R * db->pitch * 2;
     int rc = dev_alloc(db, reinterpret_cast<void **>(&db->d16), bytes);
     if (rc != QPADL_OK) return rc;
@@ -242,7 +246,36 @@ int answer_streaming(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans,
     return QPADL_OK;
 }
 
+// Batched answer on the u8 GEMM (digits read as stored): one group.
+int answer_tensor_u8(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, cudaStream_t stream) {
+    int rc = ensure_limbs(db, 8ull * B * db->pitch);
+    if (rc != QPADL_OK) return rc;
+    const uint64_t R = db->prm.rows, C = db->prm.cols;
+    QPADL_CU(launch_vec_limbs(Q, C, B, C, db->limbs, db->pitch, db->num_sms, stream));
+    const int bn = limb_gemm_bn_for(B);
+    GroupedGemmArgs args;
+    std::memset(&args, 0, sizeof(args));
+    args.a[0] = db->u8_map;
+    if (!encode_2d(&args.b[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, db->limbs, C, 4ull * B, db->pitch * 2, kLimbBoxK,
+                   static_cast<uint32_t>(bn), CU_TENSOR_MAP_SWIZZLE_128B))
+        return QPADL_ECUDA;
+    GroupDesc &g = args.g[0];
+    g.out = ans;
+    g.ld_m = 1;
+    g.ld_b = R;
+    g.M = static_cast<uint32_t>(R);
+    g.NV = B;
+    g.KB = static_cast<uint32_t>((C + kLimbBoxK - 1) / kLimbBoxK);
+    g.tile_begin = 0;
+    g.n_tiles = (4 * B + bn - 1) / bn;
+    args.ngroups = 1;
+    args.total_tiles = static_cast<uint32_t>((R + kLimbBoxM - 1) / kLimbBoxM) * g.n_tiles;
+    QPADL_CU(launch_limb_gemm_u8(bn, args, db->num_sms, db->d_status, stream));
+    return QPADL_OK;
+}
+
 int answer_tensor(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, cudaStream_t stream) {
+    if (db->u8_ok && B <= db->u8_max_batch && 4 * B <= 128) return answer_tensor_u8(db, Q, B, ans, stream);
     int rc = ensure_tensor_copy(db, stream);
     if (rc != QPADL_OK) return rc;
     rc = ensure_limbs(db, 8ull * B * db->pitch);
@@ -316,6 +349,11 @@ int qpadl_pir_setup(const qpadl_params *prm, const uint8_t *db_dev, qpadl_stream
                 return fail(QPADL_ECUDA);
         }
     }
+    db->pitch = (C + 7) / 8 * 8;
+    if (db->stream_ok) {
+        db->u8_ok = encode_2d(&db->u8_map, CU_TENSOR_MAP_DATA_TYPE_UINT8, db_dev, C, R, C, kLimbBoxK, kLimbBoxM,
+                              CU_TENSOR_MAP_SWIZZLE_64B);
+    }
     if (db->stream_ok) {
         db->pack_words = stream_pack_words(C);
         if ((rc = dev_alloc(db, reinterpret_cast<void **>(&db->qpack), 4 * db->pack_words * 4)) != QPADL_OK)
@@ -375,9 +413,11 @@ int qpadl_pir_reserve(qpadl_db *db, uint32_t max_batch, qpadl_stream_t stream) {
     if (set_device(db) != QPADL_OK) return QPADL_ECUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (max_batch >= db->tensor_min_batch) {
-        int rc = ensure_tensor_copy(db, s);
-        if (rc != QPADL_OK) return rc;
-        rc = ensure_limbs(db, 8ull * max_batch * db->pitch);
+        if (!(db->u8_ok && max_batch <= db->u8_max_batch)) {
+            int rc = ensure_tensor_copy(db, s);
+            if (rc != QPADL_OK) return rc;
+        }
+        int rc = ensure_limbs(db, 8ull * max_batch * db->pitch);
         if (rc != QPADL_OK) return rc;
     }
     QPADL_CU(cudaStreamSynchronize(s));
@@ -470,6 +510,10 @@ int qpadl_pir_set_option(qpadl_db *db, int option, int64_t value) {
             if (value != 0 && value != 1) return QPADL_EINVAL;
             db->stream_raw = static_cast<int>(value);
             return QPADL_OK;
+        case QPADL_OPT_U8_MAX_BATCH:
+            if (value < 0 || value > 32) return QPADL_EINVAL;
+            db->u8_max_batch = static_cast<uint32_t>(value);
+            return QPADL_OK;
         default: return QPADL_EINVAL;
     }
 }
@@ -480,6 +524,7 @@ int qpadl_pir_get_option(const qpadl_db *db, int option, int64_t *value) {
         case QPADL_OPT_STREAM_CHUNK: *value = db->stream_chunk; return QPADL_OK;
         case QPADL_OPT_TENSOR_MIN_BATCH: *value = db->tensor_min_batch; return QPADL_OK;
         case QPADL_OPT_STREAM_RAW: *value = db->stream_raw; return QPADL_OK;
+        case QPADL_OPT_U8_MAX_BATCH: *value = db->u8_max_batch; return QPADL_OK;
         default: return QPADL_EINVAL;
     }
 }

@@ -28,6 +28,7 @@ QPADL_SETUP_TENSOR_COPY = 0x1
 QPADL_OPT_STREAM_CHUNK = 1
 QPADL_OPT_TENSOR_MIN_BATCH = 2
 QPADL_OPT_STREAM_RAW = 3
+QPADL_OPT_U8_MAX_BATCH = 4
 
 
 class QpadlError(RuntimeError):

@@ -157,6 +157,18 @@ def test_answer_batch_tensor_ragged(R, C, B):
     assert np.array_equal(_answers(db, Q, path=1), oracle.answer_batch(D, Q, threads=oracle.max_threads()))
 
 
+@pytest.mark.parametrize("R,C", [(300, 1008), (129, 4096 + 16), (1000, 2048)])
+@pytest.mark.parametrize("B", [1, 3, 8, 17, 32])
+def test_answer_batch_u8_and_fp16_gemms_agree_with_oracle(R, C, B):
+    # B <= 32 runs the GEMM on the uint8 digits by default; 0 forces the fp16-copy GEMM
+    prm, D, db = _setup(R, C, seed=R + B)
+    Q = inputs.uniform_u32(B * C, seed=C + B, tag=inputs.TAG_MISC).reshape(B, C)
+    exp = oracle.answer_batch(D, Q, threads=oracle.max_threads())
+    for u8max in (32, 0):
+        pir.qpadl_pir_set_option(db, pir.QPADL_OPT_U8_MAX_BATCH, u8max)
+        assert np.array_equal(_answers(db, Q, path=1), exp), f"u8 max batch {u8max}"
+
+
 def test_answer_batch_linearity_on_device():
     R, C, B = 256, 2048, 8
     prm, D, db = _setup(R, C, seed=3)
