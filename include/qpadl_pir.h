@@ -95,6 +95,8 @@ int qpadl_version(void);
 #define QPADL_OPT_U8_MAX_BATCH 4     /* batches of up to this many queries (0..32, default 32)
                                         run the tensor-core GEMM on the uint8 digits as stored;
                                         larger ones use the handle's fp16 operand copy */
+#define QPADL_OPT_U8_KSTEP 5         /* digits per row per pipeline stage of that GEMM: 128 or 256;
+                                        0 (default) = 256 for batches up to 16, 128 above */
 
 /*
  * Setup (server side; Def. 1's server holds D).  Validates `prm`, records

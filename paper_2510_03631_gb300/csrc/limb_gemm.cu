@@ -134,52 +134,55 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 if (!drain_wait_g(&full[j % kGemmStages], (j / kGemmStages) & 1u)) failed = true;
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            // ---------------- MMA issuer
-            constexpr uint32_t idesc = umma_idesc_f16(kBM, BN);
-            uint32_t it = 0, ci = 0;
-            bool issued = false;
-            for (uint32_t t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
-                uint32_t d_tmem = tmem_base;
-                for (uint32_t kb = 0; kb < KB; ++kb, ++it) {
-                    if (kb % kChunkKB == 0) {
-                        const uint32_t buf = ci & 1u;
-                        if (!mbar_wait(&acc_empty[buf], ((ci >> 1) & 1u) ^ 1u, abort)) {
-                            failed = true;
-                            break;
-                        }
-                        tc_fence_after();
-                        d_tmem = tmem_base + buf * BN;
-                    }
-                    const uint32_t st = it % kGemmStages;
-                    const uint32_t ph = (it / kGemmStages) & 1u;
-                    if (!mbar_wait(&full[st], ph, abort)) {
+        // ---------------- MMA issuer: the whole warp walks the loop (warp-uniform descriptors),
+        // one elected lane issues; wait outcomes are made warp-uniform
+        constexpr uint32_t idesc = umma_idesc_f16(kBM, BN);
+        uint32_t it = 0, ci = 0;
+        bool issued = false;
+        for (uint32_t t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
+            uint32_t d_tmem = tmem_base;
+            for (uint32_t kb = 0; kb < KB; ++kb, ++it) {
+                if (kb % kChunkKB == 0) {
+                    const uint32_t buf = ci & 1u;
+                    const bool ok = mbar_wait(&acc_empty[buf], ((ci >> 1) & 1u) ^ 1u, abort);
+                    if (__any_sync(0xffffffffu, !ok)) {
                         failed = true;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = smem_addr(smem + st * Cfg::kStageBytes);
-                    const uint64_t adesc = umma_desc_sw128(sa);
-                    const uint64_t bdesc = umma_desc_sw128(sa + Cfg::kABytes);
+                    d_tmem = tmem_base + buf * BN;
+                }
+                const uint32_t st = it % kGemmStages;
+                const uint32_t ph = (it / kGemmStages) & 1u;
+                const bool ok = mbar_wait(&full[st], ph, abort);
+                if (__any_sync(0xffffffffu, !ok)) {
+                    failed = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_addr(smem + st * Cfg::kStageBytes);
+                const uint64_t adesc = umma_desc_sw128(sa);
+                const uint64_t bdesc = umma_desc_sw128(sa + Cfg::kABytes);
+                if (elect_one()) {
 #pragma unroll
                     for (int k = 0; k < kBK / 16; ++k) {
                         // advance the start address by 16 elements (32 bytes) inside the swizzle atom
                         umma_f16(d_tmem, adesc + 2u * k, bdesc + 2u * k, idesc,
                                  (kb % kChunkKB != 0 || k != 0) ? 1u : 0u);
                     }
-                    issued = true;
                     umma_commit(&empty[st]);
-                    if (kb % kChunkKB == kChunkKB - 1 || kb == KB - 1) {
-                        umma_commit(&acc_full[ci & 1u]);
-                        ++ci;
-                    }
+                    if (kb % kChunkKB == kChunkKB - 1 || kb == KB - 1) umma_commit(&acc_full[ci & 1u]);
                 }
+                __syncwarp();
+                issued = true;
+                if (kb % kChunkKB == kChunkKB - 1 || kb == KB - 1) ++ci;
             }
-            // every MMA this thread issued must finish before TMEM is released
-            if (issued) {
-                umma_commit(mma_done);
-                if (!drain_wait_g(mma_done, 0)) failed = true;
-            }
+        }
+        // every MMA this warp issued must finish before TMEM is released
+        if (issued) {
+            if (elect_one()) umma_commit(mma_done);
+            __syncwarp();
+            if (!drain_wait_g(mma_done, 0)) failed = true;
         }
     } else {
         // ---------------- epilogue (warps 2..5; TMEM lane quarter = warp % 4)

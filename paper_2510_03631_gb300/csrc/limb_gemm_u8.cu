@@ -4,23 +4,29 @@
 //
 // Same exact byte-limb algebra as limb_gemm.cu (balanced limbs in fp16,
 // fp32 accumulation over 512-deep K-chunks, int32 recombination; see there),
-// but the A operand never exists as fp16 in memory: TMA brings 128 x 64
-// digit tiles (8 KB) into shared memory, four converter warps turn each row
+// but the A operand never exists as fp16 in memory: TMA brings 128-row digit
+// tiles (128 or 256 digits per row) into shared memory from a blocked copy of
+// the digits (128 x 128 tiles stored contiguously, so each stage is one
+// contiguous 16-32 KB read), converter warps turn each row
 // into fp16 (byte-permute next to 0x64 gives 1024 + d exactly, minus 1024)
 // and store it into tensor memory, and the MMA reads A from tensor memory
 // (tcgen05.mma with A in TMEM).  Half the HBM traffic of the fp16 copy, and
-// shared memory carries only the digit tile (64-byte swizzled, so the row-
+// shared memory carries only the digit tile (128-byte swizzled, so the row-
 // per-thread reads are free of bank conflicts) and the limb tile.
 //
 // One launch can serve several databases with their own batches (the
-// serving loop's grouped launch): output tiles of all groups form one list
-// that persistent CTAs walk.
+// serving loop's grouped launch).  The work of all groups is one list of
+// units (one tile's one pipeline stage) that the persistent CTAs split into
+// equal contiguous shares across tile boundaries (stream-K), so the last
+// wave is never partial; tiles shared by two CTAs are summed with atomic
+// adds, which is exact because the result is taken mod 2^32.
 //
-// Warp roles (320 threads, one CTA per SM):
-//   warp 0      TMA producer (digit tile + limb tile per stage, 4 stages)
-//   warp 1      TMEM allocation; one thread issues the MMAs
-//   warps 2..5  epilogue: drain one of two BN-column accumulators per chunk
-//   warps 6..9  converters: digits -> fp16 A tiles in TMEM (one row per thread)
+// Warp roles (448 threads, one CTA per SM):
+//   warp 0       TMA producer (digit tile + limb tile per stage)
+//   warp 1       TMEM allocation; one thread issues the MMAs
+//   warps 2..5   epilogue: drain one of two BN-column accumulators per chunk
+//   warps 6..13  converters, two groups of four, each owning half the stages:
+//                digits -> fp16 A tiles in TMEM (one row per thread)
 #include <cstdint>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -33,23 +39,34 @@ namespace qpadl {
 namespace {
 
 constexpr int kBM = 128;
-constexpr int kBK = 64;
-constexpr int kStages = 4;
-constexpr int kChunkKB = 8;               // 512-deep exact K-chunks
-constexpr int kThreads = 320;
+constexpr int kThreads = 448;
+constexpr int kConvGroups = 2;
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kAColBase = 256;       // A slots live after the (<= 256) accumulator columns
-constexpr uint32_t kASlotCols = kBK / 2;  // 64 fp16 per row = 32 columns
 
-template <int BN>
+// BN: limb columns per tile; KS: digits per row per pipeline stage (a
+// multiple of 128: each digit tile is 128 rows x 128 bytes, 128-byte swizzle).
+template <int BN, int KS>
 struct U8Cfg {
-    static constexpr uint32_t kABytes = kBM * kBK;        // digits
-    static constexpr uint32_t kBBytes = BN * kBK * 2;     // fp16 limbs
+    static constexpr int kSubA = KS / 128;                          // digit boxes per stage
+    static constexpr int kSubB = KS / 64;                           // limb boxes per stage
+    static constexpr uint32_t kABytes = kBM * KS;
+    static constexpr uint32_t kBBoxBytes = BN * 128;
+    static constexpr uint32_t kBBytes = kSubB * kBBoxBytes;
     static constexpr uint32_t kStageBytes = kABytes + kBBytes;
-    // padded so that only one CTA fits per SM (it allocates all of TMEM)
+    static constexpr uint32_t kSlotCols = KS / 2;                   // fp16 pairs per row per stage
+    static constexpr int kSmemStages = (200 * 1024) / kStageBytes;
+    static constexpr int kTmemStages = (kTmemCols - 2 * BN) / kSlotCols;
+    // a multiple of the converter-group count: group g then owns the stages st with st % 2 == g
+    // and waits on every phase of them (a parity wait must never fall two phases behind)
+    static constexpr int kStages = ((kSmemStages < kTmemStages ? kSmemStages : kTmemStages) / kConvGroups) * kConvGroups;
+    static constexpr uint32_t kAColBase = 2 * BN;                   // A slots after the accumulators
+    static constexpr int kChunkStages = 512 / KS;                   // stages per exact 512-deep K-chunk
     static constexpr int kSmemUsed = kStages * kStageBytes + 512 + 1024;
+    // padded so that only one CTA fits per SM (it allocates all of TMEM)
     static constexpr int kSmemBytes = kSmemUsed > 120 * 1024 ? kSmemUsed : 120 * 1024;
     static constexpr int kQPT = BN / 4;
+    static_assert(kStages >= 2 && kStages % kConvGroups == 0, "stages must split evenly between converter groups");
+    static_assert(KS % 128 == 0 && 512 % KS == 0, "stage depth must divide the exact chunk");
 };
 
 __device__ __forceinline__ bool drain_wait_u(uint64_t *bar, uint32_t parity) {
@@ -61,32 +78,47 @@ __device__ __forceinline__ bool drain_wait_u(uint64_t *bar, uint32_t parity) {
     return true;
 }
 
-struct TileRef {
-    uint32_t g, m0, n0;
+// One CTA's piece of one tile: stages [ks0, ks1) of tile (m0, n0) of group g.
+struct Seg {
+    uint32_t g, m0, n0, ks0, ks1, ns;
 };
 
-__device__ __forceinline__ TileRef locate(const GroupedGemmArgs &a, uint32_t t, uint32_t bn) {
+// The next piece of this CTA's unit range [u, u_end); advances u.
+__device__ __forceinline__ bool next_seg(const GroupedGemmArgs &a, uint32_t &u, uint32_t u_end, uint32_t bn,
+                                         Seg &s) {
+    if (u >= u_end) return false;
     uint32_t g = 0;
-    while (g + 1 < a.ngroups && t >= a.g[g + 1].tile_begin) ++g;
-    const uint32_t lt = t - a.g[g].tile_begin;
-    return TileRef{g, (lt / a.g[g].n_tiles) * kBM, (lt % a.g[g].n_tiles) * bn};
+    while (g + 1 < a.ngroups && u >= a.g[g + 1].unit_begin) ++g;
+    const uint32_t ns = a.g[g].KB;
+    const uint32_t local = u - a.g[g].unit_begin;
+    const uint32_t tile = local / ns;
+    s.g = g;
+    s.m0 = (tile / a.g[g].n_tiles) * kBM;
+    s.n0 = (tile % a.g[g].n_tiles) * bn;
+    s.ks0 = local % ns;
+    s.ks1 = (ns - s.ks0 < u_end - u) ? ns : s.ks0 + (u_end - u);
+    s.ns = ns;
+    u += s.ks1 - s.ks0;
+    return true;
 }
 
 }  // namespace
 
-template <int BN>
+template <int BN, int KS>
 __global__ void __launch_bounds__(kThreads, 1)
     limb_gemm_u8_kernel(const __grid_constant__ GroupedGemmArgs args, int *__restrict__ status) {
-    using Cfg = U8Cfg<BN>;
+    using Cfg = U8Cfg<BN, KS>;
     constexpr int QPT = Cfg::kQPT;
+    constexpr int ST = Cfg::kStages;
+    constexpr int CS = Cfg::kChunkStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    // stage s: [digits 8 KB][limbs BN*128 B]; the limb tile stays 1024-aligned
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * Cfg::kStageBytes);
-    uint64_t *conv = full + kStages;
-    uint64_t *empty = conv + kStages;
-    uint64_t *acc_full = empty + kStages;   // [2]
-    uint64_t *acc_empty = acc_full + 2;     // [2]
+    // stage s: [digit boxes][limb boxes], every box 1024-aligned
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + ST * Cfg::kStageBytes);
+    uint64_t *conv = full + ST;
+    uint64_t *empty = conv + ST;
+    uint64_t *acc_full = empty + ST;   // [2]
+    uint64_t *acc_empty = acc_full + 2;
     uint64_t *mma_done = acc_empty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -95,7 +127,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < ST; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&conv[s], 4);
             mbar_init(&empty[s], 1);
@@ -116,92 +148,104 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const uint32_t tiles = args.total_tiles;
+    // this CTA's share of the units, contiguous across tile boundaries
+    const uint32_t ubeg = static_cast<uint32_t>((uint64_t)blockIdx.x * args.total_units / gridDim.x);
+    const uint32_t uend = static_cast<uint32_t>((uint64_t)(blockIdx.x + 1) * args.total_units / gridDim.x);
     bool failed = false;
 
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer
-            uint32_t it = 0;
-            for (uint32_t t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
-                const TileRef tr = locate(args, t, BN);
-                const uint32_t KB = args.g[tr.g].KB;
-                for (uint32_t kb = 0; kb < KB; ++kb, ++it) {
-                    const uint32_t st = it % kStages;
-                    const uint32_t ph = (it / kStages) & 1u;
+            uint32_t it = 0, u = ubeg;
+            Seg tr;
+            while (!failed && next_seg(args, u, uend, BN, tr)) {
+                for (uint32_t ks = tr.ks0; ks < tr.ks1; ++ks, ++it) {
+                    const uint32_t st = it % ST;
+                    const uint32_t ph = (it / ST) & 1u;
                     if (!mbar_wait(&empty[st], ph ^ 1u, abort)) {
                         failed = true;
                         break;
                     }
                     uint8_t *sa = smem + st * Cfg::kStageBytes;
+                    uint8_t *sb = sa + Cfg::kABytes;
                     mbar_arrive_expect_tx(&full[st], Cfg::kStageBytes);
-                    tma_load_2d(sa, &args.a[tr.g], &full[st], static_cast<int32_t>(kb * kBK),
-                                static_cast<int32_t>(tr.m0));
-                    tma_load_2d(sa + Cfg::kABytes, &args.b[tr.g], &full[st], static_cast<int32_t>(kb * kBK),
-                                static_cast<int32_t>(tr.n0));
+                    const int32_t k0 = static_cast<int32_t>(ks * KS);
+                    // the digits are stored blocked (128 x 128 tiles, each 16 KB contiguous), so the
+                    // kSubA tiles of this stage are one contiguous read
+                    tma_load_4d(sa, &args.a[tr.g], &full[st], 0, 0, k0 / 128, static_cast<int32_t>(tr.m0 / kBM));
+#pragma unroll
+                    for (int b = 0; b < Cfg::kSubB; ++b)
+                        tma_load_2d(sb + b * Cfg::kBBoxBytes, &args.b[tr.g], &full[st], k0 + 64 * b,
+                                    static_cast<int32_t>(tr.n0));
                 }
             }
-            const uint32_t inflight = it < (uint32_t)kStages ? it : (uint32_t)kStages;
+            const uint32_t inflight = it < (uint32_t)ST ? it : (uint32_t)ST;
             for (uint32_t j = it - inflight; j < it; ++j)
-                if (!drain_wait_u(&full[j % kStages], (j / kStages) & 1u)) failed = true;
+                if (!drain_wait_u(&full[j % ST], (j / ST) & 1u)) failed = true;
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            // ---------------- MMA issuer
-            constexpr uint32_t idesc = umma_idesc_f16(kBM, BN);
-            uint32_t it = 0, ci = 0;
-            bool issued = false;
-            for (uint32_t t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
-                const uint32_t KB = args.g[locate(args, t, BN).g].KB;
-                uint32_t d_tmem = tmem_base;
-                for (uint32_t kb = 0; kb < KB; ++kb, ++it) {
-                    if (kb % kChunkKB == 0) {
-                        const uint32_t buf = ci & 1u;
-                        if (!mbar_wait(&acc_empty[buf], ((ci >> 1) & 1u) ^ 1u, abort)) {
-                            failed = true;
-                            break;
-                        }
-                        tc_fence_after();
-                        d_tmem = tmem_base + buf * BN;
-                    }
-                    const uint32_t st = it % kStages;
-                    const uint32_t ph = (it / kStages) & 1u;
-                    if (!mbar_wait(&conv[st], ph, abort)) {   // implies the limb tile has landed too
+        // ---------------- MMA issuer: the whole warp walks the loop so the descriptors and
+        // TMEM addresses stay warp-uniform; one elected lane issues each instruction
+        constexpr uint32_t idesc = umma_idesc_f16(kBM, BN);
+        uint32_t it = 0, ci = 0, u = ubeg;
+        bool issued = false;
+        Seg sg;
+        while (!failed && next_seg(args, u, uend, BN, sg)) {
+            uint32_t d_tmem = tmem_base;
+            for (uint32_t ks = sg.ks0; ks < sg.ks1; ++ks, ++it) {
+                const uint32_t kr = ks - sg.ks0;   // exact chunks restart at every piece
+                // every wait outcome is made warp-uniform before the elected issue
+                if (kr % CS == 0) {
+                    const uint32_t buf = ci & 1u;
+                    const bool ok = mbar_wait(&acc_empty[buf], ((ci >> 1) & 1u) ^ 1u, abort);
+                    if (__any_sync(0xffffffffu, !ok)) {
                         failed = true;
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t bdesc = umma_desc_sw128(smem_addr(smem + st * Cfg::kStageBytes + Cfg::kABytes));
-                    const uint32_t a_tmem = tmem_base + kAColBase + st * kASlotCols;
-#pragma unroll
-                    for (int k = 0; k < kBK / 16; ++k)
-                        umma_f16_ts(d_tmem, a_tmem + 8u * k, bdesc + 2u * k, idesc,
-                                    (kb % kChunkKB != 0 || k != 0) ? 1u : 0u);
-                    issued = true;
-                    umma_commit(&empty[st]);   // frees the shared-memory stage and the TMEM A slot
-                    if (kb % kChunkKB == kChunkKB - 1 || kb == KB - 1) {
-                        umma_commit(&acc_full[ci & 1u]);
-                        ++ci;
-                    }
+                    d_tmem = tmem_base + buf * BN;
                 }
+                const uint32_t st = it % ST;
+                const uint32_t ph = (it / ST) & 1u;
+                const bool ok = mbar_wait(&conv[st], ph, abort);   // implies the limb boxes have landed too
+                if (__any_sync(0xffffffffu, !ok)) {
+                    failed = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sb = smem_addr(smem + st * Cfg::kStageBytes + Cfg::kABytes);
+                const uint32_t a_tmem = tmem_base + Cfg::kAColBase + st * Cfg::kSlotCols;
+                if (elect_one()) {
+#pragma unroll
+                    for (int kk = 0; kk < KS / 16; ++kk) {
+                        const uint64_t bdesc = umma_desc_sw128(sb + (kk / 4) * Cfg::kBBoxBytes) + 2u * (kk % 4);
+                        umma_f16_ts(d_tmem, a_tmem + 8u * kk, bdesc, idesc, (kr % CS != 0 || kk != 0) ? 1u : 0u);
+                    }
+                    umma_commit(&empty[st]);   // frees the shared-memory stage and the TMEM A slot
+                    if (kr % CS == CS - 1 || ks == sg.ks1 - 1) umma_commit(&acc_full[ci & 1u]);
+                }
+                __syncwarp();
+                issued = true;
+                if (kr % CS == CS - 1 || ks == sg.ks1 - 1) ++ci;
             }
-            if (issued) {
-                umma_commit(mma_done);
-                if (!drain_wait_u(mma_done, 0)) failed = true;
-            }
+        }
+        if (issued) {
+            if (elect_one()) umma_commit(mma_done);
+            __syncwarp();
+            if (!drain_wait_u(mma_done, 0)) failed = true;
         }
     } else if (warp < 6) {
         // ---------------- epilogue (warps 2..5)
         const uint32_t quarter = static_cast<uint32_t>(warp & 3);
         const uint32_t lane_addr = (quarter * 32u) << 16;
-        uint32_t ci = 0;
-        for (uint32_t t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
-            const TileRef tr = locate(args, t, BN);
+        uint32_t ci = 0, u = ubeg;
+        Seg tr;
+        while (!failed && next_seg(args, u, uend, BN, tr)) {
             const GroupDesc &gd = args.g[tr.g];
             uint32_t run[QPT];
 #pragma unroll
             for (int q = 0; q < QPT; ++q) run[q] = 0u;
-            const uint32_t nchunks = (gd.KB + kChunkKB - 1) / kChunkKB;
+            const uint32_t nchunks = (tr.ks1 - tr.ks0 + CS - 1) / CS;
             for (uint32_t c = 0; c < nchunks; ++c, ++ci) {
                 const uint32_t buf = ci & 1u;
                 if (!mbar_wait(&acc_full[buf], (ci >> 1) & 1u, abort)) {
@@ -210,17 +254,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
 #pragma unroll
-                for (int j = 0; j < BN / 32; ++j) {
-                    uint32_t v[32];
-                    tmem_ld32(tmem_base + lane_addr + buf * BN + 32u * j, v);
+                for (int j = 0; j < BN / 16; ++j) {
+                    uint32_t v[16];
+                    tmem_ld16(tmem_base + lane_addr + buf * BN + 16u * j, v);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
+                    for (int q = 0; q < 4; ++q) {
                         const uint32_t s0 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 0])));
                         const uint32_t s1 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 1])));
                         const uint32_t s2 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 2])));
                         const uint32_t s3 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 3])));
-                        run[8 * j + q] += s0 + (s1 << 8) + (s2 << 16) + (s3 << 24);
+                        run[4 * j + q] += s0 + (s1 << 8) + (s2 << 16) + (s3 << 24);
                     }
                 }
                 tc_fence_before();
@@ -229,52 +273,62 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (failed) break;
             const uint32_t row = tr.m0 + quarter * 32u + static_cast<uint32_t>(lane);
+            const bool whole = tr.ks0 == 0 && tr.ks1 == tr.ns;   // no other CTA touches this tile
             if (row < gd.M) {
                 const uint32_t v0 = tr.n0 / 4;
 #pragma unroll
                 for (int q = 0; q < QPT; ++q) {
                     const uint32_t vi = v0 + q;
-                    if (vi < gd.NV) gd.out[(uint64_t)row * gd.ld_m + (uint64_t)vi * gd.ld_b] = run[q];
+                    if (vi < gd.NV) {
+                        uint32_t *dst = gd.out + (uint64_t)row * gd.ld_m + (uint64_t)vi * gd.ld_b;
+                        if (whole) *dst = run[q];
+                        else atomicAdd(dst, run[q]);   // exact: addition mod 2^32 commutes
+                    }
                 }
             }
         }
     } else {
-        // ---------------- converters (warps 6..9): digits -> fp16 A in TMEM
+        // ---------------- converters (warps 6..13): digits -> fp16 A in TMEM
         const uint32_t quarter = static_cast<uint32_t>(warp & 3);
+        const uint32_t group = static_cast<uint32_t>(warp - 6) / 4;   // owns the stages st % 2 == group
         const uint32_t row = quarter * 32u + static_cast<uint32_t>(lane);
         const uint32_t lane_addr = (quarter * 32u) << 16;
         const __half2 k1024 = __floats2half2_rn(1024.0f, 1024.0f);
-        uint32_t it = 0;
-        for (uint32_t t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
-            const uint32_t KB = args.g[locate(args, t, BN).g].KB;
-            for (uint32_t kb = 0; kb < KB; ++kb, ++it) {
-                const uint32_t st = it % kStages;
-                const uint32_t ph = (it / kStages) & 1u;
+        uint32_t it = 0, u = ubeg;
+        Seg sg;
+        while (!failed && next_seg(args, u, uend, BN, sg)) {
+            for (uint32_t ks = sg.ks0; ks < sg.ks1; ++ks, ++it) {
+                const uint32_t st = it % ST;
+                if (st % kConvGroups != group) continue;   // this group owns every phase of its stages
+                const uint32_t ph = (it / ST) & 1u;
                 if (!mbar_wait(&full[st], ph, abort)) {
                     failed = true;
                     break;
                 }
-                const uint8_t *tile = smem + st * Cfg::kStageBytes + row * kBK;
-                const uint32_t a_tmem = tmem_base + lane_addr + kAColBase + st * kASlotCols;
+                const uint32_t a_tmem = tmem_base + lane_addr + Cfg::kAColBase + st * Cfg::kSlotCols;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    // the digit tile arrives with 64-byte swizzling: logical 16-byte chunk j of row r
-                    // sits at chunk j ^ ((r >> 1) & 3), so a quarter-warp reads distinct banks
-                    const uint32_t phys = static_cast<uint32_t>(j) ^ ((row >> 1) & 3u);
-                    const uint4 w = *reinterpret_cast<const uint4 *>(tile + 16u * phys);
-                    const uint32_t x[4] = {w.x, w.y, w.z, w.w};
-                    uint32_t o[8];
+                for (int b = 0; b < Cfg::kSubA; ++b) {
+                    const uint8_t *tile = smem + st * Cfg::kStageBytes + b * 16384 + row * 128;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        // [d0, 0x64, d1, 0x64] is the fp16 pair (1024 + d0, 1024 + d1)
-                        uint32_t lo = __byte_perm(x[q], 0x64646464u, 0x4140);
-                        uint32_t hi = __byte_perm(x[q], 0x64646464u, 0x4342);
-                        __half2 hl = __hsub2(*reinterpret_cast<__half2 *>(&lo), k1024);
-                        __half2 hh = __hsub2(*reinterpret_cast<__half2 *>(&hi), k1024);
-                        o[2 * q] = *reinterpret_cast<uint32_t *>(&hl);
-                        o[2 * q + 1] = *reinterpret_cast<uint32_t *>(&hh);
+                    for (int j = 0; j < 8; ++j) {
+                        // 128-byte swizzle: logical 16-byte chunk j of row r sits at chunk j ^ (r & 7),
+                        // so the eight rows of a quarter-warp read distinct banks
+                        const uint32_t phys = static_cast<uint32_t>(j) ^ (row & 7u);
+                        const uint4 w = *reinterpret_cast<const uint4 *>(tile + 16u * phys);
+                        const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+                        uint32_t o[8];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            // [d0, 0x64, d1, 0x64] is the fp16 pair (1024 + d0, 1024 + d1)
+                            uint32_t lo = __byte_perm(x[q], 0x64646464u, 0x4140);
+                            uint32_t hi = __byte_perm(x[q], 0x64646464u, 0x4342);
+                            __half2 hl = __hsub2(*reinterpret_cast<__half2 *>(&lo), k1024);
+                            __half2 hh = __hsub2(*reinterpret_cast<__half2 *>(&hi), k1024);
+                            o[2 * q] = *reinterpret_cast<uint32_t *>(&hl);
+                            o[2 * q + 1] = *reinterpret_cast<uint32_t *>(&hh);
+                        }
+                        tmem_st8(a_tmem + 64u * b + 8u * j, o);   // warp-uniform TMEM address
                     }
-                    tmem_st8(a_tmem + 8u * j, o);   // the TMEM address is warp-uniform
                 }
                 tmem_wait_st();
                 tc_fence_before();
@@ -296,36 +350,73 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// Blocked copy of the digits: tile (rb, cb) of 128 x 128 digits is stored
+// contiguously at (rb * CB + cb) * 16384, rows of 128 bytes; zero beyond R, C.
+__global__ void block_digits_kernel(const uint8_t *__restrict__ D, uint64_t R, uint64_t C, uint64_t CB,
+                                    uint8_t *__restrict__ blk) {
+    const uint64_t tile = blockIdx.x;   // rb * CB + cb
+    const uint64_t rb = tile / CB, cb = tile % CB;
+    const bool full = (rb * 128 + 128 <= R) && (cb * 128 + 128 <= C) && (C % 16 == 0) &&
+                      ((reinterpret_cast<uintptr_t>(D) & 15u) == 0);
+    uint8_t *dst = blk + tile * 16384;
+    for (uint32_t ch = threadIdx.x; ch < 1024; ch += blockDim.x) {   // 16-byte chunks of the tile
+        const uint32_t r = ch / 8, k = (ch % 8) * 16;
+        const uint64_t row = rb * 128 + r, col = cb * 128 + k;
+        uint4 v;
+        if (full) {
+            v = *reinterpret_cast<const uint4 *>(D + row * C + col);
+        } else {
+            uint8_t b[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) b[i] = (row < R && col + i < C) ? D[row * C + col + i] : 0;
+            v = *reinterpret_cast<const uint4 *>(b);
+        }
+        *reinterpret_cast<uint4 *>(dst + r * 128 + k) = v;
+    }
+}
+
+cudaError_t launch_block_digits(const uint8_t *D, uint64_t R, uint64_t C, uint8_t *blk, cudaStream_t stream) {
+    const uint64_t RB = (R + 127) / 128, CB = (C + 127) / 128;
+    block_digits_kernel<<<static_cast<unsigned>(RB * CB), 256, 0, stream>>>(D, R, C, CB, blk);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ host side
-template <int BN>
+template <int BN, int KS>
 static cudaError_t set_attr() {
-    return cudaFuncSetAttribute(limb_gemm_u8_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                U8Cfg<BN>::kSmemBytes);
+    return cudaFuncSetAttribute(limb_gemm_u8_kernel<BN, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                U8Cfg<BN, KS>::kSmemBytes);
 }
 
 cudaError_t prepare_limb_gemm_u8_kernels() {
     cudaError_t e;
-    if ((e = set_attr<32>()) != cudaSuccess) return e;
-    if ((e = set_attr<64>()) != cudaSuccess) return e;
-    return set_attr<128>();
+    if ((e = set_attr<32, 128>()) != cudaSuccess) return e;
+    if ((e = set_attr<32, 256>()) != cudaSuccess) return e;
+    if ((e = set_attr<64, 128>()) != cudaSuccess) return e;
+    if ((e = set_attr<64, 256>()) != cudaSuccess) return e;
+    if ((e = set_attr<128, 128>()) != cudaSuccess) return e;
+    return set_attr<128, 256>();
 }
 
-cudaError_t launch_limb_gemm_u8(int bn, const GroupedGemmArgs &args, int num_sms, int *status, cudaStream_t stream) {
-    const int grid = static_cast<int>(args.total_tiles < (uint32_t)num_sms ? args.total_tiles : (uint32_t)num_sms);
-    if (grid <= 0) return cudaSuccess;
-    switch (bn) {
-        case 32:
-            limb_gemm_u8_kernel<32><<<grid, kThreads, U8Cfg<32>::kSmemBytes, stream>>>(args, status);
-            break;
-        case 64:
-            limb_gemm_u8_kernel<64><<<grid, kThreads, U8Cfg<64>::kSmemBytes, stream>>>(args, status);
-            break;
-        case 128:
-            limb_gemm_u8_kernel<128><<<grid, kThreads, U8Cfg<128>::kSmemBytes, stream>>>(args, status);
-            break;
-        default: return cudaErrorInvalidValue;
-    }
+int limb_gemm_u8_default_ks(int bn) { return bn <= 64 ? 256 : 128; }
+
+template <int BN, int KS>
+static cudaError_t launch_u8(const GroupedGemmArgs &args, int grid, int *status, cudaStream_t stream) {
+    limb_gemm_u8_kernel<BN, KS><<<grid, kThreads, U8Cfg<BN, KS>::kSmemBytes, stream>>>(args, status);
     return cudaGetLastError();
+}
+
+cudaError_t launch_limb_gemm_u8(int bn, int ks, const GroupedGemmArgs &args, int num_sms, int *status,
+                                cudaStream_t stream) {
+    const int grid = static_cast<int>(args.total_units < (uint32_t)num_sms ? args.total_units : (uint32_t)num_sms);
+    if (grid <= 0) return cudaSuccess;
+    if (bn == 32 && ks == 128) return launch_u8<32, 128>(args, grid, status, stream);
+    if (bn == 32 && ks == 256) return launch_u8<32, 256>(args, grid, status, stream);
+    if (bn == 64 && ks == 128) return launch_u8<64, 128>(args, grid, status, stream);
+    if (bn == 64 && ks == 256) return launch_u8<64, 256>(args, grid, status, stream);
+    if (bn == 128 && ks == 128) return launch_u8<128, 128>(args, grid, status, stream);
+    if (bn == 128 && ks == 256) return launch_u8<128, 256>(args, grid, status, stream);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace qpadl

@@ -10,24 +10,36 @@ constexpr int kMaxGemmGroups = 4;
 
 // One group: a database (rows M, K columns) times NV vectors.
 struct GroupDesc {
-    uint32_t *out;          // out[i * ld_m + v * ld_b]
+    uint32_t *out;          // out[i * ld_m + v * ld_b]; must be zero where tiles are split (see below)
     uint64_t ld_m, ld_b;
-    uint32_t M, NV, KB;     // rows, vectors, 64-wide K blocks
-    uint32_t tile_begin;    // first index of this group in the launch's tile list
+    uint32_t M, NV, KB;     // rows, vectors, pipeline stages per tile (ceil(K / ks))
+    uint32_t unit_begin;    // first work unit (tile x stage) of this group in the launch
     uint32_t n_tiles;       // BN-wide tiles per 128-row tile
     uint32_t pad;
 };
 
 struct GroupedGemmArgs {
-    CUtensorMap a[kMaxGemmGroups];   // uint8 digits, 2-D {C, R}, box {64, 128}, 64-byte swizzle
+    CUtensorMap a[kMaxGemmGroups];   // blocked uint8 digits: 4-D {128, 128, C/128, R/128},
+                                     // box {128, 128, ks/128, 1}, 128-byte swizzle
     CUtensorMap b[kMaxGemmGroups];   // fp16 limbs, 2-D {C, 4 NV}, box {64, BN}, 128-byte swizzle
     GroupDesc g[kMaxGemmGroups];
-    uint32_t ngroups, total_tiles;
+    uint32_t ngroups, total_units;   // units = sum over groups of tiles x stages
 };
 
 cudaError_t prepare_limb_gemm_u8_kernels();
 
-// bn in {32, 64, 128}: limb columns per tile (the same for every group).
-cudaError_t launch_limb_gemm_u8(int bn, const GroupedGemmArgs &args, int num_sms, int *status, cudaStream_t stream);
+// Blocked copy of D: 128 x 128 digit tiles, tile (rb, cb) at (rb * ceil(C/128) + cb) * 16384.
+// blk holds ceil(R/128) * ceil(C/128) * 16384 bytes.
+cudaError_t launch_block_digits(const uint8_t *D, uint64_t R, uint64_t C, uint8_t *blk, cudaStream_t stream);
+
+// Work is split evenly over the CTAs by units (one tile's one pipeline stage),
+// across tile boundaries (stream-K): a tile wholly inside one CTA's share is
+// stored, a tile shared by CTAs is accumulated with atomic adds (exact mod
+// 2^32), so the output must be zeroed before the launch.
+// bn in {32, 64, 128}, ks in {128, 256}: limb columns per
+// tile (the same for every group) and digits per row per pipeline stage.
+int limb_gemm_u8_default_ks(int bn);
+cudaError_t launch_limb_gemm_u8(int bn, int ks, const GroupedGemmArgs &args, int num_sms, int *status,
+                                cudaStream_t stream);
 
 }  // namespace qpadl

@@ -38,9 +38,12 @@ struct qpadl_db {
     uint32_t *qpack = nullptr;       // packed limbs of up to 4 queries
     uint64_t pack_words = 0;         // per query
     // tensor-core paths
-    bool u8_ok = false;              // digits can feed the u8 GEMM directly (C % 16 == 0, aligned)
-    CUtensorMap u8_map;              // uint8 digits, box {64, 128}
+    bool u8_ok = false;              // the u8 GEMM can run (blocked copy built on first use)
+    uint8_t *blk = nullptr;          // blocked copy of the digits (128 x 128 tiles)
+    uint64_t blk_bytes = 0;
+    CUtensorMap u8_map[2];           // over blk: box {128, 128, ks/128, 1} for ks = 128, 256
     uint32_t u8_max_batch = 32;      // QPADL_OPT_U8_MAX_BATCH
+    int u8_kstep = 0;                // QPADL_OPT_U8_KSTEP (0 = per tile width default)
     __half *d16 = nullptr;           // digits as fp16, R x pitch
     uint64_t pitch = 0;              // roundup(C, 8)
     CUtensorMap a_map;
@@ -246,16 +249,43 @@ int answer_streaming(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans,
     return QPADL_OK;
 }
 
-// Batched answer on the u8 GEMM (digits read as stored): one group.
+// The blocked copy of the digits that the u8 GEMM reads, and its tensor maps.
+int ensure_blocked(qpadl_db *db, cudaStream_t stream) {
+    if (db->blk) return QPADL_OK;
+    const uint64_t R = db->prm.rows, C = db->prm.cols;
+    const uint64_t RB = (R + 127) / 128, CB = (C + 127) / 128;
+    const uint64_t bytes = RB * CB * 16384;
+    int rc = dev_alloc(db, reinterpret_cast<void **>(&db->blk), bytes);
+    if (rc != QPADL_OK) return rc;
+    db->blk_bytes = bytes;
+    QPADL_CU(launch_block_digits(db->db, R, C, db->blk, stream));
+    auto fn = encode_fn();
+    for (int i = 0; i < 2; ++i) {
+        cuuint64_t dims[4] = {128, 128, CB, RB};
+        cuuint64_t strides[3] = {128, 16384, CB * 16384};
+        cuuint32_t box[4] = {128, 128, static_cast<cuuint32_t>(i + 1), 1};
+        cuuint32_t estr[4] = {1, 1, 1, 1};
+        if (!fn || fn(&db->u8_map[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, db->blk, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return QPADL_ECUDA;
+    }
+    return QPADL_OK;
+}
+
+// Batched answer on the u8 GEMM (blocked digits, fp16 made in TMEM): one group.
 int answer_tensor_u8(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, cudaStream_t stream) {
-    int rc = ensure_limbs(db, 8ull * B * db->pitch);
+    int rc = ensure_blocked(db, stream);
+    if (rc != QPADL_OK) return rc;
+    rc = ensure_limbs(db, 8ull * B * db->pitch);
     if (rc != QPADL_OK) return rc;
     const uint64_t R = db->prm.rows, C = db->prm.cols;
     QPADL_CU(launch_vec_limbs(Q, C, B, C, db->limbs, db->pitch, db->num_sms, stream));
     const int bn = limb_gemm_bn_for(B);
+    const int ks = db->u8_kstep ? db->u8_kstep : limb_gemm_u8_default_ks(bn);
     GroupedGemmArgs args;
     std::memset(&args, 0, sizeof(args));
-    args.a[0] = db->u8_map;
+    args.a[0] = db->u8_map[ks / 128 - 1];
     if (!encode_2d(&args.b[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, db->limbs, C, 4ull * B, db->pitch * 2, kLimbBoxK,
                    static_cast<uint32_t>(bn), CU_TENSOR_MAP_SWIZZLE_128B))
         return QPADL_ECUDA;
@@ -265,12 +295,14 @@ int answer_tensor_u8(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans,
     g.ld_b = R;
     g.M = static_cast<uint32_t>(R);
     g.NV = B;
-    g.KB = static_cast<uint32_t>((C + kLimbBoxK - 1) / kLimbBoxK);
-    g.tile_begin = 0;
+    g.KB = static_cast<uint32_t>((C + ks - 1) / ks);
+    g.unit_begin = 0;
     g.n_tiles = (4 * B + bn - 1) / bn;
     args.ngroups = 1;
-    args.total_tiles = static_cast<uint32_t>((R + kLimbBoxM - 1) / kLimbBoxM) * g.n_tiles;
-    QPADL_CU(launch_limb_gemm_u8(bn, args, db->num_sms, db->d_status, stream));
+    args.total_units = static_cast<uint32_t>((R + kLimbBoxM - 1) / kLimbBoxM) * g.n_tiles * g.KB;
+    // tiles split between CTAs are accumulated with atomic adds into zeros
+    QPADL_CU(cudaMemsetAsync(ans, 0, 4ull * B * R, stream));
+    QPADL_CU(launch_limb_gemm_u8(bn, ks, args, db->num_sms, db->d_status, stream));
     return QPADL_OK;
 }
 
@@ -350,10 +382,7 @@ int qpadl_pir_setup(const qpadl_params *prm, const uint8_t *db_dev, qpadl_stream
         }
     }
     db->pitch = (C + 7) / 8 * 8;
-    if (db->stream_ok) {
-        db->u8_ok = encode_2d(&db->u8_map, CU_TENSOR_MAP_DATA_TYPE_UINT8, db_dev, C, R, C, kLimbBoxK, kLimbBoxM,
-                              CU_TENSOR_MAP_SWIZZLE_64B);
-    }
+    db->u8_ok = true;
     if (db->stream_ok) {
         db->pack_words = stream_pack_words(C);
         if ((rc = dev_alloc(db, reinterpret_cast<void **>(&db->qpack), 4 * db->pack_words * 4)) != QPADL_OK)
@@ -377,6 +406,7 @@ int qpadl_pir_destroy(qpadl_db *db) {
     dev_free(db, db->d_status, 16);
     dev_free(db, db->qpack, 4 * db->pack_words * 4);
     dev_free(db, db->d16, db->prm.rows * db->pitch * 2);
+    dev_free(db, db->blk, db->blk_bytes);
     dev_free(db, db->limbs, db->limbs_bytes);
     dev_free(db, db->stage_q, db->prm.cols * 4);
     dev_free(db, db->stage_ans, db->prm.rows * 4);
@@ -415,6 +445,10 @@ int qpadl_pir_reserve(qpadl_db *db, uint32_t max_batch, qpadl_stream_t stream) {
     if (max_batch >= db->tensor_min_batch) {
         if (!(db->u8_ok && max_batch <= db->u8_max_batch)) {
             int rc = ensure_tensor_copy(db, s);
+            if (rc != QPADL_OK) return rc;
+        }
+        if (db->u8_ok && db->u8_max_batch >= db->tensor_min_batch) {
+            int rc = ensure_blocked(db, s);
             if (rc != QPADL_OK) return rc;
         }
         int rc = ensure_limbs(db, 8ull * max_batch * db->pitch);
@@ -514,6 +548,10 @@ int qpadl_pir_set_option(qpadl_db *db, int option, int64_t value) {
             if (value < 0 || value > 32) return QPADL_EINVAL;
             db->u8_max_batch = static_cast<uint32_t>(value);
             return QPADL_OK;
+        case QPADL_OPT_U8_KSTEP:
+            if (value != 0 && value != 128 && value != 256) return QPADL_EINVAL;
+            db->u8_kstep = static_cast<int>(value);
+            return QPADL_OK;
         default: return QPADL_EINVAL;
     }
 }
@@ -525,6 +563,7 @@ int qpadl_pir_get_option(const qpadl_db *db, int option, int64_t *value) {
         case QPADL_OPT_TENSOR_MIN_BATCH: *value = db->tensor_min_batch; return QPADL_OK;
         case QPADL_OPT_STREAM_RAW: *value = db->stream_raw; return QPADL_OK;
         case QPADL_OPT_U8_MAX_BATCH: *value = db->u8_max_batch; return QPADL_OK;
+        case QPADL_OPT_U8_KSTEP: *value = db->u8_kstep; return QPADL_OK;
         default: return QPADL_EINVAL;
     }
 }

@@ -29,6 +29,7 @@ QPADL_OPT_STREAM_CHUNK = 1
 QPADL_OPT_TENSOR_MIN_BATCH = 2
 QPADL_OPT_STREAM_RAW = 3
 QPADL_OPT_U8_MAX_BATCH = 4
+QPADL_OPT_U8_KSTEP = 5
 
 
 class QpadlError(RuntimeError):

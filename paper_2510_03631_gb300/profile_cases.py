@@ -38,6 +38,8 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--chunk", type=int, default=0, help="streaming chunk width (0 = library default)")
     ap.add_argument("--raw", type=int, default=-1, help="1: single query packed inside the kernel")
+    ap.add_argument("--u8max", type=int, default=-1, help="largest batch on the uint8-digit GEMM")
+    ap.add_argument("--kstep", type=int, default=-1, help="digits per row per stage of that GEMM")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     R, C = a.rows, a.cols
@@ -48,6 +50,10 @@ def main():
         pir.qpadl_pir_set_option(db, pir.QPADL_OPT_STREAM_CHUNK, a.chunk)
     if a.raw >= 0:
         pir.qpadl_pir_set_option(db, pir.QPADL_OPT_STREAM_RAW, a.raw)
+    if a.u8max >= 0:
+        pir.qpadl_pir_set_option(db, pir.QPADL_OPT_U8_MAX_BATCH, a.u8max)
+    if a.kstep >= 0:
+        pir.qpadl_pir_set_option(db, pir.QPADL_OPT_U8_KSTEP, a.kstep)
     res = {"case": a.case, "rows": R, "cols": C, "chunk": pir.qpadl_pir_get_option(db, pir.QPADL_OPT_STREAM_CHUNK)}
     if a.case == "stream":
         X_np = inputs.uniform_u32(C, seed=2, tag=inputs.TAG_MISC)
