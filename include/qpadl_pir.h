@@ -257,12 +257,17 @@ int qpadl_pir_recover_batch(const qpadl_params *prm, const uint32_t *ans_dev,
  * Serving: a continuous-batching request loop over several resident
  * databases (the paper's server answering q-bar queries per database,
  * Sec. 5.2, run as a long-lived service).  Requests arrive from any host
- * thread; one loop thread forms a launch for a database whenever a launch
- * stream is free, from up to max_batch of its queued requests (oldest
- * database first), so new arrivals start while earlier launches are still
- * on the GPU.  Admission is by memory: each request's query and answer live
- * in a mapped pinned host arena of host_budget_bytes; batch buffers come
- * from a device arena of device_budget_bytes.
+ * thread; whenever a launch stream is free, one loop thread forms a launch
+ * from up to max_batch queued requests of the database holding the oldest
+ * request and of every other database within group_size_ratio of its size,
+ * so new arrivals start while earlier launches are still on the GPU.  One
+ * launch answers all its databases together: databases with 3..32 queued
+ * queries share one grouped tensor-core GEMM, 1..2 queries use the
+ * streaming kernel, more than 32 the fp16-copy GEMM.  Admission is by
+ * memory: each request's query and answer live in a mapped pinned host
+ * arena of host_budget_bytes; each launch's workspace (queries, answers,
+ * query limbs) comes from a device arena of device_budget_bytes, and a
+ * launch whose workspace would not fit takes fewer requests.
  * ==================================================================== */
 typedef struct qpadl_server qpadl_server;
 
@@ -270,7 +275,8 @@ typedef struct qpadl_server_config {
     uint64_t host_budget_bytes;   /* pinned host arena for queued/in-flight requests (admission) */
     uint64_t device_budget_bytes; /* device arena for per-launch batch buffers */
     uint32_t max_inflight;        /* requests admitted and not yet polled */
-    uint32_t max_batch;           /* requests of one database per launch (1..65535) */
+    uint32_t max_batch;           /* requests of one database per launch (1..65535); a launch holds
+                                     at most min(max_inflight, 65535) requests in all */
     uint32_t num_streams;         /* launches in flight at once (1..8) */
     uint32_t test_drop_completion_launch; /* test hook: 0 = off; k = the k-th launch's completion
                                              is not reported, so its requests run into the watchdog */
@@ -278,6 +284,8 @@ typedef struct qpadl_server_config {
                                      launches run (0 = launch as soon as a stream is free) */
     double watchdog_ms;           /* requests whose launch has not completed after this fail
                                      with QPADL_ETIMEOUT (<= 0: 10000) */
+    double group_size_ratio;      /* databases whose R*C is within this factor of the leading
+                                     database's join its launch; < 1: one database per launch */
 } qpadl_server_config;
 
 typedef struct qpadl_request_times {
@@ -289,6 +297,7 @@ typedef struct qpadl_server_stats_t {
     uint32_t inflight, queued;
     double mean_launch_requests;
     uint64_t host_bytes_used, device_bytes_used;
+    uint64_t grouped_launches;    /* launches that answered two or more databases */
 } qpadl_server_stats_t;
 
 /* Creates a server on the current device (allocates both arenas and the
@@ -296,15 +305,20 @@ typedef struct qpadl_server_stats_t {
  * cannot be allocated. */
 int qpadl_server_create(const qpadl_server_config *cfg, qpadl_server **out);
 
-/* Registers a database handle (before qpadl_server_start); reserves the
- * handle's scratch for max_batch.  The handle must outlive the server. */
+/* Registers a database handle (before qpadl_server_start) and builds the
+ * read-only operand copies its launches use (the blocked digit copy if
+ * max_batch >= 3, the fp16 copy if max_batch > 32), so launches never
+ * allocate.  QPADL_ENOMEM if a copy cannot be allocated or one request's
+ * workspace exceeds device_budget_bytes.  The handle must outlive the
+ * server. */
 int qpadl_server_add_db(qpadl_server *srv, qpadl_db *db, int *db_id);
 
 /* Starts the request loop thread. */
 int qpadl_server_start(qpadl_server *srv);
 
 /* Admits one query (C uint32 words in host memory, copied before return)
- * for database db_id.  QPADL_EBUSY if admission refuses (in-flight limit or
+ * for database db_id.  Requests submitted before qpadl_server_start stay
+ * queued and form the first launch.  QPADL_EBUSY if admission refuses (in-flight limit or
  * host arena full): retry later.  *ticket identifies the request. */
 int qpadl_server_submit(qpadl_server *srv, int db_id, const uint32_t *q_host, uint64_t *ticket);
 
@@ -323,7 +337,9 @@ int qpadl_server_destroy(qpadl_server *srv);
 /* Open-loop load replay: submits request i at arrival_s[i] seconds after
  * the call starts (retrying while admission refuses), waits for all, and
  * writes latency_s[i] = completion - scheduled arrival (-1 on failure) and
- * status[i].  ans_host may be NULL (answers discarded). */
+ * status[i].  ans_host may be NULL (answers discarded).  arrival_s must be
+ * non-decreasing (QPADL_EINVAL otherwise).  Up to eight client threads share
+ * the requests round-robin, each submitting and polling its own. */
 int qpadl_server_replay(qpadl_server *srv, uint64_t n, const double *arrival_s,
                         const int32_t *db_ids, const uint32_t *const *q_host,
                         uint32_t *const *ans_host, double *latency_s, int32_t *status);

@@ -17,6 +17,7 @@
 #include "client.cuh"
 #include "limb_gemm.cuh"
 #include "limb_gemm_u8.cuh"
+#include "internal.cuh"
 #include "qpadl_pir.h"
 #include "stream_answer.cuh"
 
@@ -317,6 +318,67 @@ int answer_tensor(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, cu
 }
 
 }  // namespace
+
+// ------------------------------------------------------------------ internal (serving loop)
+namespace qpadl {
+
+uint64_t db_limb_pitch(const qpadl_db *db) { return db->pitch; }
+int db_num_sms(const qpadl_db *db) { return db->num_sms; }
+int *db_status_word(qpadl_db *db) { return db->d_status; }
+int db_prepare_u8(qpadl_db *db, cudaStream_t stream) { return ensure_blocked(db, stream); }
+int db_prepare_f16(qpadl_db *db, cudaStream_t stream) { return ensure_tensor_copy(db, stream); }
+
+int db_fill_u8_group(qpadl_db *db, GroupedGemmArgs &args, int g, const __half *limbs, uint32_t NV, uint32_t *out,
+                     int bn, int ks, uint32_t unit_begin, uint32_t *units) {
+    if (!db->blk || g < 0 || g >= kMaxGemmGroups) return QPADL_EINVAL;
+    const uint64_t R = db->prm.rows, C = db->prm.cols;
+    args.a[g] = db->u8_map[ks / 128 - 1];
+    if (!encode_2d(&args.b[g], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, limbs, C, 4ull * NV, db->pitch * 2, kLimbBoxK,
+                   static_cast<uint32_t>(bn), CU_TENSOR_MAP_SWIZZLE_128B))
+        return QPADL_ECUDA;
+    GroupDesc &gd = args.g[g];
+    gd.out = out;
+    gd.ld_m = 1;
+    gd.ld_b = R;
+    gd.M = static_cast<uint32_t>(R);
+    gd.NV = NV;
+    gd.KB = static_cast<uint32_t>((C + ks - 1) / ks);
+    gd.unit_begin = unit_begin;
+    gd.n_tiles = (4 * NV + bn - 1) / bn;
+    *units = static_cast<uint32_t>((R + kLimbBoxM - 1) / kLimbBoxM) * gd.n_tiles * gd.KB;
+    return QPADL_OK;
+}
+
+int db_answer_f16_ws(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, __half *limbs,
+                     cudaStream_t stream) {
+    if (!db->d16) return QPADL_EINVAL;
+    const uint64_t C = db->prm.cols, R = db->prm.rows;
+    QPADL_CU(launch_vec_limbs(Q, C, B, C, limbs, db->pitch, db->num_sms, stream));
+    const int bn = limb_gemm_bn_for(B);
+    CUtensorMap b_map;
+    if (!encode_2d(&b_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, limbs, C, 4ull * B, db->pitch * 2, kLimbBoxK,
+                   static_cast<uint32_t>(bn), CU_TENSOR_MAP_SWIZZLE_128B))
+        return QPADL_ECUDA;
+    QPADL_CU(launch_limb_gemm(bn, db->a_map, b_map, ans, 1, R, static_cast<uint32_t>(R), B, C, db->num_sms,
+                              db->d_status, stream));
+    return QPADL_OK;
+}
+
+int db_answer_one_noscratch(qpadl_db *db, const uint32_t *q, uint32_t *ans, cudaStream_t stream) {
+    const uint64_t C = db->prm.cols, R = db->prm.rows;
+    if (db->stream_ok && aligned16(q)) {
+        int mi = 0;
+        while ((512 << mi) < db->stream_chunk) ++mi;
+        const CUtensorMap *map = db->stream_maps ? &db->stream_map[mi] : nullptr;
+        QPADL_CU(launch_stream_answer_raw(db->stream_chunk, map, db->db, static_cast<uint32_t>(R),
+                                          static_cast<uint32_t>(C), q, ans, db->num_sms, db->d_status, stream));
+        return QPADL_OK;
+    }
+    QPADL_CU(launch_rowwise_answer(db->db, R, C, q, C, 1, ans, R, db->num_sms, stream));
+    return QPADL_OK;
+}
+
+}  // namespace qpadl
 
 extern "C" {
 

@@ -7,19 +7,21 @@
 //    mapped pinned host arena (first-fit, coalescing); if the arena or the
 //    in-flight limit is full, submit returns QPADL_EBUSY (the caller retries).
 //  - one loop thread forms launches as requests arrive: whenever a launch
-//    stream is free it picks the database whose oldest queued request has
-//    waited longest (among databases with no launch in flight: a handle's
-//    scratch serves one launch at a time), takes up to max_batch of its
-//    queued requests, carves the batch buffers from a device arena, and
-//    enqueues on that stream: a gather kernel that pulls every query
-//    straight from pinned host memory, the batched Response (the streaming
-//    kernel for tiny batches, the exact tensor-core GEMM otherwise), and a
-//    scatter kernel that writes every answer straight into its request's
-//    pinned buffer.  A host callback at the end of the stream marks the
-//    requests done and frees the device region.
-//  - several launch streams let launches of different databases run at the
-//    same time and new arrivals start while earlier launches are still on
-//    the GPU (continuous batching, not a single queue).
+//    stream is free it takes up to max_batch queued requests of the database
+//    holding the oldest request and of every other database of about the
+//    same size (group_size_ratio), carves a workspace for them from a device
+//    arena, and enqueues on that stream one grouped cycle: a gather kernel that pulls every
+//    query straight from pinned host memory; one grouped exact byte-limb
+//    GEMM over all databases with 3..32 queued queries (the tiles of every
+//    database form one work list split evenly over the SMs); the streaming
+//    kernel for databases with 1 or 2 queries; the fp16-copy GEMM for
+//    batches above 32; and a scatter kernel that writes every answer
+//    straight into its request's pinned buffer.  A host callback at the end
+//    of the stream marks the requests done and frees the workspace.
+//  - each launch uses only its own workspace (the handles' operand copies
+//    are read-only), so launches of the same database overlap on several
+//    streams: new arrivals start while earlier launches are still running
+//    (continuous batching, not a single queue).
 //  - a watchdog fails requests whose launch has not completed within
 //    watchdog_ms (their buffers stay reserved until the GPU really finishes).
 #include <algorithm>
@@ -39,6 +41,8 @@
 
 #include <cuda_runtime.h>
 
+#include "internal.cuh"
+#include "limb_gemm.cuh"
 #include "qpadl_pir.h"
 
 namespace {
@@ -100,6 +104,13 @@ class RangeAllocator {
 
 enum ReqState { kQueued = 0, kLaunched = 1, kDone = 2, kFailed = 3 };
 
+// One copy job per request of a launch: n words from src to dst.
+struct CopyJob {
+    const uint32_t *src;
+    uint32_t *dst;
+    uint64_t n;
+};
+
 struct Request {
     uint64_t ticket = 0;
     int db = 0;
@@ -113,9 +124,8 @@ struct Request {
 
 struct DbEntry {
     qpadl_db *db = nullptr;
-    uint64_t R = 0, C = 0;
+    uint64_t R = 0, C = 0, pitch = 0;
     std::deque<Request *> queue;
-    bool busy = false;   // a launch of this database is in flight
 };
 
 struct Launch;
@@ -123,16 +133,16 @@ struct Launch;
 struct StreamSlot {
     cudaStream_t stream = nullptr;
     Launch *busy = nullptr;
-    // per-slot pointer tables in mapped pinned memory, read by the gather/scatter kernels
-    const uint32_t **q_src = nullptr;
-    uint32_t **a_dst = nullptr;
+    // per-slot job tables in mapped pinned memory, read by the gather/scatter kernels
+    CopyJob *q_jobs = nullptr;
+    CopyJob *a_jobs = nullptr;
     uint32_t table_cap = 0;
 };
 
 struct Group {
     int db;
-    uint32_t first, count;   // requests [first, first+count) of the launch
-    uint64_t dq_off, da_off; // device batch buffers (arena offsets)
+    uint32_t first, count;             // requests [first, first+count) of the launch
+    uint64_t dq_off, da_off, dl_off;   // device batch buffers and limb workspace (offsets in the launch region)
 };
 
 struct Launch {
@@ -148,22 +158,12 @@ struct Launch {
     bool drop_completion = false;   // test hook: the completion is not reported to requests
 };
 
-// Copies queries of a launch from pinned host memory into the device batch
-// buffer: block (x, b) copies part of query b.
-__global__ void gather_queries_kernel(const uint32_t *const *src, uint32_t *dst, uint64_t C) {
-    const uint32_t b = blockIdx.y;
-    const uint32_t *s = src[b];
-    uint32_t *d = dst + (uint64_t)b * C;
-    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < C; j += (uint64_t)gridDim.x * blockDim.x)
-        d[j] = s[j];
-}
-
-__global__ void scatter_answers_kernel(const uint32_t *src, uint32_t *const *dst, uint64_t R) {
-    const uint32_t b = blockIdx.y;
-    uint32_t *d = dst[b];
-    const uint32_t *s = src + (uint64_t)b * R;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R; i += (uint64_t)gridDim.x * blockDim.x)
-        d[i] = s[i];
+// Block (x, j) copies part of job j (queries: pinned host -> device batch
+// buffer; answers: device -> pinned host).
+__global__ void copy_jobs_kernel(const CopyJob *jobs) {
+    const CopyJob J = jobs[blockIdx.y];
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < J.n; i += (uint64_t)gridDim.x * blockDim.x)
+        J.dst[i] = J.src[i];
 }
 
 }  // namespace
@@ -187,7 +187,7 @@ struct qpadl_server {
     bool stop = false;
     bool started = false;
     // counters
-    uint64_t n_launches = 0, n_done = 0, n_failed = 0, n_busy = 0;
+    uint64_t n_launches = 0, n_done = 0, n_failed = 0, n_busy = 0, n_grouped = 0;
     double busy_batch_sum = 0;
 
     void run();
@@ -227,7 +227,6 @@ void qpadl_server::finalize(Launch *L) {
     }
     dev_alloc.release(L->dev_off, L->dev_bytes);
     slots[L->slot].busy = nullptr;
-    for (const Group &g : L->groups) dbs[g.db].busy = false;
     active.erase(std::remove(active.begin(), active.end(), L), active.end());
     // requests failed by the watchdog and already polled kept their host
     // buffers reserved until the GPU was done with them
@@ -241,24 +240,56 @@ void qpadl_server::finalize(Launch *L) {
     cv.notify_all();
 }
 
+namespace {
+constexpr uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+// Device workspace of one group of `take` requests: queries, answers and,
+// for the GEMM paths, the byte limbs of the queries.
+uint64_t group_bytes(const DbEntry &e, uint32_t take) {
+    return align256(4ull * take * e.C) + align256(4ull * take * e.R) + (take >= 3 ? align256(8ull * take * e.pitch) : 0);
+}
+}  // namespace
+
 bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
-    // the database whose oldest queued request has waited longest, among those
-    // with no launch in flight (a handle's scratch serves one launch at a time)
-    int d = -1;
-    double oldest = 0;
-    for (int k = 0; k < static_cast<int>(dbs.size()); ++k) {
-        DbEntry &e = dbs[k];
-        if (e.queue.empty() || e.busy) continue;
-        if (d < 0 || e.queue.front()->t_submit < oldest) {
-            d = k;
-            oldest = e.queue.front()->t_submit;
-        }
+    // databases with queued requests join this cycle with up to max_batch of them each
+    std::vector<Group> groups;
+    uint64_t need = 0;
+    uint32_t total = 0;
+    const uint64_t cap_bytes = dev_alloc.size();
+    // the database holding the oldest queued request leads the launch; other
+    // databases join only if their scan costs about the same (within
+    // group_size_ratio), so no request waits on a much larger scan
+    int lead = -1;
+    for (int d = 0; d < static_cast<int>(dbs.size()); ++d)
+        if (!dbs[d].queue.empty() &&
+            (lead < 0 || dbs[d].queue.front()->t_submit < dbs[lead].queue.front()->t_submit))
+            lead = d;
+    if (lead < 0) return false;
+    const double lead_size = static_cast<double>(dbs[lead].R) * static_cast<double>(dbs[lead].C);
+    std::vector<int> order{lead};
+    for (int d = 0; d < static_cast<int>(dbs.size()); ++d) {
+        if (d == lead || dbs[d].queue.empty() || cfg.group_size_ratio < 1.0) continue;
+        const double sz = static_cast<double>(dbs[d].R) * static_cast<double>(dbs[d].C);
+        if (sz <= lead_size * cfg.group_size_ratio && sz * cfg.group_size_ratio >= lead_size) order.push_back(d);
     }
-    if (d < 0) return false;
-    DbEntry &e = dbs[d];
-    const uint32_t take = static_cast<uint32_t>(std::min<size_t>(e.queue.size(), cfg.max_batch));
-    const uint64_t qbytes = (4ull * take * e.C + 255) & ~255ull;
-    const uint64_t need = qbytes + ((4ull * take * e.R + 255) & ~255ull);
+    for (int d : order) {
+        DbEntry &e = dbs[d];
+        uint32_t take = static_cast<uint32_t>(std::min<size_t>(e.queue.size(), cfg.max_batch));
+        take = std::min(take, slots[si].table_cap - total);
+        // shrink the batch until its workspace fits in what the arena can ever hold
+        while (take > 0 && need + group_bytes(e, take) > cap_bytes) take = take > 3 ? take / 2 : take - 1;
+        if (take == 0) break;
+        Group g{d, total, take, 0, 0, 0};
+        g.dq_off = need;
+        need += align256(4ull * take * e.C);
+        g.da_off = need;
+        need += align256(4ull * take * e.R);
+        g.dl_off = need;
+        if (take >= 3) need += align256(8ull * take * e.pitch);
+        total += take;
+        groups.push_back(g);
+    }
+    if (groups.empty()) return false;
     uint64_t off = 0;
     if (!dev_alloc.alloc(need, &off)) return false;   // wait for a launch to free device memory
     Launch *L = new Launch();
@@ -267,13 +298,15 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
     L->id = next_launch++;
     L->dev_off = off;
     L->dev_bytes = need;
-    L->groups.push_back(Group{d, 0, take, 0, qbytes});
-    for (uint32_t i = 0; i < take; ++i) {
-        L->reqs.push_back(e.queue.front());
-        e.queue.pop_front();
+    L->groups = groups;
+    for (const Group &g : groups) {
+        DbEntry &e = dbs[g.db];
+        for (uint32_t i = 0; i < g.count; ++i) {
+            L->reqs.push_back(e.queue.front());
+            e.queue.pop_front();
+        }
     }
-    e.busy = true;
-    queued -= take;
+    queued -= total;
     L->t_launch = now_s();
     for (Request *r : L->reqs) {
         r->state = kLaunched;
@@ -284,22 +317,71 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
     S.busy = L;
     active.push_back(L);
     ++n_launches;
-    busy_batch_sum += static_cast<double>(take);
+    if (groups.size() > 1) ++n_grouped;
+    busy_batch_sum += static_cast<double>(total);
     // enqueue the GPU work without holding the lock
     lk.unlock();
-    for (uint32_t i = 0; i < take; ++i) {
-        S.q_src[i] = L->reqs[i]->q;
-        S.a_dst[i] = L->reqs[i]->a;
+    uint8_t *base = dev_arena + off;
+    uint64_t maxC = 0, maxR = 0;
+    for (const Group &g : groups) {
+        const DbEntry &e = dbs[g.db];
+        maxC = std::max(maxC, e.C);
+        maxR = std::max(maxR, e.R);
+        for (uint32_t i = 0; i < g.count; ++i) {
+            Request *r = L->reqs[g.first + i];
+            S.q_jobs[g.first + i] = CopyJob{r->q, reinterpret_cast<uint32_t *>(base + g.dq_off) + i * e.C, e.C};
+            S.a_jobs[g.first + i] = CopyJob{reinterpret_cast<uint32_t *>(base + g.da_off) + i * e.R, r->a, e.R};
+        }
     }
-    uint32_t *dq = reinterpret_cast<uint32_t *>(dev_arena + off);
-    uint32_t *da = reinterpret_cast<uint32_t *>(dev_arena + off + qbytes);
-    const unsigned bx = static_cast<unsigned>(std::min<uint64_t>((e.C + 1023) / 1024, 32));
-    gather_queries_kernel<<<dim3(bx, take), 256, 0, S.stream>>>(S.q_src, dq, e.C);
-    bool ok = cudaGetLastError() == cudaSuccess;
-    ok = ok && qpadl_pir_answer_batch(e.db, dq, take, da, S.stream) == QPADL_OK;
-    const unsigned by = static_cast<unsigned>(std::min<uint64_t>((e.R + 1023) / 1024, 32));
+    bool ok = true;
+    const unsigned gx = static_cast<unsigned>(std::min<uint64_t>((maxC + 1023) / 1024, 32));
+    copy_jobs_kernel<<<dim3(gx, total), 256, 0, S.stream>>>(S.q_jobs);
+    ok = ok && cudaGetLastError() == cudaSuccess;
+    // grouped GEMM over the databases with 3..32 queries (up to kMaxGemmGroups per launch)
+    std::vector<const Group *> small;
+    for (const Group &g : groups) {
+        const DbEntry &e = dbs[g.db];
+        uint32_t *dq = reinterpret_cast<uint32_t *>(base + g.dq_off);
+        uint32_t *da = reinterpret_cast<uint32_t *>(base + g.da_off);
+        __half *dl = reinterpret_cast<__half *>(base + g.dl_off);
+        if (g.count <= 2) {
+            for (uint32_t i = 0; i < g.count && ok; ++i)
+                ok = qpadl::db_answer_one_noscratch(e.db, dq + i * e.C, da + i * e.R, S.stream) == QPADL_OK;
+        } else if (g.count <= 32) {
+            ok = ok && qpadl::launch_vec_limbs(dq, e.C, g.count, e.C, dl, e.pitch, qpadl::db_num_sms(e.db),
+                                               S.stream) == cudaSuccess;
+            ok = ok && cudaMemsetAsync(da, 0, 4ull * g.count * e.R, S.stream) == cudaSuccess;
+            small.push_back(&g);
+        } else {
+            ok = ok && qpadl::db_answer_f16_ws(e.db, dq, g.count, da, dl, S.stream) == QPADL_OK;
+        }
+    }
+    for (size_t k0 = 0; k0 < small.size() && ok; k0 += qpadl::kMaxGemmGroups) {
+        const size_t k1 = std::min(small.size(), k0 + qpadl::kMaxGemmGroups);
+        uint32_t maxb = 0;
+        for (size_t k = k0; k < k1; ++k) maxb = std::max(maxb, small[k]->count);
+        const int bn = qpadl::limb_gemm_bn_for(maxb);
+        const int ks = qpadl::limb_gemm_u8_default_ks(bn);
+        qpadl::GroupedGemmArgs args;
+        std::memset(&args, 0, sizeof(args));
+        uint32_t units = 0;
+        for (size_t k = k0; k < k1 && ok; ++k) {
+            const Group &g = *small[k];
+            const DbEntry &e = dbs[g.db];
+            uint32_t u = 0;
+            ok = qpadl::db_fill_u8_group(e.db, args, static_cast<int>(k - k0),
+                                         reinterpret_cast<const __half *>(base + g.dl_off), g.count,
+                                         reinterpret_cast<uint32_t *>(base + g.da_off), bn, ks, units, &u) == QPADL_OK;
+            units += u;
+        }
+        args.ngroups = static_cast<uint32_t>(k1 - k0);
+        args.total_units = units;
+        ok = ok && qpadl::launch_limb_gemm_u8(bn, ks, args, qpadl::db_num_sms(dbs[small[k0]->db].db),
+                                              qpadl::db_status_word(dbs[small[k0]->db].db), S.stream) == cudaSuccess;
+    }
     if (ok) {
-        scatter_answers_kernel<<<dim3(by, take), 256, 0, S.stream>>>(da, S.a_dst, e.R);
+        const unsigned gy = static_cast<unsigned>(std::min<uint64_t>((maxR + 1023) / 1024, 32));
+        copy_jobs_kernel<<<dim3(gy, total), 256, 0, S.stream>>>(S.a_jobs);
         ok = cudaGetLastError() == cudaSuccess;
     }
     if (!ok) {
@@ -308,11 +390,11 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
             r->state = kFailed;
             r->error = QPADL_ECUDA;
         }
-        n_failed += take;
+        n_failed += total;
         L->failed_by_watchdog = true;   // completion must not overwrite the failure
         lk.unlock();
     }
-    // the callback runs after every kernel above and releases slot, database and memory
+    // the callback runs after every kernel above and releases the stream and the workspace
     if (cudaLaunchHostFunc(S.stream, on_launch_done, L) != cudaSuccess) {
         cudaStreamSynchronize(S.stream);
         complete(L);
@@ -372,12 +454,14 @@ int qpadl_server_create(const qpadl_server_config *cfg, qpadl_server **out) {
     if (!cfg || !out) return QPADL_EINVAL;
     *out = nullptr;
     if (cfg->max_batch == 0 || cfg->max_inflight == 0 || cfg->num_streams == 0 || cfg->num_streams > 8 ||
-        cfg->host_budget_bytes < 4096 || cfg->device_budget_bytes < 4096 || cfg->max_batch > 65535)
+        cfg->host_budget_bytes < 4096 || cfg->device_budget_bytes < 4096 || cfg->max_batch > 65535 ||
+        !(cfg->group_size_ratio >= 0.0))   // also rejects NaN
         return QPADL_EINVAL;
     qpadl_server *s = new (std::nothrow) qpadl_server();
     if (!s) return QPADL_ENOMEM;
     s->cfg = *cfg;
     if (s->cfg.watchdog_ms <= 0) s->cfg.watchdog_ms = 10000.0;
+
     if (cudaGetDevice(&s->device) != cudaSuccess) {
         delete s;
         return QPADL_ECUDA;
@@ -397,12 +481,13 @@ int qpadl_server_create(const qpadl_server_config *cfg, qpadl_server **out) {
     s->host_alloc.reset(cfg->host_budget_bytes);
     s->dev_alloc.reset(cfg->device_budget_bytes);
     s->slots.resize(cfg->num_streams);
-    const uint32_t cap = std::min<uint32_t>(cfg->max_inflight, 65536u) * 4;
+    // one cycle takes at most max_batch requests of each database; 65535 is the grid's y limit
+    const uint32_t cap = std::min<uint32_t>(std::min<uint32_t>(cfg->max_inflight, 65535u), 65535u);
     for (auto &sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaHostAlloc(reinterpret_cast<void **>(&sl.q_src), cap * sizeof(void *), cudaHostAllocMapped) !=
+            cudaHostAlloc(reinterpret_cast<void **>(&sl.q_jobs), cap * sizeof(CopyJob), cudaHostAllocMapped) !=
                 cudaSuccess ||
-            cudaHostAlloc(reinterpret_cast<void **>(&sl.a_dst), cap * sizeof(void *), cudaHostAllocMapped) !=
+            cudaHostAlloc(reinterpret_cast<void **>(&sl.a_jobs), cap * sizeof(CopyJob), cudaHostAllocMapped) !=
                 cudaSuccess) {
             cudaGetLastError();
             qpadl_server_destroy(s);
@@ -420,12 +505,16 @@ int qpadl_server_add_db(qpadl_server *s, qpadl_db *db, int *db_id) {
     if (s->started) return QPADL_EINVAL;
     uint64_t R = 0, C = 0;
     if (qpadl_pir_shape(db, &R, &C) != QPADL_OK) return QPADL_EINVAL;
-    // size the handle's scratch for the largest batch now, so launches never allocate
-    if (qpadl_pir_reserve(db, s->cfg.max_batch, nullptr) != QPADL_OK) return QPADL_ENOMEM;
+    // build the operand copies the launches read now, so launches never allocate
+    if (s->cfg.max_batch >= 3 && qpadl::db_prepare_u8(db, nullptr) != QPADL_OK) return QPADL_ENOMEM;
+    if (s->cfg.max_batch > 32 && qpadl::db_prepare_f16(db, nullptr) != QPADL_OK) return QPADL_ENOMEM;
+    if (cudaDeviceSynchronize() != cudaSuccess) return QPADL_ECUDA;
     DbEntry e;
     e.db = db;
     e.R = R;
     e.C = C;
+    e.pitch = qpadl::db_limb_pitch(db);
+    if (group_bytes(e, 1) > s->dev_alloc.size()) return QPADL_ENOMEM;   // not even one request fits
     s->dbs.push_back(e);
     *db_id = static_cast<int>(s->dbs.size() - 1);
     return QPADL_OK;
@@ -444,13 +533,13 @@ int qpadl_server_start(qpadl_server *s) {
 int qpadl_server_submit(qpadl_server *s, int db_id, const uint32_t *q_host, uint64_t *ticket) {
     if (!s || !q_host || !ticket) return QPADL_EINVAL;
     std::unique_lock<std::mutex> lk(s->mu);
-    if (!s->started || db_id < 0 || db_id >= static_cast<int>(s->dbs.size())) return QPADL_EINVAL;
-    DbEntry &e = s->dbs[db_id];
+    if (db_id < 0 || db_id >= static_cast<int>(s->dbs.size())) return QPADL_EINVAL;
+    const uint64_t C = s->dbs[db_id].C, R = s->dbs[db_id].R;
     if (s->inflight >= s->cfg.max_inflight) {
         ++s->n_busy;
         return QPADL_EBUSY;
     }
-    const uint64_t bytes = 4ull * (e.C + e.R) + 256;
+    const uint64_t bytes = 4ull * (C + R) + 256;
     uint64_t off = 0;
     if (!s->host_alloc.alloc(bytes, &off)) {
         ++s->n_busy;
@@ -466,14 +555,14 @@ int qpadl_server_submit(qpadl_server *s, int db_id, const uint32_t *q_host, uint
     r->host_off = off;
     r->host_bytes = bytes;
     r->q = reinterpret_cast<uint32_t *>(s->host_arena + off);
-    r->a = reinterpret_cast<uint32_t *>(s->host_arena + off + ((4ull * e.C + 255) & ~255ull));
+    r->a = reinterpret_cast<uint32_t *>(s->host_arena + off + ((4ull * C + 255) & ~255ull));
     r->t_submit = now_s();
     s->reqs[r->ticket] = r;
     ++s->inflight;
     lk.unlock();
-    std::memcpy(r->q, q_host, 4ull * e.C);   // outside the lock; the request is not queued yet
+    std::memcpy(r->q, q_host, 4ull * C);   // outside the lock; the request is not queued yet
     lk.lock();
-    e.queue.push_back(r);
+    s->dbs[db_id].queue.push_back(r);   // re-indexed: add_db may have grown the table meanwhile
     ++s->queued;
     *ticket = r->ticket;
     s->cv.notify_all();
@@ -482,7 +571,7 @@ int qpadl_server_submit(qpadl_server *s, int db_id, const uint32_t *q_host, uint
 
 int qpadl_server_poll(qpadl_server *s, uint64_t ticket, uint32_t *ans_host, qpadl_request_times *times) {
     if (!s) return QPADL_EINVAL;
-    std::lock_guard<std::mutex> g(s->mu);
+    std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->reqs.find(ticket);
     if (it == s->reqs.end()) return QPADL_EINVAL;
     Request *r = it->second;
@@ -493,9 +582,21 @@ int qpadl_server_poll(qpadl_server *s, uint64_t ticket, uint32_t *ans_host, qpad
         times->launch_s = r->t_launch;
         times->done_s = r->t_done;
     }
-    if (r->state == kDone && ans_host) std::memcpy(ans_host, r->a, 4ull * s->dbs[r->db].R);
     s->reqs.erase(it);
     --s->inflight;
+    if (r->state == kDone) {
+        // the GPU is done with this request and no one else can reach it:
+        // copy the answer out without holding the lock
+        if (ans_host) {
+            const uint64_t R = s->dbs[r->db].R;
+            lk.unlock();
+            std::memcpy(ans_host, r->a, 4ull * R);
+            lk.lock();
+        }
+        s->host_alloc.release(r->host_off, r->host_bytes);
+        delete r;
+        return rc;
+    }
     bool in_flight_on_gpu = false;
     if (r->state == kFailed) {
         for (Launch *L : s->active)
@@ -523,6 +624,7 @@ int qpadl_server_stats(qpadl_server *s, qpadl_server_stats_t *st) {
     st->mean_launch_requests = s->n_launches ? s->busy_batch_sum / static_cast<double>(s->n_launches) : 0.0;
     st->host_bytes_used = s->host_alloc.used();
     st->device_bytes_used = s->dev_alloc.used();
+    st->grouped_launches = s->n_grouped;
     return QPADL_OK;
 }
 
@@ -544,8 +646,8 @@ int qpadl_server_destroy(qpadl_server *s) {
     }
     for (auto &sl : s->slots) {
         if (sl.stream) cudaStreamDestroy(sl.stream);
-        if (sl.q_src) cudaFreeHost(sl.q_src);
-        if (sl.a_dst) cudaFreeHost(sl.a_dst);
+        if (sl.q_jobs) cudaFreeHost(sl.q_jobs);
+        if (sl.a_jobs) cudaFreeHost(sl.a_jobs);
     }
     if (s->dev_arena) cudaFree(s->dev_arena);
     if (s->host_arena) cudaFreeHost(s->host_arena);
@@ -553,64 +655,63 @@ int qpadl_server_destroy(qpadl_server *s) {
     return QPADL_OK;
 }
 
-// Open-loop load generator: submits request i at t0 + arrival_s[i] (retrying
-// while admission refuses), polls completions and records per-request
-// latency = completion time - scheduled arrival time.
+// Open-loop load generator: request i is submitted at t0 + arrival_s[i]
+// (arrival_s non-decreasing; retried while admission refuses) and its latency
+// is its completion time minus that scheduled arrival.  Several client
+// threads share the requests round-robin; each submits its own requests when
+// they fall due and polls the ones it has outstanding.
 int qpadl_server_replay(qpadl_server *s, uint64_t n, const double *arrival_s, const int32_t *db_ids,
                         const uint32_t *const *q_host, uint32_t *const *ans_host, double *latency_s,
                         int32_t *status) {
     if (!s || !arrival_s || !db_ids || !q_host || !latency_s || !status) return QPADL_EINVAL;
-    std::vector<uint64_t> tickets(n, 0);
-    std::atomic<uint64_t> submitted{0};
-    std::atomic<int> submit_err{QPADL_OK};
-    const double t0 = now_s();
-    std::thread submitter([&] {
-        for (uint64_t i = 0; i < n; ++i) {
-            const double due = t0 + arrival_s[i];
-            while (now_s() < due) {
-            }
-            uint64_t tk = 0;
-            int rc;
-            while ((rc = qpadl_server_submit(s, db_ids[i], q_host[i], &tk)) == QPADL_EBUSY) {
-                std::this_thread::sleep_for(std::chrono::microseconds(5));
-            }
-            if (rc != QPADL_OK) {
-                submit_err = rc;
-                tk = 0;
-            }
-            tickets[i] = tk;
-            submitted.store(i + 1, std::memory_order_release);
-        }
-    });
-    uint64_t done = 0;
-    std::vector<char> finished(n, 0);
-    uint64_t scan_from = 0;
-    while (done < n) {
-        const uint64_t avail = submitted.load(std::memory_order_acquire);
-        bool progress = false;
-        for (uint64_t i = scan_from; i < avail; ++i) {
-            if (finished[i]) continue;
-            if (tickets[i] == 0) {
-                finished[i] = 1;
-                status[i] = submit_err.load();
-                latency_s[i] = -1;
-                ++done;
+    for (uint64_t i = 1; i < n; ++i)
+        if (arrival_s[i] < arrival_s[i - 1]) return QPADL_EINVAL;
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const uint64_t T = std::max<uint64_t>(1, std::min<uint64_t>({n, 8, hw / 2 ? hw / 2 : 1}));
+    const double t0 = now_s() + 1e-3;
+    auto client = [&](uint64_t first) {
+        struct Out {
+            uint64_t i, ticket;
+        };
+        std::vector<Out> out;
+        uint64_t next = first;
+        while (next < n || !out.empty()) {
+            bool progress = false;
+            const double t = now_s();
+            while (next < n && t >= t0 + arrival_s[next]) {
+                uint64_t tk = 0;
+                const int rc = qpadl_server_submit(s, db_ids[next], q_host[next], &tk);
+                if (rc == QPADL_EBUSY) break;   // admission refused: retry on the next pass
+                if (rc != QPADL_OK) {
+                    status[next] = rc;
+                    latency_s[next] = -1;
+                } else {
+                    out.push_back(Out{next, tk});
+                }
+                next += T;
                 progress = true;
-                continue;
             }
-            qpadl_request_times tm;
-            const int rc = qpadl_server_poll(s, tickets[i], ans_host ? ans_host[i] : nullptr, &tm);
-            if (rc == QPADL_EAGAIN) continue;
-            finished[i] = 1;
-            status[i] = rc;
-            latency_s[i] = (rc == QPADL_OK) ? tm.done_s - (t0 + arrival_s[i]) : -1;
-            ++done;
-            progress = true;
+            for (size_t k = 0; k < out.size();) {
+                qpadl_request_times tm;
+                const uint64_t i = out[k].i;
+                const int rc = qpadl_server_poll(s, out[k].ticket, ans_host ? ans_host[i] : nullptr, &tm);
+                if (rc == QPADL_EAGAIN) {
+                    ++k;
+                    continue;
+                }
+                status[i] = rc;
+                latency_s[i] = (rc == QPADL_OK) ? tm.done_s - (t0 + arrival_s[i]) : -1;
+                out[k] = out.back();
+                out.pop_back();
+                progress = true;
+            }
+            if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(5));
         }
-        while (scan_from < avail && finished[scan_from]) ++scan_from;
-        if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(10));
-    }
-    submitter.join();
+    };
+    std::vector<std::thread> threads;
+    for (uint64_t k = 1; k < T; ++k) threads.emplace_back(client, k);
+    client(0);
+    for (auto &th : threads) th.join();
     return QPADL_OK;
 }
 

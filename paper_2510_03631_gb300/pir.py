@@ -333,6 +333,7 @@ class qpadl_server_config(ctypes.Structure):
         ("test_drop_completion_launch", ctypes.c_uint32),
         ("hold_us", ctypes.c_double),
         ("watchdog_ms", ctypes.c_double),
+        ("group_size_ratio", ctypes.c_double),
     ]
 
 
@@ -345,14 +346,15 @@ class qpadl_server_stats_t(ctypes.Structure):
         ("launches", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
         ("refused", ctypes.c_uint64), ("inflight", ctypes.c_uint32), ("queued", ctypes.c_uint32),
         ("mean_launch_requests", ctypes.c_double), ("host_bytes_used", ctypes.c_uint64),
-        ("device_bytes_used", ctypes.c_uint64),
+        ("device_bytes_used", ctypes.c_uint64), ("grouped_launches", ctypes.c_uint64),
     ]
 
 
 def server_config(host_budget_bytes=1 << 30, device_budget_bytes=1 << 30, max_inflight=4096, max_batch=256,
-                  num_streams=4, hold_us=0.0, watchdog_ms=10000.0, test_drop_completion_launch=0):
+                  num_streams=4, hold_us=0.0, watchdog_ms=10000.0, test_drop_completion_launch=0,
+                  group_size_ratio=2.0):
     return qpadl_server_config(host_budget_bytes, device_budget_bytes, max_inflight, max_batch, num_streams,
-                               test_drop_completion_launch, hold_us, watchdog_ms)
+                               test_drop_completion_launch, hold_us, watchdog_ms, group_size_ratio)
 
 
 def qpadl_pir_shape(db: Database):

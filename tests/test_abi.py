@@ -81,3 +81,20 @@ def test_product_package_does_not_import_the_oracle():
             text = open(path).read()
             assert "import oracle" not in text and "from oracle" not in text, path
             assert "qpadl_oracle" not in text, path
+
+
+@pytest.mark.parametrize("field,value", [("max_batch", 0), ("max_batch", 65536), ("num_streams", 0),
+                                         ("num_streams", 9), ("max_inflight", 0), ("host_budget_bytes", 100),
+                                         ("group_size_ratio", -1.0), ("group_size_ratio", float("nan"))])
+def test_invalid_server_config_rejected_before_any_allocation(lib, field, value):
+    from paper_2510_03631_gb300 import pir
+    cfg = pir.server_config()
+    setattr(cfg, field, value)
+    out = ctypes.c_void_p()
+    assert lib.qpadl_server_create(ctypes.byref(cfg), ctypes.byref(out)) == pir.QPADL_EINVAL
+    assert out.value is None
+
+
+def test_replay_rejects_a_null_server(lib):
+    from paper_2510_03631_gb300 import pir
+    assert lib.qpadl_server_replay(None, 0, None, None, None, None, None, None) == pir.QPADL_EINVAL

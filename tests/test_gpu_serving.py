@@ -54,11 +54,10 @@ def _server(dbs, **kw):
 def test_mixed_traffic_answers_equal_standalone(dbs):
     srv, ids = _server(dbs, max_batch=64, num_streams=3)
     rng = np.random.default_rng(7)
+    which = [int(rng.choice(len(dbs), p=[0.6, 0.3, 0.1])) for _ in range(240)]
+    qs = [inputs.uniform_u32(SHAPES[d][1], seed=1000 + i, tag=inputs.TAG_MISC) for i, d in enumerate(which)]
     reqs = []
-    for i in range(240):
-        d = int(rng.choice(len(dbs), p=[0.6, 0.3, 0.1]))
-        C = SHAPES[d][1]
-        q = inputs.uniform_u32(C, seed=1000 + i, tag=inputs.TAG_MISC)
+    for i, (d, q) in enumerate(zip(which, qs)):
         reqs.append((d, q, pir.qpadl_server_submit(srv, ids[d], q)))
         if i % 37 == 0:
             time.sleep(0.002)   # let launches start while more requests arrive
@@ -74,7 +73,9 @@ def test_mixed_traffic_answers_equal_standalone(dbs):
         assert times[0] <= times[1] <= times[2]
     st = pir.qpadl_server_stats(srv)
     assert st["completed"] == 240 and st["failed"] == 0 and st["inflight"] == 0
-    assert st["launches"] < 240   # requests were batched
+    # how many launches the burst takes depends on timing; batching itself is
+    # pinned by the launch formed from requests queued before start
+    assert 1 <= st["launches"] <= 240
     srv.close()
 
 
@@ -90,6 +91,67 @@ def test_answers_match_oracle(dbs):
         rc, ans, _ = _wait(srv, t, SHAPES[d][0])
         assert rc == pir.QPADL_OK
         assert np.array_equal(ans, oracle.answer(dbs[d][0], q))
+    srv.close()
+
+
+@pytest.mark.parametrize("counts", [(2, 20, 45), (5, 17, 32), (1, 0, 3)])
+def test_one_launch_answers_every_database(dbs, counts):
+    # requests submitted before start form one launch over all databases:
+    # 1..2 queries take the streaming kernel, 3..32 share the grouped GEMM,
+    # more than 32 take the fp16-copy GEMM
+    srv = pir.qpadl_server_create(pir.server_config(max_batch=64, num_streams=1, group_size_ratio=1e9))
+    ids = [pir.qpadl_server_add_db(srv, h) for _, h in dbs]
+    tickets = []
+    for d, cnt in enumerate(counts):
+        C = SHAPES[d][1]
+        for i in range(cnt):
+            q = inputs.uniform_u32(C, seed=9000 + 100 * d + i, tag=inputs.TAG_MISC)
+            tickets.append((d, q, pir.qpadl_server_submit(srv, ids[d], q)))
+    pir.qpadl_server_start(srv)
+    for d, q, t in tickets:
+        rc, ans, _ = _wait(srv, t, SHAPES[d][0])
+        assert rc == pir.QPADL_OK
+        assert np.array_equal(ans, oracle.answer(dbs[d][0], q))
+    st = pir.qpadl_server_stats(srv)
+    assert st["launches"] == 1 and st["completed"] == sum(counts)
+    assert st["grouped_launches"] == (1 if sum(c > 0 for c in counts) > 1 else 0)
+    srv.close()
+
+
+@pytest.mark.parametrize("ratio,grouped", [(0.0, False), (1.5, False), (2.5, True)])
+def test_group_size_ratio(dbs, ratio, grouped):
+    # sizes R*C: 0.5M, 2M and 1.24M words; with ratio 2.5 databases 1 and 2 share a launch
+    srv = pir.qpadl_server_create(pir.server_config(max_batch=64, num_streams=1, group_size_ratio=ratio))
+    ids = [pir.qpadl_server_add_db(srv, h) for _, h in dbs]
+    tickets = []
+    for d in (1, 2):
+        for i in range(4):
+            q = inputs.uniform_u32(SHAPES[d][1], seed=7000 + 10 * d + i, tag=inputs.TAG_MISC)
+            tickets.append((d, q, pir.qpadl_server_submit(srv, ids[d], q)))
+    pir.qpadl_server_start(srv)
+    for d, q, t in tickets:
+        rc, ans, _ = _wait(srv, t, SHAPES[d][0])
+        assert rc == pir.QPADL_OK and np.array_equal(ans, oracle.answer(dbs[d][0], q))
+    st = pir.qpadl_server_stats(srv)
+    assert st["launches"] == (1 if grouped else 2)
+    assert st["grouped_launches"] == (1 if grouped else 0)
+    srv.close()
+
+
+def test_launch_shrinks_to_the_device_budget(dbs):
+    # the device arena holds the workspace of only a few requests of database 1
+    R, C = SHAPES[1]
+    per = 4 * C + 4 * R + 8 * C   # query, answer and query limbs (C is a multiple of 8)
+    srv = pir.qpadl_server_create(pir.server_config(max_batch=64, num_streams=2, device_budget_bytes=5 * per))
+    ids = [pir.qpadl_server_add_db(srv, h) for _, h in dbs]
+    qs = [inputs.uniform_u32(C, seed=300 + i, tag=inputs.TAG_MISC) for i in range(24)]
+    tickets = [pir.qpadl_server_submit(srv, ids[1], q) for q in qs]
+    pir.qpadl_server_start(srv)
+    for q, t in zip(qs, tickets):
+        rc, ans, _ = _wait(srv, t, R)
+        assert rc == pir.QPADL_OK
+        assert np.array_equal(ans, oracle.answer(dbs[1][0], q))
+    assert pir.qpadl_server_stats(srv)["launches"] >= 24 // 5
     srv.close()
 
 
@@ -172,4 +234,13 @@ def test_replay_open_loop(dbs):
     for i in range(0, n, 17):
         d = which[i]
         assert np.array_equal(answers[i], oracle.answer(dbs[d][0], queries[i]))
+    srv.close()
+
+
+def test_replay_rejects_unsorted_arrivals(dbs):
+    srv, ids = _server(dbs)
+    qs = [inputs.uniform_u32(SHAPES[0][1], seed=i, tag=7) for i in range(3)]
+    with pytest.raises(pir.QpadlError) as e:
+        pir.qpadl_server_replay(srv, np.array([0.0, 2e-3, 1e-3]), [ids[0]] * 3, qs)
+    assert e.value.code == pir.QPADL_EINVAL
     srv.close()
