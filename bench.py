@@ -329,7 +329,7 @@ def serving_measure(torch, pir, inputs, rates, duration_s, single_db_one_ms, see
 # ----------------------------------------------------------------------------- GPU arm
 def run_ours(args):
     import torch
-    from paper_2510_03631_gb300 import inputs, pir
+    from paper_2510_03631_gb300 import inputs, pir, replicas
 
     rank, world, local = _dist()
     torch.cuda.set_device(local)
@@ -434,10 +434,9 @@ def run_ours(args):
     if pir.qpadl_pir_status(db) != 0:
         raise SystemExit("bench: device status word set")
 
-    if dist is not None:
-        t = torch.tensor([step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    # the job's step time is the slowest rank's
+    step_ms = replicas.max_over_ranks(step_ms, dist, device="cuda")
+    resp_ms_avg = replicas.max_over_ranks(resp_ms_avg, dist, device="cuda")
 
     alg_bytes = R * C + 4 * C + 4 * R
     peak, peak_kind = _peaks()
@@ -513,7 +512,7 @@ def run_ours(args):
         H_np = pir.as_u32(H).reshape(R, n)
         cpu = cpu_oracle_sample(D_np, A_np, H_np, budget_s=args.cpu_budget)
 
-    gbs = world * R * C / (step_ms * 1e-3) / 1e9
+    gbs = replicas.job_rate(R * C, world, step_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC,
         "value": round(gbs, 2),

@@ -126,6 +126,19 @@ uint64_t qpadl_pir_device_bytes(const qpadl_db *db);
 /* Shape of a handle's database: *rows = R, *cols = C. */
 int qpadl_pir_shape(const qpadl_db *db, uint64_t *rows, uint64_t *cols);
 
+/*
+ * Row shard of a database for one of `world` GPUs (host only; no device
+ * access).  Answer row i depends on database row i alone (ans = D qu, Def. 1
+ * DB.Query.Response), so rank r may hold rows [*r0, *r1) of D and of H,
+ * answer every query on them, and the ranks' answers concatenate in rank
+ * order with no reduction.  Shards are whole 128-row tiles (the GEMM tile
+ * height) except the last, as even as that allows; a rank may get an empty
+ * shard when rows < 128 * world.  A shard is set up as its own handle:
+ * qpadl_pir_setup with rows = *r1 - *r0 and db_dev + *r0 * C.
+ * QPADL_EINVAL if world == 0, rank >= world or an output pointer is NULL.
+ */
+int qpadl_pir_shard_rows(uint64_t rows, uint32_t world, uint32_t rank, uint64_t *r0, uint64_t *r1);
+
 /* Pre-sizes the handle's scratch so that later Response calls with batches
  * of up to max_batch queries allocate nothing (tensor-core operand copy of D
  * and limb scratch when max_batch reaches the tensor-core threshold).  May

@@ -500,6 +500,15 @@ int qpadl_pir_shape(const qpadl_db *db, uint64_t *rows, uint64_t *cols) {
     return QPADL_OK;
 }
 
+int qpadl_pir_shard_rows(uint64_t rows, uint32_t world, uint32_t rank, uint64_t *r0, uint64_t *r1) {
+    if (world == 0 || rank >= world || !r0 || !r1) return QPADL_EINVAL;
+    const uint64_t tiles = (rows + kLimbBoxM - 1) / kLimbBoxM;
+    const uint64_t t0 = tiles * rank / world, t1 = tiles * (rank + 1ull) / world;
+    *r0 = std::min<uint64_t>(rows, t0 * kLimbBoxM);
+    *r1 = std::min<uint64_t>(rows, t1 * kLimbBoxM);
+    return QPADL_OK;
+}
+
 int qpadl_pir_reserve(qpadl_db *db, uint32_t max_batch, qpadl_stream_t stream) {
     if (!db || max_batch == 0) return QPADL_EINVAL;
     if (set_device(db) != QPADL_OK) return QPADL_ECUDA;

@@ -81,6 +81,8 @@ _SIGS = {
     "qpadl_pir_recover": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
     "qpadl_pir_shape": ([_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "qpadl_pir_reserve": ([_P, ctypes.c_uint32, _P], ctypes.c_int),
+    "qpadl_pir_shard_rows": ([ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
+                              ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "qpadl_server_create": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
     "qpadl_server_add_db": ([_P, _P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "qpadl_server_start": ([_P], ctypes.c_int),
@@ -361,6 +363,14 @@ def qpadl_pir_shape(db: Database):
     r, c = ctypes.c_uint64(), ctypes.c_uint64()
     _check(load().qpadl_pir_shape(db.handle, ctypes.byref(r), ctypes.byref(c)), "qpadl_pir_shape")
     return int(r.value), int(c.value)
+
+
+def qpadl_pir_shard_rows(rows: int, world: int, rank: int):
+    """Rows [r0, r1) that rank `rank` of `world` holds (host only)."""
+    r0, r1 = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().qpadl_pir_shard_rows(int(rows), int(world), int(rank), ctypes.byref(r0), ctypes.byref(r1)),
+           "qpadl_pir_shard_rows")
+    return int(r0.value), int(r1.value)
 
 
 def qpadl_pir_reserve(db: Database, max_batch: int, stream=None):
