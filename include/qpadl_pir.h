@@ -267,6 +267,52 @@ int qpadl_pir_recover_batch(const qpadl_params *prm, const uint32_t *ans_dev,
                             uint8_t *out_dev, qpadl_stream_t stream);
 
 /* ======================================================================
+ * Client context: batched Query and Recover on the tensor cores
+ * (Def. 1 Client.Query and Client.BlockReconst for many secrets at once).
+ *
+ * X s mod 2^32 (X = A or H, uint32) needs only the byte-limb products
+ * x_u s_l with u + l <= 3.  The context keeps X's four balanced byte-limb
+ * planes (fp16, side by side along K: rows x 4n) on the device; each call
+ * expands the secrets into shifted limb rows and runs one exact tcgen05 GEMM
+ * whose epilogue is Query's (+ e_b + Delta at col_b) or Recover's
+ * (round((ans_b - .)/Delta) mod p).  Results equal qpadl_pir_query_batch /
+ * qpadl_pir_recover_batch bit for bit.
+ * ==================================================================== */
+typedef struct qpadl_client qpadl_client;
+
+/* Builds the context on the current device from A_dev (C x n uint32) and,
+ * if H_dev is not NULL, the hint H_dev (R x n uint32); both are read only
+ * during the call (the context keeps limb-plane copies: 8 C n and 8 R n
+ * bytes) plus a workspace for max_batch secrets (32 n max_batch bytes;
+ * larger calls run in chunks of max_batch).  prm gives R, C, n and p.
+ * QPADL_EINVAL for bad parameters, a NULL A_dev or max_batch outside
+ * 1..65536; QPADL_ENOMEM if device memory runs out.  Calls on one context
+ * share its workspace: issue them on one stream (or order them). */
+int qpadl_client_create(const qpadl_params *prm, const uint32_t *A_dev, const uint32_t *H_dev,
+                        uint32_t max_batch, qpadl_stream_t stream, qpadl_client **out);
+
+/* B queries: S_dev B x n (secret b in row b), E_dev B x C int32, cols_dev B
+ * target columns (each < C, not checked on the host), Q_dev B x C. */
+int qpadl_client_query_batch(qpadl_client *c, const uint32_t *S_dev, const int32_t *E_dev,
+                             const uint32_t *cols_dev, uint32_t B, uint32_t *Q_dev,
+                             qpadl_stream_t stream);
+
+/* B recoveries: ans_dev B x R, S_dev B x n, out_dev B x R digits.
+ * QPADL_EINVAL if the context was built without H. */
+int qpadl_client_recover_batch(qpadl_client *c, const uint32_t *ans_dev, const uint32_t *S_dev,
+                               uint32_t B, uint8_t *out_dev, qpadl_stream_t stream);
+
+/* Synchronises the device; QPADL_ETIMEOUT (and clears it) if a kernel of
+ * this context gave up a bounded wait since the last call. */
+int qpadl_client_status(qpadl_client *c);
+
+/* Bytes of device memory the context owns. */
+uint64_t qpadl_client_device_bytes(const qpadl_client *c);
+
+/* Waits for the device and frees the context (NULL is fine). */
+int qpadl_client_destroy(qpadl_client *c);
+
+/* ======================================================================
  * Serving: a continuous-batching request loop over several resident
  * databases (the paper's server answering q-bar queries per database,
  * Sec. 5.2, run as a long-lived service).  Requests arrive from any host

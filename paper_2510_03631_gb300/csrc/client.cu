@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include "client.cuh"
+#include "epilogues.cuh"
 
 namespace qpadl {
 
@@ -32,35 +33,6 @@ __global__ void gen_a_kernel(uint64_t seed, uint64_t total, uint32_t *__restrict
     for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride)
         A[e] = static_cast<uint32_t>(splitmix64_at(seed, e) >> 32);
 }
-
-// Epilogues shared by the matvec and the GEMM.
-struct QueryEpi {
-    const int32_t *e;        // noise, row b at e + b * e_ld
-    uint64_t e_ld;
-    const uint32_t *cols;    // target column per vector (device) or nullptr
-    uint64_t col;            // target column when cols == nullptr
-    uint32_t delta;
-    uint32_t *q;             // output, vector b at q + b * q_ld
-    uint64_t q_ld;
-    __device__ __forceinline__ void operator()(uint64_t j, uint32_t b, uint32_t dot) const {
-        const uint64_t target = cols ? cols[b] : col;
-        uint32_t v = dot + static_cast<uint32_t>(e[b * e_ld + j]);
-        if (j == target) v += delta;
-        q[b * q_ld + j] = v;
-    }
-};
-
-struct RecoverEpi {
-    const uint32_t *ans;     // answer b at ans + b * ans_ld
-    uint64_t ans_ld;
-    uint32_t shift;          // 32 - log2 p
-    uint8_t *out;            // digits of vector b at out + b * out_ld
-    uint64_t out_ld;
-    __device__ __forceinline__ void operator()(uint64_t i, uint32_t b, uint32_t dot) const {
-        const uint32_t x = ans[b * ans_ld + i] - dot;
-        out[b * out_ld + i] = static_cast<uint8_t>((x + (1u << (shift - 1))) >> shift);
-    }
-};
 
 // y = X[i] . w for every row i of X (rows x n), then epilogue(i, 0, y).
 template <class Epi>
@@ -210,10 +182,16 @@ __global__ void __launch_bounds__(256) u32_gemm_nt_kernel(const uint32_t *__rest
     for (int a = 0; a < 8; ++a) {
         const uint64_t i = i0 + ty + 16 * a;
         if (i >= M) continue;
+        uint32_t pre_v[8];   // all loads of the row's outputs before any of its stores
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const uint32_t b = b0 + tx + 16 * c;
-            if (b < N) epi(i, b, acc[a][c]);
+            pre_v[c] = b < N ? epi.pre(i, b) : 0u;
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint32_t b = b0 + tx + 16 * c;
+            if (b < N) epi.put(i, b, acc[a][c], pre_v[c]);
         }
     }
 }

@@ -1,0 +1,65 @@
+// Output epilogues of the client steps and of the limb GEMM.  Each is called
+// once per output element with (row of the matrix operand, vector index,
+// the mod-2^32 dot product of that row with that vector).  pre() gathers
+// what the element needs from memory and put() finishes it, so a caller
+// with many elements per thread can issue all their loads before any store
+// (a store through one pointer could otherwise alias the next load, which
+// serialises every element behind a full memory round trip).
+#pragma once
+#include <cstdint>
+
+namespace qpadl {
+
+// Plain store: out[i * ld_m + b * ld_b] = dot.
+struct StoreEpi {
+    uint32_t *out;
+    uint64_t ld_m, ld_b;
+    __device__ __forceinline__ uint32_t pre(uint64_t, uint32_t) const { return 0u; }
+    __device__ __forceinline__ void put(uint64_t i, uint32_t b, uint32_t dot, uint32_t) const {
+        out[i * ld_m + (uint64_t)b * ld_b] = dot;
+    }
+    __device__ __forceinline__ void operator()(uint64_t i, uint32_t b, uint32_t dot) const { put(i, b, dot, 0u); }
+};
+
+// Query (Def. 1 Client.Query): q_b[j] = (A s_b)[j] + e_b[j] + Delta [j == col_b]  mod 2^32.
+struct QueryEpi {
+    const int32_t *e;        // noise, row b at e + b * e_ld
+    uint64_t e_ld;
+    const uint32_t *cols;    // target column per vector (device) or nullptr
+    uint64_t col;            // target column when cols == nullptr
+    uint32_t delta;
+    uint32_t *q;             // output, vector b at q + b * q_ld
+    uint64_t q_ld;
+    // e_b[j] + Delta [j == col_b]
+    __device__ __forceinline__ uint32_t pre(uint64_t j, uint32_t b) const {
+        const uint64_t target = cols ? cols[b] : col;
+        return static_cast<uint32_t>(e[b * e_ld + j]) + (j == target ? delta : 0u);
+    }
+    __device__ __forceinline__ void put(uint64_t j, uint32_t b, uint32_t dot, uint32_t pre_v) const {
+        q[b * q_ld + j] = dot + pre_v;
+    }
+    __device__ __forceinline__ void operator()(uint64_t j, uint32_t b, uint32_t dot) const {
+        put(j, b, dot, pre(j, b));
+    }
+};
+
+// Recover (Def. 1 Client.BlockReconst): d_b[i] = round((ans_b[i] - (H s_b)[i]) / Delta) mod p,
+// as (x + Delta/2) >> (32 - log2 p) in uint32 arithmetic.
+struct RecoverEpi {
+    const uint32_t *ans;     // answer b at ans + b * ans_ld
+    uint64_t ans_ld;
+    uint32_t shift;          // 32 - log2 p
+    uint8_t *out;            // digits of vector b at out + b * out_ld
+    uint64_t out_ld;
+    // ans_b[i]
+    __device__ __forceinline__ uint32_t pre(uint64_t i, uint32_t b) const { return ans[b * ans_ld + i]; }
+    __device__ __forceinline__ void put(uint64_t i, uint32_t b, uint32_t dot, uint32_t a) const {
+        const uint32_t x = a - dot;
+        out[b * out_ld + i] = static_cast<uint8_t>((x + (1u << (shift - 1))) >> shift);
+    }
+    __device__ __forceinline__ void operator()(uint64_t i, uint32_t b, uint32_t dot) const {
+        put(i, b, dot, pre(i, b));
+    }
+};
+
+}  // namespace qpadl

@@ -25,11 +25,26 @@
 //               thread issues tcgen05.mma M=128, N=BN, K=16 (4 per stage).
 //   warps 2..5  epilogue: drain one accumulator per 512-deep K-chunk while
 //               the MMA fills the other.
-// Output element (row i, vector b) goes to out[i * ld_m + b * ld_b].
+// Output element (row i, vector b) goes through an epilogue functor: a plain
+// store for the Response and the hint, the Query or Recover epilogue when the
+// matrix operand is the limb planes of A or H (client batches, below).
+//
+// Client batches (Def. 1 Client.Query / Client.BlockReconst for B secrets).
+// For a uint32 matrix X (A or H) and secrets S, (X s_b)[i] mod 2^32 needs
+// the limb products a_u * s_l with u + l <= 3 only (the others are multiples
+// of 2^32).  The matrix operand holds X's limb planes side by side along K
+// (row i: [x_0[i][.], x_1[i][.], x_2[i][.], x_3[i][.]], 4n entries) and the
+// vector operand holds, for secret b and shift t, the row
+// [s_t, s_{t-1}, .., s_0, 0, ..] (limb t-u of s_b under plane u, zero for
+// u > t).  Their product is sum_{u <= t} x_u . s_{t-u}, the coefficient of
+// 2^{8t}, and the usual recombination sum_t 2^{8t} (.) gives X s_b mod 2^32.
+// Every product is at most 128 * 128 in magnitude, so a 512-deep chunk is
+// exact in fp32 here as well.
 #include <cstdint>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "epilogues.cuh"
 #include "limb_gemm.cuh"
 #include "ptx.cuh"
 
@@ -60,11 +75,10 @@ __device__ __forceinline__ bool drain_wait_g(uint64_t *bar, uint32_t parity) {
     return true;
 }
 
-template <int BN>
+template <int BN, class Epi>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     limb_gemm_kernel(const __grid_constant__ CUtensorMap a_map, const __grid_constant__ CUtensorMap b_map,
-                     uint32_t *__restrict__ out, uint64_t ld_m, uint64_t ld_b, uint32_t M, uint32_t NV,
-                     uint32_t KB, int *__restrict__ status) {
+                     Epi epi, uint32_t M, uint32_t NV, uint32_t KB, int *__restrict__ status) {
     using Cfg = GemmCfg<BN>;
     constexpr int QPT = Cfg::kQPT;
     extern __shared__ uint8_t smem_raw[];
@@ -224,10 +238,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             if (failed) break;
             const uint32_t row = m0 + quarter * 32u + static_cast<uint32_t>(lane);
             if (row < M) {
+                // groups of up to 16 outputs: all their loads first, then all their stores
+                constexpr int G = QPT < 16 ? QPT : 16;
 #pragma unroll
-                for (int q = 0; q < QPT; ++q) {
-                    const uint32_t vi = v0 + q;
-                    if (vi < NV) out[(uint64_t)row * ld_m + (uint64_t)vi * ld_b] = run[q];
+                for (int g = 0; g < QPT; g += G) {
+                    uint32_t pre_v[G];
+#pragma unroll
+                    for (int q = 0; q < G; ++q) pre_v[q] = (v0 + g + q < NV) ? epi.pre(row, v0 + g + q) : 0u;
+#pragma unroll
+                    for (int q = 0; q < G; ++q)
+                        if (v0 + g + q < NV) epi.put(row, v0 + g + q, run[g + q], pre_v[q]);
                 }
             }
         }
@@ -331,20 +351,66 @@ __global__ void mat_col_limbs_kernel(const uint32_t *__restrict__ A, uint64_t C,
     }
 }
 
+// X (uint32, rows x n row-major) -> its limb planes side by side (fp16,
+// rows x pitch): L[i][u * n + k] = limb u of X[i][k].  Entries past 4n are
+// never read (the tensor map ends at 4n).
+__global__ void mat_row_limbs_kernel(const uint32_t *__restrict__ X, uint64_t rows, uint32_t n,
+                                     __half *__restrict__ L, uint64_t pitch) {
+    const uint64_t total = rows * n;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = e / n;
+        const uint32_t k = static_cast<uint32_t>(e - i * n);
+        float c[4];
+        balanced_limbs(X[e], c);
+        __half *dst = L + i * pitch + k;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dst[(uint64_t)u * n] = __float2half_rn(c[u]);
+    }
+}
+
+// S (uint32, B x n, secret b in row b) -> shifted limb rows (fp16, 4B x
+// pitch): row 4b + t holds limb t-u of s_b under plane u (u <= t), zero
+// under planes u > t.
+__global__ void secret_limbs_kernel(const uint32_t *__restrict__ S, uint32_t B, uint32_t n,
+                                    __half *__restrict__ V, uint64_t pitch) {
+    const uint64_t total = (uint64_t)B * n;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t b = e / n;
+        const uint32_t k = static_cast<uint32_t>(e - b * n);
+        float c[4];
+        balanced_limbs(S[e], c);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            __half *row = V + (4 * b + t) * pitch + k;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) row[(uint64_t)u * n] = __float2half_rn(u <= t ? c[t - u] : 0.0f);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ host side
-template <int BN>
+template <int BN, class Epi>
 static cudaError_t set_gemm_attr() {
-    return cudaFuncSetAttribute(limb_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(limb_gemm_kernel<BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 GemmCfg<BN>::kSmemBytes);
+}
+
+template <class Epi>
+static cudaError_t set_gemm_attrs() {
+    cudaError_t e;
+    if ((e = set_gemm_attr<32, Epi>()) != cudaSuccess) return e;
+    if ((e = set_gemm_attr<64, Epi>()) != cudaSuccess) return e;
+    if ((e = set_gemm_attr<128, Epi>()) != cudaSuccess) return e;
+    return set_gemm_attr<256, Epi>();
 }
 
 cudaError_t prepare_limb_gemm_kernels() {
     cudaError_t e;
-    if ((e = set_gemm_attr<32>()) != cudaSuccess) return e;
-    if ((e = set_gemm_attr<64>()) != cudaSuccess) return e;
-    if ((e = set_gemm_attr<128>()) != cudaSuccess) return e;
-    if ((e = set_gemm_attr<256>()) != cudaSuccess) return e;
-    return cudaSuccess;
+    if ((e = set_gemm_attrs<StoreEpi>()) != cudaSuccess) return e;
+    if ((e = set_gemm_attrs<QueryEpi>()) != cudaSuccess) return e;
+    return set_gemm_attrs<RecoverEpi>();
 }
 
 int limb_gemm_bn_for(uint32_t nv) {
@@ -355,28 +421,50 @@ int limb_gemm_bn_for(uint32_t nv) {
     return 256;
 }
 
-template <int BN>
-static cudaError_t launch_bn(const CUtensorMap &a_map, const CUtensorMap &b_map, uint32_t *out, uint64_t ld_m,
-                             uint64_t ld_b, uint32_t M, uint32_t NV, uint32_t KB, int grid, int *status,
-                             cudaStream_t stream) {
-    limb_gemm_kernel<BN><<<grid, kGemmThreads, GemmCfg<BN>::kSmemBytes, stream>>>(a_map, b_map, out, ld_m, ld_b, M,
-                                                                                  NV, KB, status);
+template <class Epi>
+static cudaError_t launch_epi(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, const Epi &epi, uint32_t M,
+                              uint32_t NV, uint64_t K, int num_sms, int *status, cudaStream_t stream) {
+    const uint32_t KB = static_cast<uint32_t>((K + kBK - 1) / kBK);
+    const uint64_t tiles = (uint64_t)((M + kBM - 1) / kBM) * ((4ull * NV + bn - 1) / bn);
+    const int grid = static_cast<int>(tiles < (uint64_t)num_sms ? tiles : (uint64_t)num_sms);
+    switch (bn) {
+        case 32:
+            limb_gemm_kernel<32, Epi><<<grid, kGemmThreads, GemmCfg<32>::kSmemBytes, stream>>>(a_map, b_map, epi, M,
+                                                                                               NV, KB, status);
+            break;
+        case 64:
+            limb_gemm_kernel<64, Epi><<<grid, kGemmThreads, GemmCfg<64>::kSmemBytes, stream>>>(a_map, b_map, epi, M,
+                                                                                               NV, KB, status);
+            break;
+        case 128:
+            limb_gemm_kernel<128, Epi><<<grid, kGemmThreads, GemmCfg<128>::kSmemBytes, stream>>>(a_map, b_map, epi,
+                                                                                                 M, NV, KB, status);
+            break;
+        case 256:
+            limb_gemm_kernel<256, Epi><<<grid, kGemmThreads, GemmCfg<256>::kSmemBytes, stream>>>(a_map, b_map, epi,
+                                                                                                 M, NV, KB, status);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_limb_gemm(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, uint32_t *out,
                              uint64_t ld_m, uint64_t ld_b, uint32_t M, uint32_t NV, uint64_t K, int num_sms,
                              int *status, cudaStream_t stream) {
-    const uint32_t KB = static_cast<uint32_t>((K + kBK - 1) / kBK);
-    const uint64_t tiles = (uint64_t)((M + kBM - 1) / kBM) * ((4ull * NV + bn - 1) / bn);
-    const int grid = static_cast<int>(tiles < (uint64_t)num_sms ? tiles : (uint64_t)num_sms);
-    switch (bn) {
-        case 32: return launch_bn<32>(a_map, b_map, out, ld_m, ld_b, M, NV, KB, grid, status, stream);
-        case 64: return launch_bn<64>(a_map, b_map, out, ld_m, ld_b, M, NV, KB, grid, status, stream);
-        case 128: return launch_bn<128>(a_map, b_map, out, ld_m, ld_b, M, NV, KB, grid, status, stream);
-        case 256: return launch_bn<256>(a_map, b_map, out, ld_m, ld_b, M, NV, KB, grid, status, stream);
-        default: return cudaErrorInvalidValue;
-    }
+    return launch_epi(bn, a_map, b_map, StoreEpi{out, ld_m, ld_b}, M, NV, K, num_sms, status, stream);
+}
+
+cudaError_t launch_limb_gemm_query(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, const QueryEpi &epi,
+                                   uint32_t M, uint32_t NV, uint64_t K, int num_sms, int *status,
+                                   cudaStream_t stream) {
+    return launch_epi(bn, a_map, b_map, epi, M, NV, K, num_sms, status, stream);
+}
+
+cudaError_t launch_limb_gemm_recover(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map,
+                                     const RecoverEpi &epi, uint32_t M, uint32_t NV, uint64_t K, int num_sms,
+                                     int *status, cudaStream_t stream) {
+    return launch_epi(bn, a_map, b_map, epi, M, NV, K, num_sms, status, stream);
 }
 
 cudaError_t launch_db_to_f16(const uint8_t *D, uint64_t R, uint64_t C, __half *D16, uint64_t pitch, int num_sms,
@@ -397,6 +485,18 @@ cudaError_t launch_mat_col_limbs(const uint32_t *A, uint64_t C, uint32_t n, __ha
                                  cudaStream_t stream) {
     dim3 grid(static_cast<unsigned>((C + 31) / 32), (n + 31) / 32);
     mat_col_limbs_kernel<<<grid, dim3(32, 8), 0, stream>>>(A, C, n, L, pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mat_row_limbs(const uint32_t *X, uint64_t rows, uint32_t n, __half *L, uint64_t pitch, int num_sms,
+                                 cudaStream_t stream) {
+    mat_row_limbs_kernel<<<num_sms * 8, 256, 0, stream>>>(X, rows, n, L, pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_secret_limbs(const uint32_t *S, uint32_t B, uint32_t n, __half *V, uint64_t pitch, int num_sms,
+                                cudaStream_t stream) {
+    secret_limbs_kernel<<<num_sms * 4, 256, 0, stream>>>(S, B, n, V, pitch);
     return cudaGetLastError();
 }
 

@@ -5,6 +5,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "epilogues.cuh"
+
 namespace qpadl {
 
 constexpr int kLimbBoxK = 64;    // fp16 elements per TMA box row (128 bytes, 128-byte swizzle)
@@ -21,11 +23,24 @@ cudaError_t launch_limb_gemm(int bn, const CUtensorMap &a_map, const CUtensorMap
                              uint64_t ld_m, uint64_t ld_b, uint32_t M, uint32_t NV, uint64_t K, int num_sms,
                              int *status, cudaStream_t stream);
 
+// The same product with the Query / Recover epilogue (client batches: a_map
+// covers the limb planes of A or H, b_map the shifted secret limb rows).
+cudaError_t launch_limb_gemm_query(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, const QueryEpi &epi,
+                                   uint32_t M, uint32_t NV, uint64_t K, int num_sms, int *status,
+                                   cudaStream_t stream);
+cudaError_t launch_limb_gemm_recover(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map,
+                                     const RecoverEpi &epi, uint32_t M, uint32_t NV, uint64_t K, int num_sms,
+                                     int *status, cudaStream_t stream);
+
 cudaError_t launch_db_to_f16(const uint8_t *D, uint64_t R, uint64_t C, __half *D16, uint64_t pitch, int num_sms,
                              cudaStream_t stream);
 cudaError_t launch_vec_limbs(const uint32_t *X, uint64_t x_ld, uint32_t NV, uint64_t C, __half *L, uint64_t pitch,
                              int num_sms, cudaStream_t stream);
 cudaError_t launch_mat_col_limbs(const uint32_t *A, uint64_t C, uint32_t n, __half *L, uint64_t pitch,
                                  cudaStream_t stream);
+cudaError_t launch_mat_row_limbs(const uint32_t *X, uint64_t rows, uint32_t n, __half *L, uint64_t pitch, int num_sms,
+                                 cudaStream_t stream);
+cudaError_t launch_secret_limbs(const uint32_t *S, uint32_t B, uint32_t n, __half *V, uint64_t pitch, int num_sms,
+                                cudaStream_t stream);
 
 }  // namespace qpadl

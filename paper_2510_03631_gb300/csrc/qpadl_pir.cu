@@ -4,6 +4,7 @@
 // and the choice of kernel; the arithmetic lives in stream_answer.cu
 // (single/few-query Response), limb_gemm.cu (batched Response and hint) and
 // client.cu (Setup's generator, Query, Recover).
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -53,6 +54,21 @@ struct qpadl_db {
     // host-buffer calls
     uint32_t *stage_q = nullptr;
     uint32_t *stage_ans = nullptr;
+    uint64_t owned_bytes = 0;
+};
+
+// Client context for batched Query / Recover on the tensor cores.
+struct qpadl_client {
+    qpadl_params prm;
+    int device = 0;
+    int num_sms = 0;
+    uint32_t max_batch = 0;
+    uint64_t pitch = 0;              // fp16 elements per limb-plane row: roundup(4n, 8)
+    __half *a_planes = nullptr;      // C x pitch: limb planes of A side by side
+    __half *h_planes = nullptr;      // R x pitch: limb planes of H (optional)
+    __half *v = nullptr;             // 4 max_batch x pitch: shifted secret limbs
+    CUtensorMap a_map, h_map;
+    int *d_status = nullptr;
     uint64_t owned_bytes = 0;
 };
 
@@ -676,5 +692,153 @@ int qpadl_pir_recover_batch(const qpadl_params *prm, const uint32_t *ans_dev, co
                                   reinterpret_cast<cudaStream_t>(stream)));
     return QPADL_OK;
 }
+
+// ------------------------------------------------------------------ client context
+
+int qpadl_client_destroy(qpadl_client *c) {
+    if (!c) return QPADL_OK;
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != c->device) cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    if (c->a_planes) cudaFree(c->a_planes);
+    if (c->h_planes) cudaFree(c->h_planes);
+    if (c->v) cudaFree(c->v);
+    if (c->d_status) cudaFree(c->d_status);
+    if (cur >= 0 && cur != c->device) cudaSetDevice(cur);
+    delete c;
+    return QPADL_OK;
+}
+
+int qpadl_client_create(const qpadl_params *prm, const uint32_t *A_dev, const uint32_t *H_dev, uint32_t max_batch,
+                        qpadl_stream_t stream, qpadl_client **out) {
+    if (!out) return QPADL_EINVAL;
+    *out = nullptr;
+    int rc = validate_params(prm);
+    if (rc != QPADL_OK) return rc;
+    if (!A_dev || max_batch == 0 || max_batch > 65536) return QPADL_EINVAL;
+    qpadl_client *c = new (std::nothrow) qpadl_client();
+    if (!c) return QPADL_ENOMEM;
+    c->prm = *prm;
+    c->max_batch = max_batch;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    auto fail = [&](int code) {
+        qpadl_client_destroy(c);
+        return code;
+    };
+    auto alloc = [&](void **p, uint64_t bytes) {
+        if (cudaMalloc(p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return false;
+        }
+        c->owned_bytes += bytes;
+        return true;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) return fail(QPADL_ECUDA);
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        return fail(QPADL_ECUDA);
+    if ((rc = prepare_device(c->device)) != QPADL_OK) return fail(rc);
+    const uint64_t n = prm->n, R = prm->rows, C = prm->cols;
+    c->pitch = (4 * n + 7) / 8 * 8;
+    if (!alloc(reinterpret_cast<void **>(&c->d_status), 16)) return fail(QPADL_ENOMEM);
+    if (!alloc(reinterpret_cast<void **>(&c->a_planes), 2 * C * c->pitch)) return fail(QPADL_ENOMEM);
+    if (H_dev && !alloc(reinterpret_cast<void **>(&c->h_planes), 2 * R * c->pitch)) return fail(QPADL_ENOMEM);
+    if (!alloc(reinterpret_cast<void **>(&c->v), 2ull * 4 * max_batch * c->pitch)) return fail(QPADL_ENOMEM);
+    if (cudaMemsetAsync(c->d_status, 0, 16, s) != cudaSuccess) return fail(QPADL_ECUDA);
+    if (cuda_fail(launch_mat_row_limbs(A_dev, C, prm->n, c->a_planes, c->pitch, c->num_sms, s), "A limb planes") !=
+        QPADL_OK)
+        return fail(QPADL_ECUDA);
+    if (!encode_2d(&c->a_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, c->a_planes, 4 * n, C, c->pitch * 2, kLimbBoxK,
+                   kLimbBoxM, CU_TENSOR_MAP_SWIZZLE_128B))
+        return fail(QPADL_ECUDA);
+    if (H_dev) {
+        if (cuda_fail(launch_mat_row_limbs(H_dev, R, prm->n, c->h_planes, c->pitch, c->num_sms, s),
+                      "H limb planes") != QPADL_OK)
+            return fail(QPADL_ECUDA);
+        if (!encode_2d(&c->h_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, c->h_planes, 4 * n, R, c->pitch * 2, kLimbBoxK,
+                       kLimbBoxM, CU_TENSOR_MAP_SWIZZLE_128B))
+            return fail(QPADL_ECUDA);
+    }
+    *out = c;
+    return QPADL_OK;
+}
+
+namespace {
+
+int client_set_device(const qpadl_client *c) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return QPADL_ECUDA;
+    if (cur != c->device && cudaSetDevice(c->device) != cudaSuccess) return QPADL_ECUDA;
+    return QPADL_OK;
+}
+
+// Shifted secret limbs of Bc secrets into c->v and the tensor map over them.
+int client_secret_operand(qpadl_client *c, const uint32_t *S, uint32_t Bc, int bn, CUtensorMap *map,
+                          cudaStream_t s) {
+    const uint32_t n = c->prm.n;
+    QPADL_CU(launch_secret_limbs(S, Bc, n, c->v, c->pitch, c->num_sms, s));
+    if (!encode_2d(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, c->v, 4ull * n, 4ull * Bc, c->pitch * 2, kLimbBoxK,
+                   static_cast<uint32_t>(bn), CU_TENSOR_MAP_SWIZZLE_128B))
+        return QPADL_ECUDA;
+    return QPADL_OK;
+}
+
+}  // namespace
+
+int qpadl_client_query_batch(qpadl_client *c, const uint32_t *S_dev, const int32_t *E_dev, const uint32_t *cols_dev,
+                             uint32_t B, uint32_t *Q_dev, qpadl_stream_t stream) {
+    if (!c || !S_dev || !E_dev || !cols_dev || !Q_dev || B == 0) return QPADL_EINVAL;
+    if (client_set_device(c) != QPADL_OK) return QPADL_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t C = c->prm.cols, n = c->prm.n;
+    const uint32_t delta = static_cast<uint32_t>((1ull << 32) / c->prm.p);
+    for (uint32_t b0 = 0; b0 < B; b0 += c->max_batch) {
+        const uint32_t Bc = std::min(B - b0, c->max_batch);
+        const int bn = limb_gemm_bn_for(Bc);
+        CUtensorMap v_map;
+        int rc = client_secret_operand(c, S_dev + (uint64_t)b0 * n, Bc, bn, &v_map, s);
+        if (rc != QPADL_OK) return rc;
+        const QueryEpi epi{E_dev + (uint64_t)b0 * C, C, cols_dev + b0, 0, delta, Q_dev + (uint64_t)b0 * C, C};
+        QPADL_CU(launch_limb_gemm_query(bn, c->a_map, v_map, epi, static_cast<uint32_t>(C), Bc, 4 * n, c->num_sms,
+                                        c->d_status, s));
+    }
+    return QPADL_OK;
+}
+
+int qpadl_client_recover_batch(qpadl_client *c, const uint32_t *ans_dev, const uint32_t *S_dev, uint32_t B,
+                               uint8_t *out_dev, qpadl_stream_t stream) {
+    if (!c || !ans_dev || !S_dev || !out_dev || B == 0 || !c->h_planes) return QPADL_EINVAL;
+    if (client_set_device(c) != QPADL_OK) return QPADL_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t R = c->prm.rows, n = c->prm.n;
+    const uint32_t shift = 32u - static_cast<uint32_t>(log2_exact(c->prm.p));
+    for (uint32_t b0 = 0; b0 < B; b0 += c->max_batch) {
+        const uint32_t Bc = std::min(B - b0, c->max_batch);
+        const int bn = limb_gemm_bn_for(Bc);
+        CUtensorMap v_map;
+        int rc = client_secret_operand(c, S_dev + (uint64_t)b0 * n, Bc, bn, &v_map, s);
+        if (rc != QPADL_OK) return rc;
+        const RecoverEpi epi{ans_dev + (uint64_t)b0 * R, R, shift, out_dev + (uint64_t)b0 * R, R};
+        QPADL_CU(launch_limb_gemm_recover(bn, c->h_map, v_map, epi, static_cast<uint32_t>(R), Bc, 4 * n,
+                                          c->num_sms, c->d_status, s));
+    }
+    return QPADL_OK;
+}
+
+int qpadl_client_status(qpadl_client *c) {
+    if (!c) return QPADL_EINVAL;
+    if (client_set_device(c) != QPADL_OK) return QPADL_ECUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return QPADL_ECUDA;
+    int st = 0;
+    if (cudaMemcpy(&st, c->d_status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return QPADL_ECUDA;
+    if (st != 0) {
+        const int zero = 0;
+        cudaMemcpy(c->d_status, &zero, 4, cudaMemcpyHostToDevice);
+        return QPADL_ETIMEOUT;
+    }
+    return QPADL_OK;
+}
+
+uint64_t qpadl_client_device_bytes(const qpadl_client *c) { return c ? c->owned_bytes : 0; }
 
 }  // extern "C"

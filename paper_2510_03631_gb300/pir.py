@@ -83,6 +83,12 @@ _SIGS = {
     "qpadl_pir_reserve": ([_P, ctypes.c_uint32, _P], ctypes.c_int),
     "qpadl_pir_shard_rows": ([ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
                               ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "qpadl_client_create": ([_P, _P, _P, ctypes.c_uint32, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "qpadl_client_query_batch": ([_P, _P, _P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
+    "qpadl_client_recover_batch": ([_P, _P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
+    "qpadl_client_status": ([_P], ctypes.c_int),
+    "qpadl_client_device_bytes": ([_P], ctypes.c_uint64),
+    "qpadl_client_destroy": ([_P], ctypes.c_int),
     "qpadl_server_create": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
     "qpadl_server_add_db": ([_P, _P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "qpadl_server_start": ([_P], ctypes.c_int),
@@ -311,6 +317,66 @@ def qpadl_pir_recover_batch(prm: qpadl_params, ans: torch.Tensor, H: torch.Tenso
         _dev(S, torch.int32, B * n, "S"), B, _dev(out, torch.uint8, B * R, "out"), _stream(stream)),
         "qpadl_pir_recover_batch")
     return out
+
+
+class Client:
+    """Handle returned by qpadl_client_create (owns the C context)."""
+
+    def __init__(self, handle: ctypes.c_void_p, prm: qpadl_params, has_hint: bool):
+        self.handle = handle
+        self.prm = prm
+        self.has_hint = has_hint
+
+    def close(self):
+        if self.handle:
+            load().qpadl_client_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qpadl_client_create(prm: qpadl_params, A: torch.Tensor, H: torch.Tensor | None = None, max_batch: int = 1024,
+                        stream=None) -> Client:
+    C, R, n = int(prm.cols), int(prm.rows), int(prm.n)
+    pa = _dev(A, torch.int32, C * n, "A")
+    ph = _dev(H, torch.int32, R * n, "H") if H is not None else None
+    h = ctypes.c_void_p()
+    _check(load().qpadl_client_create(ctypes.byref(prm), pa, ph, int(max_batch), _stream(stream), ctypes.byref(h)),
+           "qpadl_client_create")
+    return Client(h, prm, H is not None)
+
+
+def qpadl_client_query_batch(c: Client, S: torch.Tensor, E: torch.Tensor, cols: torch.Tensor, Q: torch.Tensor,
+                             stream=None) -> torch.Tensor:
+    C, n = int(c.prm.cols), int(c.prm.n)
+    B = int(cols.numel())
+    _check(load().qpadl_client_query_batch(
+        c.handle, _dev(S, torch.int32, B * n, "S"), _dev(E, torch.int32, B * C, "E"),
+        _dev(cols, torch.int32, B, "cols"), B, _dev(Q, torch.int32, B * C, "Q"), _stream(stream)),
+        "qpadl_client_query_batch")
+    return Q
+
+
+def qpadl_client_recover_batch(c: Client, ans: torch.Tensor, S: torch.Tensor, out: torch.Tensor,
+                               stream=None) -> torch.Tensor:
+    R, n = int(c.prm.rows), int(c.prm.n)
+    B = S.numel() // n
+    _check(load().qpadl_client_recover_batch(
+        c.handle, _dev(ans, torch.int32, B * R, "ans"), _dev(S, torch.int32, B * n, "S"), B,
+        _dev(out, torch.uint8, B * R, "out"), _stream(stream)), "qpadl_client_recover_batch")
+    return out
+
+
+def qpadl_client_status(c: Client) -> int:
+    return int(load().qpadl_client_status(c.handle))
+
+
+def qpadl_client_device_bytes(c: Client) -> int:
+    return int(load().qpadl_client_device_bytes(c.handle))
 
 
 def as_u32(t: torch.Tensor):

@@ -3,6 +3,7 @@
     python -m paper_2510_03631_gb300.profile_cases stream --rows 8192 --cols 32768 --reps 3
     python -m paper_2510_03631_gb300.profile_cases gemm   --rows 8192 --cols 32768 --batch 256 --reps 2
     python -m paper_2510_03631_gb300.profile_cases hint   --rows 8192 --cols 32768 --n 1024 --reps 1
+    python -m paper_2510_03631_gb300.profile_cases qbatch --cols 32768 --n 1024 --batch 1024 --client 1
 
 Each case builds one database of the given size on cuda:0 (uniform digits,
 seed 1), runs the chosen entry point `reps` times after one warm-up call,
@@ -22,6 +23,11 @@ import torch
 from . import inputs, pir
 
 
+def _dots(X: np.ndarray, s: np.ndarray) -> np.ndarray:
+    """Row dot products X s mod 2^32 (uint64 products wrap mod 2^64, which keeps the low 32 bits)."""
+    return ((X.astype(np.uint64) * s.astype(np.uint64)[None, :]).sum(axis=1) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+
+
 def _row_check(D_row: np.ndarray, X: np.ndarray, got: np.ndarray):
     exp = (X.astype(np.uint64) * D_row.astype(np.uint64)[None, :]).sum(axis=1) & np.uint64(0xFFFFFFFF)
     if not np.array_equal(exp.astype(np.uint32), got):
@@ -30,7 +36,7 @@ def _row_check(D_row: np.ndarray, X: np.ndarray, got: np.ndarray):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["stream", "gemm", "hint", "query", "recover"])
+    ap.add_argument("case", choices=["stream", "gemm", "hint", "query", "recover", "qbatch", "rbatch"])
     ap.add_argument("--rows", type=int, default=8192)
     ap.add_argument("--cols", type=int, default=32768)
     ap.add_argument("--batch", type=int, default=256)
@@ -40,6 +46,8 @@ def main():
     ap.add_argument("--raw", type=int, default=-1, help="1: single query packed inside the kernel")
     ap.add_argument("--u8max", type=int, default=-1, help="largest batch on the uint8-digit GEMM")
     ap.add_argument("--kstep", type=int, default=-1, help="digits per row per stage of that GEMM")
+    ap.add_argument("--client", type=int, default=1, help="qbatch/rbatch: 1 = tensor-core client context, "
+                                                            "0 = CUDA-core batch entry point")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     R, C = a.rows, a.cols
@@ -92,6 +100,52 @@ def main():
         out_row = None
         res["alg_bytes"] = rows * n * 4 + 4 * n + 8 * rows
         res["n"] = n
+    elif a.case in ("qbatch", "rbatch"):
+        # B queries over A (C x n) or B recoveries over H (R x n)
+        n, B = a.n, a.batch
+        rows = C if a.case == "qbatch" else R
+        X = torch.empty(rows * n, dtype=torch.int32, device="cuda")
+        pir.qpadl_pir_gen_a(pir.params(R, rows, n, seed=3), X)
+        S_np = inputs.secrets(B, n, seed=4)
+        S = pir.from_u32(S_np.reshape(-1))
+        cprm = pir.params(R if a.case == "rbatch" else 1, rows if a.case == "qbatch" else C, n)
+        cl = None
+        if a.case == "qbatch":
+            E_np = inputs.noise_batch(B, rows, seed=5)
+            E = torch.from_numpy(E_np.reshape(-1)).cuda()
+            cols = inputs.target_columns(B, rows, seed=6)
+            cols_t = torch.from_numpy(cols.astype(np.int32)).cuda()
+            Q = torch.empty(B * rows, dtype=torch.int32, device="cuda")
+            if a.client:
+                cl = pir.qpadl_client_create(cprm, X, None, max_batch=B)
+                fn = lambda: pir.qpadl_client_query_batch(cl, S, E, cols_t, Q)
+            else:
+                fn = lambda: pir.qpadl_pir_query_batch(cprm, X, S, E, cols_t, Q)
+            def check():
+                # first query, sampled rows: dot + e + Delta at the target column
+                idx = np.unique(np.r_[0:64, rows - 64:rows, int(cols[0])].clip(0, rows - 1))
+                exp = _dots(pir.as_u32(X).reshape(rows, n)[idx], S_np[0]) + E_np[0][idx].astype(np.uint32)
+                exp = exp + np.where(idx == int(cols[0]), np.uint32(1 << 24), np.uint32(0))
+                return np.array_equal(pir.as_u32(Q)[:rows][idx], exp.astype(np.uint32))
+        else:
+            ans_np = inputs.uniform_u32(B * rows, seed=6, tag=inputs.TAG_MISC)
+            ans = pir.from_u32(ans_np)
+            out = torch.empty(B * rows, dtype=torch.uint8, device="cuda")
+            Xr = X
+            if a.client:
+                A_dummy = torch.zeros(C * n, dtype=torch.int32, device="cuda")
+                cl = pir.qpadl_client_create(cprm, A_dummy, Xr, max_batch=B)
+                fn = lambda: pir.qpadl_client_recover_batch(cl, ans, S, out)
+            else:
+                fn = lambda: pir.qpadl_pir_recover_batch(cprm, ans, Xr, S, out)
+            def check():
+                # first recovery, sampled rows: (ans - dot + Delta/2) >> 24
+                idx = np.unique(np.r_[0:64, rows - 64:rows].clip(0, rows - 1))
+                x = (ans_np[:rows][idx] - _dots(pir.as_u32(X).reshape(rows, n)[idx], S_np[0])).astype(np.uint32)
+                exp = ((x.astype(np.uint64) + (1 << 23)) & 0xFFFFFFFF) >> 24
+                return np.array_equal(out.cpu().numpy()[:rows][idx], exp.astype(np.uint8))
+        out_row = None
+        res.update(n=n, batch=B, client=a.client, u32_macs=rows * n * B, fp16_mma_flops=2 * rows * 4 * n * 4 * B)
     else:
         n = a.n
         A = torch.empty(C * n, dtype=torch.int32, device="cuda")
@@ -116,6 +170,11 @@ def main():
         raise SystemExit("profile case: device status word set")
     if out_row is not None:
         _row_check(D_np[R // 2], X_chk, out_row())
+    if a.case in ("qbatch", "rbatch"):
+        if not check():
+            raise SystemExit("profile case: first vector differs from the host recomputation")
+        if cl is not None and pir.qpadl_client_status(cl) != 0:
+            raise SystemExit("profile case: client status word set")
     res["ms"] = times
     ms = min(times)
     if "alg_bytes" in res:

@@ -123,3 +123,30 @@ def test_small_batches_both_paths_full_size(big, B):
         torch.cuda.synchronize()
         ans_np = pir.as_u32(ans).reshape(B, R)
         _check_rows(big["D"], rows, ans_np[:, rows], Q_np)
+
+
+def test_client_batch_full_size(big):
+    # 1024 queries and recoveries through the tensor-core client context
+    B = 1024
+    S_np = inputs.secrets(B, N, seed=700)
+    E_np = inputs.noise_batch(B, C, seed=701)
+    cols = inputs.target_columns(B, C, seed=702)
+    S = pir.from_u32(S_np.reshape(-1))
+    E = torch.from_numpy(E_np.reshape(-1)).cuda()
+    cols_t = torch.from_numpy(cols.astype(np.int32)).cuda()
+    cl = pir.qpadl_client_create(big["prm"], big["A"], big["H"], max_batch=B)
+    Q = torch.empty(B * C, dtype=torch.int32, device="cuda")
+    pir.qpadl_client_query_batch(cl, S, E, cols_t, Q)
+    ans = torch.empty(B * R, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_answer_batch(big["db"], Q, ans)
+    out = torch.empty(B * R, dtype=torch.uint8, device="cuda")
+    pir.qpadl_client_recover_batch(cl, ans, S, out)
+    torch.cuda.synchronize()
+    assert pir.qpadl_client_status(cl) == pir.QPADL_OK
+    A_np = pir.as_u32(big["A"]).reshape(C, N)
+    Q_np = pir.as_u32(Q).reshape(B, C)
+    for b in (0, 1, 511, B - 1):
+        assert np.array_equal(Q_np[b], oracle.query(A_np, S_np[b], E_np[b], int(cols[b]), 1 << 24))
+    # Recover(Answer(Query(col))) = D[:, col] for all 1024 queries over every row
+    assert np.array_equal(out.cpu().numpy().reshape(B, R), big["D"][:, cols].T)
+    cl.close()
