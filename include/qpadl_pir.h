@@ -309,6 +309,14 @@ int qpadl_client_status(qpadl_client *c);
 /* Bytes of device memory the context owns. */
 uint64_t qpadl_client_device_bytes(const qpadl_client *c);
 
+/* Client options (every setting gives the same results):
+ * QPADL_CLIENT_OPT_SKIP_ZERO_BLOCKS (default 1): when n is a multiple of 512
+ *   and a call carries more than 8 secrets, skip the (plane u, shift t)
+ *   blocks with u > t, whose secret limbs are zero (10 of 16 blocks run);
+ *   0 runs all 16.  QPADL_EINVAL for an unknown option or value. */
+#define QPADL_CLIENT_OPT_SKIP_ZERO_BLOCKS 1
+int qpadl_client_set_option(qpadl_client *c, int option, int64_t value);
+
 /* Waits for the device and frees the context (NULL is fine). */
 int qpadl_client_destroy(qpadl_client *c);
 

@@ -40,7 +40,17 @@
 // 2^{8t}, and the usual recombination sum_t 2^{8t} (.) gives X s_b mod 2^32.
 // Every product is at most 128 * 128 in magnitude, so a 512-deep chunk is
 // exact in fp32 here as well.
+//
+// Planed mode (n a multiple of 512, BN >= 64) skips the zero blocks: each
+// 512-deep chunk lies inside one limb plane u, and only the shifts t >= u
+// need it.  A tile's vector rows are then ordered by descending shift (row
+// (3 - t) * BN/4 + q for vector q of the tile), so the active shifts of
+// plane u are the first (4 - u) * BN/4 rows: each MMA of the chunk takes
+// N = (4 - u) * BN/4 and the epilogue drains only those columns, adding
+// each shift times 2^{8t}.  That runs 10 of the 16 (plane, shift) blocks
+// with MMAs no narrower than BN/4.
 #include <cstdint>
+#include <type_traits>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -75,10 +85,12 @@ __device__ __forceinline__ bool drain_wait_g(uint64_t *bar, uint32_t parity) {
     return true;
 }
 
-template <int BN, class Epi>
+template <int BN, class Epi, bool PLANED>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     limb_gemm_kernel(const __grid_constant__ CUtensorMap a_map, const __grid_constant__ CUtensorMap b_map,
-                     Epi epi, uint32_t M, uint32_t NV, uint32_t KB, int *__restrict__ status) {
+                     Epi epi, uint32_t M, uint32_t NV, uint32_t KB, uint32_t plane_chunks,
+                     int *__restrict__ status) {
+    static_assert(!PLANED || BN >= 64, "a shift group needs N = BN/4 >= 16");
     using Cfg = GemmCfg<BN>;
     constexpr int QPT = Cfg::kQPT;
     extern __shared__ uint8_t smem_raw[];
@@ -178,11 +190,21 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 const uint64_t adesc = umma_desc_sw128(sa);
                 const uint64_t bdesc = umma_desc_sw128(sa + Cfg::kABytes);
                 if (elect_one()) {
+                    if constexpr (PLANED) {
+                        // limb plane u of this chunk: the active shifts are the first (4 - u) * BN/4 rows
+                        const uint32_t u = (kb / kChunkKB) / plane_chunks;
+                        const uint32_t idesc_u = umma_idesc_f16(kBM, (4u - u) * (BN / 4));
 #pragma unroll
-                    for (int k = 0; k < kBK / 16; ++k) {
-                        // advance the start address by 16 elements (32 bytes) inside the swizzle atom
-                        umma_f16(d_tmem, adesc + 2u * k, bdesc + 2u * k, idesc,
-                                 (kb % kChunkKB != 0 || k != 0) ? 1u : 0u);
+                        for (int k = 0; k < kBK / 16; ++k)
+                            umma_f16(d_tmem, adesc + 2u * k, bdesc + 2u * k, idesc_u,
+                                     (kb % kChunkKB != 0 || k != 0) ? 1u : 0u);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < kBK / 16; ++k) {
+                            // advance the start address by 16 elements (32 bytes) inside the swizzle atom
+                            umma_f16(d_tmem, adesc + 2u * k, bdesc + 2u * k, idesc,
+                                     (kb % kChunkKB != 0 || k != 0) ? 1u : 0u);
+                        }
                     }
                     umma_commit(&empty[st]);
                     if (kb % kChunkKB == kChunkKB - 1 || kb == KB - 1) umma_commit(&acc_full[ci & 1u]);
@@ -217,18 +239,45 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     break;
                 }
                 tc_fence_after();
+                if constexpr (PLANED) {
+                    // active shifts of this chunk's plane; column (3 - t)*QPT + q holds shift t of vector q
+                    const uint32_t u = c / plane_chunks;
+                    for (uint32_t t = u; t < 4; ++t) {
+                        const uint32_t col0 = tmem_base + lane_addr + buf * BN + (3u - t) * QPT;
+                        if constexpr (QPT >= 32) {
 #pragma unroll
-                for (int j = 0; j < BN / 32; ++j) {
-                    uint32_t v[32];
-                    tmem_ld32(tmem_base + lane_addr + buf * BN + 32u * j, v);
-                    tmem_wait_ld();
+                            for (int j = 0; j < QPT / 32; ++j) {
+                                uint32_t v[32];
+                                tmem_ld32(col0 + 32u * j, v);
+                                tmem_wait_ld();
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const uint32_t s0 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 0])));
-                        const uint32_t s1 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 1])));
-                        const uint32_t s2 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 2])));
-                        const uint32_t s3 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 3])));
-                        run[8 * j + q] += s0 + (s1 << 8) + (s2 << 16) + (s3 << 24);
+                                for (int q = 0; q < 32; ++q)
+                                    run[32 * j + q] +=
+                                        static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[q]))) << (8u * t);
+                            }
+                        } else {
+                            uint32_t v[16];
+                            tmem_ld16(col0, v);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int q = 0; q < QPT; ++q)
+                                run[q] += static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[q]))) << (8u * t);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < BN / 32; ++j) {
+                        uint32_t v[32];
+                        tmem_ld32(tmem_base + lane_addr + buf * BN + 32u * j, v);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const uint32_t s0 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 0])));
+                            const uint32_t s1 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 1])));
+                            const uint32_t s2 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 2])));
+                            const uint32_t s3 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 3])));
+                            run[8 * j + q] += s0 + (s1 << 8) + (s2 << 16) + (s3 << 24);
+                        }
                     }
                 }
                 tc_fence_before();
@@ -390,27 +439,59 @@ __global__ void secret_limbs_kernel(const uint32_t *__restrict__ S, uint32_t B, 
     }
 }
 
+// Planed layout of the same rows for tiles of BN = 4 * qpt rows: vector b
+// (of Bp = B rounded up to qpt; vectors >= B are zero) and shift t go to row
+// (b / qpt) * 4 qpt + (3 - t) * qpt + b % qpt.
+__global__ void secret_limbs_planed_kernel(const uint32_t *__restrict__ S, uint32_t B, uint32_t Bp, uint32_t n,
+                                           uint32_t qpt, __half *__restrict__ V, uint64_t pitch) {
+    const uint64_t total = (uint64_t)Bp * n;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = static_cast<uint32_t>(e / n);
+        const uint32_t k = static_cast<uint32_t>(e - (uint64_t)b * n);
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+        if (b < B) balanced_limbs(S[e], c);
+        const uint64_t row0 = (uint64_t)(b / qpt) * 4 * qpt + b % qpt;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            __half *row = V + (row0 + (uint64_t)(3 - t) * qpt) * pitch + k;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) row[(uint64_t)u * n] = __float2half_rn(u <= t ? c[t - u] : 0.0f);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ host side
-template <int BN, class Epi>
+template <int BN, class Epi, bool PLANED>
 static cudaError_t set_gemm_attr() {
-    return cudaFuncSetAttribute(limb_gemm_kernel<BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(limb_gemm_kernel<BN, Epi, PLANED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 GemmCfg<BN>::kSmemBytes);
 }
 
 template <class Epi>
 static cudaError_t set_gemm_attrs() {
     cudaError_t e;
-    if ((e = set_gemm_attr<32, Epi>()) != cudaSuccess) return e;
-    if ((e = set_gemm_attr<64, Epi>()) != cudaSuccess) return e;
-    if ((e = set_gemm_attr<128, Epi>()) != cudaSuccess) return e;
-    return set_gemm_attr<256, Epi>();
+    if ((e = set_gemm_attr<32, Epi, false>()) != cudaSuccess) return e;
+    if ((e = set_gemm_attr<64, Epi, false>()) != cudaSuccess) return e;
+    if ((e = set_gemm_attr<128, Epi, false>()) != cudaSuccess) return e;
+    return set_gemm_attr<256, Epi, false>();
+}
+
+template <class Epi>
+static cudaError_t set_planed_attrs() {
+    cudaError_t e;
+    if ((e = set_gemm_attr<64, Epi, true>()) != cudaSuccess) return e;
+    if ((e = set_gemm_attr<128, Epi, true>()) != cudaSuccess) return e;
+    return set_gemm_attr<256, Epi, true>();
 }
 
 cudaError_t prepare_limb_gemm_kernels() {
     cudaError_t e;
     if ((e = set_gemm_attrs<StoreEpi>()) != cudaSuccess) return e;
     if ((e = set_gemm_attrs<QueryEpi>()) != cudaSuccess) return e;
-    return set_gemm_attrs<RecoverEpi>();
+    if ((e = set_gemm_attrs<RecoverEpi>()) != cudaSuccess) return e;
+    if ((e = set_planed_attrs<QueryEpi>()) != cudaSuccess) return e;
+    return set_planed_attrs<RecoverEpi>();
 }
 
 int limb_gemm_bn_for(uint32_t nv) {
@@ -421,30 +502,45 @@ int limb_gemm_bn_for(uint32_t nv) {
     return 256;
 }
 
+template <int BN, class Epi, bool PLANED>
+static void launch_one(int grid, const CUtensorMap &a_map, const CUtensorMap &b_map, const Epi &epi, uint32_t M,
+                       uint32_t NV, uint32_t KB, uint32_t plane_chunks, int *status, cudaStream_t stream) {
+    limb_gemm_kernel<BN, Epi, PLANED><<<grid, kGemmThreads, GemmCfg<BN>::kSmemBytes, stream>>>(
+        a_map, b_map, epi, M, NV, KB, plane_chunks, status);
+}
+
+// plane_chunks > 0 selects planed mode (then bn >= 64 and K = 4 * 512 * plane_chunks).
 template <class Epi>
 static cudaError_t launch_epi(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, const Epi &epi, uint32_t M,
-                              uint32_t NV, uint64_t K, int num_sms, int *status, cudaStream_t stream) {
+                              uint32_t NV, uint64_t K, uint32_t plane_chunks, int num_sms, int *status,
+                              cudaStream_t stream) {
     const uint32_t KB = static_cast<uint32_t>((K + kBK - 1) / kBK);
     const uint64_t tiles = (uint64_t)((M + kBM - 1) / kBM) * ((4ull * NV + bn - 1) / bn);
     const int grid = static_cast<int>(tiles < (uint64_t)num_sms ? tiles : (uint64_t)num_sms);
-    switch (bn) {
-        case 32:
-            limb_gemm_kernel<32, Epi><<<grid, kGemmThreads, GemmCfg<32>::kSmemBytes, stream>>>(a_map, b_map, epi, M,
-                                                                                               NV, KB, status);
-            break;
-        case 64:
-            limb_gemm_kernel<64, Epi><<<grid, kGemmThreads, GemmCfg<64>::kSmemBytes, stream>>>(a_map, b_map, epi, M,
-                                                                                               NV, KB, status);
-            break;
-        case 128:
-            limb_gemm_kernel<128, Epi><<<grid, kGemmThreads, GemmCfg<128>::kSmemBytes, stream>>>(a_map, b_map, epi,
-                                                                                                 M, NV, KB, status);
-            break;
-        case 256:
-            limb_gemm_kernel<256, Epi><<<grid, kGemmThreads, GemmCfg<256>::kSmemBytes, stream>>>(a_map, b_map, epi,
-                                                                                                 M, NV, KB, status);
-            break;
-        default: return cudaErrorInvalidValue;
+    if (plane_chunks == 0) {
+        switch (bn) {
+            case 32: launch_one<32, Epi, false>(grid, a_map, b_map, epi, M, NV, KB, 1, status, stream); break;
+            case 64: launch_one<64, Epi, false>(grid, a_map, b_map, epi, M, NV, KB, 1, status, stream); break;
+            case 128: launch_one<128, Epi, false>(grid, a_map, b_map, epi, M, NV, KB, 1, status, stream); break;
+            case 256: launch_one<256, Epi, false>(grid, a_map, b_map, epi, M, NV, KB, 1, status, stream); break;
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        if constexpr (std::is_same<Epi, StoreEpi>::value) {
+            return cudaErrorInvalidValue;
+        } else {
+            if (K != 4ull * 512 * plane_chunks) return cudaErrorInvalidValue;
+            switch (bn) {
+                case 64: launch_one<64, Epi, true>(grid, a_map, b_map, epi, M, NV, KB, plane_chunks, status, stream); break;
+                case 128:
+                    launch_one<128, Epi, true>(grid, a_map, b_map, epi, M, NV, KB, plane_chunks, status, stream);
+                    break;
+                case 256:
+                    launch_one<256, Epi, true>(grid, a_map, b_map, epi, M, NV, KB, plane_chunks, status, stream);
+                    break;
+                default: return cudaErrorInvalidValue;
+            }
+        }
     }
     return cudaGetLastError();
 }
@@ -452,19 +548,19 @@ static cudaError_t launch_epi(int bn, const CUtensorMap &a_map, const CUtensorMa
 cudaError_t launch_limb_gemm(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, uint32_t *out,
                              uint64_t ld_m, uint64_t ld_b, uint32_t M, uint32_t NV, uint64_t K, int num_sms,
                              int *status, cudaStream_t stream) {
-    return launch_epi(bn, a_map, b_map, StoreEpi{out, ld_m, ld_b}, M, NV, K, num_sms, status, stream);
+    return launch_epi(bn, a_map, b_map, StoreEpi{out, ld_m, ld_b}, M, NV, K, 0, num_sms, status, stream);
 }
 
 cudaError_t launch_limb_gemm_query(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, const QueryEpi &epi,
-                                   uint32_t M, uint32_t NV, uint64_t K, int num_sms, int *status,
-                                   cudaStream_t stream) {
-    return launch_epi(bn, a_map, b_map, epi, M, NV, K, num_sms, status, stream);
+                                   uint32_t M, uint32_t NV, uint64_t K, uint32_t plane_chunks, int num_sms,
+                                   int *status, cudaStream_t stream) {
+    return launch_epi(bn, a_map, b_map, epi, M, NV, K, plane_chunks, num_sms, status, stream);
 }
 
 cudaError_t launch_limb_gemm_recover(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map,
-                                     const RecoverEpi &epi, uint32_t M, uint32_t NV, uint64_t K, int num_sms,
-                                     int *status, cudaStream_t stream) {
-    return launch_epi(bn, a_map, b_map, epi, M, NV, K, num_sms, status, stream);
+                                     const RecoverEpi &epi, uint32_t M, uint32_t NV, uint64_t K,
+                                     uint32_t plane_chunks, int num_sms, int *status, cudaStream_t stream) {
+    return launch_epi(bn, a_map, b_map, epi, M, NV, K, plane_chunks, num_sms, status, stream);
 }
 
 cudaError_t launch_db_to_f16(const uint8_t *D, uint64_t R, uint64_t C, __half *D16, uint64_t pitch, int num_sms,
@@ -497,6 +593,13 @@ cudaError_t launch_mat_row_limbs(const uint32_t *X, uint64_t rows, uint32_t n, _
 cudaError_t launch_secret_limbs(const uint32_t *S, uint32_t B, uint32_t n, __half *V, uint64_t pitch, int num_sms,
                                 cudaStream_t stream) {
     secret_limbs_kernel<<<num_sms * 4, 256, 0, stream>>>(S, B, n, V, pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_secret_limbs_planed(const uint32_t *S, uint32_t B, uint32_t n, uint32_t qpt, __half *V,
+                                       uint64_t pitch, int num_sms, cudaStream_t stream) {
+    const uint32_t Bp = (B + qpt - 1) / qpt * qpt;
+    secret_limbs_planed_kernel<<<num_sms * 4, 256, 0, stream>>>(S, B, Bp, n, qpt, V, pitch);
     return cudaGetLastError();
 }
 

@@ -70,6 +70,7 @@ struct qpadl_client {
     CUtensorMap a_map, h_map;
     int *d_status = nullptr;
     uint64_t owned_bytes = 0;
+    bool planed = true;              // skip the zero (plane, shift) blocks when n % 512 == 0
 };
 
 namespace {
@@ -743,7 +744,9 @@ int qpadl_client_create(const qpadl_params *prm, const uint32_t *A_dev, const ui
     if (!alloc(reinterpret_cast<void **>(&c->d_status), 16)) return fail(QPADL_ENOMEM);
     if (!alloc(reinterpret_cast<void **>(&c->a_planes), 2 * C * c->pitch)) return fail(QPADL_ENOMEM);
     if (H_dev && !alloc(reinterpret_cast<void **>(&c->h_planes), 2 * R * c->pitch)) return fail(QPADL_ENOMEM);
-    if (!alloc(reinterpret_cast<void **>(&c->v), 2ull * 4 * max_batch * c->pitch)) return fail(QPADL_ENOMEM);
+    // room for the planed layout: 4 rows per vector, vectors rounded up to 64
+    const uint64_t vrows = 4ull * ((max_batch + 63) / 64 * 64);
+    if (!alloc(reinterpret_cast<void **>(&c->v), 2ull * vrows * c->pitch)) return fail(QPADL_ENOMEM);
     if (cudaMemsetAsync(c->d_status, 0, 16, s) != cudaSuccess) return fail(QPADL_ECUDA);
     if (cuda_fail(launch_mat_row_limbs(A_dev, C, prm->n, c->a_planes, c->pitch, c->num_sms, s), "A limb planes") !=
         QPADL_OK)
@@ -772,12 +775,25 @@ int client_set_device(const qpadl_client *c) {
     return QPADL_OK;
 }
 
+// Planed mode applies when every 512-deep chunk lies in one limb plane and a
+// shift group is at least 16 columns wide.
+uint32_t client_plane_chunks(const qpadl_client *c, int bn) {
+    return (c->planed && c->prm.n % 512 == 0 && bn >= 64) ? c->prm.n / 512 : 0u;
+}
+
 // Shifted secret limbs of Bc secrets into c->v and the tensor map over them.
-int client_secret_operand(qpadl_client *c, const uint32_t *S, uint32_t Bc, int bn, CUtensorMap *map,
-                          cudaStream_t s) {
+int client_secret_operand(qpadl_client *c, const uint32_t *S, uint32_t Bc, int bn, uint32_t plane_chunks,
+                          CUtensorMap *map, cudaStream_t s) {
     const uint32_t n = c->prm.n;
-    QPADL_CU(launch_secret_limbs(S, Bc, n, c->v, c->pitch, c->num_sms, s));
-    if (!encode_2d(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, c->v, 4ull * n, 4ull * Bc, c->pitch * 2, kLimbBoxK,
+    uint64_t rows = 4ull * Bc;
+    if (plane_chunks) {
+        const uint32_t qpt = static_cast<uint32_t>(bn / 4);
+        QPADL_CU(launch_secret_limbs_planed(S, Bc, n, qpt, c->v, c->pitch, c->num_sms, s));
+        rows = 4ull * ((Bc + qpt - 1) / qpt * qpt);
+    } else {
+        QPADL_CU(launch_secret_limbs(S, Bc, n, c->v, c->pitch, c->num_sms, s));
+    }
+    if (!encode_2d(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, c->v, 4ull * n, rows, c->pitch * 2, kLimbBoxK,
                    static_cast<uint32_t>(bn), CU_TENSOR_MAP_SWIZZLE_128B))
         return QPADL_ECUDA;
     return QPADL_OK;
@@ -795,12 +811,13 @@ int qpadl_client_query_batch(qpadl_client *c, const uint32_t *S_dev, const int32
     for (uint32_t b0 = 0; b0 < B; b0 += c->max_batch) {
         const uint32_t Bc = std::min(B - b0, c->max_batch);
         const int bn = limb_gemm_bn_for(Bc);
+        const uint32_t pc = client_plane_chunks(c, bn);
         CUtensorMap v_map;
-        int rc = client_secret_operand(c, S_dev + (uint64_t)b0 * n, Bc, bn, &v_map, s);
+        int rc = client_secret_operand(c, S_dev + (uint64_t)b0 * n, Bc, bn, pc, &v_map, s);
         if (rc != QPADL_OK) return rc;
         const QueryEpi epi{E_dev + (uint64_t)b0 * C, C, cols_dev + b0, 0, delta, Q_dev + (uint64_t)b0 * C, C};
-        QPADL_CU(launch_limb_gemm_query(bn, c->a_map, v_map, epi, static_cast<uint32_t>(C), Bc, 4 * n, c->num_sms,
-                                        c->d_status, s));
+        QPADL_CU(launch_limb_gemm_query(bn, c->a_map, v_map, epi, static_cast<uint32_t>(C), Bc, 4 * n, pc,
+                                        c->num_sms, c->d_status, s));
     }
     return QPADL_OK;
 }
@@ -815,11 +832,12 @@ int qpadl_client_recover_batch(qpadl_client *c, const uint32_t *ans_dev, const u
     for (uint32_t b0 = 0; b0 < B; b0 += c->max_batch) {
         const uint32_t Bc = std::min(B - b0, c->max_batch);
         const int bn = limb_gemm_bn_for(Bc);
+        const uint32_t pc = client_plane_chunks(c, bn);
         CUtensorMap v_map;
-        int rc = client_secret_operand(c, S_dev + (uint64_t)b0 * n, Bc, bn, &v_map, s);
+        int rc = client_secret_operand(c, S_dev + (uint64_t)b0 * n, Bc, bn, pc, &v_map, s);
         if (rc != QPADL_OK) return rc;
         const RecoverEpi epi{ans_dev + (uint64_t)b0 * R, R, shift, out_dev + (uint64_t)b0 * R, R};
-        QPADL_CU(launch_limb_gemm_recover(bn, c->h_map, v_map, epi, static_cast<uint32_t>(R), Bc, 4 * n,
+        QPADL_CU(launch_limb_gemm_recover(bn, c->h_map, v_map, epi, static_cast<uint32_t>(R), Bc, 4 * n, pc,
                                           c->num_sms, c->d_status, s));
     }
     return QPADL_OK;
@@ -840,5 +858,16 @@ int qpadl_client_status(qpadl_client *c) {
 }
 
 uint64_t qpadl_client_device_bytes(const qpadl_client *c) { return c ? c->owned_bytes : 0; }
+
+int qpadl_client_set_option(qpadl_client *c, int option, int64_t value) {
+    if (!c) return QPADL_EINVAL;
+    switch (option) {
+        case QPADL_CLIENT_OPT_SKIP_ZERO_BLOCKS:
+            if (value != 0 && value != 1) return QPADL_EINVAL;
+            c->planed = value != 0;
+            return QPADL_OK;
+        default: return QPADL_EINVAL;
+    }
+}
 
 }  // extern "C"

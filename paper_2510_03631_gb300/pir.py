@@ -88,6 +88,7 @@ _SIGS = {
     "qpadl_client_recover_batch": ([_P, _P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
     "qpadl_client_status": ([_P], ctypes.c_int),
     "qpadl_client_device_bytes": ([_P], ctypes.c_uint64),
+    "qpadl_client_set_option": ([_P, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
     "qpadl_client_destroy": ([_P], ctypes.c_int),
     "qpadl_server_create": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
     "qpadl_server_add_db": ([_P, _P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -373,6 +374,13 @@ def qpadl_client_recover_batch(c: Client, ans: torch.Tensor, S: torch.Tensor, ou
 
 def qpadl_client_status(c: Client) -> int:
     return int(load().qpadl_client_status(c.handle))
+
+
+QPADL_CLIENT_OPT_SKIP_ZERO_BLOCKS = 1
+
+
+def qpadl_client_set_option(c: Client, option: int, value: int):
+    _check(load().qpadl_client_set_option(c.handle, int(option), int(value)), "qpadl_client_set_option")
 
 
 def qpadl_client_device_bytes(c: Client) -> int:

@@ -63,17 +63,51 @@ def test_query_and_recover_match_oracle(cuda, R, C, n, B, max_batch):
     cl.close()
 
 
+# n a multiple of 512 and B > 8: shift groups of 16, 32 and 64 columns, ragged last tiles, chunked batches
+@pytest.mark.parametrize("R,C,n,B,max_batch", [(1000, 1500, 512, 12, 64), (700, 600, 512, 24, 1024),
+                                               (300, 2048 + 40, 1024, 37, 1024), (513, 1000, 1024, 150, 70)])
+@pytest.mark.parametrize("skip", [0, 1])
+def test_zero_block_skipping_on_and_off(cuda, R, C, n, B, max_batch, skip):
+    seed = 3 * R + C + n + B
+    D = inputs.db_digits(R, C, 256, seed=seed)
+    A_np = inputs.public_matrix(C, n, seed=seed + 1)
+    H_np = oracle.hint(D, A_np, threads=oracle.max_threads())
+    S_np = inputs.secrets(B, n, seed=seed + 2)
+    E_np = inputs.noise_batch(B, C, seed=seed + 3)
+    cols = inputs.target_columns(B, C, seed=seed + 4)
+    cl = pir.qpadl_client_create(pir.params(R, C, n, seed=seed), _dev_u32(A_np), _dev_u32(H_np),
+                                 max_batch=max_batch)
+    pir.qpadl_client_set_option(cl, pir.QPADL_CLIENT_OPT_SKIP_ZERO_BLOCKS, skip)
+    Q = torch.empty(B * C, dtype=torch.int32, device="cuda")
+    pir.qpadl_client_query_batch(cl, _dev_u32(S_np), torch.from_numpy(E_np.reshape(-1)).cuda(),
+                                 torch.from_numpy(cols.astype(np.int32)).cuda(), Q)
+    torch.cuda.synchronize()
+    Q_np = pir.as_u32(Q).reshape(B, C)
+    for b in range(B):
+        assert np.array_equal(Q_np[b], oracle.query(A_np, S_np[b], E_np[b], int(cols[b]), 1 << 24)), b
+    ans_np = oracle.answer_batch(D, Q_np, threads=oracle.max_threads())
+    out = torch.empty(B * R, dtype=torch.uint8, device="cuda")
+    pir.qpadl_client_recover_batch(cl, _dev_u32(ans_np), _dev_u32(S_np), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(B, R)
+    for b in range(0, B, 7):
+        assert np.array_equal(got[b], oracle.recover(ans_np[b], H_np, S_np[b])), b
+    assert np.array_equal(got, D[:, cols].T)
+    assert pir.qpadl_client_status(cl) == pir.QPADL_OK
+    cl.close()
+
+
 @pytest.mark.parametrize("a_word,s_word", [(0xFFFFFFFF, 0xFFFFFFFF), (0x80808080, 0x80808080),
                                            (0x7F7F7F7F, 0x80808080), (0x80808080, 0x7F7F7F7F),
                                            (0x7F7F7F7F, 0x7F7F7F7F), (0x00800080, 0xFF7FFF80)])
 def test_limb_boundary_values(cuda, a_word, s_word):
     # every limb at +-127/-128 pushes each 512-deep chunk to its exactness bound
-    R, C, n, B = 256, 512, 1024, 4
+    R, C, n, B = 256, 512, 1024, 16   # B = 16: planed mode, shift groups of 16 columns
     A_np = np.full((C, n), a_word, dtype=np.uint32)
     S_np = np.full((B, n), s_word, dtype=np.uint32)
     H_np = np.full((R, n), a_word, dtype=np.uint32)
     E_np = np.zeros((B, C), dtype=np.int32)
-    cols = np.array([0, 1, C - 1, 77], dtype=np.int32)
+    cols = np.array([0, 1, C - 1, 77] * 4, dtype=np.int32)
     prm = pir.params(R, C, n)
     cl = pir.qpadl_client_create(prm, _dev_u32(A_np), _dev_u32(H_np), max_batch=B)
     Q = torch.empty(B * C, dtype=torch.int32, device="cuda")
@@ -131,4 +165,8 @@ def test_errors(cuda):
     with pytest.raises(pir.QpadlError) as e:   # built without the hint
         pir.qpadl_client_recover_batch(cl, ans, S, out)
     assert e.value.code == pir.QPADL_EINVAL
+    for opt, val in ((pir.QPADL_CLIENT_OPT_SKIP_ZERO_BLOCKS, 2), (99, 0)):
+        with pytest.raises(pir.QpadlError) as e:
+            pir.qpadl_client_set_option(cl, opt, val)
+        assert e.value.code == pir.QPADL_EINVAL
     cl.close()
