@@ -288,15 +288,24 @@ def serving_measure(torch, pir, inputs, rates, duration_s, single_db_one_ms, see
         qs = [pools[d][i % 32] for i, d in enumerate(which)]
         st_before = pir.qpadl_server_stats(srv)
         t0 = time.perf_counter()
-        lat, st = pir.qpadl_server_replay(srv, arr, [ids[d] for d in which], qs, None)
+        lat, st, tm = pir.qpadl_server_replay(srv, arr, [ids[d] for d in which], qs, None, with_times=True)
         wall = time.perf_counter() - t0
         st_after = pir.qpadl_server_stats(srv)
         good = lat[st == 0] * 1e3
+        tm_ok = tm[st == 0] * 1e3   # (submit, launch, done) ms after the scheduled arrival
         launches = st_after["launches"] - st_before["launches"]
         runs.append({"offered_qps": rate, "requests": n, "completed": int((st == 0).sum()),
                      "achieved_qps": round(n / wall, 1), "p50_ms": round(_pct(good, 50), 3),
                      "p99_ms": round(_pct(good, 99), 3), "mean_requests_per_launch": round(n / max(launches, 1), 2),
-                     "launches_over_several_dbs": st_after["grouped_launches"] - st_before["grouped_launches"]})
+                     "launches_over_several_dbs": st_after["grouped_launches"] - st_before["grouped_launches"],
+                     "p99_ms_split": {"submit_lag": round(_pct(tm_ok[:, 0], 99), 3),
+                                      "queued": round(_pct(tm_ok[:, 1] - tm_ok[:, 0], 99), 3),
+                                      "on_gpu": round(_pct(tm_ok[:, 2] - tm_ok[:, 1], 99), 3)},
+                     "max_ms": round(float(good.max()), 3) if len(good) else None,
+                     "worst_split_ms": ([round(float(x), 3) for x in (tm_ok[int(good.argmax()), 0],
+                                                                     tm_ok[int(good.argmax()), 1] - tm_ok[int(good.argmax()), 0],
+                                                                     tm_ok[int(good.argmax()), 2] - tm_ok[int(good.argmax()), 1])]
+                                        if len(good) else None)})
     srv.close()
 
     # the 1 GiB database alone: batched serving vs one query at a time
@@ -366,6 +375,48 @@ def run_ours(args):
         e1.record()
         torch.cuda.synchronize()
         hint_ms.append(e0.elapsed_time(e1))
+
+    # ---- client side of the offline/hint workload: 1024 Queries and 1024 Recovers in one
+    # batch each through the tensor-core client context (checked end to end)
+    client = None
+    if not args.quick:
+        BC = 1024
+        S_c = inputs.secrets(BC, n, seed=seed + 60)
+        cols_c = inputs.target_columns(BC, C, seed=seed + 62)
+        S_cd = pir.from_u32(S_c.reshape(-1))
+        E_cd = torch.from_numpy(inputs.noise_batch(BC, C, seed=seed + 61).reshape(-1)).cuda()
+        cols_cd = torch.from_numpy(cols_c.astype(np.int32)).cuda()
+        Q_c = torch.empty(BC * C, dtype=torch.int32, device="cuda")
+        ans_c = torch.empty(BC * R, dtype=torch.int32, device="cuda")
+        out_c = torch.empty(BC * R, dtype=torch.uint8, device="cuda")
+        cl = pir.qpadl_client_create(prm, A, H, max_batch=BC)
+
+        def timed(fn, reps=5):
+            fn()
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return min(ts)
+
+        q_ms = timed(lambda: pir.qpadl_client_query_batch(cl, S_cd, E_cd, cols_cd, Q_c))
+        pir.qpadl_pir_answer_batch(db, Q_c, ans_c)
+        r_ms = timed(lambda: pir.qpadl_client_recover_batch(cl, ans_c, S_cd, out_c))
+        simt_q_ms = timed(lambda: pir.qpadl_pir_query_batch(prm, A, S_cd, E_cd, cols_cd, Q_c), reps=2)
+        if not np.array_equal(out_c.cpu().numpy().reshape(BC, R), D_np[:, cols_c].T):
+            raise SystemExit("bench: client batch round trip differs from the database")
+        if pir.qpadl_client_status(cl) != 0:
+            raise SystemExit("bench: client status word set")
+        client = {"batch": BC, "query_ms": round(q_ms, 4), "recover_ms": round(r_ms, 4),
+                  "query_cuda_core_gemm_ms": round(simt_q_ms, 4),
+                  "u32_macs_per_call": C * n * BC,
+                  "note": "tensor-core client context (qpadl_client_*), min of 5; round trip checked"}
+        cl.close()
+        del Q_c, ans_c, out_c, E_cd
 
     K, W = args.steps, args.warmup
     P = 64   # pool of distinct queries; step i uses slot i % P
@@ -538,6 +589,7 @@ def run_ours(args):
                      "alg_bytes_per_launch": alg_bytes},
         "batched": {"one_at_a_time_qps": round(one_qps, 1), "sweep": sweep},
         "hint_ms": round(min(hint_ms), 3),
+        "client_batch_1024": client,
         "serving": serving,
         "gpu_launches": 4 * K,
         "timing": "CUDA events around K replays of per-step CUDA graphs (64-query pool)",

@@ -405,11 +405,14 @@ int qpadl_server_destroy(qpadl_server *srv);
  * the call starts (retrying while admission refuses), waits for all, and
  * writes latency_s[i] = completion - scheduled arrival (-1 on failure) and
  * status[i].  ans_host may be NULL (answers discarded).  arrival_s must be
- * non-decreasing (QPADL_EINVAL otherwise).  Up to eight client threads share
- * the requests round-robin, each submitting and polling its own. */
+ * non-decreasing (QPADL_EINVAL otherwise).  Up to four client threads share
+ * the requests round-robin, each submitting and polling its own.  times
+ * (may be NULL) receives, per completed request, its submit, launch and
+ * completion times in seconds after its scheduled arrival. */
 int qpadl_server_replay(qpadl_server *srv, uint64_t n, const double *arrival_s,
                         const int32_t *db_ids, const uint32_t *const *q_host,
-                        uint32_t *const *ans_host, double *latency_s, int32_t *status);
+                        uint32_t *const *ans_host, double *latency_s, int32_t *status,
+                        qpadl_request_times *times);
 
 #ifdef __cplusplus
 }

@@ -657,17 +657,18 @@ int qpadl_server_destroy(qpadl_server *s) {
 
 // Open-loop load generator: request i is submitted at t0 + arrival_s[i]
 // (arrival_s non-decreasing; retried while admission refuses) and its latency
-// is its completion time minus that scheduled arrival.  Several client
+// is its completion time minus that scheduled arrival.  Up to four client
 // threads share the requests round-robin; each submits its own requests when
-// they fall due and polls the ones it has outstanding.
+// they fall due (sleeping through long gaps, spinning over short ones) and
+// polls the ones it has outstanding.
 int qpadl_server_replay(qpadl_server *s, uint64_t n, const double *arrival_s, const int32_t *db_ids,
                         const uint32_t *const *q_host, uint32_t *const *ans_host, double *latency_s,
-                        int32_t *status) {
+                        int32_t *status, qpadl_request_times *times) {
     if (!s || !arrival_s || !db_ids || !q_host || !latency_s || !status) return QPADL_EINVAL;
     for (uint64_t i = 1; i < n; ++i)
         if (arrival_s[i] < arrival_s[i - 1]) return QPADL_EINVAL;
     const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const uint64_t T = std::max<uint64_t>(1, std::min<uint64_t>({n, 8, hw / 2 ? hw / 2 : 1}));
+    const uint64_t T = std::max<uint64_t>(1, std::min<uint64_t>({n, 4, hw / 4 ? hw / 4 : 1}));
     const double t0 = now_s() + 1e-3;
     auto client = [&](uint64_t first) {
         struct Out {
@@ -675,6 +676,7 @@ int qpadl_server_replay(qpadl_server *s, uint64_t n, const double *arrival_s, co
         };
         std::vector<Out> out;
         uint64_t next = first;
+        double last_poll = 0.0;
         while (next < n || !out.empty()) {
             bool progress = false;
             const double t = now_s();
@@ -691,7 +693,11 @@ int qpadl_server_replay(qpadl_server *s, uint64_t n, const double *arrival_s, co
                 next += T;
                 progress = true;
             }
-            for (size_t k = 0; k < out.size();) {
+            // poll at most every 20 us: spinning pollers would otherwise crowd the server's lock
+            const double tp = now_s();
+            const bool poll_now = tp - last_poll >= 20e-6 || next >= n;
+            if (poll_now) last_poll = tp;
+            for (size_t k = 0; poll_now && k < out.size();) {
                 qpadl_request_times tm;
                 const uint64_t i = out[k].i;
                 const int rc = qpadl_server_poll(s, out[k].ticket, ans_host ? ans_host[i] : nullptr, &tm);
@@ -701,11 +707,25 @@ int qpadl_server_replay(qpadl_server *s, uint64_t n, const double *arrival_s, co
                 }
                 status[i] = rc;
                 latency_s[i] = (rc == QPADL_OK) ? tm.done_s - (t0 + arrival_s[i]) : -1;
+                if (times) {
+                    // relative to the scheduled arrival of request i
+                    times[i].submit_s = tm.submit_s - (t0 + arrival_s[i]);
+                    times[i].launch_s = tm.launch_s - (t0 + arrival_s[i]);
+                    times[i].done_s = tm.done_s - (t0 + arrival_s[i]);
+                }
                 out[k] = out.back();
                 out.pop_back();
                 progress = true;
             }
-            if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(5));
+            if (!progress) {
+                // sleep through long gaps (waking 100 us early) and spin over the last stretch,
+                // so submissions leave on schedule despite the OS timer slack
+                const double gap = next < n ? t0 + arrival_s[next] - now_s() : 1e-3;
+                if (gap > 2e-4)
+                    std::this_thread::sleep_for(std::chrono::duration<double>(std::min(gap - 1e-4, 1e-3)));
+                else
+                    std::this_thread::yield();
+            }
         }
     };
     std::vector<std::thread> threads;

@@ -97,7 +97,7 @@ _SIGS = {
     "qpadl_server_poll": ([_P, ctypes.c_uint64, _P, _P], ctypes.c_int),
     "qpadl_server_stats": ([_P, _P], ctypes.c_int),
     "qpadl_server_destroy": ([_P], ctypes.c_int),
-    "qpadl_server_replay": ([_P, ctypes.c_uint64, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "qpadl_server_replay": ([_P, ctypes.c_uint64, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "qpadl_pir_recover_batch": ([_P, _P, _P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
 }
 
@@ -516,9 +516,10 @@ def qpadl_server_destroy(srv: Server):
     srv.close()
 
 
-def qpadl_server_replay(srv: Server, arrival_s, db_ids, queries, answers=None):
-    """Open-loop replay (native): returns (latency_s, status) numpy arrays.
-    queries / answers: lists of numpy uint32 arrays (kept alive by the caller)."""
+def qpadl_server_replay(srv: Server, arrival_s, db_ids, queries, answers=None, with_times: bool = False):
+    """Open-loop replay (native): returns (latency_s, status) numpy arrays, plus an
+    n x 3 array of (submit, launch, done) seconds after each scheduled arrival when
+    with_times.  queries / answers: lists of numpy uint32 arrays (kept alive by the caller)."""
     import numpy as np
     n = len(arrival_s)
     arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
@@ -527,7 +528,10 @@ def qpadl_server_replay(srv: Server, arrival_s, db_ids, queries, answers=None):
     ap = (ctypes.c_void_p * n)(*[a.ctypes.data for a in answers]) if answers is not None else None
     lat = np.zeros(n, dtype=np.float64)
     st = np.zeros(n, dtype=np.int32)
+    tm = np.zeros((n, 3), dtype=np.float64) if with_times else None
     _check(load().qpadl_server_replay(srv.handle, n, ctypes.c_void_p(arr.ctypes.data),
                                       ctypes.c_void_p(ids.ctypes.data), qp, ap, ctypes.c_void_p(lat.ctypes.data),
-                                      ctypes.c_void_p(st.ctypes.data)), "qpadl_server_replay")
-    return lat, st
+                                      ctypes.c_void_p(st.ctypes.data),
+                                      ctypes.c_void_p(tm.ctypes.data) if with_times else None),
+           "qpadl_server_replay")
+    return (lat, st, tm) if with_times else (lat, st)

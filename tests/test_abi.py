@@ -97,4 +97,4 @@ def test_invalid_server_config_rejected_before_any_allocation(lib, field, value)
 
 def test_replay_rejects_a_null_server(lib):
     from paper_2510_03631_gb300 import pir
-    assert lib.qpadl_server_replay(None, 0, None, None, None, None, None, None) == pir.QPADL_EINVAL
+    assert lib.qpadl_server_replay(None, 0, None, None, None, None, None, None, None) == pir.QPADL_EINVAL

@@ -228,9 +228,12 @@ def test_replay_open_loop(dbs):
     which = inputs.skewed_choice(n, (0.6, 0.3, 0.1), seed=4)
     queries = [inputs.uniform_u32(SHAPES[d][1], seed=500 + i, tag=7) for i, d in enumerate(which)]
     answers = [np.zeros(SHAPES[d][0], dtype=np.uint32) for d in which]
-    lat, st = pir.qpadl_server_replay(srv, arr, [ids[d] for d in which], queries, answers)
+    lat, st, tm = pir.qpadl_server_replay(srv, arr, [ids[d] for d in which], queries, answers, with_times=True)
     assert (st == pir.QPADL_OK).all()
     assert (lat > 0).all()
+    # submit, launch and completion follow the scheduled arrival in order; latency is completion
+    assert (tm[:, 0] >= -1e-6).all() and (tm[:, 1] >= tm[:, 0]).all() and (tm[:, 2] >= tm[:, 1]).all()
+    assert np.allclose(tm[:, 2], lat)
     for i in range(0, n, 17):
         d = which[i]
         assert np.array_equal(answers[i], oracle.answer(dbs[d][0], queries[i]))
