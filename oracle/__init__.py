@@ -40,7 +40,10 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            # QPADL_ORACLE_LIB names an alternative build of qpadl_oracle.c: the
+            # mutation tests load deliberately broken copies through it to show
+            # that the pins catch each planted mistake
+            lib = ctypes.CDLL(os.environ.get("QPADL_ORACLE_LIB") or build())
             u64, i32, u32 = ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32
             P = ctypes.c_void_p
             lib.oracle_splitmix64.argtypes = [u64, u64]
