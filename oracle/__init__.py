@@ -54,9 +54,13 @@ def _load():
             lib.oracle_answer.argtypes = [P, u64, u64, P, P, i32]
             lib.oracle_answer_batch.argtypes = [P, u64, u64, P, u64, P, i32]
             lib.oracle_recover.argtypes = [P, P, u64, u64, P, u32, P]
+            lib.oracle_chor_answer.argtypes = [P, u64, u64, P, u64, u64, P, i32]
+            lib.oracle_chor_query.argtypes = [P, u64, u64, u64, P]
+            lib.oracle_chor_reconstruct.argtypes = [P, u64, u64, P]
             lib.oracle_max_threads.restype = i32
             for f in ("oracle_gen_a", "oracle_hint", "oracle_query", "oracle_answer",
-                      "oracle_answer_batch", "oracle_recover"):
+                      "oracle_answer_batch", "oracle_recover", "oracle_chor_answer", "oracle_chor_query",
+                      "oracle_chor_reconstruct"):
                 getattr(lib, f).restype = None
             _lib = lib
     return _lib
@@ -159,3 +163,43 @@ def recover(ans: np.ndarray, H: np.ndarray, s: np.ndarray, p: int = 256) -> np.n
 def delta_for(p: int) -> int:
     """Scale Delta = q / p with q = 2^32."""
     return (1 << 32) // p
+
+
+def chor_answer(DB: np.ndarray, r: int, Q: np.ndarray, threads: int = 1) -> np.ndarray:
+    """Chor Response over GF(2): DB is r x w uint32 words (r rows of 32 w bits),
+    Q is B x qw words (qw = ceil(r / 32), bit i of query b = row i selected);
+    returns B x w words, the XOR of the selected rows for each query."""
+    DB = _c(DB, np.uint32)
+    Q = _c(Q, np.uint32)
+    if DB.ndim != 2 or DB.shape[0] != r:
+        raise ValueError("DB must be r x w words")
+    w = DB.shape[1]
+    qw = (r + 31) // 32
+    if Q.ndim != 2 or Q.shape[1] != qw:
+        raise ValueError("Q must be B x ceil(r/32) words")
+    B = Q.shape[0]
+    out = np.empty((B, w), dtype=np.uint32)
+    _load().oracle_chor_answer(_p(DB), r, w, _p(Q), qw, B, _p(out), threads)
+    return out
+
+
+def chor_query(shares: np.ndarray, theta: int) -> np.ndarray:
+    """ENS client query: (ell-1) x qw random words -> ell x qw query words, the
+    last being the XOR of the others with the unit vector at theta."""
+    shares = _c(shares, np.uint32)
+    ell = shares.shape[0] + 1
+    qw = shares.shape[1]
+    if not 0 <= theta < 32 * qw:
+        raise ValueError("theta out of range")
+    out = np.empty((ell, qw), dtype=np.uint32)
+    _load().oracle_chor_query(_p(shares), ell, qw, theta, _p(out))
+    return out
+
+
+def chor_reconstruct(responses: np.ndarray) -> np.ndarray:
+    """ENS reconstruction: XOR of the ell responses (ell x w words)."""
+    responses = _c(responses, np.uint32)
+    ell, w = responses.shape
+    out = np.empty(w, dtype=np.uint32)
+    _load().oracle_chor_reconstruct(_p(responses), ell, w, _p(out))
+    return out

@@ -142,6 +142,66 @@ void oracle_recover(const uint32_t *ans, const uint32_t *H, uint64_t R, uint64_t
     }
 }
 
+/* ---------------------------------------------------------------------------
+ * Chor-style PIR over GF(2) (Sec. 5.2 "Parallel Chor-PIR", Alg. 3; the ENS
+ * instantiation of Sec. 7).  The database is r rows of b bits, a record is a
+ * row, and the server's response to an r-bit query q is rho = q . DB over
+ * GF(2): the XOR of the rows whose query bit is set.
+ * Packing (a reading; the paper fixes none): bit c of row i is bit c % 32 of
+ * word db[i * w + c / 32] (w = b / 32 words per row); bit i of a query is bit
+ * i % 32 of word q[i / 32] (qw = ceil(r / 32) words); query bits at positions
+ * >= r are ignored.  Query b of a batch starts at q + b * qw, its response at
+ * out + b * w.
+ */
+void oracle_chor_answer(const uint32_t *db, uint64_t r, uint64_t w, const uint32_t *q, uint64_t qw,
+                        uint64_t B, uint32_t *out, int nthreads)
+{
+    int nt = oracle_threads(nthreads);
+    (void)nt;
+#pragma omp parallel for num_threads(nt) schedule(static)
+    for (int64_t b = 0; b < (int64_t)B; ++b) {
+        uint32_t *rho = out + (uint64_t)b * w;
+        const uint32_t *qb = q + (uint64_t)b * qw;
+        for (uint64_t c = 0; c < w; ++c)
+            rho[c] = 0;
+        for (uint64_t i = 0; i < r; ++i) {
+            if ((qb[i / 32] >> (i % 32)) & 1u) {
+                for (uint64_t c = 0; c < w; ++c)
+                    rho[c] ^= db[i * w + c];
+            }
+        }
+    }
+}
+
+/* Client query of the ENS instantiation (Sec. 7): given ell - 1 uniformly
+ * random r-bit vectors, the last vector is their XOR with the unit vector
+ * e_theta.  shares: (ell - 1) x qw words; queries: ell x qw words. */
+void oracle_chor_query(const uint32_t *shares, uint64_t ell, uint64_t qw, uint64_t theta, uint32_t *queries)
+{
+    for (uint64_t k = 0; k < qw; ++k) {
+        uint32_t acc = 0;
+        for (uint64_t j = 0; j + 1 < ell; ++j) {
+            queries[j * qw + k] = shares[j * qw + k];
+            acc ^= shares[j * qw + k];
+        }
+        if (k == theta / 32)
+            acc ^= 1u << (theta % 32);
+        queries[(ell - 1) * qw + k] = acc;
+    }
+}
+
+/* Reconstruction of the ENS instantiation (Sec. 7): D_theta = XOR of the ell
+ * responses.  responses: ell x w words; out: w words. */
+void oracle_chor_reconstruct(const uint32_t *responses, uint64_t ell, uint64_t w, uint32_t *out)
+{
+    for (uint64_t c = 0; c < w; ++c) {
+        uint32_t acc = 0;
+        for (uint64_t j = 0; j < ell; ++j)
+            acc ^= responses[j * w + c];
+        out[c] = acc;
+    }
+}
+
 int oracle_max_threads(void)
 {
 #ifdef _OPENMP

@@ -175,6 +175,23 @@ def skewed_choice(count: int, weights, seed: int) -> np.ndarray:
 
 
 # Named workloads: sizes of the spectrum-database configurations measured here.
+def chor_db(rows: int, bits: int, seed: int) -> np.ndarray:
+    """Chor database: rows x bits uniform bits, packed rows x (bits / 32) uint32 words."""
+    if bits % 32:
+        raise ValueError("bits must be a multiple of 32")
+    return uniform_u32(rows * (bits // 32), seed, TAG_DB).reshape(rows, bits // 32)
+
+
+def chor_queries(batch: int, rows: int, seed: int) -> np.ndarray:
+    """Uniformly random rows-bit query vectors (what each server sees), packed
+    batch x ceil(rows / 32) words, bits at positions >= rows cleared."""
+    qw = (rows + 31) // 32
+    Q = uniform_u32(batch * qw, seed, TAG_MISC).reshape(batch, qw)
+    if rows % 32:
+        Q[:, -1] &= np.uint32((1 << (rows % 32)) - 1)
+    return Q
+
+
 WORKLOADS = {
     "tiny": dict(rows=1024, cols=1024, n=512, p=256, sigma=6.4),
     "single_1gib": dict(rows=32768, cols=32768, n=1024, p=256, sigma=6.4),
@@ -182,4 +199,6 @@ WORKLOADS = {
     "hint_1gib": dict(rows=32768, cols=32768, n=1024, p=256, sigma=6.4, batch=1024),
     "serving": dict(dbs=[(4096, 4096), (16384, 16384), (32768, 32768), (65536, 32768)],
                     n=1024, p=256, sigma=6.4, skew=(0.60, 0.25, 0.10, 0.05)),
+    # Chor Response over GF(2): 1 GiB of bits, 32768 records of 32 KiB (262144 bits)
+    "chor_1gib": dict(rows=32768, bits=262144, batches=(1, 8, 32, 128, 256, 1024)),
 }

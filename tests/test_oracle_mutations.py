@@ -43,6 +43,13 @@ MUTATIONS = [
     ("recover mask added", "uint32_t x = ans[i] - mask;", "uint32_t x = ans[i] + mask;"),
     ("recover shift off by one", "uint32_t shift = 32u - log2_p;", "uint32_t shift = 31u - log2_p;"),
     ("recover transposed H", "mask += H[i * n + k] * s[k];", "mask += H[k * R + i] * s[k];"),
+    ("chor OR instead of XOR", "rho[c] ^= db[i * w + c];", "rho[c] |= db[i * w + c];"),
+    ("chor query bit order", "if ((qb[i / 32] >> (i % 32)) & 1u) {", "if ((qb[i / 32] >> (31 - i % 32)) & 1u) {"),
+    ("chor last row skipped", "for (uint64_t i = 0; i < r; ++i) {\n            if ((qb",
+     "for (uint64_t i = 0; i + 1 < r; ++i) {\n            if ((qb"),
+    ("chor unit bit misplaced", "acc ^= 1u << (theta % 32);", "acc ^= 1u << ((theta + 1) % 32);"),
+    ("chor reconstruct drops a response", "for (uint64_t j = 0; j < ell; ++j)\n            acc ^= responses",
+     "for (uint64_t j = 1; j < ell; ++j)\n            acc ^= responses"),
 ]
 
 

@@ -273,3 +273,98 @@ def test_noise_distribution():
     assert abs(e.mean()) < 0.1
     assert abs(e.std() - np.sqrt(6.4 ** 2 + 1 / 12)) < 0.1
     assert np.abs(e).max() <= 64
+
+
+# ----------------------------------------------------------------------------- Chor over GF(2)
+# Sec. 5.2 "Parallel Chor-PIR": rho = q . DB over GF(2), the XOR of the rows
+# whose query bit is set; Sec. 7 (ENS): ell - 1 random queries plus their XOR
+# with e_theta, and D_theta = XOR of the ell responses.
+
+def _bits(words: np.ndarray, nbits: int) -> np.ndarray:
+    """Unpack uint32 words (LSB first) into a 0/1 int64 array of nbits."""
+    b = ((words[..., :, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(*words.shape[:-1], -1)
+    return b[..., :nbits].astype(np.int64)
+
+
+def test_chor_hand_worked_example():
+    # three 32-bit rows; query selects rows 0 and 2
+    DB = np.array([[0x0000000F], [0x000000F0], [0x00000F0F]], dtype=np.uint32)
+    Q = np.array([[0b101]], dtype=np.uint32)
+    assert oracle.chor_answer(DB, 3, Q)[0, 0] == 0x0000000F ^ 0x00000F0F == 0x00000F00
+
+
+def test_chor_brute_force_python_ints():
+    rng = np.random.default_rng(11)
+    r, w = 37, 3
+    DB = rng.integers(0, 2**32, (r, w), dtype=np.uint64).astype(np.uint32)
+    Q = rng.integers(0, 2**32, (5, 2), dtype=np.uint64).astype(np.uint32)
+    Q[:, 1] &= (1 << (r - 32)) - 1
+    got = oracle.chor_answer(DB, r, Q)
+    rows = [sum(int(DB[i, c]) << (32 * c) for c in range(w)) for i in range(r)]
+    for b in range(5):
+        qint = int(Q[b, 0]) | (int(Q[b, 1]) << 32)
+        acc = 0
+        for i in range(r):
+            if (qint >> i) & 1:
+                acc ^= rows[i]
+        assert sum(int(got[b, c]) << (32 * c) for c in range(w)) == acc
+
+
+def test_chor_equals_integer_matmul_mod_2():
+    # GF(2) product = integer product of the 0/1 matrices, reduced mod 2 (numpy matmul)
+    r, bits = 300, 256
+    DB = inputs.chor_db(r, bits, seed=5)
+    Q = inputs.chor_queries(9, r, seed=6)
+    got = oracle.chor_answer(DB, r, Q)
+    exp = (_bits(Q, r) @ _bits(DB, bits)) % 2
+    assert np.array_equal(_bits(got, bits), exp)
+
+
+def test_chor_unit_queries_select_rows():
+    r, bits = 70, 128
+    DB = inputs.chor_db(r, bits, seed=7)
+    Q = np.zeros((r, (r + 31) // 32), dtype=np.uint32)
+    for t in range(r):
+        Q[t, t // 32] = np.uint32(1 << (t % 32))
+    assert np.array_equal(oracle.chor_answer(DB, r, Q), DB)
+
+
+def test_chor_zero_all_ones_linearity_and_padding():
+    r, bits = 45, 96
+    DB = inputs.chor_db(r, bits, seed=8)
+    qw = (r + 31) // 32
+    zero = np.zeros((1, qw), dtype=np.uint32)
+    assert not oracle.chor_answer(DB, r, zero).any()
+    ones = np.full((1, qw), 0xFFFFFFFF, dtype=np.uint32)   # bits past r are ignored
+    assert np.array_equal(oracle.chor_answer(DB, r, ones)[0], np.bitwise_xor.reduce(DB, axis=0))
+    q1, q2 = inputs.chor_queries(1, r, seed=9), inputs.chor_queries(1, r, seed=10)
+    a = oracle.chor_answer(DB, r, np.concatenate([q1, q2, q1 ^ q2]))
+    assert np.array_equal(a[2], a[0] ^ a[1])
+    garbage = q1.copy()
+    garbage[0, -1] |= np.uint32(0xFFFFFFFF << (r % 32) & 0xFFFFFFFF)
+    assert np.array_equal(oracle.chor_answer(DB, r, garbage), a[:1])
+
+
+@pytest.mark.parametrize("ell", [2, 3, 5])
+def test_chor_ens_protocol_recovers_the_record(ell):
+    r, bits = 200, 160
+    DB = inputs.chor_db(r, bits, seed=12)
+    qw = (r + 31) // 32
+    for theta in (0, 31, 32, 199):
+        shares = inputs.chor_queries(ell - 1, r, seed=100 + theta)
+        queries = oracle.chor_query(shares, theta)
+        assert queries.shape == (ell, qw)
+        # the last query differs from the XOR of the others in exactly bit theta
+        diff = np.bitwise_xor.reduce(queries, axis=0)
+        exp = np.zeros(qw, dtype=np.uint32)
+        exp[theta // 32] = np.uint32(1 << (theta % 32))
+        assert np.array_equal(diff, exp)
+        responses = oracle.chor_answer(DB, r, queries)
+        assert np.array_equal(oracle.chor_reconstruct(responses), DB[theta])
+
+
+def test_chor_thread_count_invariance():
+    r, bits = 513, 1024
+    DB = inputs.chor_db(r, bits, seed=13)
+    Q = inputs.chor_queries(16, r, seed=14)
+    assert np.array_equal(oracle.chor_answer(DB, r, Q, threads=1), oracle.chor_answer(DB, r, Q, threads=4))
