@@ -321,6 +321,42 @@ int qpadl_client_set_option(qpadl_client *c, int option, int64_t value);
 int qpadl_client_destroy(qpadl_client *c);
 
 /* ======================================================================
+ * Chor-style Response over GF(2) (Sec. 5.2 "Parallel Chor-PIR", Alg. 3;
+ * the ENS instantiation of Sec. 7): the database is `rows` records of `bits`
+ * bits, the server's answer to an rows-bit query q is rho = q . DB over
+ * GF(2), the XOR of the records whose query bit is set.  The client XORs
+ * the answers of ell servers to its ell queries (ell - 1 random, the last
+ * their XOR with the unit vector e_theta) and obtains record theta.
+ *
+ * Packing: bit c of record i is bit c % 32 of word i * (bits/32) + c / 32;
+ * bit i of a query is bit i % 32 of its word i / 32 (ceil(rows/32) words per
+ * query; bits at positions >= rows are ignored).
+ * ==================================================================== */
+typedef struct qpadl_chor qpadl_chor;
+
+/* Binds a resident database (db_dev: rows x bits/32 uint32 words, caller-
+ * owned, 16-byte aligned, kept until destroy) on the current device and
+ * allocates the handle's scratch (32 bytes per row).  QPADL_EINVAL if rows
+ * is 0 or >= 2^31, bits is not a positive multiple of 128, or db_dev is
+ * NULL or misaligned. */
+int qpadl_chor_setup(uint64_t rows, uint64_t bits, const uint32_t *db_dev, qpadl_stream_t stream,
+                     qpadl_chor **out);
+
+/* Answers B queries (Q_dev: B x ceil(rows/32) words, query b in row b) in
+ * one pass over the database per 256 queries; out_dev: B x bits/32 words
+ * (answer b in row b), overwritten.  Calls on one handle share its scratch:
+ * issue them on one stream (or order them). */
+int qpadl_chor_answer_batch(qpadl_chor *h, const uint32_t *Q_dev, uint32_t B, uint32_t *out_dev,
+                            qpadl_stream_t stream);
+
+/* Synchronises the device; QPADL_ETIMEOUT (and clears it) if a kernel of this
+ * handle gave up a bounded wait since the last call. */
+int qpadl_chor_status(qpadl_chor *h);
+
+/* Waits for the device and frees the handle (not the database). */
+int qpadl_chor_destroy(qpadl_chor *h);
+
+/* ======================================================================
  * Serving: a continuous-batching request loop over several resident
  * databases (the paper's server answering q-bar queries per database,
  * Sec. 5.2, run as a long-lived service).  Requests arrive from any host

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include "chor.cuh"
 #include "client.cuh"
 #include "limb_gemm.cuh"
 #include "limb_gemm_u8.cuh"
@@ -73,6 +74,19 @@ struct qpadl_client {
     bool planed = true;              // skip the zero (plane, shift) blocks when n % 512 == 0
 };
 
+// Chor-style GF(2) database handle.
+struct qpadl_chor {
+    uint64_t rows = 0;
+    uint32_t words = 0;              // W = bits / 32 per row
+    uint64_t qw = 0;                 // query words: ceil(rows / 32)
+    const uint32_t *db = nullptr;    // caller-owned, rows x W words
+    int device = 0;
+    int num_sms = 0;
+    uint32_t *qt = nullptr;          // transposed selector bits: rows x 8 words
+    int *d_status = nullptr;
+    uint64_t owned_bytes = 0;
+};
+
 namespace {
 
 constexpr int kMaxN = 16384;
@@ -129,6 +143,7 @@ int prepare_device(int dev) {
     QPADL_CU(prepare_limb_gemm_kernels());
     QPADL_CU(prepare_limb_gemm_u8_kernels());
     QPADL_CU(prepare_client_kernels());
+    QPADL_CU(prepare_chor_kernels());
     prepared[dev] = true;
     return QPADL_OK;
 }
@@ -868,6 +883,97 @@ int qpadl_client_set_option(qpadl_client *c, int option, int64_t value) {
             return QPADL_OK;
         default: return QPADL_EINVAL;
     }
+}
+
+// ------------------------------------------------------------------ Chor-style GF(2) Response
+
+int qpadl_chor_destroy(qpadl_chor *h) {
+    if (!h) return QPADL_OK;
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != h->device) cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    if (h->qt) cudaFree(h->qt);
+    if (h->d_status) cudaFree(h->d_status);
+    if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
+    delete h;
+    return QPADL_OK;
+}
+
+int qpadl_chor_setup(uint64_t rows, uint64_t bits, const uint32_t *db_dev, qpadl_stream_t stream,
+                     qpadl_chor **out) {
+    if (!out) return QPADL_EINVAL;
+    *out = nullptr;
+    if (!db_dev || rows == 0 || rows >= (1ull << 31) || bits == 0 || bits % 128 != 0 || bits / 32 >= (1ull << 31) ||
+        (reinterpret_cast<uintptr_t>(db_dev) & 15u) != 0)
+        return QPADL_EINVAL;
+    qpadl_chor *h = new (std::nothrow) qpadl_chor();
+    if (!h) return QPADL_ENOMEM;
+    h->rows = rows;
+    h->words = static_cast<uint32_t>(bits / 32);
+    h->qw = (rows + 31) / 32;
+    h->db = db_dev;
+    auto fail = [&](int code) {
+        qpadl_chor_destroy(h);
+        return code;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess) return fail(QPADL_ECUDA);
+    if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
+        return fail(QPADL_ECUDA);
+    int rc = prepare_device(h->device);
+    if (rc != QPADL_OK) return fail(rc);
+    const uint64_t qt_bytes = 4ull * rows * 8;
+    if (cudaMalloc(reinterpret_cast<void **>(&h->qt), qt_bytes) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void **>(&h->d_status), 16) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QPADL_ENOMEM);
+    }
+    h->owned_bytes = qt_bytes + 16;
+    if (cudaMemsetAsync(h->d_status, 0, 16, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return fail(QPADL_ECUDA);
+    *out = h;
+    return QPADL_OK;
+}
+
+int qpadl_chor_answer_batch(qpadl_chor *h, const uint32_t *Q_dev, uint32_t B, uint32_t *out_dev,
+                            qpadl_stream_t stream) {
+    if (!h || !Q_dev || !out_dev || B == 0) return QPADL_EINVAL;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return QPADL_ECUDA;
+    if (cur != h->device && cudaSetDevice(h->device) != cudaSuccess) return QPADL_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t W = h->words;
+    QPADL_CU(cudaMemsetAsync(out_dev, 0, 4ull * W * B, s));
+    for (uint32_t b0 = 0; b0 < B; b0 += kChorMaxBatch) {
+        const uint32_t Bc = std::min(B - b0, kChorMaxBatch);
+        uint32_t tw = 0, rb = 0, boxw = 0, qtw = 0;
+        if (!chor_launch_shape(Bc, &tw, &rb, &boxw, &qtw)) return QPADL_EINVAL;
+        QPADL_CU(launch_chor_transpose(Q_dev + (uint64_t)b0 * h->qw, h->qw, Bc, h->rows, qtw, h->qt, h->num_sms, s));
+        CUtensorMap db_map, qt_map;
+        if (!encode_2d(&db_map, CU_TENSOR_MAP_DATA_TYPE_UINT32, h->db, W, h->rows, W * 4, boxw, rb,
+                       CU_TENSOR_MAP_SWIZZLE_NONE) ||
+            !encode_2d(&qt_map, CU_TENSOR_MAP_DATA_TYPE_UINT32, h->qt, qtw, h->rows, 4ull * qtw, qtw, rb,
+                       CU_TENSOR_MAP_SWIZZLE_NONE))
+            return QPADL_ECUDA;
+        QPADL_CU(launch_chor_answer(db_map, qt_map, h->rows, static_cast<uint32_t>(W), Bc, qtw,
+                                    out_dev + (uint64_t)b0 * W, h->num_sms, h->d_status, s));
+    }
+    return QPADL_OK;
+}
+
+int qpadl_chor_status(qpadl_chor *h) {
+    if (!h) return QPADL_EINVAL;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return QPADL_ECUDA;
+    if (cur != h->device && cudaSetDevice(h->device) != cudaSuccess) return QPADL_ECUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return QPADL_ECUDA;
+    int st = 0;
+    if (cudaMemcpy(&st, h->d_status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return QPADL_ECUDA;
+    if (st != 0) {
+        const int zero = 0;
+        cudaMemcpy(h->d_status, &zero, 4, cudaMemcpyHostToDevice);
+        return QPADL_ETIMEOUT;
+    }
+    return QPADL_OK;
 }
 
 }  // extern "C"

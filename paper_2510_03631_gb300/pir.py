@@ -90,6 +90,10 @@ _SIGS = {
     "qpadl_client_device_bytes": ([_P], ctypes.c_uint64),
     "qpadl_client_set_option": ([_P, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
     "qpadl_client_destroy": ([_P], ctypes.c_int),
+    "qpadl_chor_setup": ([ctypes.c_uint64, ctypes.c_uint64, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "qpadl_chor_answer_batch": ([_P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
+    "qpadl_chor_status": ([_P], ctypes.c_int),
+    "qpadl_chor_destroy": ([_P], ctypes.c_int),
     "qpadl_server_create": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
     "qpadl_server_add_db": ([_P, _P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "qpadl_server_start": ([_P], ctypes.c_int),
@@ -385,6 +389,58 @@ def qpadl_client_set_option(c: Client, option: int, value: int):
 
 def qpadl_client_device_bytes(c: Client) -> int:
     return int(load().qpadl_client_device_bytes(c.handle))
+
+
+class ChorDatabase:
+    """Handle returned by qpadl_chor_setup (owns the C handle, keeps the database alive)."""
+
+    def __init__(self, handle: ctypes.c_void_p, rows: int, bits: int, db: torch.Tensor):
+        self.handle = handle
+        self.rows = rows
+        self.bits = bits
+        self.db = db
+
+    @property
+    def words(self) -> int:
+        return self.bits // 32
+
+    @property
+    def query_words(self) -> int:
+        return (self.rows + 31) // 32
+
+    def close(self):
+        if self.handle:
+            load().qpadl_chor_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qpadl_chor_setup(rows: int, bits: int, db: torch.Tensor, stream=None) -> ChorDatabase:
+    """db: rows x bits/32 int32 words (bit c of record i = bit c % 32 of word c / 32)."""
+    pd = _dev(db, torch.int32, int(rows) * (int(bits) // 32), "db")
+    h = ctypes.c_void_p()
+    _check(load().qpadl_chor_setup(int(rows), int(bits), pd, _stream(stream), ctypes.byref(h)), "qpadl_chor_setup")
+    return ChorDatabase(h, int(rows), int(bits), db)
+
+
+def qpadl_chor_answer_batch(h: ChorDatabase, Q: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """Q: B x ceil(rows/32) int32 words; out: B x bits/32 int32 words."""
+    B = Q.numel() // h.query_words
+    if B * h.query_words != Q.numel() or B == 0:
+        raise ValueError("Q must hold B x ceil(rows/32) words")
+    _check(load().qpadl_chor_answer_batch(h.handle, _dev(Q, torch.int32, B * h.query_words, "Q"), B,
+                                          _dev(out, torch.int32, B * h.words, "out"), _stream(stream)),
+           "qpadl_chor_answer_batch")
+    return out
+
+
+def qpadl_chor_status(h: ChorDatabase) -> int:
+    return int(load().qpadl_chor_status(h.handle))
 
 
 def as_u32(t: torch.Tensor):
