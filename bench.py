@@ -335,6 +335,57 @@ def serving_measure(torch, pir, inputs, rates, duration_s, single_db_one_ms, see
     }
 
 
+def chor_measure(torch, pir, inputs, seed=31):
+    """Chor Response over GF(2) (Sec. 5.2, Alg. 3) on a 1 GiB bit database:
+    32768 records of 262144 bits; batches of uniformly random queries, one
+    pass over the database per 256 queries.  Checks query 0 of every batch on
+    its first 64 words against a host XOR of the selected records."""
+    w = inputs.WORKLOADS["chor_1gib"]
+    rows, bits = w["rows"], w["bits"]
+    W = bits // 32
+    DB_np = inputs.chor_db(rows, bits, seed=seed)
+    h = pir.qpadl_chor_setup(rows, bits, torch.from_numpy(DB_np.view(np.int32).reshape(-1)).cuda())
+    peak, peak_kind = _peaks()
+    res = {"workload": f"{rows} records x {bits} bits (1 GiB)", "batches": {}}
+    one_qps = None
+    for B in w["batches"]:
+        Q_np = inputs.chor_queries(B, rows, seed=seed + B)
+        Q = torch.from_numpy(Q_np.view(np.int32).reshape(-1)).cuda()
+        out = torch.empty(B * W, dtype=torch.int32, device="cuda")
+        pir.qpadl_chor_answer_batch(h, Q, out)
+        torch.cuda.synchronize()
+        reps = 20 if B <= 32 else 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            pir.qpadl_chor_answer_batch(h, Q, out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        sel = ((Q_np[0][np.arange(rows) // 32] >> (np.arange(rows) % 32).astype(np.uint32)) & 1).astype(bool)
+        exp = np.bitwise_xor.reduce(DB_np[sel, :64], axis=0)
+        if not np.array_equal(pir.as_u32(out)[:64], exp) or pir.qpadl_chor_status(h) != 0:
+            raise SystemExit("bench: Chor answer differs from the host XOR")
+        qps = B / (ms * 1e-3)
+        if B == 1:
+            one_qps = qps
+        alg = rows * W * 4 + B * ((rows + 31) // 32) * 4 + B * W * 4
+        ent = {"ms": round(ms, 4), "queries_per_s": round(qps, 1),
+               "db_scan_gbs": round(B * rows * W * 4 / (ms * 1e-3) / 1e9, 1),
+               "kernel": "four-Russians" if B >= pir.qpadl_chor_get_option(h, pir.QPADL_CHOR_OPT_M4RM_MIN_BATCH)
+               else "masked-XOR scan"}
+        if one_qps:
+            ent["x_vs_one_at_a_time"] = round(qps / one_qps, 2)
+        if B == 1:
+            ent["roofline"] = {"bound": "hbm", "achieved": round(alg / (ms * 1e-3) / 1e9, 1), "peak": peak,
+                               "unit": "GB/s", "frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4),
+                               "peak_kind": peak_kind, "alg_bytes_per_launch": alg}
+        res["batches"][str(B)] = ent
+        del Q, out
+    h.close()
+    return res
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_ours(args):
     import torch
@@ -549,12 +600,15 @@ def run_ours(args):
         raise SystemExit("bench: e2e recovered record differs")
 
     serving = None
+    chor = None
     if not args.quick:
         db.close()
         del D
         torch.cuda.empty_cache()
         serving = serving_measure(torch, pir, inputs, rates=(1000, 5000, 10000, 20000, 50000),
                                   duration_s=1.0, single_db_one_ms=resp_ms_avg)
+        torch.cuda.empty_cache()
+        chor = chor_measure(torch, pir, inputs)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -591,6 +645,7 @@ def run_ours(args):
         "hint_ms": round(min(hint_ms), 3),
         "client_batch_1024": client,
         "serving": serving,
+        "chor_gf2": chor,
         "gpu_launches": 4 * K,
         "timing": "CUDA events around K replays of per-step CUDA graphs (64-query pool)",
         "e2e": {"value": round(R * C / e2e_s / 1e9, 2), "unit": "GB/s", "ms_per_step": round(e2e_s * 1e3, 4),

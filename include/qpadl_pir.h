@@ -349,6 +349,15 @@ int qpadl_chor_setup(uint64_t rows, uint64_t bits, const uint32_t *db_dev, qpadl
 int qpadl_chor_answer_batch(qpadl_chor *h, const uint32_t *Q_dev, uint32_t B, uint32_t *out_dev,
                             qpadl_stream_t stream);
 
+/* Options (every setting gives the same results):
+ * QPADL_CHOR_OPT_M4RM_MIN_BATCH (1..257, default 48): batches (per chunk of
+ *   256) of at least this many queries use the four-Russians kernel (4-row
+ *   XOR tables in shared memory, looked up by 4 query bits); smaller ones the
+ *   masked-XOR scan.  257 disables the four-Russians kernel. */
+#define QPADL_CHOR_OPT_M4RM_MIN_BATCH 1
+int qpadl_chor_set_option(qpadl_chor *h, int option, int64_t value);
+int qpadl_chor_get_option(qpadl_chor *h, int option, int64_t *value);
+
 /* Synchronises the device; QPADL_ETIMEOUT (and clears it) if a kernel of this
  * handle gave up a bounded wait since the last call. */
 int qpadl_chor_status(qpadl_chor *h);

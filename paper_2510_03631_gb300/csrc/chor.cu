@@ -22,8 +22,16 @@
 //  3. When a CTA leaves a column tile it folds its partial XORs into the
 //     zeroed response with 32-bit atomic XORs: XOR is exact, associative and
 //     commutative, so the split over CTAs changes nothing.
+//  4. Large batches take chor_m4rm_kernel instead (the method of four
+//     Russians): per band of 64 rows the CTA builds, for each group of 4
+//     rows, the 16 XOR combinations of those rows over its 64-word column
+//     tile in shared memory, and each query then adds one table entry per
+//     4 rows, indexed by its 4 selector bits: 4 XORs per 4 rows x 4 words
+//     instead of 16 masked XORs, at one 16-byte shared load per lookup.
+//     Thread = (word quad, group of 16 queries), 256 queries per pass.
 // Every mbarrier wait is bounded (2 s of %globaltimer); a CTA that gives up
 // raises the status word and leaves, no kernel traps.
+#include <algorithm>
 #include <cstdint>
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -197,6 +205,194 @@ __global__ void __launch_bounds__(kChorThreads + 32, 1)
     }
 }
 
+// ------------------------------------------------------------------ four Russians
+constexpr uint32_t kM4TW = 64;                    // column tile (words)
+constexpr uint32_t kM4RB = 64;                    // band (rows) = two query words
+constexpr uint32_t kM4Tables = kM4RB / 4;         // 4-row tables per band
+constexpr uint32_t kM4Quads = kM4TW / 4;          // 16: half a warp spans a tile row
+constexpr int kM4QB = 16;                         // queries per thread
+constexpr uint32_t kM4StageBytes = kM4RB * kM4TW * 4;          // 16 KB of database words
+constexpr uint32_t kM4QWords = kM4RB / 32;                     // query words per band
+constexpr uint32_t kM4QBytes = kM4QWords * kChorMaxBatch * 4;   // 2 KB of query words
+constexpr uint32_t kM4TableBytes = kM4Tables * 16 * kM4TW * 4;  // 64 KB: [table][entry][quad] of uint4
+
+// Q (B x qw words) -> QS (roundup(qw, 2) x 256 words): QS[k][b] = word k of
+// query b (zero for b >= B or k >= qw; bits at positions >= r cleared).
+__global__ void chor_words_kernel(const uint32_t *__restrict__ Q, uint64_t qw, uint32_t B, uint64_t r,
+                                  uint32_t *__restrict__ QS) {
+    const uint64_t total = (qw + kM4QWords - 1) / kM4QWords * kM4QWords * kChorMaxBatch;
+    const uint32_t tail = static_cast<uint32_t>(r % 32);
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = e / kChorMaxBatch;
+        const uint32_t b = static_cast<uint32_t>(e - k * kChorMaxBatch);
+        uint32_t v = (b < B && k < qw) ? Q[(uint64_t)b * qw + k] : 0u;
+        if (tail && k == qw - 1) v &= (1u << tail) - 1u;
+        QS[e] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kChorThreads + 32, 1)
+    chor_m4rm_kernel(const __grid_constant__ CUtensorMap db_map, const uint32_t *__restrict__ QS, uint64_t r,
+                     uint32_t W, uint32_t B, uint32_t *__restrict__ out, int *__restrict__ status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *db_st = smem;                                               // [stage] 32 rows x 128 words
+    uint8_t *q_st = db_st + kChorStages * kM4StageBytes;                 // [stage] 256 query words
+    uint8_t *tab = q_st + kChorStages * kM4QBytes;                       // [2][table][entry][quad] uint4
+    uint64_t *full = reinterpret_cast<uint64_t *>(tab + 2 * kM4TableBytes);
+    uint64_t *empty = full + kChorStages;
+    uint64_t *built = empty + kChorStages;   // [2]: every consumer warp has written its part of table buffer b
+    volatile int *abort = reinterpret_cast<volatile int *>(built + 2);
+
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kChorStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kChorThreads / 32);
+        }
+        mbar_init(&built[0], kChorThreads / 32);
+        mbar_init(&built[1], kChorThreads / 32);
+        *abort = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    const uint64_t n_tiles = (W + kM4TW - 1) / kM4TW;
+    const uint64_t n_bands = (r + kM4RB - 1) / kM4RB;
+    const uint64_t units = n_tiles * n_bands;
+    const uint64_t u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
+    bool failed = false;
+
+    if (warp == kChorThreads / 32) {
+        // ---------------- producer: database tile band + the band's query words
+        if (lane == 0) {
+            tma_prefetch_desc(&db_map);
+            uint32_t it = 0;
+            for (uint64_t u = u0; u < u1; ++u, ++it) {
+                const uint32_t st = it % kChorStages, ph = (it / kChorStages) & 1u;
+                if (!mbar_wait(&empty[st], ph ^ 1u, abort)) {
+                    failed = true;
+                    break;
+                }
+                const uint64_t tile = u / n_bands, band = u - tile * n_bands;
+                mbar_arrive_expect_tx(&full[st], kM4StageBytes + kM4QBytes);
+                tma_load_2d(db_st + st * kM4StageBytes, &db_map, &full[st], static_cast<int32_t>(tile * kM4TW),
+                            static_cast<int32_t>(band * kM4RB));
+                bulk_load(q_st + st * kM4QBytes, QS + band * kM4QWords * kChorMaxBatch, kM4QBytes, &full[st]);
+            }
+            const uint32_t inflight = it < (uint32_t)kChorStages ? it : (uint32_t)kChorStages;
+            for (uint32_t j = it - inflight; j < it; ++j) {
+                const uint64_t t0 = global_ns();
+                while (!mbar_test(&full[j % kChorStages], (j / kChorStages) & 1u))
+                    if (global_ns() - t0 > QPADL_WAIT_NS) {
+                        failed = true;
+                        break;
+                    }
+            }
+        }
+    } else {
+        // ---------------- consumers: thread = (word quad of the tile, group of 16 queries)
+        const uint32_t quad = lane & 15, g = warp * 2 + (lane >> 4);
+        // table parts built by this thread: tables bt + 8 i, word quad bq, entries 8 hh .. 8 hh + 7
+        const uint32_t bt = warp, bq = lane & 15, hh = lane >> 4;
+        uint32_t acc[kM4QB][4];
+#pragma unroll
+        for (int j = 0; j < kM4QB; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0u;
+        const bool active = g * kM4QB < B;
+        uint64_t cur_tile = u0 < u1 ? u0 / n_bands : 0;
+        auto flush = [&](uint64_t tile) {
+            const uint64_t w0 = tile * kM4TW + quad * 4;
+#pragma unroll
+            for (int j = 0; j < kM4QB; ++j) {
+                const uint32_t b = g * kM4QB + j;
+                if (b < B) {
+                    uint32_t *o = out + (uint64_t)b * W + w0;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (w0 + k < W && acc[j][k]) atomicXor(o + k, acc[j][k]);
+                }
+                acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0u;
+            }
+        };
+        auto X = [](uint4 a, uint4 b) { return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w); };
+        uint32_t it = 0;
+        for (uint64_t u = u0; u < u1; ++u, ++it) {
+            const uint64_t tile = u / n_bands;
+            if (tile != cur_tile) {
+                flush(cur_tile);
+                cur_tile = tile;
+            }
+            const uint32_t st = it % kChorStages, ph = (it / kChorStages) & 1u;
+            const bool ok = mbar_wait(&full[st], ph, abort);
+            if (__any_sync(0xffffffffu, !ok)) {
+                failed = true;
+                break;
+            }
+#pragma unroll
+            for (uint32_t half = 0; half < kM4Tables / 8; ++half) {
+                // table bt + 8 half: entry m = XOR of the rows whose bit is set in m; entries 8..15 add row 3
+                const uint32_t tb = bt + 8 * half;
+                const uint4 *rows = reinterpret_cast<const uint4 *>(db_st + st * kM4StageBytes) + bq;
+                const uint4 x0 = rows[(4 * tb + 0) * kM4Quads], x1 = rows[(4 * tb + 1) * kM4Quads];
+                const uint4 x2 = rows[(4 * tb + 2) * kM4Quads];
+                const uint4 z = hh ? rows[(4 * tb + 3) * kM4Quads] : make_uint4(0u, 0u, 0u, 0u);
+                uint4 *Tq = reinterpret_cast<uint4 *>(tab + (it & 1u) * kM4TableBytes) + (tb * 16 + 8 * hh) * kM4Quads + bq;
+                const uint4 x01 = X(x0, x1);
+                Tq[0 * kM4Quads] = z;
+                Tq[1 * kM4Quads] = X(z, x0);
+                Tq[2 * kM4Quads] = X(z, x1);
+                Tq[3 * kM4Quads] = X(z, x01);
+                Tq[4 * kM4Quads] = X(z, x2);
+                Tq[5 * kM4Quads] = X(X(z, x0), x2);
+                Tq[6 * kM4Quads] = X(X(z, x1), x2);
+                Tq[7 * kM4Quads] = X(X(z, x01), x2);
+            }
+            // query 32 warp + lane's words for the band's rows
+            static_assert(kM4QWords == 2, "two query words per band");
+            uint32_t qwd[kM4QWords];
+#pragma unroll
+            for (uint32_t k = 0; k < kM4QWords; ++k)
+                qwd[k] = reinterpret_cast<const uint32_t *>(q_st + st * kM4QBytes)[k * kChorMaxBatch + warp * 32 + lane];
+            // every warp's part of the tables must be written before any warp reads them; a bounded
+            // mbarrier wait instead of a CTA barrier, so a warp that gave up cannot hang the others.
+            // Buffer b = it & 1 completes a phase every second iteration.
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&built[it & 1u]);
+            const bool tok = mbar_wait(&built[it & 1u], (it >> 1) & 1u, abort);
+            if (__any_sync(0xffffffffu, !tok)) {
+                failed = true;
+                break;
+            }
+            if (__any_sync(0xffffffffu, active)) {
+                const uint4 *T0 = reinterpret_cast<const uint4 *>(tab + (it & 1u) * kM4TableBytes) + quad;
+#pragma unroll 1
+                for (uint32_t k = 0; k < kM4QWords; ++k) {
+                    const uint32_t qk = k ? qwd[1] : qwd[0];
+#pragma unroll
+                    for (int j = 0; j < kM4QB; ++j) {
+                        const uint32_t qv = __shfl_sync(0xffffffffu, qk, (lane & 16u) | static_cast<uint32_t>(j));
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) {
+                            const uint4 v = T0[((8 * k + t) * 16 + ((qv >> (4 * t)) & 15u)) * kM4Quads];
+                            acc[j][0] ^= v.x;
+                            acc[j][1] ^= v.y;
+                            acc[j][2] ^= v.z;
+                            acc[j][3] ^= v.w;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
+        }
+        if (!failed && u0 < u1) flush(cur_tile);
+    }
+    if (failed) {
+        *abort = 1;
+        *status = kDevTimeout;
+    }
+}
+
 // ------------------------------------------------------------------ host side
 static bool chor_pick(uint32_t B, int *qb, int *qg) {
     if (B == 0 || B > kChorMaxBatch) return false;
@@ -226,8 +422,15 @@ static cudaError_t chor_attr() {
                                 chor_smem_bytes<QB, QG>());
 }
 
+static int chor_m4rm_smem_bytes() {
+    return kChorStages * (kM4StageBytes + kM4QBytes) + 2 * kM4TableBytes + (2 * kChorStages + 2) * 8 + 16 + 1024;
+}
+
 cudaError_t prepare_chor_kernels() {
     cudaError_t e;
+    if ((e = cudaFuncSetAttribute(chor_m4rm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  chor_m4rm_smem_bytes())) != cudaSuccess)
+        return e;
     if ((e = chor_attr<1, 1>()) != cudaSuccess) return e;
     if ((e = chor_attr<2, 1>()) != cudaSuccess) return e;
     if ((e = chor_attr<4, 1>()) != cudaSuccess) return e;
@@ -288,6 +491,21 @@ cudaError_t launch_chor_answer(const CUtensorMap &db_map, const CUtensorMap &qt_
         case 4: return launch_qbg<32, 4>(db_map, qt_map, r, W, B, qtw, out, num_sms, status, stream);
         default: return launch_qbg<32, 8>(db_map, qt_map, r, W, B, qtw, out, num_sms, status, stream);
     }
+}
+
+cudaError_t launch_chor_words(const uint32_t *Q, uint64_t qw, uint32_t B, uint64_t r, uint32_t *QS, int num_sms,
+                              cudaStream_t stream) {
+    chor_words_kernel<<<num_sms * 4, 256, 0, stream>>>(Q, qw, B, r, QS);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chor_m4rm(const CUtensorMap &db_map, const uint32_t *QS, uint64_t r, uint32_t W, uint32_t B,
+                             uint32_t *out, int num_sms, int *status, cudaStream_t stream) {
+    if (B == 0 || B > kChorMaxBatch) return cudaErrorInvalidValue;
+    const uint64_t units = ((W + kM4TW - 1) / kM4TW) * ((r + kM4RB - 1) / kM4RB);
+    const int grid = static_cast<int>(units < (uint64_t)num_sms ? units : (uint64_t)num_sms);
+    chor_m4rm_kernel<<<grid, kChorThreads + 32, chor_m4rm_smem_bytes(), stream>>>(db_map, QS, r, W, B, out, status);
+    return cudaGetLastError();
 }
 
 }  // namespace qpadl

@@ -24,4 +24,18 @@ cudaError_t launch_chor_answer(const CUtensorMap &db_map, const CUtensorMap &qt_
                                uint32_t B, uint32_t qtw, uint32_t *out, int num_sms, int *status,
                                cudaStream_t stream);
 
+// Four-Russians path (large batches): box shape of its database map.
+constexpr uint32_t kChorM4TileWords = 64;
+constexpr uint32_t kChorM4BandRows = 64;
+
+// Q (B x qw words) -> QS (qw x 256 words): word k of query b at QS[k * 256 + b];
+// the buffer must hold roundup(qw, 2) x 256 words (a band reads two query words).
+cudaError_t launch_chor_words(const uint32_t *Q, uint64_t qw, uint32_t B, uint64_t r, uint32_t *QS, int num_sms,
+                              cudaStream_t stream);
+
+// out (B x W words, zeroed by the caller) ^= the responses of B <= 256 queries;
+// db_map covers the database {W, r} words with box {64, 64}.
+cudaError_t launch_chor_m4rm(const CUtensorMap &db_map, const uint32_t *QS, uint64_t r, uint32_t W, uint32_t B,
+                             uint32_t *out, int num_sms, int *status, cudaStream_t stream);
+
 }  // namespace qpadl

@@ -82,9 +82,10 @@ struct qpadl_chor {
     const uint32_t *db = nullptr;    // caller-owned, rows x W words
     int device = 0;
     int num_sms = 0;
-    uint32_t *qt = nullptr;          // transposed selector bits: rows x 8 words
+    uint32_t *qt = nullptr;          // selector scratch: rows x 8 words or ceil(rows/32) x 256 words
     int *d_status = nullptr;
     uint64_t owned_bytes = 0;
+    uint32_t m4rm_min_batch = 48;    // batches from this size take the four-Russians kernel
 };
 
 namespace {
@@ -921,7 +922,7 @@ int qpadl_chor_setup(uint64_t rows, uint64_t bits, const uint32_t *db_dev, qpadl
         return fail(QPADL_ECUDA);
     int rc = prepare_device(h->device);
     if (rc != QPADL_OK) return fail(rc);
-    const uint64_t qt_bytes = 4ull * rows * 8;
+    const uint64_t qt_bytes = 4ull * std::max<uint64_t>(rows * 8, (h->qw + 1) / 2 * 2 * kChorMaxBatch);
     if (cudaMalloc(reinterpret_cast<void **>(&h->qt), qt_bytes) != cudaSuccess ||
         cudaMalloc(reinterpret_cast<void **>(&h->d_status), 16) != cudaSuccess) {
         cudaGetLastError();
@@ -945,6 +946,16 @@ int qpadl_chor_answer_batch(qpadl_chor *h, const uint32_t *Q_dev, uint32_t B, ui
     QPADL_CU(cudaMemsetAsync(out_dev, 0, 4ull * W * B, s));
     for (uint32_t b0 = 0; b0 < B; b0 += kChorMaxBatch) {
         const uint32_t Bc = std::min(B - b0, kChorMaxBatch);
+        if (Bc >= h->m4rm_min_batch) {
+            QPADL_CU(launch_chor_words(Q_dev + (uint64_t)b0 * h->qw, h->qw, Bc, h->rows, h->qt, h->num_sms, s));
+            CUtensorMap db_map;
+            if (!encode_2d(&db_map, CU_TENSOR_MAP_DATA_TYPE_UINT32, h->db, W, h->rows, W * 4, kChorM4TileWords,
+                           kChorM4BandRows, CU_TENSOR_MAP_SWIZZLE_NONE))
+                return QPADL_ECUDA;
+            QPADL_CU(launch_chor_m4rm(db_map, h->qt, h->rows, static_cast<uint32_t>(W), Bc,
+                                      out_dev + (uint64_t)b0 * W, h->num_sms, h->d_status, s));
+            continue;
+        }
         uint32_t tw = 0, rb = 0, boxw = 0, qtw = 0;
         if (!chor_launch_shape(Bc, &tw, &rb, &boxw, &qtw)) return QPADL_EINVAL;
         QPADL_CU(launch_chor_transpose(Q_dev + (uint64_t)b0 * h->qw, h->qw, Bc, h->rows, qtw, h->qt, h->num_sms, s));
@@ -958,6 +969,25 @@ int qpadl_chor_answer_batch(qpadl_chor *h, const uint32_t *Q_dev, uint32_t B, ui
                                     out_dev + (uint64_t)b0 * W, h->num_sms, h->d_status, s));
     }
     return QPADL_OK;
+}
+
+int qpadl_chor_set_option(qpadl_chor *h, int option, int64_t value) {
+    if (!h) return QPADL_EINVAL;
+    switch (option) {
+        case QPADL_CHOR_OPT_M4RM_MIN_BATCH:
+            if (value < 1 || value > (int64_t)kChorMaxBatch + 1) return QPADL_EINVAL;
+            h->m4rm_min_batch = static_cast<uint32_t>(value);
+            return QPADL_OK;
+        default: return QPADL_EINVAL;
+    }
+}
+
+int qpadl_chor_get_option(qpadl_chor *h, int option, int64_t *value) {
+    if (!h || !value) return QPADL_EINVAL;
+    switch (option) {
+        case QPADL_CHOR_OPT_M4RM_MIN_BATCH: *value = h->m4rm_min_batch; return QPADL_OK;
+        default: return QPADL_EINVAL;
+    }
 }
 
 int qpadl_chor_status(qpadl_chor *h) {

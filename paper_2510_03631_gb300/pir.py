@@ -93,6 +93,8 @@ _SIGS = {
     "qpadl_chor_setup": ([ctypes.c_uint64, ctypes.c_uint64, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "qpadl_chor_answer_batch": ([_P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
     "qpadl_chor_status": ([_P], ctypes.c_int),
+    "qpadl_chor_set_option": ([_P, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
+    "qpadl_chor_get_option": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "qpadl_chor_destroy": ([_P], ctypes.c_int),
     "qpadl_server_create": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
     "qpadl_server_add_db": ([_P, _P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -437,6 +439,19 @@ def qpadl_chor_answer_batch(h: ChorDatabase, Q: torch.Tensor, out: torch.Tensor,
                                           _dev(out, torch.int32, B * h.words, "out"), _stream(stream)),
            "qpadl_chor_answer_batch")
     return out
+
+
+QPADL_CHOR_OPT_M4RM_MIN_BATCH = 1
+
+
+def qpadl_chor_set_option(h: ChorDatabase, option: int, value: int):
+    _check(load().qpadl_chor_set_option(h.handle, int(option), int(value)), "qpadl_chor_set_option")
+
+
+def qpadl_chor_get_option(h: ChorDatabase, option: int) -> int:
+    v = ctypes.c_int64()
+    _check(load().qpadl_chor_get_option(h.handle, int(option), ctypes.byref(v)), "qpadl_chor_get_option")
+    return int(v.value)
 
 
 def qpadl_chor_status(h: ChorDatabase) -> int:

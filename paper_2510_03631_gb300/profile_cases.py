@@ -34,11 +34,51 @@ def _row_check(D_row: np.ndarray, X: np.ndarray, got: np.ndarray):
         raise SystemExit("profile case: output row differs from the host recomputation")
 
 
+def _chor_case(a):
+    """Chor GF(2) Response: rows x bits database, a batch of uniformly random queries."""
+    rows, bits, B = a.rows, a.bits, a.batch
+    W = bits // 32
+    DB_np = inputs.chor_db(rows, bits, seed=1)
+    Q_np = inputs.chor_queries(B, rows, seed=2)
+    h = pir.qpadl_chor_setup(rows, bits, torch.from_numpy(DB_np.view(np.int32).reshape(-1)).cuda())
+    if a.m4rm >= 0:
+        pir.qpadl_chor_set_option(h, pir.QPADL_CHOR_OPT_M4RM_MIN_BATCH, a.m4rm)
+    Q = torch.from_numpy(Q_np.view(np.int32).reshape(-1)).cuda()
+    out = torch.empty(B * W, dtype=torch.int32, device="cuda")
+    fn = lambda: pir.qpadl_chor_answer_batch(h, Q, out)
+    fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(a.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    if pir.qpadl_chor_status(h) != 0:
+        raise SystemExit("profile case: device status word set")
+    # host recomputation of query 0 on the first 64 words: XOR of the selected rows
+    sel = ((Q_np[0][np.arange(rows) // 32] >> (np.arange(rows) % 32).astype(np.uint32)) & 1).astype(bool)
+    exp = np.bitwise_xor.reduce(DB_np[sel, :64], axis=0) if sel.any() else np.zeros(64, np.uint32)
+    if not np.array_equal(pir.as_u32(out)[:64], exp):
+        raise SystemExit("profile case: output differs from the host recomputation")
+    ms = min(times)
+    alg = rows * W * 4 + B * ((rows + 31) // 32) * 4 + B * W * 4
+    print(json.dumps({"case": "chor", "rows": rows, "bits": bits, "batch": B, "ms": times, "alg_bytes": alg,
+                      "m4rm_min_batch": pir.qpadl_chor_get_option(h, pir.QPADL_CHOR_OPT_M4RM_MIN_BATCH),
+                      "gbs": alg / (ms * 1e-3) / 1e9, "queries_per_s": B / (ms * 1e-3),
+                      "db_scan_gbs": B * rows * W * 4 / (ms * 1e-3) / 1e9}))
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["stream", "gemm", "hint", "query", "recover", "qbatch", "rbatch"])
+    ap.add_argument("case", choices=["stream", "gemm", "hint", "query", "recover", "qbatch", "rbatch", "chor"])
     ap.add_argument("--rows", type=int, default=8192)
     ap.add_argument("--cols", type=int, default=32768)
+    ap.add_argument("--bits", type=int, default=262144, help="chor: bits per record")
+    ap.add_argument("--m4rm", type=int, default=-1, help="chor: smallest batch on the four-Russians kernel")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--reps", type=int, default=3)
@@ -50,6 +90,8 @@ def main():
                                                             "0 = CUDA-core batch entry point")
     a = ap.parse_args()
     torch.cuda.set_device(0)
+    if a.case == "chor":
+        return _chor_case(a)
     R, C = a.rows, a.cols
     D_np = inputs.db_digits(R, C, 256, seed=1)
     prm = pir.params(R, C, a.n, seed=1)

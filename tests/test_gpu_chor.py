@@ -39,22 +39,27 @@ CASES = [(100, 128, 1), (33, 128, 7), (1000, 1024, 3), (777, 4096 + 128, 17), (5
 
 
 @pytest.mark.parametrize("rows,bits,B", CASES)
-def test_chor_matches_oracle(cuda, rows, bits, B):
+@pytest.mark.parametrize("m4rm_min", [257, 1])   # masked-XOR scan only / four-Russians kernel only
+def test_chor_matches_oracle(cuda, rows, bits, B, m4rm_min):
     DB = inputs.chor_db(rows, bits, seed=rows + bits)
     Q = inputs.chor_queries(B, rows, seed=rows * 7 + B)
     h = pir.qpadl_chor_setup(rows, bits, _dev(DB))
+    pir.qpadl_chor_set_option(h, pir.QPADL_CHOR_OPT_M4RM_MIN_BATCH, m4rm_min)
+    assert pir.qpadl_chor_get_option(h, pir.QPADL_CHOR_OPT_M4RM_MIN_BATCH) == m4rm_min
     got = _answer(h, Q)
     assert np.array_equal(got, oracle.chor_answer(DB, rows, Q, threads=oracle.max_threads()))
     h.close()
 
 
-def test_padding_bits_are_ignored(cuda):
+@pytest.mark.parametrize("m4rm_min", [257, 1])
+def test_padding_bits_are_ignored(cuda, m4rm_min):
     rows, bits = 45, 256
     DB = inputs.chor_db(rows, bits, seed=3)
     Q = inputs.chor_queries(5, rows, seed=4)
     noisy = Q.copy()
     noisy[:, -1] |= np.uint32(0xFFFFFFFF << (rows % 32) & 0xFFFFFFFF)
     h = pir.qpadl_chor_setup(rows, bits, _dev(DB))
+    pir.qpadl_chor_set_option(h, pir.QPADL_CHOR_OPT_M4RM_MIN_BATCH, m4rm_min)
     assert np.array_equal(_answer(h, noisy), oracle.chor_answer(DB, rows, Q))
     h.close()
 
@@ -91,9 +96,15 @@ def test_errors(cuda):
     with pytest.raises(pir.QpadlError) as e:   # misaligned database pointer
         pir.qpadl_chor_setup(8, 128, DB[1:])
     assert e.value.code == pir.QPADL_EINVAL
+    h = pir.qpadl_chor_setup(8, 128, DB)
+    for opt, val in ((pir.QPADL_CHOR_OPT_M4RM_MIN_BATCH, 0), (pir.QPADL_CHOR_OPT_M4RM_MIN_BATCH, 258), (9, 1)):
+        with pytest.raises(pir.QpadlError) as e:
+            pir.qpadl_chor_set_option(h, opt, val)
+        assert e.value.code == pir.QPADL_EINVAL
+    h.close()
 
 
-@pytest.mark.parametrize("B", [1, 256])
+@pytest.mark.parametrize("B", [1, 16, 256, 300])
 def test_full_size_sampled_columns(cuda, B):
     w = inputs.WORKLOADS["chor_1gib"]
     rows, bits = w["rows"], w["bits"]
