@@ -57,10 +57,14 @@ def _load():
             lib.oracle_chor_answer.argtypes = [P, u64, u64, P, u64, u64, P, i32]
             lib.oracle_chor_query.argtypes = [P, u64, u64, u64, P]
             lib.oracle_chor_reconstruct.argtypes = [P, u64, u64, P]
+            lib.oracle_goldberg_answer.argtypes = [P, u64, u64, P, u64, u32, P, i32]
+            lib.oracle_goldberg_query.argtypes = [P, u64, u64, u64, P, u64, u32, P]
+            lib.oracle_goldberg_reconstruct.argtypes = [P, P, u64, u64, u32, P]
             lib.oracle_max_threads.restype = i32
             for f in ("oracle_gen_a", "oracle_hint", "oracle_query", "oracle_answer",
                       "oracle_answer_batch", "oracle_recover", "oracle_chor_answer", "oracle_chor_query",
-                      "oracle_chor_reconstruct"):
+                      "oracle_chor_reconstruct", "oracle_goldberg_answer", "oracle_goldberg_query",
+                      "oracle_goldberg_reconstruct"):
                 getattr(lib, f).restype = None
             _lib = lib
     return _lib
@@ -202,4 +206,40 @@ def chor_reconstruct(responses: np.ndarray) -> np.ndarray:
     ell, w = responses.shape
     out = np.empty(w, dtype=np.uint32)
     _load().oracle_chor_reconstruct(_p(responses), ell, w, _p(out))
+    return out
+
+
+def goldberg_answer(D: np.ndarray, Q: np.ndarray, p: int, threads: int = 1) -> np.ndarray:
+    """Goldberg Response over Z_p: D is R x C bytes (record j = column j), Q is
+    B x C field elements (uint32 < p); returns B x R, rho = D q mod p."""
+    D = _c(D, np.uint8)
+    Q = _c(np.atleast_2d(Q), np.uint32)
+    R, C = D.shape
+    B = Q.shape[0]
+    if Q.shape != (B, C):
+        raise ValueError("Q must be B x C")
+    out = np.empty((B, R), dtype=np.uint32)
+    _load().oracle_goldberg_answer(_p(D), R, C, _p(Q), B, p, _p(out), threads)
+    return out
+
+
+def goldberg_query(coef: np.ndarray, theta: int, alpha: np.ndarray, p: int) -> np.ndarray:
+    """FTR client: coef is C x t (the non-constant coefficients of the C
+    polynomials); returns ell x C queries, query k = the polynomials at alpha[k]."""
+    coef = _c(coef, np.uint32)
+    alpha = _c(alpha, np.uint32)
+    C, t = coef.shape
+    ell = alpha.shape[0]
+    out = np.empty((ell, C), dtype=np.uint32)
+    _load().oracle_goldberg_query(_p(coef), C, t, theta, _p(alpha), ell, p, _p(out))
+    return out
+
+
+def goldberg_reconstruct(responses: np.ndarray, alpha: np.ndarray, p: int) -> np.ndarray:
+    """Lagrange interpolation at 0 of k responses (k x R) at the points alpha (k)."""
+    responses = _c(responses, np.uint32)
+    alpha = _c(alpha, np.uint32)
+    k, R = responses.shape
+    out = np.empty(R, dtype=np.uint32)
+    _load().oracle_goldberg_reconstruct(_p(responses), _p(alpha), k, R, p, _p(out))
     return out

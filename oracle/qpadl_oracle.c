@@ -202,6 +202,86 @@ void oracle_chor_reconstruct(const uint32_t *responses, uint64_t ell, uint64_t w
     }
 }
 
+/* ---------------------------------------------------------------------------
+ * Goldberg-style PIR over a prime field Z_p (Sec. 5.2 "Parallel Goldberg-PIR",
+ * Alg. 4; the FTR instantiation of Sec. 7).  The paper names no field; the
+ * reading here is a prime p <= 257, so that every byte of the database is a
+ * field element when p = 257.  The database keeps the layout of the lattice
+ * scheme (R x C bytes, record j = column j), a query is C field elements
+ * and the response R field elements:
+ *     rho[i] = sum_j q[j] * D[i][j]  mod p.
+ * Query b of a batch is q + b * C, its response out + b * R. */
+void oracle_goldberg_answer(const uint8_t *D, uint64_t R, uint64_t C, const uint32_t *q, uint64_t B,
+                            uint32_t p, uint32_t *out, int nthreads)
+{
+    int nt = oracle_threads(nthreads);
+    (void)nt;
+    for (uint64_t b = 0; b < B; ++b) {
+        const uint32_t *qb = q + b * C;
+#pragma omp parallel for num_threads(nt) schedule(static)
+        for (int64_t i = 0; i < (int64_t)R; ++i) {
+            uint64_t acc = 0;
+            for (uint64_t j = 0; j < C; ++j)
+                acc = (acc + (uint64_t)qb[j] * D[(uint64_t)i * C + j]) % p;
+            out[b * R + (uint64_t)i] = (uint32_t)acc;
+        }
+    }
+}
+
+static uint32_t oracle_pow_mod(uint32_t x, uint32_t e, uint32_t p)
+{
+    uint64_t r = 1, b = x % p;
+    while (e) {
+        if (e & 1u)
+            r = r * b % p;
+        b = b * b % p;
+        e >>= 1;
+    }
+    return (uint32_t)r;
+}
+
+/* FTR client query (Sec. 7): record index j gets a degree-t polynomial
+ * f_j(x) = [j == theta] + sum_{u=1..t} coef[j][u-1] x^u over Z_p, and server k
+ * (evaluation point alpha[k], distinct and nonzero) receives
+ * q_k[j] = f_j(alpha[k]).  coef: C x t (uniform in Z_p); queries: ell x C. */
+void oracle_goldberg_query(const uint32_t *coef, uint64_t C, uint64_t t, uint64_t theta, const uint32_t *alpha,
+                           uint64_t ell, uint32_t p, uint32_t *queries)
+{
+    for (uint64_t k = 0; k < ell; ++k) {
+        for (uint64_t j = 0; j < C; ++j) {
+            /* Horner from the highest coefficient down to the constant term */
+            uint64_t v = 0;
+            for (uint64_t u = t; u >= 1; --u)
+                v = (v * alpha[k] + coef[j * t + (u - 1)]) % p;
+            v = (v * alpha[k] + (j == theta ? 1u : 0u)) % p;
+            queries[k * C + j] = (uint32_t)v;
+        }
+    }
+}
+
+/* Reconstruction (Sec. 5.1, FTR): Lagrange interpolation at 0 of the
+ * responses of k servers, out[i] = sum_s lambda_s * R_s[i] mod p with
+ * lambda_s = prod_{m != s} alpha_m / (alpha_m - alpha_s); p prime, so the
+ * inverse is x^(p-2).  responses: k x R. */
+void oracle_goldberg_reconstruct(const uint32_t *responses, const uint32_t *alpha, uint64_t k, uint64_t R,
+                                 uint32_t p, uint32_t *out)
+{
+    for (uint64_t i = 0; i < R; ++i)
+        out[i] = 0;
+    for (uint64_t s = 0; s < k; ++s) {
+        uint64_t num = 1, den = 1;
+        for (uint64_t m = 0; m < k; ++m) {
+            if (m == s)
+                continue;
+            num = num * alpha[m] % p;
+            den = den * ((alpha[m] + p - alpha[s]) % p) % p;
+        }
+        const uint64_t lambda = num * oracle_pow_mod((uint32_t)den, p - 2, p) % p;
+        for (uint64_t i = 0; i < R; ++i)
+            out[i] = (uint32_t)((out[i] + lambda * responses[s * R + i]) % p);
+    }
+}
+
 int oracle_max_threads(void)
 {
 #ifdef _OPENMP

@@ -50,6 +50,16 @@ MUTATIONS = [
     ("chor unit bit misplaced", "acc ^= 1u << (theta % 32);", "acc ^= 1u << ((theta + 1) % 32);"),
     ("chor reconstruct drops a response", "for (uint64_t j = 0; j < ell; ++j)\n            acc ^= responses",
      "for (uint64_t j = 1; j < ell; ++j)\n            acc ^= responses"),
+    ("goldberg wrong modulus", "acc = (acc + (uint64_t)qb[j] * D[(uint64_t)i * C + j]) % p;",
+     "acc = (acc + (uint64_t)qb[j] * D[(uint64_t)i * C + j]) % (p + 1);"),
+    ("goldberg transposed D", "acc = (acc + (uint64_t)qb[j] * D[(uint64_t)i * C + j]) % p;",
+     "acc = (acc + (uint64_t)qb[j] * D[j * R + (uint64_t)i]) % p;"),
+    ("goldberg secret at the wrong record", "(j == theta ? 1u : 0u)", "(j == theta + 1 ? 1u : 0u)"),
+    ("goldberg reversed coefficients", "v = (v * alpha[k] + coef[j * t + (u - 1)]) % p;",
+     "v = (v * alpha[k] + coef[j * t + (t - u)]) % p;"),
+    ("goldberg Lagrange denominator sign", "den = den * ((alpha[m] + p - alpha[s]) % p) % p;",
+     "den = den * ((alpha[s] + p - alpha[m]) % p) % p;"),
+    ("goldberg Lagrange numerator point", "num = num * alpha[m] % p;", "num = num * alpha[s] % p;"),
 ]
 
 

@@ -368,3 +368,69 @@ def test_chor_thread_count_invariance():
     DB = inputs.chor_db(r, bits, seed=13)
     Q = inputs.chor_queries(16, r, seed=14)
     assert np.array_equal(oracle.chor_answer(DB, r, Q, threads=1), oracle.chor_answer(DB, r, Q, threads=4))
+
+
+# ----------------------------------------------------------------------------- Goldberg over Z_p
+# Sec. 5.2 "Parallel Goldberg-PIR": rho = q . DB over a field (here Z_p, p prime <= 257);
+# Sec. 7 (FTR): Shamir shares f_j(alpha_k) of e_theta, Lagrange reconstruction at 0.
+
+def test_goldberg_hand_worked_example():
+    # two records (columns) of three bytes, p = 7: q = (2, 3) -> 2 * col0 + 3 * col1 mod 7
+    D = np.array([[1, 4], [6, 6], [0, 5]], dtype=np.uint8)
+    got = oracle.goldberg_answer(D, np.array([[2, 3]], dtype=np.uint32), 7)
+    assert got.tolist() == [[(2 + 12) % 7, (12 + 18) % 7, 15 % 7]] == [[0, 2, 1]]
+
+
+@pytest.mark.parametrize("p", [257, 251, 101, 2])
+def test_goldberg_equals_integer_matmul_mod_p(p):
+    R, C, B = 70, 130, 6
+    D = (inputs.db_digits(R, C, 256, seed=p).astype(np.int64) % p).astype(np.uint8)
+    Q = (inputs.uniform_u32(B * C, seed=p + 1, tag=inputs.TAG_MISC) % p).reshape(B, C)
+    exp = (Q.astype(np.int64) @ D.T.astype(np.int64)) % p
+    assert np.array_equal(oracle.goldberg_answer(D, Q, p), exp.astype(np.uint32))
+
+
+def test_goldberg_brute_force_python_ints():
+    p, R, C = 257, 5, 9
+    rng = np.random.default_rng(3)
+    D = rng.integers(0, 256, (R, C), dtype=np.uint8)
+    q = rng.integers(0, p, C).astype(np.uint32)
+    got = oracle.goldberg_answer(D, q[None, :], p)[0]
+    for i in range(R):
+        assert int(got[i]) == sum(int(q[j]) * int(D[i, j]) for j in range(C)) % p
+
+
+def test_goldberg_unit_queries_linearity_and_ones():
+    p, R, C = 257, 40, 33
+    D = inputs.db_digits(R, C, 256, seed=9)
+    E = np.eye(C, dtype=np.uint32)
+    assert np.array_equal(oracle.goldberg_answer(D, E, p), D.T.astype(np.uint32))
+    ones = np.ones((1, C), dtype=np.uint32)
+    assert np.array_equal(oracle.goldberg_answer(D, ones, p)[0], (D.astype(np.int64).sum(axis=1) % p).astype(np.uint32))
+    q1 = (inputs.uniform_u32(C, seed=1, tag=7) % p)[None, :]
+    q2 = (inputs.uniform_u32(C, seed=2, tag=7) % p)[None, :]
+    a = oracle.goldberg_answer(D, np.concatenate([q1, q2, (q1 + q2) % p]), p)
+    assert np.array_equal(a[2], (a[0] + a[1]) % p)
+
+
+@pytest.mark.parametrize("p,t,ell", [(257, 1, 2), (257, 2, 4), (251, 3, 5), (101, 2, 3)])
+def test_goldberg_ftr_protocol_recovers_the_record(p, t, ell):
+    R, C = 24, 50
+    D = (inputs.db_digits(R, C, 256, seed=p + t).astype(np.int64) % p).astype(np.uint8)
+    alpha = np.arange(1, ell + 1, dtype=np.uint32)
+    for theta in (0, 17, C - 1):
+        coef = (inputs.uniform_u32(C * t, seed=theta + 5, tag=7) % p).reshape(C, t)
+        queries = oracle.goldberg_query(coef, theta, alpha, p)
+        # query k evaluates every polynomial at alpha_k: f_j(0) = [j == theta] is hidden behind degree t
+        x = np.zeros(C, dtype=np.int64)
+        x[theta] = 1
+        for k in range(ell):
+            direct = x.copy()
+            for u in range(1, t + 1):
+                direct = (direct + coef[:, u - 1].astype(np.int64) * pow(int(alpha[k]), u, p)) % p
+            assert np.array_equal(queries[k], direct.astype(np.uint32))
+        responses = oracle.goldberg_answer(D, queries, p)
+        # any t + 1 of the ell responses interpolate the record
+        for sub in (list(range(t + 1)), list(range(ell - t - 1, ell))):
+            rec = oracle.goldberg_reconstruct(responses[sub], alpha[sub], p)
+            assert np.array_equal(rec, D[:, theta].astype(np.uint32))
