@@ -321,6 +321,44 @@ int qpadl_client_set_option(qpadl_client *c, int option, int64_t value);
 int qpadl_client_destroy(qpadl_client *c);
 
 /* ======================================================================
+ * Goldberg-style Response over Z_p (Sec. 5.2 "Parallel Goldberg-PIR",
+ * Alg. 4; the FTR instantiation of Sec. 7): the server's answer to a query
+ * q in Z_p^C is rho = D q mod p.  The paper names no field; here p is a
+ * prime <= 257 (p = 257 takes every byte as a field element).  The database
+ * keeps the layout of the lattice scheme: R x C bytes, record j = column j;
+ * the client's queries are Shamir shares of e_theta (degree-t polynomials
+ * at distinct points) and Lagrange interpolation of t + 1 answers at 0
+ * gives record theta.
+ * ==================================================================== */
+typedef struct qpadl_goldberg qpadl_goldberg;
+
+/* Binds a resident database (db_dev: rows x cols bytes, each < p, caller-
+ * owned, kept until destroy).  QPADL_EINVAL if p is not a prime in [2, 257],
+ * cols is 0 or above 65792 (the exact-sum bound), a byte is >= p (checked on
+ * the device when p < 256), or db_dev is NULL. */
+int qpadl_goldberg_setup(uint64_t rows, uint64_t cols, uint32_t p, const uint8_t *db_dev,
+                         qpadl_stream_t stream, qpadl_goldberg **out);
+
+/* Answers B queries: Q_dev B x cols field elements (uint32, each < p; larger
+ * values give unspecified answers), out_dev B x rows elements in [0, p).
+ * Below the GEMM threshold the streaming kernel computes the exact integer
+ * sums and a second kernel reduces them mod p; from it, one exact tcgen05
+ * GEMM with each query as a single centred fp16 row and a mod-p epilogue
+ * (builds the handle's fp16 operand copy on first use). */
+int qpadl_goldberg_answer_batch(qpadl_goldberg *h, const uint32_t *Q_dev, uint32_t B, uint32_t *out_dev,
+                                qpadl_stream_t stream);
+
+/* QPADL_GOLDBERG_OPT_GEMM_MIN_BATCH (default 5): smallest batch on the GEMM. */
+#define QPADL_GOLDBERG_OPT_GEMM_MIN_BATCH 1
+int qpadl_goldberg_set_option(qpadl_goldberg *h, int option, int64_t value);
+
+/* As qpadl_pir_status, for the handle's kernels. */
+int qpadl_goldberg_status(qpadl_goldberg *h);
+
+/* Waits for the device and frees the handle (not the database). */
+int qpadl_goldberg_destroy(qpadl_goldberg *h);
+
+/* ======================================================================
  * Chor-style Response over GF(2) (Sec. 5.2 "Parallel Chor-PIR", Alg. 3;
  * the ENS instantiation of Sec. 7): the database is `rows` records of `bits`
  * bits, the server's answer to an rows-bit query q is rho = q . DB over

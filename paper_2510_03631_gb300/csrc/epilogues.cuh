@@ -10,8 +10,12 @@
 
 namespace qpadl {
 
+// kLimbs: limb rows per vector in the GEMM's vector operand (4 byte limbs
+// recombined as sum_k 2^{8k} s_k; 1 = each row is its own vector).
+
 // Plain store: out[i * ld_m + b * ld_b] = dot.
 struct StoreEpi {
+    static constexpr int kLimbs = 4;
     uint32_t *out;
     uint64_t ld_m, ld_b;
     __device__ __forceinline__ uint32_t pre(uint64_t, uint32_t) const { return 0u; }
@@ -23,6 +27,7 @@ struct StoreEpi {
 
 // Query (Def. 1 Client.Query): q_b[j] = (A s_b)[j] + e_b[j] + Delta [j == col_b]  mod 2^32.
 struct QueryEpi {
+    static constexpr int kLimbs = 4;
     const int32_t *e;        // noise, row b at e + b * e_ld
     uint64_t e_ld;
     const uint32_t *cols;    // target column per vector (device) or nullptr
@@ -46,6 +51,7 @@ struct QueryEpi {
 // Recover (Def. 1 Client.BlockReconst): d_b[i] = round((ans_b[i] - (H s_b)[i]) / Delta) mod p,
 // as (x + Delta/2) >> (32 - log2 p) in uint32 arithmetic.
 struct RecoverEpi {
+    static constexpr int kLimbs = 4;
     const uint32_t *ans;     // answer b at ans + b * ans_ld
     uint64_t ans_ld;
     uint32_t shift;          // 32 - log2 p
@@ -60,6 +66,23 @@ struct RecoverEpi {
     __device__ __forceinline__ void operator()(uint64_t i, uint32_t b, uint32_t dot) const {
         put(i, b, dot, pre(i, b));
     }
+};
+
+// Goldberg Response over Z_p (Sec. 5.2, Alg. 4): the vector operand holds
+// each query once, centred into [-128, 128], so dot is the exact signed
+// integer sum (|sum| < 2^31 for fewer than 65793 columns); out = dot mod p.
+struct ModPEpi {
+    static constexpr int kLimbs = 1;
+    uint32_t *out;
+    uint64_t ld_m, ld_b;
+    int32_t p;
+    __device__ __forceinline__ uint32_t pre(uint64_t, uint32_t) const { return 0u; }
+    __device__ __forceinline__ void put(uint64_t i, uint32_t b, uint32_t dot, uint32_t) const {
+        int32_t r = static_cast<int32_t>(dot) % p;
+        if (r < 0) r += p;
+        out[i * ld_m + (uint64_t)b * ld_b] = static_cast<uint32_t>(r);
+    }
+    __device__ __forceinline__ void operator()(uint64_t i, uint32_t b, uint32_t dot) const { put(i, b, dot, 0u); }
 };
 
 }  // namespace qpadl

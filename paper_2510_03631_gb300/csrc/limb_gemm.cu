@@ -92,7 +92,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                      int *__restrict__ status) {
     static_assert(!PLANED || BN >= 64, "a shift group needs N = BN/4 >= 16");
     using Cfg = GemmCfg<BN>;
-    constexpr int QPT = Cfg::kQPT;
+    constexpr int LPV = Epi::kLimbs;   // limb rows per vector
+    static_assert(LPV == 4 || (LPV == 1 && !PLANED && BN <= 64), "one-limb vectors: plain mode, BN <= 64");
+    constexpr int QPT = BN / LPV;      // vectors per tile
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + kGemmStages * Cfg::kStageBytes);
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const uint32_t tmem_base = *tmem_slot;
 
     const uint32_t m_tiles = (M + kBM - 1) / kBM;
-    const uint32_t n_tiles = (NV * 4 + BN - 1) / BN;
+    const uint32_t n_tiles = (NV * LPV + BN - 1) / BN;
     const uint32_t tiles = m_tiles * n_tiles;
     bool failed = false;
 
@@ -263,6 +265,17 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                             for (int q = 0; q < QPT; ++q)
                                 run[q] += static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[q]))) << (8u * t);
                         }
+                    }
+                } else if constexpr (LPV == 1) {
+                    // every column is its own vector
+#pragma unroll
+                    for (int j = 0; j < BN / 32; ++j) {
+                        uint32_t v[32];
+                        tmem_ld32(tmem_base + lane_addr + buf * BN + 32u * j, v);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int q = 0; q < 32; ++q)
+                            run[32 * j + q] += static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[q])));
                     }
                 } else {
 #pragma unroll
@@ -491,7 +504,9 @@ cudaError_t prepare_limb_gemm_kernels() {
     if ((e = set_gemm_attrs<QueryEpi>()) != cudaSuccess) return e;
     if ((e = set_gemm_attrs<RecoverEpi>()) != cudaSuccess) return e;
     if ((e = set_planed_attrs<QueryEpi>()) != cudaSuccess) return e;
-    return set_planed_attrs<RecoverEpi>();
+    if ((e = set_planed_attrs<RecoverEpi>()) != cudaSuccess) return e;
+    if ((e = set_gemm_attr<32, ModPEpi, false>()) != cudaSuccess) return e;
+    return set_gemm_attr<64, ModPEpi, false>();
 }
 
 int limb_gemm_bn_for(uint32_t nv) {
@@ -515,7 +530,17 @@ static cudaError_t launch_epi(int bn, const CUtensorMap &a_map, const CUtensorMa
                               uint32_t NV, uint64_t K, uint32_t plane_chunks, int num_sms, int *status,
                               cudaStream_t stream) {
     const uint32_t KB = static_cast<uint32_t>((K + kBK - 1) / kBK);
-    const uint64_t tiles = (uint64_t)((M + kBM - 1) / kBM) * ((4ull * NV + bn - 1) / bn);
+    const uint64_t tiles = (uint64_t)((M + kBM - 1) / kBM) * (((uint64_t)Epi::kLimbs * NV + bn - 1) / bn);
+    if constexpr (Epi::kLimbs == 1) {
+        const int grid1 = static_cast<int>(tiles < (uint64_t)num_sms ? tiles : (uint64_t)num_sms);
+        if (plane_chunks) return cudaErrorInvalidValue;
+        switch (bn) {
+            case 32: launch_one<32, Epi, false>(grid1, a_map, b_map, epi, M, NV, KB, 1, status, stream); break;
+            case 64: launch_one<64, Epi, false>(grid1, a_map, b_map, epi, M, NV, KB, 1, status, stream); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    } else {
     const int grid = static_cast<int>(tiles < (uint64_t)num_sms ? tiles : (uint64_t)num_sms);
     if (plane_chunks == 0) {
         switch (bn) {
@@ -543,6 +568,7 @@ static cudaError_t launch_epi(int bn, const CUtensorMap &a_map, const CUtensorMa
         }
     }
     return cudaGetLastError();
+    }
 }
 
 cudaError_t launch_limb_gemm(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, uint32_t *out,
@@ -561,6 +587,11 @@ cudaError_t launch_limb_gemm_recover(int bn, const CUtensorMap &a_map, const CUt
                                      const RecoverEpi &epi, uint32_t M, uint32_t NV, uint64_t K,
                                      uint32_t plane_chunks, int num_sms, int *status, cudaStream_t stream) {
     return launch_epi(bn, a_map, b_map, epi, M, NV, K, plane_chunks, num_sms, status, stream);
+}
+
+cudaError_t launch_limb_gemm_modp(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, const ModPEpi &epi,
+                                  uint32_t M, uint32_t NV, uint64_t K, int num_sms, int *status, cudaStream_t stream) {
+    return launch_epi(bn, a_map, b_map, epi, M, NV, K, 0, num_sms, status, stream);
 }
 
 cudaError_t launch_db_to_f16(const uint8_t *D, uint64_t R, uint64_t C, __half *D16, uint64_t pitch, int num_sms,
@@ -600,6 +631,37 @@ cudaError_t launch_secret_limbs_planed(const uint32_t *S, uint32_t B, uint32_t n
                                        uint64_t pitch, int num_sms, cudaStream_t stream) {
     const uint32_t Bp = (B + qpt - 1) / qpt * qpt;
     secret_limbs_planed_kernel<<<num_sms * 4, 256, 0, stream>>>(S, B, Bp, n, qpt, V, pitch);
+    return cudaGetLastError();
+}
+
+// Goldberg queries (B x C field elements < p) -> one fp16 row per query,
+// centred: q if q <= p / 2, else q - p (|value| <= 128 for p <= 257).
+__global__ void centred_rows_kernel(const uint32_t *__restrict__ Q, uint32_t B, uint64_t C, uint32_t p,
+                                    __half *__restrict__ L, uint64_t pitch) {
+    const uint64_t total = (uint64_t)B * C;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t b = e / C, j = e - b * C;
+        const uint32_t q = Q[e];
+        const int v = q <= p / 2 ? static_cast<int>(q) : static_cast<int>(q) - static_cast<int>(p);
+        L[b * pitch + j] = __int2half_rn(v);
+    }
+}
+
+// x[i] = x[i] mod p for n words (uint32, the exact non-negative sums of the streaming path).
+__global__ void mod_p_kernel(uint32_t *__restrict__ x, uint64_t n, uint32_t p) {
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (uint64_t)gridDim.x * blockDim.x)
+        x[e] %= p;
+}
+
+cudaError_t launch_centred_rows(const uint32_t *Q, uint32_t B, uint64_t C, uint32_t p, __half *L, uint64_t pitch,
+                                int num_sms, cudaStream_t stream) {
+    centred_rows_kernel<<<num_sms * 4, 256, 0, stream>>>(Q, B, C, p, L, pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mod_p(uint32_t *x, uint64_t n, uint32_t p, int num_sms, cudaStream_t stream) {
+    mod_p_kernel<<<num_sms * 4, 256, 0, stream>>>(x, n, p);
     return cudaGetLastError();
 }
 

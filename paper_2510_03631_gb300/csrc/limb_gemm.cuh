@@ -34,6 +34,14 @@ cudaError_t launch_limb_gemm_recover(int bn, const CUtensorMap &a_map, const CUt
                                      const RecoverEpi &epi, uint32_t M, uint32_t NV, uint64_t K,
                                      uint32_t plane_chunks, int num_sms, int *status, cudaStream_t stream);
 
+// Goldberg Response: out = D * X mod p with one centred fp16 row per vector
+// (b_map box 64 x bn rows, bn 32 or 64), through ModPEpi.
+cudaError_t launch_limb_gemm_modp(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, const ModPEpi &epi,
+                                  uint32_t M, uint32_t NV, uint64_t K, int num_sms, int *status, cudaStream_t stream);
+cudaError_t launch_centred_rows(const uint32_t *Q, uint32_t B, uint64_t C, uint32_t p, __half *L, uint64_t pitch,
+                                int num_sms, cudaStream_t stream);
+cudaError_t launch_mod_p(uint32_t *x, uint64_t n, uint32_t p, int num_sms, cudaStream_t stream);
+
 cudaError_t launch_db_to_f16(const uint8_t *D, uint64_t R, uint64_t C, __half *D16, uint64_t pitch, int num_sms,
                              cudaStream_t stream);
 cudaError_t launch_vec_limbs(const uint32_t *X, uint64_t x_ld, uint32_t NV, uint64_t C, __half *L, uint64_t pitch,

@@ -74,6 +74,14 @@ struct qpadl_client {
     bool planed = true;              // skip the zero (plane, shift) blocks when n % 512 == 0
 };
 
+// Goldberg-style Z_p database handle: the lattice handle of the same bytes
+// (streaming kernel, fp16 operand copy, limb scratch) plus the field.
+struct qpadl_goldberg {
+    qpadl_db *db = nullptr;
+    uint32_t p = 0;
+    uint32_t gemm_min_batch = 5;     // batches from this size take the one-limb GEMM
+};
+
 // Chor-style GF(2) database handle.
 struct qpadl_chor {
     uint64_t rows = 0;
@@ -91,6 +99,8 @@ struct qpadl_chor {
 namespace {
 
 constexpr int kMaxN = 16384;
+// Goldberg sums stay exact (|centred sum| < 2^31, unsigned sum < 2^32) below this many columns
+constexpr uint64_t kGoldbergMaxCols = 65792;
 
 int cuda_fail(cudaError_t e, const char *what) {
     if (e == cudaSuccess) return QPADL_OK;
@@ -1005,5 +1015,98 @@ int qpadl_chor_status(qpadl_chor *h) {
     }
     return QPADL_OK;
 }
+
+// ------------------------------------------------------------------ Goldberg-style Z_p Response
+
+int qpadl_goldberg_destroy(qpadl_goldberg *h) {
+    if (!h) return QPADL_OK;
+    qpadl_pir_destroy(h->db);
+    delete h;
+    return QPADL_OK;
+}
+
+int qpadl_goldberg_setup(uint64_t rows, uint64_t cols, uint32_t p, const uint8_t *db_dev, qpadl_stream_t stream,
+                         qpadl_goldberg **out) {
+    if (!out) return QPADL_EINVAL;
+    *out = nullptr;
+    if (!db_dev || p < 2 || p > 257 || cols == 0 || cols > kGoldbergMaxCols) return QPADL_EINVAL;
+    for (uint32_t d = 2; d * d <= p; ++d)
+        if (p % d == 0) return QPADL_EINVAL;   // the field needs a prime modulus
+    qpadl_goldberg *h = new (std::nothrow) qpadl_goldberg();
+    if (!h) return QPADL_ENOMEM;
+    h->p = p;
+    // the lattice handle of the same bytes; its scheme parameters (n, modulus) are not used here
+    qpadl_params prm{rows, cols, 1, 32, 256, 0, 0.0, 1};
+    int rc = qpadl_pir_setup(&prm, db_dev, stream, &h->db);
+    if (rc != QPADL_OK) {
+        delete h;
+        return rc;
+    }
+    if (p < 256) {   // every byte must be a field element
+        qpadl_db *db = h->db;
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        int mx = 0;
+        max_digit_kernel<<<db->num_sms * 4, 256, 0, s>>>(db_dev, rows * cols, db->d_status + 1);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&mx, db->d_status + 1, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            qpadl_goldberg_destroy(h);
+            return QPADL_ECUDA;
+        }
+        if (mx >= static_cast<int>(p)) {
+            qpadl_goldberg_destroy(h);
+            return QPADL_EINVAL;
+        }
+    }
+    *out = h;
+    return QPADL_OK;
+}
+
+int qpadl_goldberg_answer_batch(qpadl_goldberg *h, const uint32_t *Q_dev, uint32_t B, uint32_t *out_dev,
+                                qpadl_stream_t stream) {
+    if (!h || !Q_dev || !out_dev || B == 0) return QPADL_EINVAL;
+    qpadl_db *db = h->db;
+    if (set_device(db) != QPADL_OK) return QPADL_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t R = db->prm.rows, C = db->prm.cols;
+    if (B < h->gemm_min_batch) {
+        // exact integer sums (no wrap below kGoldbergMaxCols columns), then mod p
+        int rc = answer_streaming(db, Q_dev, B, out_dev, s);
+        if (rc != QPADL_OK) return rc;
+        QPADL_CU(launch_mod_p(out_dev, (uint64_t)B * R, h->p, db->num_sms, s));
+        return QPADL_OK;
+    }
+    int rc = ensure_tensor_copy(db, s);
+    if (rc != QPADL_OK) return rc;
+    // one centred fp16 row per query, in chunks that the limb scratch holds
+    constexpr uint32_t kChunk = 1024;
+    if ((rc = ensure_limbs(db, 2ull * std::min(B, kChunk) * db->pitch)) != QPADL_OK) return rc;
+    for (uint32_t b0 = 0; b0 < B; b0 += kChunk) {
+        const uint32_t Bc = std::min(B - b0, kChunk);
+        QPADL_CU(launch_centred_rows(Q_dev + (uint64_t)b0 * C, Bc, C, h->p, db->limbs, db->pitch, db->num_sms, s));
+        const int bn = Bc <= 32 ? 32 : 64;
+        CUtensorMap b_map;
+        if (!encode_2d(&b_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, db->limbs, C, Bc, db->pitch * 2, kLimbBoxK,
+                       static_cast<uint32_t>(bn), CU_TENSOR_MAP_SWIZZLE_128B))
+            return QPADL_ECUDA;
+        const ModPEpi epi{out_dev + (uint64_t)b0 * R, 1, R, static_cast<int32_t>(h->p)};
+        QPADL_CU(launch_limb_gemm_modp(bn, db->a_map, b_map, epi, static_cast<uint32_t>(R), Bc, C, db->num_sms,
+                                       db->d_status, s));
+    }
+    return QPADL_OK;
+}
+
+int qpadl_goldberg_set_option(qpadl_goldberg *h, int option, int64_t value) {
+    if (!h) return QPADL_EINVAL;
+    switch (option) {
+        case QPADL_GOLDBERG_OPT_GEMM_MIN_BATCH:
+            if (value < 1 || value > (int64_t)UINT32_MAX) return QPADL_EINVAL;
+            h->gemm_min_batch = static_cast<uint32_t>(value);
+            return QPADL_OK;
+        default: return QPADL_EINVAL;
+    }
+}
+
+int qpadl_goldberg_status(qpadl_goldberg *h) { return h ? qpadl_pir_status(h->db) : QPADL_EINVAL; }
 
 }  // extern "C"

@@ -90,6 +90,12 @@ _SIGS = {
     "qpadl_client_device_bytes": ([_P], ctypes.c_uint64),
     "qpadl_client_set_option": ([_P, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
     "qpadl_client_destroy": ([_P], ctypes.c_int),
+    "qpadl_goldberg_setup": ([ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P, _P, ctypes.POINTER(_P)],
+                             ctypes.c_int),
+    "qpadl_goldberg_answer_batch": ([_P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
+    "qpadl_goldberg_set_option": ([_P, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
+    "qpadl_goldberg_status": ([_P], ctypes.c_int),
+    "qpadl_goldberg_destroy": ([_P], ctypes.c_int),
     "qpadl_chor_setup": ([ctypes.c_uint64, ctypes.c_uint64, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "qpadl_chor_answer_batch": ([_P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
     "qpadl_chor_status": ([_P], ctypes.c_int),
@@ -391,6 +397,59 @@ def qpadl_client_set_option(c: Client, option: int, value: int):
 
 def qpadl_client_device_bytes(c: Client) -> int:
     return int(load().qpadl_client_device_bytes(c.handle))
+
+
+class GoldbergDatabase:
+    """Handle returned by qpadl_goldberg_setup (owns the C handle, keeps the database alive)."""
+
+    def __init__(self, handle: ctypes.c_void_p, rows: int, cols: int, p: int, db: torch.Tensor):
+        self.handle = handle
+        self.rows = rows
+        self.cols = cols
+        self.p = p
+        self.db = db
+
+    def close(self):
+        if self.handle:
+            load().qpadl_goldberg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+QPADL_GOLDBERG_OPT_GEMM_MIN_BATCH = 1
+
+
+def qpadl_goldberg_setup(rows: int, cols: int, p: int, db: torch.Tensor, stream=None) -> GoldbergDatabase:
+    """db: rows x cols uint8 field elements (record j = column j)."""
+    pd = _dev(db, torch.uint8, int(rows) * int(cols), "db")
+    h = ctypes.c_void_p()
+    _check(load().qpadl_goldberg_setup(int(rows), int(cols), int(p), pd, _stream(stream), ctypes.byref(h)),
+           "qpadl_goldberg_setup")
+    return GoldbergDatabase(h, int(rows), int(cols), int(p), db)
+
+
+def qpadl_goldberg_answer_batch(h: GoldbergDatabase, Q: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """Q: B x cols int32 field elements; out: B x rows int32."""
+    B = Q.numel() // h.cols
+    if B * h.cols != Q.numel() or B == 0:
+        raise ValueError("Q must hold B x cols elements")
+    _check(load().qpadl_goldberg_answer_batch(h.handle, _dev(Q, torch.int32, B * h.cols, "Q"), B,
+                                              _dev(out, torch.int32, B * h.rows, "out"), _stream(stream)),
+           "qpadl_goldberg_answer_batch")
+    return out
+
+
+def qpadl_goldberg_set_option(h: GoldbergDatabase, option: int, value: int):
+    _check(load().qpadl_goldberg_set_option(h.handle, int(option), int(value)), "qpadl_goldberg_set_option")
+
+
+def qpadl_goldberg_status(h: GoldbergDatabase) -> int:
+    return int(load().qpadl_goldberg_status(h.handle))
 
 
 class ChorDatabase:
