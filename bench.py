@@ -386,6 +386,48 @@ def chor_measure(torch, pir, inputs, seed=31):
     return res
 
 
+def goldberg_measure(torch, pir, inputs, seed=41):
+    """Goldberg Response over Z_257 (Sec. 5.2, Alg. 4) on the 1 GiB byte
+    database (32768 records of 32768 bytes): batches of uniform field
+    elements; sampled rows checked against a host dot product mod p."""
+    w = inputs.WORKLOADS["single_1gib"]
+    R, C, p = w["rows"], w["cols"], 257
+    D_np = inputs.db_digits(R, C, 256, seed=seed)
+    h = pir.qpadl_goldberg_setup(R, C, p, torch.from_numpy(D_np).cuda())
+    res = {"workload": f"{C} records x {R} bytes (1 GiB), p = {p}", "batches": {}}
+    one_qps = None
+    rows = np.array([0, R // 3, R - 1])
+    for B in (1, 8, 32, 256, 1024):
+        Q_np = (inputs.uniform_u32(B * C, seed=seed + B, tag=inputs.TAG_MISC) % p).reshape(B, C)
+        Q = pir.from_u32(Q_np.reshape(-1))
+        out = torch.empty(B * R, dtype=torch.int32, device="cuda")
+        pir.qpadl_goldberg_answer_batch(h, Q, out)
+        torch.cuda.synchronize()
+        reps = 20 if B <= 32 else 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            pir.qpadl_goldberg_answer_batch(h, Q, out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        got = pir.as_u32(out).reshape(B, R)[:2, rows]
+        exp = (Q_np[:2].astype(np.int64) @ D_np[rows].T.astype(np.int64)) % p
+        if not np.array_equal(got, exp.astype(np.uint32)) or pir.qpadl_goldberg_status(h) != 0:
+            raise SystemExit("bench: Goldberg answer differs from the host dot product")
+        qps = B / (ms * 1e-3)
+        one_qps = one_qps or qps
+        ent = {"ms": round(ms, 4), "queries_per_s": round(qps, 1),
+               "db_scan_gbs": round(B * R * C / (ms * 1e-3) / 1e9, 1), "x_vs_one_at_a_time": round(qps / one_qps, 2),
+               "path": "one-limb GEMM" if B >= 5 else "streaming + mod p"}
+        if B >= 5:
+            ent["fp16_tflops"] = round(2 * R * C * B / (ms * 1e-3) / 1e12, 1)
+        res["batches"][str(B)] = ent
+        del Q, out
+    h.close()
+    return res
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_ours(args):
     import torch
@@ -600,7 +642,7 @@ def run_ours(args):
         raise SystemExit("bench: e2e recovered record differs")
 
     serving = None
-    chor = None
+    chor = goldberg = None
     if not args.quick:
         db.close()
         del D
@@ -609,6 +651,8 @@ def run_ours(args):
                                   duration_s=1.0, single_db_one_ms=resp_ms_avg)
         torch.cuda.empty_cache()
         chor = chor_measure(torch, pir, inputs)
+        torch.cuda.empty_cache()
+        goldberg = goldberg_measure(torch, pir, inputs)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -646,6 +690,7 @@ def run_ours(args):
         "client_batch_1024": client,
         "serving": serving,
         "chor_gf2": chor,
+        "goldberg_zp": goldberg,
         "gpu_launches": 4 * K,
         "timing": "CUDA events around K replays of per-step CUDA graphs (64-query pool)",
         "e2e": {"value": round(R * C / e2e_s / 1e9, 2), "unit": "GB/s", "ms_per_step": round(e2e_s * 1e3, 4),
