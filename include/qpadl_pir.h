@@ -96,7 +96,7 @@ int qpadl_version(void);
                                         run the tensor-core GEMM on the uint8 digits as stored;
                                         larger ones use the handle's fp16 operand copy */
 #define QPADL_OPT_U8_KSTEP 5         /* digits per row per pipeline stage of that GEMM: 128 or 256;
-                                        0 (default) = 256 for batches up to 16, 128 above */
+                                        0 (default) = 128 */
 
 /*
  * Setup (server side; Def. 1's server holds D).  Validates `prm`, records
@@ -149,6 +149,29 @@ int qpadl_pir_reserve(qpadl_db *db, uint32_t max_batch, qpadl_stream_t stream);
  * option or an unsupported value.  Host-only; enqueues nothing. */
 int qpadl_pir_set_option(qpadl_db *db, int option, int64_t value);
 int qpadl_pir_get_option(const qpadl_db *db, int option, int64_t *value);
+
+/* Autotuner: times this handle's exact-path choices on the device with CUDA
+ * events (uniform synthetic queries, answers discarded) and keeps the
+ * fastest; every choice gives the same results.  Tunes, in order:
+ *  - one query: QPADL_OPT_STREAM_CHUNK in {1024, 2048, 4096} x
+ *    QPADL_OPT_STREAM_RAW in {0, 1};
+ *  - if max_batch >= 2: QPADL_OPT_U8_KSTEP in {128, 256} at
+ *    min(max(max_batch, 4), 16) queries (when that batch takes the uint8-
+ *    digit GEMM), then QPADL_OPT_TENSOR_MIN_BATCH = the first B in 2..4 at
+ *    which the tensor path beats the streaming kernel (5 if none does).
+ * Allocates and frees scratch for 16 queries and answers, may build the
+ * blocked digit copy, and synchronises the stream.  report (may be NULL)
+ * receives the times in ms (-1 where a choice does not apply). */
+typedef struct qpadl_tune_report {
+    double single_ms[3][2];     /* [chunk 1024, 2048, 4096][raw 0, 1] */
+    double u8_kstep_ms[2];      /* [128, 256] at tuned_batch queries */
+    double stream_ms[3];        /* B = 2, 3, 4 on the streaming kernel */
+    double tensor_ms[3];        /* B = 2, 3, 4 on the tensor path */
+    uint32_t tuned_batch;
+    int32_t stream_chunk, stream_raw, u8_kstep;   /* the chosen settings */
+    uint32_t tensor_min_batch;
+} qpadl_tune_report;
+int qpadl_pir_autotune(qpadl_db *db, uint32_t max_batch, qpadl_stream_t stream, qpadl_tune_report *report);
 
 /*
  * Setup, public matrix: A_dev[j*n + k] = upper 32 bits of output number

@@ -42,6 +42,7 @@ constexpr int kBM = 128;
 constexpr int kThreads = 448;
 constexpr int kConvGroups = 2;
 constexpr uint32_t kTmemCols = 512;
+constexpr int kPrefetch = 8;   // stages of digit tiles pulled into L2 ahead of their loads
 
 // BN: limb columns per tile; KS: digits per row per pipeline stage (a
 // multiple of 128: each digit tile is 128 rows x 128 bytes, 128-byte swizzle).
@@ -156,12 +157,29 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer
+            // A second walker over the same stage sequence, kPrefetch stages ahead, pulls each digit
+            // box into L2 before its load is issued, so the loads see L2 rather than HBM latency.
+            uint32_t pu = ubeg, pks = 0;
+            Seg ps;
+            bool pvalid = next_seg(args, pu, uend, BN, ps);
+            if (pvalid) pks = ps.ks0;
+            auto prefetch_next = [&]() {
+                if (!pvalid) return;
+                tma_prefetch_l2_4d(&args.a[ps.g], 0, 0, static_cast<int32_t>(pks * KS / 128),
+                                   static_cast<int32_t>(ps.m0 / kBM));
+                if (++pks >= ps.ks1) {
+                    pvalid = next_seg(args, pu, uend, BN, ps);
+                    if (pvalid) pks = ps.ks0;
+                }
+            };
+            for (int i = 0; i < kPrefetch; ++i) prefetch_next();
             uint32_t it = 0, u = ubeg;
             Seg tr;
             while (!failed && next_seg(args, u, uend, BN, tr)) {
                 for (uint32_t ks = tr.ks0; ks < tr.ks1; ++ks, ++it) {
                     const uint32_t st = it % ST;
                     const uint32_t ph = (it / ST) & 1u;
+                    prefetch_next();
                     if (!mbar_wait(&empty[st], ph ^ 1u, abort)) {
                         failed = true;
                         break;
@@ -398,7 +416,8 @@ cudaError_t prepare_limb_gemm_u8_kernels() {
     return set_attr<128, 256>();
 }
 
-int limb_gemm_u8_default_ks(int bn) { return bn <= 64 ? 256 : 128; }
+// 128-digit stages for every tile width: with 256 the TMEM A slots allow only two stages in flight
+int limb_gemm_u8_default_ks(int) { return 128; }
 
 template <int BN, int KS>
 static cudaError_t launch_u8(const GroupedGemmArgs &args, int grid, int *status, cudaStream_t stream) {

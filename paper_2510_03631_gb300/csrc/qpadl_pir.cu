@@ -423,6 +423,31 @@ int db_answer_one_noscratch(qpadl_db *db, const uint32_t *q, uint32_t *ans, cuda
 
 }  // namespace qpadl
 
+namespace {
+
+// Mean CUDA-event time of `reps` calls of fn on stream s after one warm-up call; < 0 on failure.
+template <class F>
+double time_calls(F fn, cudaStream_t s, int reps) {
+    if (fn() != QPADL_OK) return -1.0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return -1.0;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return -1.0;
+    }
+    double ms = -1.0;
+    bool ok = cudaEventRecord(e0, s) == cudaSuccess;
+    for (int i = 0; i < reps && ok; ++i) ok = fn() == QPADL_OK;
+    ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+    float t = 0.f;
+    if (ok && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms = t / reps;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *qpadl_strerror(int code) {
@@ -680,6 +705,92 @@ int qpadl_pir_get_option(const qpadl_db *db, int option, int64_t *value) {
         case QPADL_OPT_U8_KSTEP: *value = db->u8_kstep; return QPADL_OK;
         default: return QPADL_EINVAL;
     }
+}
+
+int qpadl_pir_autotune(qpadl_db *db, uint32_t max_batch, qpadl_stream_t stream, qpadl_tune_report *report) {
+    if (!db || max_batch == 0) return QPADL_EINVAL;
+    if (set_device(db) != QPADL_OK) return QPADL_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t R = db->prm.rows, C = db->prm.cols;
+    qpadl_tune_report rep;
+    std::memset(&rep, 0, sizeof(rep));
+    const uint32_t BT = std::min<uint32_t>(std::max<uint32_t>(max_batch, 4u), 16u);
+    uint32_t *Q = nullptr, *A = nullptr;
+    if (cudaMalloc(reinterpret_cast<void **>(&Q), 4ull * C * BT) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void **>(&A), 4ull * R * BT) != cudaSuccess) {
+        cudaGetLastError();
+        if (Q) cudaFree(Q);
+        return QPADL_ENOMEM;
+    }
+    auto done = [&](int rc) {
+        cudaStreamSynchronize(s);
+        cudaFree(Q);
+        cudaFree(A);
+        if (rc == QPADL_OK && report) *report = rep;
+        return rc;
+    };
+    // synthetic queries (uniform words); the answers are discarded
+    if (cuda_fail(launch_gen_a(0x9E3779B97F4A7C15ull, C * BT, 1, Q, db->num_sms, s), "tune queries") != QPADL_OK)
+        return done(QPADL_ECUDA);
+    constexpr int kReps = 5;
+    // 1. one query: chunk width x in-kernel packing
+    const int chunks[3] = {1024, 2048, 4096};
+    double best = 1e30;
+    int best_chunk = db->stream_chunk, best_raw = db->stream_raw;
+    for (int ci = 0; ci < 3; ++ci) {
+        for (int raw = 0; raw < 2; ++raw) {
+            rep.single_ms[ci][raw] = -1.0;
+            if (!db->stream_ok || !stream_config_valid(1, chunks[ci])) continue;
+            db->stream_chunk = chunks[ci];
+            db->stream_raw = raw;
+            const double ms = time_calls([&] { return answer_streaming(db, Q, 1, A, s); }, s, kReps);
+            rep.single_ms[ci][raw] = ms;
+            if (ms > 0 && ms < best) {
+                best = ms;
+                best_chunk = chunks[ci];
+                best_raw = raw;
+            }
+        }
+    }
+    db->stream_chunk = best_chunk;
+    db->stream_raw = best_raw;
+    // 2. small batches: digit-tile depth of the uint8 GEMM, then the streaming/tensor crossover
+    rep.tuned_batch = BT;
+    if (max_batch >= 2) {
+        if (db->u8_ok && db->u8_max_batch >= BT) {
+            const int ks[2] = {128, 256};
+            double kbest = 1e30;
+            int kpick = db->u8_kstep;
+            for (int k = 0; k < 2; ++k) {
+                db->u8_kstep = ks[k];
+                const double ms = time_calls([&] { return answer_tensor(db, Q, BT, A, s); }, s, kReps);
+                rep.u8_kstep_ms[k] = ms;
+                if (ms > 0 && ms < kbest) {
+                    kbest = ms;
+                    kpick = ks[k];
+                }
+            }
+            db->u8_kstep = kpick;
+        }
+        uint32_t threshold = db->tensor_min_batch;
+        for (uint32_t B = 2; B <= 4; ++B) {
+            const double ms_s = time_calls([&] { return answer_streaming(db, Q, B, A, s); }, s, kReps);
+            const double ms_t = time_calls([&] { return answer_tensor(db, Q, B, A, s); }, s, kReps);
+            rep.stream_ms[B - 2] = ms_s;
+            rep.tensor_ms[B - 2] = ms_t;
+            if (ms_s > 0 && ms_t > 0 && ms_t < ms_s) {
+                threshold = B;
+                break;
+            }
+            threshold = B + 1;
+        }
+        db->tensor_min_batch = threshold;
+    }
+    rep.stream_chunk = db->stream_chunk;
+    rep.stream_raw = db->stream_raw;
+    rep.u8_kstep = db->u8_kstep;
+    rep.tensor_min_batch = db->tensor_min_batch;
+    return done(QPADL_OK);
 }
 
 int qpadl_pir_answer_host(qpadl_db *db, const uint32_t *q_host, uint32_t *ans_host, qpadl_stream_t stream) {

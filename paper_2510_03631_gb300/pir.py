@@ -102,6 +102,7 @@ _SIGS = {
     "qpadl_chor_set_option": ([_P, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
     "qpadl_chor_get_option": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "qpadl_chor_destroy": ([_P], ctypes.c_int),
+    "qpadl_pir_autotune": ([_P, ctypes.c_uint32, _P, _P], ctypes.c_int),
     "qpadl_server_create": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
     "qpadl_server_add_db": ([_P, _P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "qpadl_server_start": ([_P], ctypes.c_int),
@@ -575,6 +576,29 @@ def qpadl_pir_shard_rows(rows: int, world: int, rank: int):
     _check(load().qpadl_pir_shard_rows(int(rows), int(world), int(rank), ctypes.byref(r0), ctypes.byref(r1)),
            "qpadl_pir_shard_rows")
     return int(r0.value), int(r1.value)
+
+
+class qpadl_tune_report(ctypes.Structure):
+    _fields_ = [
+        ("single_ms", (ctypes.c_double * 2) * 3),
+        ("u8_kstep_ms", ctypes.c_double * 2),
+        ("stream_ms", ctypes.c_double * 3),
+        ("tensor_ms", ctypes.c_double * 3),
+        ("tuned_batch", ctypes.c_uint32),
+        ("stream_chunk", ctypes.c_int32), ("stream_raw", ctypes.c_int32), ("u8_kstep", ctypes.c_int32),
+        ("tensor_min_batch", ctypes.c_uint32),
+    ]
+
+
+def qpadl_pir_autotune(db: Database, max_batch: int, stream=None) -> dict:
+    """Time the handle's exact-path choices on the device and keep the fastest; returns the report."""
+    rep = qpadl_tune_report()
+    _check(load().qpadl_pir_autotune(db.handle, int(max_batch), _stream(stream), ctypes.byref(rep)),
+           "qpadl_pir_autotune")
+    return {"single_ms": [[rep.single_ms[c][r] for r in range(2)] for c in range(3)],
+            "u8_kstep_ms": list(rep.u8_kstep_ms), "stream_ms": list(rep.stream_ms), "tensor_ms": list(rep.tensor_ms),
+            "tuned_batch": rep.tuned_batch, "stream_chunk": rep.stream_chunk, "stream_raw": rep.stream_raw,
+            "u8_kstep": rep.u8_kstep, "tensor_min_batch": rep.tensor_min_batch}
 
 
 def qpadl_pir_reserve(db: Database, max_batch: int, stream=None):
