@@ -309,6 +309,7 @@ def serving_measure(torch, pir, inputs, rates, duration_s, single_db_one_ms, see
                                                                      tm_ok[int(good.argmax()), 1] - tm_ok[int(good.argmax()), 0],
                                                                      tm_ok[int(good.argmax()), 2] - tm_ok[int(good.argmax()), 1])]
                                         if len(good) else None)})
+    enq_us = pir.qpadl_server_stats(srv)["mean_enqueue_us"]
     srv.close()
 
     # the 1 GiB database alone: batched serving vs one query at a time
@@ -330,6 +331,7 @@ def serving_measure(torch, pir, inputs, rates, duration_s, single_db_one_ms, see
         "databases": [f"{R}x{C}" for R, C in shapes], "skew": list(skew), "n_lwe": n_lwe,
         "answers_checked_in_mix": n0, "streams": 4, "max_batch": 256, "group_size_ratio": 2.0,
         "rates": runs,
+        "mean_enqueue_us_per_launch": round(enq_us, 2),
         "single_1gib_saturation": {
             "offered_qps": 200000, "requests": n1, "achieved_qps": round(qps1, 1),
             "p50_ms": round(_pct(good1, 50), 3), "p99_ms": round(_pct(good1, 99), 3),

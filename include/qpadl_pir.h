@@ -471,6 +471,7 @@ typedef struct qpadl_server_stats_t {
     double mean_launch_requests;
     uint64_t host_bytes_used, device_bytes_used;
     uint64_t grouped_launches;    /* launches that answered two or more databases */
+    double mean_enqueue_us;       /* host time per launch spent enqueueing its kernels */
 } qpadl_server_stats_t;
 
 /* Creates a server on the current device (allocates both arenas and the

@@ -189,6 +189,7 @@ struct qpadl_server {
     // counters
     uint64_t n_launches = 0, n_done = 0, n_failed = 0, n_busy = 0, n_grouped = 0;
     double busy_batch_sum = 0;
+    double enqueue_s = 0;   // host time spent enqueueing launches
 
     void run();
     bool form_launch(int slot_idx, std::unique_lock<std::mutex> &lk);
@@ -321,6 +322,7 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
     busy_batch_sum += static_cast<double>(total);
     // enqueue the GPU work without holding the lock
     lk.unlock();
+    const double t_enq0 = now_s();
     uint8_t *base = dev_arena + off;
     uint64_t maxC = 0, maxR = 0;
     for (const Group &g : groups) {
@@ -399,7 +401,9 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
         cudaStreamSynchronize(S.stream);
         complete(L);
     }
+    const double t_enq = now_s() - t_enq0;
     lk.lock();
+    enqueue_s += t_enq;
     return true;
 }
 
@@ -625,6 +629,7 @@ int qpadl_server_stats(qpadl_server *s, qpadl_server_stats_t *st) {
     st->host_bytes_used = s->host_alloc.used();
     st->device_bytes_used = s->dev_alloc.used();
     st->grouped_launches = s->n_grouped;
+    st->mean_enqueue_us = s->n_launches ? 1e6 * s->enqueue_s / static_cast<double>(s->n_launches) : 0.0;
     return QPADL_OK;
 }
 
