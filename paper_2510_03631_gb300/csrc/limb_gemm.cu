@@ -20,7 +20,7 @@
 //
 // Kernel shape (one CTA per SM, persistent over output tiles):
 //   warp 0      TMA producer: 128x64 tile of D16 and BNx64 tile of limbs per
-//               stage, 128-byte swizzle, 4-stage mbarrier ring.
+//               stage, 128-byte swizzle, mbarrier ring of 4 (BN = 256) to 8 stages.
 //   warp 1      allocates TMEM (two BN-column fp32 accumulators) and one
 //               thread issues tcgen05.mma M=128, N=BN, K=16 (4 per stage).
 //   warps 2..5  epilogue: drain one accumulator per 512-deep K-chunk while
@@ -62,7 +62,6 @@ namespace qpadl {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;          // fp16 elements per 128-byte swizzled row
-constexpr int kGemmStages = 4;
 constexpr int kChunkKB = 8;      // 8 x 64 = 512-deep exact K-chunks
 constexpr int kGemmThreads = 192;
 
@@ -72,7 +71,10 @@ struct GemmCfg {
     static constexpr uint32_t kBBytes = BN * kBK * 2;
     static constexpr uint32_t kStageBytes = kABytes + kBBytes;
     static constexpr uint32_t kTmemCols = (2 * BN < 32) ? 32 : 2 * BN;
-    static constexpr int kSmemBytes = kGemmStages * kStageBytes + 256 + 1024;
+    // as many stages as fit in about 192 KB, at most 8: narrow tiles (small batches, one-limb
+    // vectors) get a deeper ring, since each of their stages carries little MMA work
+    static constexpr int kStages = (192 * 1024 / kStageBytes) < 8 ? (192 * 1024 / kStageBytes) : 8;
+    static constexpr int kSmemBytes = kStages * kStageBytes + 256 + 1024;
     static constexpr int kQPT = BN / 4;   // vectors per tile
 };
 
@@ -92,6 +94,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                      int *__restrict__ status) {
     static_assert(!PLANED || BN >= 64, "a shift group needs N = BN/4 >= 16");
     using Cfg = GemmCfg<BN>;
+    constexpr int kGemmStages = Cfg::kStages;
     constexpr int LPV = Epi::kLimbs;   // limb rows per vector
     static_assert(LPV == 4 || (LPV == 1 && !PLANED && BN <= 64), "one-limb vectors: plain mode, BN <= 64");
     constexpr int QPT = BN / LPV;      // vectors per tile
@@ -376,10 +379,32 @@ __device__ __forceinline__ void balanced_limbs(uint32_t x, float (&c)[4]) {
 // limb k of vector v in row 4v + k.  One block per vector at a time.
 __global__ void vec_limbs_kernel(const uint32_t *__restrict__ X, uint64_t x_ld, uint32_t NV, uint64_t C,
                                  __half *__restrict__ L, uint64_t pitch) {
-    for (uint32_t v = blockIdx.x; v < NV; v += gridDim.x) {
-        const uint32_t *src = X + (uint64_t)v * x_ld;
-        __half *dst = L + 4ull * v * pitch;
-        for (uint64_t j = threadIdx.x; j < C; j += blockDim.x) {
+    // block (x, y): vector y, columns [2048 x, 2048 x + 2048), 8 consecutive columns per thread,
+    // so even a handful of vectors spreads over the whole GPU
+    constexpr uint32_t kCols = 8;
+    const uint32_t v = blockIdx.y;
+    const uint32_t *src = X + (uint64_t)v * x_ld;
+    __half *dst = L + 4ull * v * pitch;
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) && (pitch % 8 == 0) &&
+                     ((reinterpret_cast<uintptr_t>(L) & 15u) == 0);
+    const uint64_t j0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * kCols;
+    if (j0 >= C) return;
+    if (vec && j0 + kCols <= C) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(src + j0);
+        const uint4 b = *reinterpret_cast<const uint4 *>(src + j0 + 4);
+        const uint32_t x[kCols] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        __align__(16) __half h[4][kCols];
+#pragma unroll
+        for (uint32_t i = 0; i < kCols; ++i) {
+            float c[4];
+            balanced_limbs(x[i], c);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) h[k][i] = __float2half_rn(c[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) *reinterpret_cast<uint4 *>(dst + k * pitch + j0) = *reinterpret_cast<const uint4 *>(h[k]);
+    } else {
+        for (uint64_t j = j0; j < C && j < j0 + kCols; ++j) {
             float c[4];
             balanced_limbs(src[j], c);
 #pragma unroll
@@ -603,8 +628,14 @@ cudaError_t launch_db_to_f16(const uint8_t *D, uint64_t R, uint64_t C, __half *D
 
 cudaError_t launch_vec_limbs(const uint32_t *X, uint64_t x_ld, uint32_t NV, uint64_t C, __half *L, uint64_t pitch,
                              int num_sms, cudaStream_t stream) {
-    const uint32_t blocks = NV < (uint32_t)(num_sms * 8) ? NV : (uint32_t)(num_sms * 8);
-    vec_limbs_kernel<<<blocks, 256, 0, stream>>>(X, x_ld, NV, C, L, pitch);
+    (void)num_sms;
+    if (NV == 0 || C == 0) return cudaSuccess;
+    for (uint32_t v0 = 0; v0 < NV; v0 += 65535) {   // grid.y limit
+        const uint32_t nv = NV - v0 < 65535 ? NV - v0 : 65535;
+        const dim3 grid(static_cast<unsigned>((C + 2047) / 2048), nv);
+        vec_limbs_kernel<<<grid, 256, 0, stream>>>(X + (uint64_t)v0 * x_ld, x_ld, nv, C, L + 4ull * v0 * pitch,
+                                                    pitch);
+    }
     return cudaGetLastError();
 }
 

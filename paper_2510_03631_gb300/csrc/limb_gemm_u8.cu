@@ -21,12 +21,19 @@
 // wave is never partial; tiles shared by two CTAs are summed with atomic
 // adds, which is exact because the result is taken mod 2^32.
 //
-// Warp roles (448 threads, one CTA per SM):
-//   warp 0       TMA producer (digit tile + limb tile per stage)
+// Three rings decouple the stages (a stage = KS digits of a 128-row tile):
+//   digit tiles in shared memory (freed as soon as they are converted),
+//   limb tiles in shared memory (freed when the MMA that reads them completes),
+//   fp16 A slots in TMEM (freed when the MMA that reads them completes),
+// so the digit loads run ahead of the MMA instead of waiting for it.
+//
+// Warp roles (480 threads, one CTA per SM):
+//   warp 0       TMA producer of the digit tiles (plus L2 prefetch ahead of them)
 //   warp 1       TMEM allocation; one thread issues the MMAs
 //   warps 2..5   epilogue: drain one of two BN-column accumulators per chunk
-//   warps 6..13  converters, two groups of four, each owning half the stages:
+//   warps 6..13  converters, two groups of four, each owning every other stage:
 //                digits -> fp16 A tiles in TMEM (one row per thread)
+//   warp 14      TMA producer of the limb tiles
 #include <cstdint>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -39,7 +46,7 @@ namespace qpadl {
 namespace {
 
 constexpr int kBM = 128;
-constexpr int kThreads = 448;
+constexpr int kThreads = 480;
 constexpr int kConvGroups = 2;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kPrefetch = 8;   // stages of digit tiles pulled into L2 ahead of their loads
@@ -50,24 +57,27 @@ template <int BN, int KS>
 struct U8Cfg {
     static constexpr int kSubA = KS / 128;                          // digit boxes per stage
     static constexpr int kSubB = KS / 64;                           // limb boxes per stage
-    static constexpr uint32_t kABytes = kBM * KS;
+    static constexpr uint32_t kDigBytes = kBM * KS;                 // one digit slot
     static constexpr uint32_t kBBoxBytes = BN * 128;
-    static constexpr uint32_t kBBytes = kSubB * kBBoxBytes;
-    static constexpr uint32_t kStageBytes = kABytes + kBBytes;
+    static constexpr uint32_t kLimbBytes = kSubB * kBBoxBytes;      // one limb slot
     static constexpr uint32_t kSlotCols = KS / 2;                   // fp16 pairs per row per stage
-    static constexpr int kSmemStages = (200 * 1024) / kStageBytes;
-    static constexpr int kTmemStages = (kTmemCols - 2 * BN) / kSlotCols;
-    // a multiple of the converter-group count: group g then owns the stages st with st % 2 == g
-    // and waits on every phase of them (a parity wait must never fall two phases behind)
-    static constexpr int kStages = ((kSmemStages < kTmemStages ? kSmemStages : kTmemStages) / kConvGroups) * kConvGroups;
+    // Digit and A-slot counts are even: converter group g owns the stages with it % 2 == g and
+    // so every phase of the slots with index % 2 == g (a parity wait never falls two phases behind).
+    static constexpr int kSA = (((kTmemCols - 2 * BN) / kSlotCols) / 2) * 2;
+    static constexpr int kSD = KS == 128 ? (BN == 128 ? 6 : 8) : (BN == 128 ? 2 : 4);
+    static constexpr int kSLfit = (192 * 1024 - kSD * kDigBytes) / kLimbBytes;
+    static constexpr int kSL = kSLfit < 8 ? kSLfit : 8;
     static constexpr uint32_t kAColBase = 2 * BN;                   // A slots after the accumulators
     static constexpr int kChunkStages = 512 / KS;                   // stages per exact 512-deep K-chunk
-    static constexpr int kSmemUsed = kStages * kStageBytes + 512 + 1024;
+    static constexpr uint32_t kLimbBase = kSD * kDigBytes;
+    static constexpr uint32_t kBarBase = kLimbBase + kSL * kLimbBytes;
+    static constexpr int kSmemUsed = kBarBase + (2 * kSD + 2 * kSL + 2 * kSA + 5) * 8 + 16 + 1024;
     // padded so that only one CTA fits per SM (it allocates all of TMEM)
     static constexpr int kSmemBytes = kSmemUsed > 120 * 1024 ? kSmemUsed : 120 * 1024;
     static constexpr int kQPT = BN / 4;
-    static_assert(kStages >= 2 && kStages % kConvGroups == 0, "stages must split evenly between converter groups");
+    static_assert(kSA >= 2 && kSD >= 2 && kSD % 2 == 0 && kSL >= 2, "ring sizes");
     static_assert(KS % 128 == 0 && 512 % KS == 0, "stage depth must divide the exact chunk");
+    static_assert(kSmemUsed <= 227 * 1024, "shared memory");
 };
 
 __device__ __forceinline__ bool drain_wait_u(uint64_t *bar, uint32_t parity) {
@@ -110,15 +120,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     limb_gemm_u8_kernel(const __grid_constant__ GroupedGemmArgs args, int *__restrict__ status) {
     using Cfg = U8Cfg<BN, KS>;
     constexpr int QPT = Cfg::kQPT;
-    constexpr int ST = Cfg::kStages;
+    constexpr int SD = Cfg::kSD, SL = Cfg::kSL, SA = Cfg::kSA;
     constexpr int CS = Cfg::kChunkStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    // stage s: [digit boxes][limb boxes], every box 1024-aligned
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + ST * Cfg::kStageBytes);
-    uint64_t *conv = full + ST;
-    uint64_t *empty = conv + ST;
-    uint64_t *acc_full = empty + ST;   // [2]
+    uint8_t *dig = smem;                       // [SD] digit slots, each kSubA 16 KB boxes
+    uint8_t *limb = smem + Cfg::kLimbBase;     // [SL] limb slots, each kSubB boxes, 1024-aligned
+    uint64_t *dfull = reinterpret_cast<uint64_t *>(smem + Cfg::kBarBase);
+    uint64_t *dfree = dfull + SD;
+    uint64_t *lfull = dfree + SD;
+    uint64_t *lfree = lfull + SL;
+    uint64_t *aready = lfree + SL;
+    uint64_t *afree = aready + SA;
+    uint64_t *acc_full = afree + SA;   // [2]
     uint64_t *acc_empty = acc_full + 2;
     uint64_t *mma_done = acc_empty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
@@ -128,10 +142,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < ST; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&conv[s], 4);
-            mbar_init(&empty[s], 1);
+        for (int s = 0; s < SD; ++s) {
+            mbar_init(&dfull[s], 1);
+            mbar_init(&dfree[s], 4);   // the four warps of the converter group that owns the slot
+        }
+        for (int s = 0; s < SL; ++s) {
+            mbar_init(&lfull[s], 1);
+            mbar_init(&lfree[s], 1);
+        }
+        for (int s = 0; s < SA; ++s) {
+            mbar_init(&aready[s], 4);
+            mbar_init(&afree[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
@@ -154,11 +175,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t uend = static_cast<uint32_t>((uint64_t)(blockIdx.x + 1) * args.total_units / gridDim.x);
     bool failed = false;
 
+    // waits until every copy this thread issued into `ring` has landed (so the CTA can exit)
+    auto drain_ring = [&](uint64_t *ring, int slots, uint32_t issued) {
+        const uint32_t inflight = issued < (uint32_t)slots ? issued : (uint32_t)slots;
+        for (uint32_t j = issued - inflight; j < issued; ++j)
+            if (!drain_wait_u(&ring[j % slots], (j / slots) & 1u)) failed = true;
+    };
+
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- TMA producer
+            // ---------------- digit producer
             // A second walker over the same stage sequence, kPrefetch stages ahead, pulls each digit
-            // box into L2 before its load is issued, so the loads see L2 rather than HBM latency.
+            // box into L2 before its load is issued.
             uint32_t pu = ubeg, pks = 0;
             Seg ps;
             bool pvalid = next_seg(args, pu, uend, BN, ps);
@@ -177,29 +205,42 @@ __global__ void __launch_bounds__(kThreads, 1)
             Seg tr;
             while (!failed && next_seg(args, u, uend, BN, tr)) {
                 for (uint32_t ks = tr.ks0; ks < tr.ks1; ++ks, ++it) {
-                    const uint32_t st = it % ST;
-                    const uint32_t ph = (it / ST) & 1u;
+                    const uint32_t sd = it % SD;
                     prefetch_next();
-                    if (!mbar_wait(&empty[st], ph ^ 1u, abort)) {
+                    if (!mbar_wait(&dfree[sd], ((it / SD) & 1u) ^ 1u, abort)) {
                         failed = true;
                         break;
                     }
-                    uint8_t *sa = smem + st * Cfg::kStageBytes;
-                    uint8_t *sb = sa + Cfg::kABytes;
-                    mbar_arrive_expect_tx(&full[st], Cfg::kStageBytes);
-                    const int32_t k0 = static_cast<int32_t>(ks * KS);
+                    mbar_arrive_expect_tx(&dfull[sd], Cfg::kDigBytes);
                     // the digits are stored blocked (128 x 128 tiles, each 16 KB contiguous), so the
                     // kSubA tiles of this stage are one contiguous read
-                    tma_load_4d(sa, &args.a[tr.g], &full[st], 0, 0, k0 / 128, static_cast<int32_t>(tr.m0 / kBM));
-#pragma unroll
-                    for (int b = 0; b < Cfg::kSubB; ++b)
-                        tma_load_2d(sb + b * Cfg::kBBoxBytes, &args.b[tr.g], &full[st], k0 + 64 * b,
-                                    static_cast<int32_t>(tr.n0));
+                    tma_load_4d(dig + sd * Cfg::kDigBytes, &args.a[tr.g], &dfull[sd], 0, 0,
+                                static_cast<int32_t>(ks * KS / 128), static_cast<int32_t>(tr.m0 / kBM));
                 }
             }
-            const uint32_t inflight = it < (uint32_t)ST ? it : (uint32_t)ST;
-            for (uint32_t j = it - inflight; j < it; ++j)
-                if (!drain_wait_u(&full[j % ST], (j / ST) & 1u)) failed = true;
+            drain_ring(dfull, SD, it);
+        }
+    } else if (warp == 14) {
+        if (lane == 0) {
+            // ---------------- limb producer
+            uint32_t it = 0, u = ubeg;
+            Seg tr;
+            while (!failed && next_seg(args, u, uend, BN, tr)) {
+                for (uint32_t ks = tr.ks0; ks < tr.ks1; ++ks, ++it) {
+                    const uint32_t sl = it % SL;
+                    if (!mbar_wait(&lfree[sl], ((it / SL) & 1u) ^ 1u, abort)) {
+                        failed = true;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&lfull[sl], Cfg::kLimbBytes);
+                    const int32_t k0 = static_cast<int32_t>(ks * KS);
+#pragma unroll
+                    for (int b = 0; b < Cfg::kSubB; ++b)
+                        tma_load_2d(limb + sl * Cfg::kLimbBytes + b * Cfg::kBBoxBytes, &args.b[tr.g], &lfull[sl],
+                                    k0 + 64 * b, static_cast<int32_t>(tr.n0));
+                }
+            }
+            drain_ring(lfull, SL, it);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer: the whole warp walks the loop so the descriptors and
@@ -223,23 +264,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                     d_tmem = tmem_base + buf * BN;
                 }
-                const uint32_t st = it % ST;
-                const uint32_t ph = (it / ST) & 1u;
-                const bool ok = mbar_wait(&conv[st], ph, abort);   // implies the limb boxes have landed too
+                const uint32_t sa = it % SA, sl = it % SL;
+                bool ok = mbar_wait(&aready[sa], (it / SA) & 1u, abort);
+                ok = ok && mbar_wait(&lfull[sl], (it / SL) & 1u, abort);
                 if (__any_sync(0xffffffffu, !ok)) {
                     failed = true;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t sb = smem_addr(smem + st * Cfg::kStageBytes + Cfg::kABytes);
-                const uint32_t a_tmem = tmem_base + Cfg::kAColBase + st * Cfg::kSlotCols;
+                const uint32_t sb = smem_addr(limb + sl * Cfg::kLimbBytes);
+                const uint32_t a_tmem = tmem_base + Cfg::kAColBase + sa * Cfg::kSlotCols;
                 if (elect_one()) {
 #pragma unroll
                     for (int kk = 0; kk < KS / 16; ++kk) {
                         const uint64_t bdesc = umma_desc_sw128(sb + (kk / 4) * Cfg::kBBoxBytes) + 2u * (kk % 4);
                         umma_f16_ts(d_tmem, a_tmem + 8u * kk, bdesc, idesc, (kr % CS != 0 || kk != 0) ? 1u : 0u);
                     }
-                    umma_commit(&empty[st]);   // frees the shared-memory stage and the TMEM A slot
+                    umma_commit(&afree[sa]);   // the TMEM A slot and
+                    umma_commit(&lfree[sl]);   // the limb slot are free once these MMAs complete
                     if (kr % CS == CS - 1 || ks == sg.ks1 - 1) umma_commit(&acc_full[ci & 1u]);
                 }
                 __syncwarp();
@@ -308,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // ---------------- converters (warps 6..13): digits -> fp16 A in TMEM
         const uint32_t quarter = static_cast<uint32_t>(warp & 3);
-        const uint32_t group = static_cast<uint32_t>(warp - 6) / 4;   // owns the stages st % 2 == group
+        const uint32_t group = static_cast<uint32_t>(warp - 6) / 4;   // owns the stages it % 2 == group
         const uint32_t row = quarter * 32u + static_cast<uint32_t>(lane);
         const uint32_t lane_addr = (quarter * 32u) << 16;
         const __half2 k1024 = __floats2half2_rn(1024.0f, 1024.0f);
@@ -316,17 +358,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         Seg sg;
         while (!failed && next_seg(args, u, uend, BN, sg)) {
             for (uint32_t ks = sg.ks0; ks < sg.ks1; ++ks, ++it) {
-                const uint32_t st = it % ST;
-                if (st % kConvGroups != group) continue;   // this group owns every phase of its stages
-                const uint32_t ph = (it / ST) & 1u;
-                if (!mbar_wait(&full[st], ph, abort)) {
+                if (it % kConvGroups != group) continue;   // this group owns every phase of its slots
+                const uint32_t sd = it % SD, sa = it % SA;
+                bool ok = mbar_wait(&dfull[sd], (it / SD) & 1u, abort);
+                ok = ok && mbar_wait(&afree[sa], ((it / SA) & 1u) ^ 1u, abort);
+                if (__any_sync(0xffffffffu, !ok)) {
                     failed = true;
                     break;
                 }
-                const uint32_t a_tmem = tmem_base + lane_addr + Cfg::kAColBase + st * Cfg::kSlotCols;
+                tc_fence_after();   // the MMA that last read this A slot has completed
+                const uint32_t a_tmem = tmem_base + lane_addr + Cfg::kAColBase + sa * Cfg::kSlotCols;
 #pragma unroll
                 for (int b = 0; b < Cfg::kSubA; ++b) {
-                    const uint8_t *tile = smem + st * Cfg::kStageBytes + b * 16384 + row * 128;
+                    const uint8_t *tile = dig + sd * Cfg::kDigBytes + b * 16384 + row * 128;
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         // 128-byte swizzle: logical 16-byte chunk j of row r sits at chunk j ^ (r & 7),
@@ -348,10 +392,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tmem_st8(a_tmem + 64u * b + 8u * j, o);   // warp-uniform TMEM address
                     }
                 }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&dfree[sd]);   // the digit slot has been read
                 tmem_wait_st();
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&conv[st]);
+                if (lane == 0) mbar_arrive(&aready[sa]);
             }
         }
     }

@@ -72,9 +72,41 @@ def _chor_case(a):
     h.close()
 
 
+def _goldberg_case(a):
+    """Goldberg Response over Z_257 on a rows x cols byte database, a batch of uniform field elements."""
+    R, C, B, p = a.rows, a.cols, a.batch, 257
+    D_np = inputs.db_digits(R, C, 256, seed=1)
+    h = pir.qpadl_goldberg_setup(R, C, p, torch.from_numpy(D_np).cuda())
+    Q_np = (inputs.uniform_u32(B * C, seed=2, tag=inputs.TAG_MISC) % p).reshape(B, C)
+    Q = pir.from_u32(Q_np.reshape(-1))
+    out = torch.empty(B * R, dtype=torch.int32, device="cuda")
+    fn = lambda: pir.qpadl_goldberg_answer_batch(h, Q, out)
+    fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(a.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    if pir.qpadl_goldberg_status(h) != 0:
+        raise SystemExit("profile case: device status word set")
+    exp = (Q_np[:, :].astype(np.int64) @ D_np[R // 2].astype(np.int64)) % p
+    if not np.array_equal(pir.as_u32(out).reshape(B, R)[:, R // 2], exp.astype(np.uint32)):
+        raise SystemExit("profile case: output differs from the host recomputation")
+    ms = min(times)
+    print(json.dumps({"case": "goldberg", "rows": R, "cols": C, "batch": B, "ms": times,
+                      "fp16_mma_flops": 2 * R * C * B, "tflops": 2 * R * C * B / (ms * 1e-3) / 1e12,
+                      "queries_per_s": B / (ms * 1e-3)}))
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["stream", "gemm", "hint", "query", "recover", "qbatch", "rbatch", "chor"])
+    ap.add_argument("case", choices=["stream", "gemm", "hint", "query", "recover", "qbatch", "rbatch", "chor",
+                                     "goldberg"])
     ap.add_argument("--rows", type=int, default=8192)
     ap.add_argument("--cols", type=int, default=32768)
     ap.add_argument("--bits", type=int, default=262144, help="chor: bits per record")
@@ -92,6 +124,8 @@ def main():
     torch.cuda.set_device(0)
     if a.case == "chor":
         return _chor_case(a)
+    if a.case == "goldberg":
+        return _goldberg_case(a)
     R, C = a.rows, a.cols
     D_np = inputs.db_digits(R, C, 256, seed=1)
     prm = pir.params(R, C, a.n, seed=1)
