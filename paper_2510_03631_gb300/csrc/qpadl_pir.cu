@@ -79,7 +79,8 @@ struct qpadl_client {
 struct qpadl_goldberg {
     qpadl_db *db = nullptr;
     uint32_t p = 0;
-    uint32_t gemm_min_batch = 5;     // batches from this size take the one-limb GEMM
+    uint32_t gemm_min_batch = 5;     // batches from this size take a tensor-core GEMM
+    uint32_t u8_max_batch = 32;      // ... the uint8-digit one up to this size, the one-limb fp16 one above
 };
 
 // Chor-style GF(2) database handle.
@@ -1187,6 +1188,14 @@ int qpadl_goldberg_answer_batch(qpadl_goldberg *h, const uint32_t *Q_dev, uint32
         QPADL_CU(launch_mod_p(out_dev, (uint64_t)B * R, h->p, db->num_sms, s));
         return QPADL_OK;
     }
+    if (B <= h->u8_max_batch && db->u8_ok && 4 * B <= 128) {
+        // the four-limb uint8-digit GEMM gives the exact integer sums (no wrap below
+        // kGoldbergMaxCols columns), then mod p
+        int rc = answer_tensor_u8(db, Q_dev, B, out_dev, s);
+        if (rc != QPADL_OK) return rc;
+        QPADL_CU(launch_mod_p(out_dev, (uint64_t)B * R, h->p, db->num_sms, s));
+        return QPADL_OK;
+    }
     int rc = ensure_tensor_copy(db, s);
     if (rc != QPADL_OK) return rc;
     // one centred fp16 row per query, in chunks that the limb scratch holds
@@ -1213,6 +1222,10 @@ int qpadl_goldberg_set_option(qpadl_goldberg *h, int option, int64_t value) {
         case QPADL_GOLDBERG_OPT_GEMM_MIN_BATCH:
             if (value < 1 || value > (int64_t)UINT32_MAX) return QPADL_EINVAL;
             h->gemm_min_batch = static_cast<uint32_t>(value);
+            return QPADL_OK;
+        case QPADL_GOLDBERG_OPT_U8_MAX_BATCH:
+            if (value < 0 || value > 32) return QPADL_EINVAL;
+            h->u8_max_batch = static_cast<uint32_t>(value);
             return QPADL_OK;
         default: return QPADL_EINVAL;
     }

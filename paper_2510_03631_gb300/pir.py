@@ -423,6 +423,7 @@ class GoldbergDatabase:
 
 
 QPADL_GOLDBERG_OPT_GEMM_MIN_BATCH = 1
+QPADL_GOLDBERG_OPT_U8_MAX_BATCH = 2
 
 
 def qpadl_goldberg_setup(rows: int, cols: int, p: int, db: torch.Tensor, stream=None) -> GoldbergDatabase:

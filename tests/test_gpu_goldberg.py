@@ -24,9 +24,11 @@ def _db(R, C, p, seed):
     return (inputs.db_digits(R, C, 256, seed=seed).astype(np.int64) % p).astype(np.uint8)
 
 
-def _answer(h, Q_np, gemm_min=None):
+def _answer(h, Q_np, gemm_min=None, u8max=None):
     if gemm_min is not None:
         pir.qpadl_goldberg_set_option(h, pir.QPADL_GOLDBERG_OPT_GEMM_MIN_BATCH, gemm_min)
+    if u8max is not None:
+        pir.qpadl_goldberg_set_option(h, pir.QPADL_GOLDBERG_OPT_U8_MAX_BATCH, u8max)
     B = Q_np.shape[0]
     out = torch.empty(B * h.rows, dtype=torch.int32, device="cuda")
     pir.qpadl_goldberg_answer_batch(h, pir.from_u32(np.ascontiguousarray(Q_np).reshape(-1)), out)
@@ -40,19 +42,19 @@ CASES = [(300, 1000, 257, 1), (257, 513, 251, 4), (1000, 2048, 257, 5), (700, 40
 
 
 @pytest.mark.parametrize("R,C,p,B", CASES)
-@pytest.mark.parametrize("gemm_min", [1, 1 << 30])   # tensor-core GEMM only / streaming only
-def test_goldberg_matches_oracle(cuda, R, C, p, B, gemm_min):
+@pytest.mark.parametrize("gemm_min,u8max", [(1, 32), (1, 0), (1 << 30, 32)])   # u8 GEMM / one-limb GEMM / streaming
+def test_goldberg_matches_oracle(cuda, R, C, p, B, gemm_min, u8max):
     D = _db(R, C, p, seed=R + C)
     Q = (inputs.uniform_u32(B * C, seed=B + p, tag=inputs.TAG_MISC) % p).reshape(B, C)
     h = pir.qpadl_goldberg_setup(R, C, p, torch.from_numpy(D).cuda())
-    got = _answer(h, Q, gemm_min)
+    got = _answer(h, Q, gemm_min, u8max)
     assert np.array_equal(got, oracle.goldberg_answer(D, Q, p, threads=oracle.max_threads()))
     h.close()
 
 
-@pytest.mark.parametrize("gemm_min", [1, 1 << 30])
+@pytest.mark.parametrize("gemm_min,u8max", [(1, 32), (1, 0), (1 << 30, 32)])
 @pytest.mark.parametrize("qval", [256, 128, 129])
-def test_exact_sum_bounds(cuda, gemm_min, qval):
+def test_exact_sum_bounds(cuda, gemm_min, u8max, qval):
     # the largest allowed record count with every byte 255: the unsigned sum of the streaming
     # path and the centred sum of the GEMM both stay exact
     R, C, p, B = 128, 65792, 257, 6
@@ -60,7 +62,7 @@ def test_exact_sum_bounds(cuda, gemm_min, qval):
     D[::3, ::7] = 0
     Q = np.full((B, C), qval, dtype=np.uint32)
     h = pir.qpadl_goldberg_setup(R, C, p, torch.from_numpy(D).cuda())
-    got = _answer(h, Q, gemm_min)
+    got = _answer(h, Q, gemm_min, u8max)
     assert np.array_equal(got, oracle.goldberg_answer(D, Q, p, threads=oracle.max_threads()))
     h.close()
 
