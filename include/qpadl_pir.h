@@ -432,6 +432,23 @@ int qpadl_chor_status(qpadl_chor *h);
 int qpadl_chor_destroy(qpadl_chor *h);
 
 /* ======================================================================
+ * Failure-detection self-test.  Every wait of the library's TMA/tcgen05
+ * kernels on an mbarrier is bounded (2 s of %globaltimer): a kernel that
+ * gives up raises its CTA's abort flag, lets its own copies land, frees its
+ * TMEM and records QPADL_ETIMEOUT in a status word, so the host learns of
+ * the failure and the CUDA context stays usable; nothing traps.
+ * ==================================================================== */
+
+/* Runs that same bounded wait in a one-warp kernel on a barrier that nothing
+ * arrives on (arrive = 0: it must give up after about 2 s and write
+ * QPADL_ETIMEOUT's device code 1 to *status_dev) or on one completed first
+ * (arrive != 0: it must return at once and write 0).  *waited_ns_dev gets
+ * the time the wait took.  Both pointers are device memory (int32, uint64).
+ * Asynchronous on stream; QPADL_EINVAL for NULL pointers. */
+int qpadl_selftest_bounded_wait(int arrive, int32_t *status_dev, uint64_t *waited_ns_dev,
+                                qpadl_stream_t stream);
+
+/* ======================================================================
  * Serving: a continuous-batching request loop over several resident
  * databases (the paper's server answering q-bar queries per database,
  * Sec. 5.2, run as a long-lived service).  Requests arrive from any host

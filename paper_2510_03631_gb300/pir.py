@@ -103,6 +103,7 @@ _SIGS = {
     "qpadl_chor_get_option": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "qpadl_chor_destroy": ([_P], ctypes.c_int),
     "qpadl_pir_autotune": ([_P, ctypes.c_uint32, _P, _P], ctypes.c_int),
+    "qpadl_selftest_bounded_wait": ([ctypes.c_int, _P, _P, _P], ctypes.c_int),
     "qpadl_server_create": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
     "qpadl_server_add_db": ([_P, _P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "qpadl_server_start": ([_P], ctypes.c_int),
@@ -691,3 +692,15 @@ def qpadl_server_replay(srv: Server, arrival_s, db_ids, queries, answers=None, w
                                       ctypes.c_void_p(tm.ctypes.data) if with_times else None),
            "qpadl_server_replay")
     return (lat, st, tm) if with_times else (lat, st)
+
+
+def qpadl_selftest_bounded_wait(arrive: bool, stream=None):
+    """Run the library's bounded mbarrier wait on a barrier nothing arrives on (arrive=False)
+    or on a completed one; returns (device status code, nanoseconds waited)."""
+    st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    ns = torch.zeros(1, dtype=torch.int64, device="cuda")
+    _check(load().qpadl_selftest_bounded_wait(1 if arrive else 0, ctypes.c_void_p(st.data_ptr()),
+                                              ctypes.c_void_p(ns.data_ptr()), _stream(stream)),
+           "qpadl_selftest_bounded_wait")
+    torch.cuda.synchronize()
+    return int(st.item()), int(ns.item())
