@@ -96,8 +96,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     using Cfg = GemmCfg<BN>;
     constexpr int kGemmStages = Cfg::kStages;
     constexpr int LPV = Epi::kLimbs;   // limb rows per vector
-    static_assert(LPV == 4 || (LPV == 1 && !PLANED && BN <= 64), "one-limb vectors: plain mode, BN <= 64");
+    static_assert(LPV == 4 || (LPV == 1 && !PLANED), "one-limb vectors: plain mode");
     constexpr int QPT = BN / LPV;      // vectors per tile
+    // one-limb tiles wider than 64 keep their running sums in TMEM, reduced mod p after every
+    // chunk (a residue below p plus one 512-deep chunk stays below 2^24, so fp32 stays exact)
+    constexpr bool TMEMSUM = LPV == 1 && BN > 64;
+    constexpr int RUN = TMEMSUM ? 1 : QPT;   // running sums kept in registers
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + kGemmStages * Cfg::kStageBytes);
@@ -208,7 +212,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                         for (int k = 0; k < kBK / 16; ++k) {
                             // advance the start address by 16 elements (32 bytes) inside the swizzle atom
                             umma_f16(d_tmem, adesc + 2u * k, bdesc + 2u * k, idesc,
-                                     (kb % kChunkKB != 0 || k != 0) ? 1u : 0u);
+                                     ((TMEMSUM && kb >= 2u * kChunkKB) || kb % kChunkKB != 0 || k != 0) ? 1u
+                                                                                                         : 0u);
                         }
                     }
                     umma_commit(&empty[st]);
@@ -233,9 +238,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         for (uint32_t t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
             const uint32_t m0 = (t / n_tiles) * kBM;
             const uint32_t v0 = (t % n_tiles) * QPT;
-            uint32_t run[QPT];
+            uint32_t run[RUN];
 #pragma unroll
-            for (int q = 0; q < QPT; ++q) run[q] = 0u;
+            for (int q = 0; q < RUN; ++q) run[q] = 0u;
             const uint32_t nchunks = (KB + kChunkKB - 1) / kChunkKB;
             for (uint32_t c = 0; c < nchunks; ++c, ++ci) {
                 const uint32_t buf = ci & 1u;
@@ -244,7 +249,62 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                if constexpr (PLANED) {
+                if constexpr (TMEMSUM) {
+                    const float pf = static_cast<float>(epi.p), inv = 1.0f / pf;
+                    const uint32_t cur = tmem_base + lane_addr + buf * BN;
+                    if (c + 1 < nchunks) {
+                        // reduce this buffer's running sums mod p in place
+#pragma unroll 1
+                        for (int j = 0; j < BN / 32; ++j) {
+                            uint32_t v[32];
+                            tmem_ld32(cur + 32u * j, v);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int q = 0; q < 32; ++q) {
+                                const float x = __uint_as_float(v[q]);
+                                float r = fmaf(-floorf(x * inv), pf, x);   // exact: integers below 2^24
+                                r = r < 0.f ? r + pf : (r >= pf ? r - pf : r);
+                                v[q] = __float_as_uint(r);
+                            }
+                            tmem_st32(cur + 32u * j, v);
+                        }
+                        tmem_wait_st();
+                        if (c + 2 < nchunks) {
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+                        }
+                        // the second-to-last chunk's buffer is held for the final combine
+                        continue;
+                    }
+                    // last chunk: its buffer plus the other buffer's residue, mod p, to the output
+                    const uint32_t oth = tmem_base + lane_addr + (buf ^ 1u) * BN;
+                    const uint32_t row = m0 + quarter * 32u + static_cast<uint32_t>(lane);
+                    const int32_t ip = epi.p;
+#pragma unroll 1
+                    for (int j = 0; j < BN / 32; ++j) {
+                        uint32_t v[32], w[32];
+                        tmem_ld32(cur + 32u * j, v);
+                        if (nchunks >= 2) tmem_ld32(oth + 32u * j, w);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            int32_t x = __float2int_rn(__uint_as_float(v[q]));
+                            if (nchunks >= 2) x += __float2int_rn(__uint_as_float(w[q]));
+                            int32_t r = x % ip;
+                            if (r < 0) r += ip;
+                            const uint32_t vi = v0 + 32u * j + q;
+                            if (row < M && vi < NV) epi.put(row, vi, static_cast<uint32_t>(r), 0u);
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        mbar_arrive(&acc_empty[buf]);
+                        if (nchunks >= 2) mbar_arrive(&acc_empty[buf ^ 1u]);
+                    }
+                    continue;
+                } else if constexpr (PLANED) {
                     // active shifts of this chunk's plane; column (3 - t)*QPT + q holds shift t of vector q
                     const uint32_t u = c / plane_chunks;
                     for (uint32_t t = u; t < 4; ++t) {
@@ -301,6 +361,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 if (lane == 0) mbar_arrive(&acc_empty[buf]);
             }
             if (failed) break;
+            if constexpr (TMEMSUM) continue;   // the last chunk already wrote the tile
             const uint32_t row = m0 + quarter * 32u + static_cast<uint32_t>(lane);
             if (row < M) {
                 // groups of up to 16 outputs: all their loads first, then all their stores
@@ -531,7 +592,8 @@ cudaError_t prepare_limb_gemm_kernels() {
     if ((e = set_planed_attrs<QueryEpi>()) != cudaSuccess) return e;
     if ((e = set_planed_attrs<RecoverEpi>()) != cudaSuccess) return e;
     if ((e = set_gemm_attr<32, ModPEpi, false>()) != cudaSuccess) return e;
-    return set_gemm_attr<64, ModPEpi, false>();
+    if ((e = set_gemm_attr<64, ModPEpi, false>()) != cudaSuccess) return e;
+    return set_gemm_attr<256, ModPEpi, false>();
 }
 
 int limb_gemm_bn_for(uint32_t nv) {
@@ -562,6 +624,7 @@ static cudaError_t launch_epi(int bn, const CUtensorMap &a_map, const CUtensorMa
         switch (bn) {
             case 32: launch_one<32, Epi, false>(grid1, a_map, b_map, epi, M, NV, KB, 1, status, stream); break;
             case 64: launch_one<64, Epi, false>(grid1, a_map, b_map, epi, M, NV, KB, 1, status, stream); break;
+            case 256: launch_one<256, Epi, false>(grid1, a_map, b_map, epi, M, NV, KB, 1, status, stream); break;
             default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();

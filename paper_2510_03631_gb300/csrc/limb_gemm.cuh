@@ -35,7 +35,8 @@ cudaError_t launch_limb_gemm_recover(int bn, const CUtensorMap &a_map, const CUt
                                      uint32_t plane_chunks, int num_sms, int *status, cudaStream_t stream);
 
 // Goldberg Response: out = D * X mod p with one centred fp16 row per vector
-// (b_map box 64 x bn rows, bn 32 or 64), through ModPEpi.
+// (b_map box 64 x bn rows; bn 32 or 64 keep the running sums in registers,
+// 256 keeps them in TMEM, reduced mod p after every chunk), through ModPEpi.
 cudaError_t launch_limb_gemm_modp(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, const ModPEpi &epi,
                                   uint32_t M, uint32_t NV, uint64_t K, int num_sms, int *status, cudaStream_t stream);
 cudaError_t launch_centred_rows(const uint32_t *Q, uint32_t B, uint64_t C, uint32_t p, __half *L, uint64_t pitch,

@@ -1204,7 +1204,8 @@ int qpadl_goldberg_answer_batch(qpadl_goldberg *h, const uint32_t *Q_dev, uint32
     for (uint32_t b0 = 0; b0 < B; b0 += kChunk) {
         const uint32_t Bc = std::min(B - b0, kChunk);
         QPADL_CU(launch_centred_rows(Q_dev + (uint64_t)b0 * C, Bc, C, h->p, db->limbs, db->pitch, db->num_sms, s));
-        const int bn = Bc <= 32 ? 32 : 64;
+        // up to 64 queries: running sums in registers; more: 256-wide tiles with the sums in TMEM
+        const int bn = Bc <= 32 ? 32 : (Bc <= 64 ? 64 : 256);
         CUtensorMap b_map;
         if (!encode_2d(&b_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, db->limbs, C, Bc, db->pitch * 2, kLimbBoxK,
                        static_cast<uint32_t>(bn), CU_TENSOR_MAP_SWIZZLE_128B))

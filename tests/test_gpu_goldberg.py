@@ -38,7 +38,8 @@ def _answer(h, Q_np, gemm_min=None, u8max=None):
 
 
 CASES = [(300, 1000, 257, 1), (257, 513, 251, 4), (1000, 2048, 257, 5), (700, 4096 + 48, 101, 33),
-         (129, 300, 257, 64), (2000, 1024, 257, 200), (384, 512, 2, 7), (50, 777, 257, 1100)]
+         (129, 300, 257, 64), (2000, 1024, 257, 200), (384, 512, 2, 7), (50, 777, 257, 1100),
+         (640, 512, 257, 65), (333, 1500, 101, 300)]
 
 
 @pytest.mark.parametrize("R,C,p,B", CASES)
@@ -52,12 +53,13 @@ def test_goldberg_matches_oracle(cuda, R, C, p, B, gemm_min, u8max):
     h.close()
 
 
-@pytest.mark.parametrize("gemm_min,u8max", [(1, 32), (1, 0), (1 << 30, 32)])
+@pytest.mark.parametrize("gemm_min,u8max,B", [(1, 32, 6), (1, 0, 6), (1 << 30, 32, 6), (1, 0, 70)])
 @pytest.mark.parametrize("qval", [256, 128, 129])
-def test_exact_sum_bounds(cuda, gemm_min, u8max, qval):
+def test_exact_sum_bounds(cuda, gemm_min, u8max, B, qval):
     # the largest allowed record count with every byte 255: the unsigned sum of the streaming
-    # path and the centred sum of the GEMM both stay exact
-    R, C, p, B = 128, 65792, 257, 6
+    # path, the four-limb sums of the u8 GEMM, the centred register sums (6 queries) and the
+    # TMEM-resident residues reduced mod p after every chunk (70 queries) all stay exact
+    R, C, p = 128, 65792, 257
     D = np.full((R, C), 255, dtype=np.uint8)
     D[::3, ::7] = 0
     Q = np.full((B, C), qval, dtype=np.uint32)
