@@ -355,10 +355,18 @@ int answer_tensor(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, cu
     if (db->u8_ok && B <= db->u8_max_batch && 4 * B <= 128) return answer_tensor_u8(db, Q, B, ans, stream);
     int rc = ensure_tensor_copy(db, stream);
     if (rc != QPADL_OK) return rc;
-    rc = ensure_limbs(db, 8ull * B * db->pitch);
+    // chunks of at most 4096 queries bound the limb scratch (8 bytes per query per column)
+    constexpr uint32_t kChunk = 4096;
+    rc = ensure_limbs(db, 8ull * std::min(B, kChunk) * db->pitch);
     if (rc != QPADL_OK) return rc;
-    QPADL_CU(launch_vec_limbs(Q, db->prm.cols, B, db->prm.cols, db->limbs, db->pitch, db->num_sms, stream));
-    return run_limb_gemm(db, B, ans, 1, db->prm.rows, stream);
+    const uint64_t C = db->prm.cols, R = db->prm.rows;
+    for (uint32_t b0 = 0; b0 < B; b0 += kChunk) {
+        const uint32_t Bc = std::min(B - b0, kChunk);
+        QPADL_CU(launch_vec_limbs(Q + (uint64_t)b0 * C, C, Bc, C, db->limbs, db->pitch, db->num_sms, stream));
+        rc = run_limb_gemm(db, Bc, ans + (uint64_t)b0 * R, 1, R, stream);
+        if (rc != QPADL_OK) return rc;
+    }
+    return QPADL_OK;
 }
 
 }  // namespace
@@ -591,7 +599,8 @@ int qpadl_pir_reserve(qpadl_db *db, uint32_t max_batch, qpadl_stream_t stream) {
             int rc = ensure_blocked(db, s);
             if (rc != QPADL_OK) return rc;
         }
-        int rc = ensure_limbs(db, 8ull * max_batch * db->pitch);
+        // the batched paths work in chunks of at most 4096 queries
+        int rc = ensure_limbs(db, 8ull * std::min<uint32_t>(max_batch, 4096u) * db->pitch);
         if (rc != QPADL_OK) return rc;
     }
     QPADL_CU(cudaStreamSynchronize(s));

@@ -150,7 +150,8 @@ def test_answer_batch_both_paths(B):
     assert np.array_equal(_answers(db, Q), exp)
 
 
-@pytest.mark.parametrize("R,C,B", [(129, 1537, 40), (128, 64, 3), (1, 8, 5), (513, 4100, 70), (1024, 1024, 256)])
+@pytest.mark.parametrize("R,C,B", [(129, 1537, 40), (128, 64, 3), (1, 8, 5), (513, 4100, 70), (1024, 1024, 256),
+                                   (64, 256, 4096 + 300)])   # the last one crosses the 4096-query chunk
 def test_answer_batch_tensor_ragged(R, C, B):
     prm, D, db = _setup(R, C, seed=R)
     Q = inputs.uniform_u32(B * C, seed=C, tag=inputs.TAG_MISC).reshape(B, C)
