@@ -480,10 +480,14 @@ def run_ours(args):
     tune = pir.qpadl_pir_autotune(db, 1024)
     raw = tune["stream_raw"] == 1
 
+    # single-GPU characterisations (batch sweep, client batches, serving, Chor, Goldberg) run
+    # at N = 1 only: at N > 1 every rank is an independent replica of the timed step
+    extras = world == 1 and not args.quick
+
     # ---- client side of the offline/hint workload: 1024 Queries and 1024 Recovers in one
     # batch each through the tensor-core client context (checked end to end)
     client = None
-    if not args.quick:
+    if extras:
         BC = 1024
         S_c = inputs.secrets(BC, n, seed=seed + 60)
         cols_c = inputs.target_columns(BC, C, seed=seed + 62)
@@ -601,7 +605,7 @@ def run_ours(args):
     # ---- batched Response sweep vs one-at-a-time on the same database
     one_qps = 1e3 / resp_ms_avg
     sweep = {}
-    if not args.quick:
+    if extras:
         for B in (1, 8, 32, 128, 256, 1024):
             QB = torch.randint(-2**31, 2**31 - 1, (B * C,), dtype=torch.int32, device="cuda")
             AB = torch.empty(B * R, dtype=torch.int32, device="cuda")
@@ -654,7 +658,7 @@ def run_ours(args):
 
     serving = None
     chor = goldberg = None
-    if not args.quick:
+    if extras:
         db.close()
         del D
         torch.cuda.empty_cache()
@@ -712,7 +716,7 @@ def run_ours(args):
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
-    if args.quick:
+    if not extras:
         db.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
