@@ -4,7 +4,13 @@
 // what the element needs from memory and put() finishes it, so a caller
 // with many elements per thread can issue all their loads before any store
 // (a store through one pointer could otherwise alias the next load, which
-// serialises every element behind a full memory round trip).
+// serialises every element behind a full memory round trip).  prefetch()
+// pulls what the epilogue of one output tile will read into L2 ahead of it
+// (rows i0 .. i0+127 of vectors b0 .. b0+nb-1).
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 #pragma once
 #include <cstdint>
 
@@ -18,6 +24,7 @@ struct StoreEpi {
     static constexpr int kLimbs = 4;
     uint32_t *out;
     uint64_t ld_m, ld_b;
+    __device__ __forceinline__ void prefetch(uint64_t, uint32_t, uint32_t) const {}
     __device__ __forceinline__ uint32_t pre(uint64_t, uint32_t) const { return 0u; }
     __device__ __forceinline__ void put(uint64_t i, uint32_t b, uint32_t dot, uint32_t) const {
         out[i * ld_m + (uint64_t)b * ld_b] = dot;
@@ -35,6 +42,10 @@ struct QueryEpi {
     uint32_t delta;
     uint32_t *q;             // output, vector b at q + b * q_ld
     uint64_t q_ld;
+    __device__ __forceinline__ void prefetch(uint64_t j0, uint32_t b0, uint32_t nb) const {
+        for (uint32_t b = b0; b < b0 + nb; ++b)
+            for (uint32_t l = 0; l < 4; ++l) prefetch_l2(e + b * e_ld + j0 + 32u * l);   // 128 rows x 4 B
+    }
     // e_b[j] + Delta [j == col_b]
     __device__ __forceinline__ uint32_t pre(uint64_t j, uint32_t b) const {
         const uint64_t target = cols ? cols[b] : col;
@@ -57,6 +68,10 @@ struct RecoverEpi {
     uint32_t shift;          // 32 - log2 p
     uint8_t *out;            // digits of vector b at out + b * out_ld
     uint64_t out_ld;
+    __device__ __forceinline__ void prefetch(uint64_t i0, uint32_t b0, uint32_t nb) const {
+        for (uint32_t b = b0; b < b0 + nb; ++b)
+            for (uint32_t l = 0; l < 4; ++l) prefetch_l2(ans + b * ans_ld + i0 + 32u * l);
+    }
     // ans_b[i]
     __device__ __forceinline__ uint32_t pre(uint64_t i, uint32_t b) const { return ans[b * ans_ld + i]; }
     __device__ __forceinline__ void put(uint64_t i, uint32_t b, uint32_t dot, uint32_t a) const {
@@ -76,6 +91,7 @@ struct ModPEpi {
     uint32_t *out;
     uint64_t ld_m, ld_b;
     int32_t p;
+    __device__ __forceinline__ void prefetch(uint64_t, uint32_t, uint32_t) const {}
     __device__ __forceinline__ uint32_t pre(uint64_t, uint32_t) const { return 0u; }
     __device__ __forceinline__ void put(uint64_t i, uint32_t b, uint32_t dot, uint32_t) const {
         int32_t r = static_cast<int32_t>(dot) % p;

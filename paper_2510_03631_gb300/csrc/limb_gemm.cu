@@ -151,6 +151,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             for (uint32_t t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
                 const int32_t m0 = static_cast<int32_t>((t / n_tiles) * kBM);
                 const int32_t n0 = static_cast<int32_t>((t % n_tiles) * BN);
+                {
+                    // what this tile's epilogue will read (Query noise, Recover answers) into L2 now
+                    const uint32_t v0 = (t % n_tiles) * QPT;
+                    const uint32_t nv = v0 < NV ? (NV - v0 < (uint32_t)QPT ? NV - v0 : (uint32_t)QPT) : 0u;
+                    if (static_cast<uint32_t>(m0) + kBM <= M) epi.prefetch(static_cast<uint64_t>(m0), v0, nv);
+                }
                 for (uint32_t kb = 0; kb < KB; ++kb, ++it) {
                     const uint32_t st = it % kGemmStages;
                     const uint32_t ph = (it / kGemmStages) & 1u;
