@@ -289,6 +289,18 @@ int qpadl_pir_recover_batch(const qpadl_params *prm, const uint32_t *ans_dev,
                             const uint32_t *H_dev, const uint32_t *S_dev, uint32_t B,
                             uint8_t *out_dev, qpadl_stream_t stream);
 
+/*
+ * Status of the handle-free single-vector Query and Recover kernels.  For
+ * n in {512, 1024, 2048} (with 16-byte aligned matrix and secret) those two
+ * calls stream the matrix through shared memory behind barrier waits that
+ * give up after a bounded time; a wait that gives up leaves that call's
+ * output incomplete and records QPADL_ETIMEOUT in one status word per
+ * device.  This call waits for the current device (cudaDeviceSynchronize),
+ * returns the word (QPADL_OK or QPADL_ETIMEOUT; QPADL_ECUDA if the device
+ * cannot be read) and clears it.
+ */
+int qpadl_pir_client_status(void);
+
 /* ======================================================================
  * Client context: batched Query and Recover on the tensor cores
  * (Def. 1 Client.Query and Client.BlockReconst for many secrets at once).

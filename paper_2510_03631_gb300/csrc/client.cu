@@ -10,14 +10,19 @@
 // Single queries are HBM-bound matrix-vector products: one warp per row of A
 // or H; for n in {512, 1024, 2048} each lane keeps its slice of the secret
 // in registers and issues all of a row's 16-byte loads (two rows at a time)
-// before using them; other n use a shared-memory copy of the secret.
+// before using them, and the kernel overlaps its start with the end of the
+// kernel before it (programmatic dependent launch); other n use a
+// shared-memory copy of the secret.
 // Batches are u32 GEMMs (Y = X * W^T over Z_{2^32}) on the CUDA cores with
 // 8x8 register blocking.
 #include <cstdint>
+#include <mutex>
+
 #include <cuda_runtime.h>
 
 #include "client.cuh"
 #include "epilogues.cuh"
+#include "ptx.cuh"
 
 namespace qpadl {
 
@@ -61,71 +66,200 @@ __global__ void matvec_kernel(const uint32_t *__restrict__ X, uint64_t rows, uin
     }
 }
 
-// Same product for n = 128 * NK: warp w owns rows [w rows / W, (w+1) rows / W).
+// Same product for n = 128 * NK with the rows of X streamed through shared
+// memory by bulk copies: CTA b owns the row band [b rows / G, (b+1) rows / G);
+// one lane of warp 0 copies it in stages of 8 consecutive rows (one copy per
+// stage) into a ring of kStages buffers; consumer warp c takes row c of every
+// stage (band rows c, c + 8, c + 16, ...).  Each lane keeps its slice of the
+// vector in registers.  A consumer takes its rows in runs of 32: lane t
+// gathers the epilogue input of the run's row t when the run begins and
+// keeps that row's dot product, so a run ends in one epilogue per lane
+// instead of a memory round trip per row.
+// Launched with programmatic dependent launch: before griddepcontrol.wait the
+// kernel only lets its successor be scheduled and pulls its first stages of X
+// into L2 (a hint that moves nothing into the CTA), so it never consumes data
+// that the preceding kernel may still be writing.  Every barrier wait is
+// bounded; a wait that gives up records kDevTimeout in *status.
+constexpr int kMvRows = 8;   // rows per stage = consumer warps
+constexpr int kMvThreads = 32 * (1 + kMvRows);
+template <int NK>
+struct MvCfg {
+    static constexpr uint32_t kRowBytes = 512u * NK;
+    static constexpr uint32_t kStageBytes = kMvRows * kRowBytes;
+    static constexpr int kStages = (196608u / kStageBytes) < 12u ? static_cast<int>(196608u / kStageBytes) : 12;
+    static constexpr uint32_t kSmemBytes = kStages * kStageBytes + 2 * kStages * 8 + 16 + 128;   // + alignment slack
+};
+
 template <int NK, class Epi>
-__global__ void __launch_bounds__(256) matvec_reg_kernel(const uint32_t *__restrict__ X, uint64_t rows,
-                                                         const uint32_t *__restrict__ w, Epi epi) {
+__global__ void __launch_bounds__(kMvThreads, 1)
+    matvec_tma_kernel(const uint32_t *__restrict__ X, uint64_t rows, const uint32_t *__restrict__ w, Epi epi,
+                      int *__restrict__ status) {
+    using Cfg = MvCfg<NK>;
+    constexpr int ST = Cfg::kStages;
     constexpr uint32_t n = 128 * NK;
+    extern __shared__ uint8_t mv_smem_raw[];
+    uint8_t *buf = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(mv_smem_raw) + 127) & ~uintptr_t(127));
+    uint64_t *full = reinterpret_cast<uint64_t *>(buf + ST * Cfg::kStageBytes);
+    uint64_t *empty = full + ST;
+    volatile int *abort = reinterpret_cast<volatile int *>(empty + ST);
+    const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    const uint64_t r0 = (uint64_t)blockIdx.x * rows / gridDim.x;
+    const uint64_t r1 = (uint64_t)(blockIdx.x + 1) * rows / gridDim.x;
+    const uint32_t nst = static_cast<uint32_t>((r1 - r0 + kMvRows - 1) / kMvRows);
+    auto stage_bytes = [&](uint32_t t) {
+        const uint64_t g0 = r0 + (uint64_t)t * kMvRows;
+        const uint64_t nr = r1 - g0 < (uint64_t)kMvRows ? r1 - g0 : (uint64_t)kMvRows;
+        return static_cast<uint32_t>(nr * Cfg::kRowBytes);
+    };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kMvRows);
+        }
+        *abort = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+        // ---------------- producer
+        if (lane == 0) {
+            for (uint32_t t = 0; t < nst && t < (uint32_t)ST; ++t)
+                bulk_prefetch_l2(X + (r0 + (uint64_t)t * kMvRows) * n, stage_bytes(t));
+            griddep_launch_dependents();
+            griddep_wait();
+            bool ok = true;
+            uint32_t t = 0;
+            for (; t < nst; ++t) {
+                const uint32_t st = t % ST;
+                if (!mbar_wait(&empty[st], ((t / ST) & 1u) ^ 1u, abort)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t bytes = stage_bytes(t);
+                mbar_arrive_expect_tx(&full[st], bytes);
+                bulk_load(buf + st * Cfg::kStageBytes, X + (r0 + (uint64_t)t * kMvRows) * n, bytes, &full[st]);
+            }
+            // never leave while copies issued here are still landing
+            const uint32_t inflight = t < (uint32_t)ST ? t : (uint32_t)ST;
+            for (uint32_t j = t - inflight; j < t; ++j)
+                if (!mbar_drain(&full[j % ST], (j / ST) & 1u)) ok = false;
+            if (!ok && status) *status = kDevTimeout;
+        }
+        return;
+    }
+
+    // ---------------- consumers
+    griddep_wait();
+    const int c = warp - 1;
     uint4 sw[NK];
 #pragma unroll
     for (int m = 0; m < NK; ++m) sw[m] = *reinterpret_cast<const uint4 *>(w + 4 * lane + 128 * m);
-    const uint64_t W = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    const uint64_t wid = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const uint64_t r0 = wid * rows / W, r1 = (wid + 1) * rows / W;
-    auto dot = [&](const uint4 (&a)[NK]) {
-        uint32_t acc = 0;
+    const uint64_t my0 = r0 + c;   // this warp's rows: my0 + 8 t
+    const uint32_t my_n = r1 > my0 ? static_cast<uint32_t>((r1 - my0 + kMvRows - 1) / kMvRows) : 0u;
+    uint32_t pv = 0, mine = 0;
+    for (uint32_t t = 0; t < nst; ++t) {
+        const uint32_t k = t & 31u;
+        if (k == 0) {
+            if (t && t - 32 + lane < my_n) epi.put(my0 + (uint64_t)kMvRows * (t - 32 + lane), 0u, mine, pv);
+            pv = t + lane < my_n ? epi.pre(my0 + (uint64_t)kMvRows * (t + lane), 0u) : 0u;
+        }
+        const uint32_t st = t % ST;
+        if (!mbar_wait(&full[st], (t / ST) & 1u, abort)) {
+            if (status) *status = kDevTimeout;
+            return;
+        }
+        const bool have = t < my_n;   // warp-uniform
+        uint4 a[NK];
+        if (have) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(buf + st * Cfg::kStageBytes + c * Cfg::kRowBytes) + lane;
 #pragma unroll
-        for (int m = 0; m < NK; ++m) acc += a[m].x * sw[m].x + a[m].y * sw[m].y + a[m].z * sw[m].z + a[m].w * sw[m].w;
+            for (int m = 0; m < NK; ++m) a[m] = src[32 * m];
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+        if (have) {
+            uint32_t acc = 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        return acc;
-    };
-    uint64_t i = r0;
-    for (; i + 1 < r1; i += 2) {
-        const uint4 *x0 = reinterpret_cast<const uint4 *>(X + i * n) + lane;
-        const uint4 *x1 = reinterpret_cast<const uint4 *>(X + (i + 1) * n) + lane;
-        uint4 a[NK], b[NK];
+            for (int m = 0; m < NK; ++m)
+                acc += a[m].x * sw[m].x + a[m].y * sw[m].y + a[m].z * sw[m].z + a[m].w * sw[m].w;
 #pragma unroll
-        for (int m = 0; m < NK; ++m) a[m] = __ldg(x0 + 32 * m);
-#pragma unroll
-        for (int m = 0; m < NK; ++m) b[m] = __ldg(x1 + 32 * m);
-        const uint32_t da = dot(a), db = dot(b);
-        if (lane == 0) {
-            epi(i, 0u, da);
-            epi(i + 1, 0u, db);
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == static_cast<int>(k)) mine = acc;
         }
     }
-    if (i < r1) {
-        const uint4 *x0 = reinterpret_cast<const uint4 *>(X + i * n) + lane;
-        uint4 a[NK];
-#pragma unroll
-        for (int m = 0; m < NK; ++m) a[m] = __ldg(x0 + 32 * m);
-        const uint32_t da = dot(a);
-        if (lane == 0) epi(i, 0u, da);
+    if (nst) {
+        const uint32_t t0 = ((nst - 1) / 32u) * 32u;   // the last run
+        if (t0 + lane < my_n) epi.put(my0 + (uint64_t)kMvRows * (t0 + lane), 0u, mine, pv);
     }
+}
+
+// Status word of the handle-free client kernels (one per process and
+// device; read and cleared by client_status_take).
+static __device__ int g_client_status;
+
+template <class Epi>
+static cudaError_t set_matvec_attrs() {
+    cudaError_t e = cudaFuncSetAttribute(matvec_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 4);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(matvec_tma_kernel<4, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 MvCfg<4>::kSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(matvec_tma_kernel<8, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 MvCfg<8>::kSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(matvec_tma_kernel<16, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 MvCfg<16>::kSmemBytes);
+    return e;
+}
+
+// Once per device, with that device current: kernel attributes and the
+// device address of the status word.  Returns nullptr on failure.
+static std::mutex g_client_mu;
+static int *g_client_status_ptr[64];
+static int *client_status_word() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> g(g_client_mu);
+    if (!g_client_status_ptr[dev]) {
+        void *p = nullptr;
+        if (set_matvec_attrs<QueryEpi>() != cudaSuccess || set_matvec_attrs<RecoverEpi>() != cudaSuccess ||
+            cudaGetSymbolAddress(&p, g_client_status) != cudaSuccess)
+            return nullptr;
+        g_client_status_ptr[dev] = static_cast<int *>(p);
+    }
+    return g_client_status_ptr[dev];
+}
+
+template <int NK, class Epi>
+static cudaError_t launch_matvec_tma(const uint32_t *X, uint64_t rows, const uint32_t *w, const Epi &epi,
+                                     int num_sms, int *status, cudaStream_t stream) {
+    const uint64_t want = (rows + kMvRows - 1) / kMvRows;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(want < (uint64_t)num_sms ? want : (uint64_t)num_sms));
+    cfg.blockDim = dim3(kMvThreads);
+    cfg.dynamicSmemBytes = MvCfg<NK>::kSmemBytes;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, matvec_tma_kernel<NK, Epi>, X, rows, w, epi, status);
 }
 
 template <class Epi>
 static cudaError_t launch_matvec(const uint32_t *X, uint64_t rows, uint32_t n, const uint32_t *w, const Epi &epi,
                                  int num_sms, cudaStream_t stream) {
     const bool aligned = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(w)) & 15u) == 0;
-    if (aligned && (n == 512 || n == 1024 || n == 2048)) {
-        // one resident wave: blocks per SM from the kernel's occupancy
-        auto launch = [&](auto kernel) -> cudaError_t {
-            int occ = 0;
-            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 256, 0);
-            if (e != cudaSuccess) return e;
-            const uint64_t blocks = (uint64_t)num_sms * (occ > 0 ? occ : 1);
-            if (rows < 8 * blocks) return cudaErrorNotReady;   // too few rows: generic kernel
-            kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(X, rows, w, epi);
-            return cudaGetLastError();
-        };
-        cudaError_t e = cudaErrorNotReady;
-        if (n == 512) e = launch(matvec_reg_kernel<4, Epi>);
-        else if (n == 1024) e = launch(matvec_reg_kernel<8, Epi>);
-        else e = launch(matvec_reg_kernel<16, Epi>);
-        if (e != cudaErrorNotReady) return e;
+    if (aligned && rows > 0 && (n == 512 || n == 1024 || n == 2048)) {
+        int *status = client_status_word();
+        if (!status) return cudaErrorUnknown;
+        if (n == 512) return launch_matvec_tma<4>(X, rows, w, epi, num_sms, status, stream);
+        if (n == 1024) return launch_matvec_tma<8>(X, rows, w, epi, num_sms, status, stream);
+        return launch_matvec_tma<16>(X, rows, w, epi, num_sms, status, stream);
     }
     const uint64_t want = (rows + 7) / 8;
     const uint64_t cap = (uint64_t)num_sms * 8;
@@ -230,11 +364,17 @@ cudaError_t launch_recover_batch(const uint32_t *ans, const uint32_t *H, uint64_
     return cudaGetLastError();
 }
 
-cudaError_t prepare_client_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(matvec_kernel<QueryEpi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         16384 * 4);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(matvec_kernel<RecoverEpi>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 4);
+cudaError_t prepare_client_kernels() { return client_status_word() ? cudaSuccess : cudaErrorUnknown; }
+
+// Waits for the current device, then returns and clears its status word.
+cudaError_t client_status_take(int *out) {
+    *out = 0;
+    int *p = client_status_word();
+    if (!p) return cudaErrorUnknown;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(out, p, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && *out) e = cudaMemset(p, 0, sizeof(int));
+    return e;
 }
 
 }  // namespace qpadl

@@ -6,6 +6,7 @@
 namespace qpadl {
 
 cudaError_t prepare_client_kernels();
+cudaError_t client_status_take(int *out);
 cudaError_t launch_gen_a(uint64_t seed, uint64_t C, uint32_t n, uint32_t *A, int num_sms, cudaStream_t stream);
 cudaError_t launch_query(const uint32_t *A, uint64_t C, uint32_t n, const uint32_t *s, const int32_t *e,
                          uint64_t col, uint32_t delta, uint32_t *q, int num_sms, cudaStream_t stream);

@@ -77,6 +77,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
     }
 }
 
+// Wait for a phase without the CTA's abort flag: used to let copies this
+// thread issued land before it exits.  Gives up after QPADL_WAIT_NS.
+__device__ __forceinline__ bool mbar_drain(uint64_t *bar, uint32_t parity) {
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_test(bar, parity)) {
+        if (global_ns() - t0 > QPADL_WAIT_NS) return false;
+    }
+    return true;
+}
+
 // One lane of the (fully active) warp gets true.
 __device__ __forceinline__ bool elect_one() {
     uint32_t pred = 0;
@@ -150,6 +161,13 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
             smem_addr(dst)),
         "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
+}
+
+// Pull `bytes` (a multiple of 16, 16-byte aligned) of global memory into L2
+// ahead of its use (no shared memory, no barrier).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(src)), "r"(bytes)
+                 : "memory");
 }
 
 // ------------------------------------------------------------------ tcgen05

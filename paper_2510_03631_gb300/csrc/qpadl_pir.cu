@@ -645,6 +645,12 @@ int qpadl_pir_query(const qpadl_params *prm, const uint32_t *A_dev, const uint32
     return QPADL_OK;
 }
 
+int qpadl_pir_client_status(void) {
+    int w = 0;
+    if (client_status_take(&w) != cudaSuccess) return QPADL_ECUDA;
+    return w ? QPADL_ETIMEOUT : QPADL_OK;
+}
+
 int qpadl_pir_query_batch(const qpadl_params *prm, const uint32_t *A_dev, const uint32_t *S_dev,
                           const int32_t *E_dev, const uint32_t *cols_dev, uint32_t B, uint32_t *Q_dev,
                           qpadl_stream_t stream) {

@@ -113,6 +113,7 @@ _SIGS = {
     "qpadl_server_destroy": ([_P], ctypes.c_int),
     "qpadl_server_replay": ([_P, ctypes.c_uint64, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "qpadl_pir_recover_batch": ([_P, _P, _P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
+    "qpadl_pir_client_status": ([], ctypes.c_int),
 }
 
 
@@ -332,6 +333,12 @@ def qpadl_pir_recover_batch(prm: qpadl_params, ans: torch.Tensor, H: torch.Tenso
         _dev(S, torch.int32, B * n, "S"), B, _dev(out, torch.uint8, B * R, "out"), _stream(stream)),
         "qpadl_pir_recover_batch")
     return out
+
+
+def qpadl_pir_client_status() -> int:
+    """Waits for the current device; returns and clears the status word of the
+    handle-free Query/Recover kernels (QPADL_OK or QPADL_ETIMEOUT)."""
+    return int(load().qpadl_pir_client_status())
 
 
 class Client:

@@ -244,9 +244,11 @@ def test_query_single_and_batch(C, n):
 
 
 @pytest.mark.parametrize("C,n", [(1000, 128), (777, 132), (4096, 1024), (1, 256), (300, 4000), (9000, 512),
-                                 (5000, 2048), (4867, 1024)])
+                                 (5000, 2048), (4867, 1024), (80000, 1024), (80001, 2048)])
 def test_query_and_recover_matvec_shapes(C, n):
-    # n in {512, 1024, 2048} with enough rows takes the register-resident kernel; others the generic one
+    # n in {512, 1024, 2048} with enough rows takes the register-resident kernel; others the generic one.
+    # The last two give each warp of the register kernel more than one run of 32 rows (one or two
+    # resident blocks of 8 warps per SM): the runs' gathered epilogue inputs and ragged last run.
     prm = pir.params(C, C, n, seed=n + C)
     A = torch.empty(C * n, dtype=torch.int32, device="cuda")
     pir.qpadl_pir_gen_a(prm, A)
@@ -264,6 +266,7 @@ def test_query_and_recover_matvec_shapes(C, n):
     pir.qpadl_pir_recover(prm, pir.from_u32(ans_o), A, pir.from_u32(s_o), out)
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), oracle.recover(ans_o, A_o, s_o))
+    assert pir.qpadl_pir_client_status() == pir.QPADL_OK
 
 
 @pytest.mark.parametrize("p", [256, 16, 2])
