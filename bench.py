@@ -478,6 +478,14 @@ def run_ours(args):
     # choices (streaming chunk width, in-kernel query packing, small-batch GEMM depth and the
     # streaming/tensor crossover) timed on this GPU; the timed steps below use the result
     tune = pir.qpadl_pir_autotune(db, 1024)
+    # a profiler serialises and slows every launch, so the tuner can choose differently
+    # under one: these pin the streaming variant the plain run chose
+    if args.stream_chunk:
+        pir.qpadl_pir_set_option(db, pir.QPADL_OPT_STREAM_CHUNK, args.stream_chunk)
+        tune["stream_chunk"] = args.stream_chunk
+    if args.stream_raw >= 0:
+        pir.qpadl_pir_set_option(db, pir.QPADL_OPT_STREAM_RAW, args.stream_raw)
+        tune["stream_raw"] = args.stream_raw
     raw = tune["stream_raw"] == 1
 
     # single-GPU characterisations (batch sweep, client batches, serving, Chor, Goldberg) run
@@ -758,6 +766,10 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the batch sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--stream-chunk", type=int, default=0,
+                    help="pin the single-query streaming chunk width after tuning (profiling runs)")
+    ap.add_argument("--stream-raw", type=int, default=-1,
+                    help="pin in-kernel query packing (1) or the separate pack kernel (0) after tuning")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

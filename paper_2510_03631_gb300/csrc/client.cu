@@ -7,12 +7,12 @@
 //  Query    (Def. 1 Client.Query)      qu = A s + e + Delta * u_col   mod 2^32
 //  Recover  (Def. 1 Client.BlockReconst) d = round((ans - H s) / Delta) mod p
 //
-// Single queries are HBM-bound matrix-vector products: one warp per row of A
-// or H; for n in {512, 1024, 2048} each lane keeps its slice of the secret
-// in registers and issues all of a row's 16-byte loads (two rows at a time)
-// before using them, and the kernel overlaps its start with the end of the
-// kernel before it (programmatic dependent launch); other n use a
-// shared-memory copy of the secret.
+// Single queries are HBM-bound matrix-vector products over A or H.  For
+// n in {512, 1024, 2048} the rows stream through a shared-memory ring fed by
+// bulk copies, each consumer warp takes one row per stage with the secret in
+// registers, and the kernel overlaps its start with the end of the kernel
+// before it (programmatic dependent launch); other n use one warp per row
+// and a shared-memory copy of the secret.
 // Batches are u32 GEMMs (Y = X * W^T over Z_{2^32}) on the CUDA cores with
 // 8x8 register blocking.
 #include <cstdint>
