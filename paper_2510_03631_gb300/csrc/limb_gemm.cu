@@ -99,9 +99,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     static_assert(LPV == 4 || (LPV == 1 && !PLANED), "one-limb vectors: plain mode");
     constexpr int QPT = BN / LPV;      // vectors per tile
     // one-limb tiles wider than 64 keep their running sums in TMEM, reduced mod p after every
-    // chunk (a residue below p plus one 512-deep chunk stays below 2^24, so fp32 stays exact)
+    // chunk (a representative |r| <= 1.5 p plus one chunk stays below 2^24, so fp32 stays exact)
     constexpr bool TMEMSUM = LPV == 1 && BN > 64;
+    static_assert(!TMEMSUM || BN % 128 == 0, "the mod-p pass takes 128 columns per load batch");
     constexpr int RUN = TMEMSUM ? 1 : QPT;   // running sums kept in registers
+    // K-steps per exact chunk: digits times limbs or centred vector entries (|product| <=
+    // 255 * 128) sum to at most 16,711,680 over 512, and with a reduced representative
+    // (|r| <= 1.5 p <= 386) added still below 2^24
+    constexpr uint32_t CKB = static_cast<uint32_t>(kChunkKB);
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + kGemmStages * Cfg::kStageBytes);
@@ -183,7 +188,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         for (uint32_t t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
             uint32_t d_tmem = tmem_base;
             for (uint32_t kb = 0; kb < KB; ++kb, ++it) {
-                if (kb % kChunkKB == 0) {
+                if (kb % CKB == 0) {
                     const uint32_t buf = ci & 1u;
                     const bool ok = mbar_wait(&acc_empty[buf], ((ci >> 1) & 1u) ^ 1u, abort);
                     if (__any_sync(0xffffffffu, !ok)) {
@@ -207,27 +212,27 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 if (elect_one()) {
                     if constexpr (PLANED) {
                         // limb plane u of this chunk: the active shifts are the first (4 - u) * BN/4 rows
-                        const uint32_t u = (kb / kChunkKB) / plane_chunks;
+                        const uint32_t u = (kb / CKB) / plane_chunks;
                         const uint32_t idesc_u = umma_idesc_f16(kBM, (4u - u) * (BN / 4));
 #pragma unroll
                         for (int k = 0; k < kBK / 16; ++k)
                             umma_f16(d_tmem, adesc + 2u * k, bdesc + 2u * k, idesc_u,
-                                     (kb % kChunkKB != 0 || k != 0) ? 1u : 0u);
+                                     (kb % CKB != 0 || k != 0) ? 1u : 0u);
                     } else {
 #pragma unroll
                         for (int k = 0; k < kBK / 16; ++k) {
                             // advance the start address by 16 elements (32 bytes) inside the swizzle atom
                             umma_f16(d_tmem, adesc + 2u * k, bdesc + 2u * k, idesc,
-                                     ((TMEMSUM && kb >= 2u * kChunkKB) || kb % kChunkKB != 0 || k != 0) ? 1u
+                                     ((TMEMSUM && kb >= 2u * CKB) || kb % CKB != 0 || k != 0) ? 1u
                                                                                                          : 0u);
                         }
                     }
                     umma_commit(&empty[st]);
-                    if (kb % kChunkKB == kChunkKB - 1 || kb == KB - 1) umma_commit(&acc_full[ci & 1u]);
+                    if (kb % CKB == CKB - 1 || kb == KB - 1) umma_commit(&acc_full[ci & 1u]);
                 }
                 __syncwarp();
                 issued = true;
-                if (kb % kChunkKB == kChunkKB - 1 || kb == KB - 1) ++ci;
+                if (kb % CKB == CKB - 1 || kb == KB - 1) ++ci;
             }
         }
         // every MMA this warp issued must finish before TMEM is released
@@ -247,7 +252,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             uint32_t run[RUN];
 #pragma unroll
             for (int q = 0; q < RUN; ++q) run[q] = 0u;
-            const uint32_t nchunks = (KB + kChunkKB - 1) / kChunkKB;
+            const uint32_t nchunks = (KB + CKB - 1) / CKB;
             for (uint32_t c = 0; c < nchunks; ++c, ++ci) {
                 const uint32_t buf = ci & 1u;
                 if (!mbar_wait(&acc_full[buf], (ci >> 1) & 1u, abort)) {
@@ -259,20 +264,28 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     const float pf = static_cast<float>(epi.p), inv = 1.0f / pf;
                     const uint32_t cur = tmem_base + lane_addr + buf * BN;
                     if (c + 1 < nchunks) {
-                        // reduce this buffer's running sums mod p in place
+                        // replace this buffer's running sums by small representatives of their
+                        // residues mod p: q = x / p rounded to an integer through the 1.5 * 2^23
+                        // rounding constant (off by at most one where |x / p| >= 2^22, i.e. p < 4),
+                        // r = x - q p with |r| <= 1.5 p.  q p and r are integers below 2^24, so the
+                        // fused multiply-add is exact.  Four 32-column loads per wait.
+                        constexpr float kRound = 12582912.0f;
 #pragma unroll 1
-                        for (int j = 0; j < BN / 32; ++j) {
-                            uint32_t v[32];
-                            tmem_ld32(cur + 32u * j, v);
+                        for (int j0 = 0; j0 < BN / 32; j0 += 4) {
+                            uint32_t v[4][32];
+#pragma unroll
+                            for (int g = 0; g < 4; ++g) tmem_ld32(cur + 32u * (j0 + g), v[g]);
                             tmem_wait_ld();
 #pragma unroll
-                            for (int q = 0; q < 32; ++q) {
-                                const float x = __uint_as_float(v[q]);
-                                float r = fmaf(-floorf(x * inv), pf, x);   // exact: integers below 2^24
-                                r = r < 0.f ? r + pf : (r >= pf ? r - pf : r);
-                                v[q] = __float_as_uint(r);
+                            for (int g = 0; g < 4; ++g) {
+#pragma unroll
+                                for (int q = 0; q < 32; ++q) {
+                                    const float x = __uint_as_float(v[g][q]);
+                                    const float qf = __fsub_rn(__fmaf_rn(x, inv, kRound), kRound);
+                                    v[g][q] = __float_as_uint(__fmaf_rn(-qf, pf, x));
+                                }
+                                tmem_st32(cur + 32u * (j0 + g), v[g]);
                             }
-                            tmem_st32(cur + 32u * j, v);
                         }
                         tmem_wait_st();
                         if (c + 2 < nchunks) {
@@ -336,30 +349,35 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                         }
                     }
                 } else if constexpr (LPV == 1) {
-                    // every column is its own vector
+                    // every column is its own vector; all loads before one wait
+                    uint32_t v[BN / 32][32];
 #pragma unroll
-                    for (int j = 0; j < BN / 32; ++j) {
-                        uint32_t v[32];
-                        tmem_ld32(tmem_base + lane_addr + buf * BN + 32u * j, v);
-                        tmem_wait_ld();
+                    for (int j = 0; j < BN / 32; ++j) tmem_ld32(tmem_base + lane_addr + buf * BN + 32u * j, v[j]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < BN / 32; ++j)
 #pragma unroll
                         for (int q = 0; q < 32; ++q)
-                            run[32 * j + q] += static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[q])));
-                    }
+                            run[32 * j + q] += static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[j][q])));
                 } else {
+                    // two 32-column loads per wait
+                    constexpr int JB = BN / 32 < 2 ? BN / 32 : 2;
 #pragma unroll
-                    for (int j = 0; j < BN / 32; ++j) {
-                        uint32_t v[32];
-                        tmem_ld32(tmem_base + lane_addr + buf * BN + 32u * j, v);
+                    for (int j0 = 0; j0 < BN / 32; j0 += JB) {
+                        uint32_t v[JB][32];
+#pragma unroll
+                        for (int g = 0; g < JB; ++g) tmem_ld32(tmem_base + lane_addr + buf * BN + 32u * (j0 + g), v[g]);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const uint32_t s0 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 0])));
-                            const uint32_t s1 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 1])));
-                            const uint32_t s2 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 2])));
-                            const uint32_t s3 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 3])));
-                            run[8 * j + q] += s0 + (s1 << 8) + (s2 << 16) + (s3 << 24);
-                        }
+                        for (int g = 0; g < JB; ++g)
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                const uint32_t s0 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[g][4 * q + 0])));
+                                const uint32_t s1 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[g][4 * q + 1])));
+                                const uint32_t s2 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[g][4 * q + 2])));
+                                const uint32_t s3 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[g][4 * q + 3])));
+                                run[8 * (j0 + g) + q] += s0 + (s1 << 8) + (s2 << 16) + (s3 << 24);
+                            }
                     }
                 }
                 tc_fence_before();
