@@ -30,6 +30,10 @@ struct StoreEpi {
         out[i * ld_m + (uint64_t)b * ld_b] = dot;
     }
     __device__ __forceinline__ void operator()(uint64_t i, uint32_t b, uint32_t dot) const { put(i, b, dot, 0u); }
+    // one CTA's part of the element (split tiles; the output starts at zero)
+    __device__ __forceinline__ void add(uint64_t i, uint32_t b, uint32_t part) const {
+        atomicAdd(out + i * ld_m + (uint64_t)b * ld_b, part);
+    }
 };
 
 // Query (Def. 1 Client.Query): q_b[j] = (A s_b)[j] + e_b[j] + Delta [j == col_b]  mod 2^32.

@@ -87,10 +87,41 @@ __device__ __forceinline__ bool drain_wait_g(uint64_t *bar, uint32_t parity) {
     return true;
 }
 
+// Work schedule of one CTA.  Tiles [0, dp_tiles) are whole-tile work dealt
+// round-robin (tile b, b + G, ...: neighbouring CTAs share the rows of D).
+// The remaining tiles are split stream-K style: their chunks (tile-major)
+// form one range that the G CTAs cut into G contiguous, nearly equal
+// pieces, so the last wave ends evenly.  A piece is tile t, chunks [c0, c1).
+struct Piece {
+    uint32_t t, c0, c1;
+};
+struct PieceIter {
+    uint32_t t, u, u_end;
+    __device__ __forceinline__ PieceIter(uint32_t tiles, uint32_t dp_tiles, uint32_t nchunks) {
+        t = blockIdx.x;
+        const uint64_t U = (uint64_t)(tiles - dp_tiles) * nchunks;
+        u = static_cast<uint32_t>((uint64_t)blockIdx.x * U / gridDim.x);
+        u_end = static_cast<uint32_t>((uint64_t)(blockIdx.x + 1) * U / gridDim.x);
+    }
+    __device__ __forceinline__ bool next(Piece &p, uint32_t dp_tiles, uint32_t nchunks) {
+        if (t < dp_tiles) {
+            p = Piece{t, 0u, nchunks};
+            t += gridDim.x;
+            return true;
+        }
+        if (u >= u_end) return false;
+        const uint32_t c0 = u % nchunks;
+        const uint32_t c1 = nchunks - c0 < u_end - u ? nchunks : c0 + (u_end - u);
+        p = Piece{dp_tiles + u / nchunks, c0, c1};
+        u += c1 - c0;
+        return true;
+    }
+};
+
 template <int BN, class Epi, bool PLANED>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     limb_gemm_kernel(const __grid_constant__ CUtensorMap a_map, const __grid_constant__ CUtensorMap b_map,
-                     Epi epi, uint32_t M, uint32_t NV, uint32_t KB, uint32_t plane_chunks,
+                     Epi epi, uint32_t M, uint32_t NV, uint32_t KB, uint32_t plane_chunks, uint32_t dp_tiles_arg,
                      int *__restrict__ status) {
     static_assert(!PLANED || BN >= 64, "a shift group needs N = BN/4 >= 16");
     using Cfg = GemmCfg<BN>;
@@ -145,6 +176,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const uint32_t m_tiles = (M + kBM - 1) / kBM;
     const uint32_t n_tiles = (NV * LPV + BN - 1) / BN;
     const uint32_t tiles = m_tiles * n_tiles;
+    const uint32_t nchunks = (KB + CKB - 1) / CKB;
+    // only a plain store can take split tiles (their pieces add into a zeroed output)
+    constexpr bool kSplit = std::is_same<Epi, StoreEpi>::value;
+    const uint32_t dp_tiles = kSplit && dp_tiles_arg < tiles ? dp_tiles_arg : tiles;
     bool failed = false;
 
     if (warp == 0) {
@@ -153,7 +188,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             tma_prefetch_desc(&a_map);
             tma_prefetch_desc(&b_map);
             uint32_t it = 0;
-            for (uint32_t t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
+            PieceIter pit(tiles, dp_tiles, nchunks);
+            Piece pc;
+            while (!failed && pit.next(pc, dp_tiles, nchunks)) {
+                const uint32_t t = pc.t;
+                const uint32_t kb0 = pc.c0 * CKB, kb1 = pc.c1 * CKB < KB ? pc.c1 * CKB : KB;
                 const int32_t m0 = static_cast<int32_t>((t / n_tiles) * kBM);
                 const int32_t n0 = static_cast<int32_t>((t % n_tiles) * BN);
                 {
@@ -162,7 +201,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     const uint32_t nv = v0 < NV ? (NV - v0 < (uint32_t)QPT ? NV - v0 : (uint32_t)QPT) : 0u;
                     if (static_cast<uint32_t>(m0) + kBM <= M) epi.prefetch(static_cast<uint64_t>(m0), v0, nv);
                 }
-                for (uint32_t kb = 0; kb < KB; ++kb, ++it) {
+                for (uint32_t kb = kb0; kb < kb1; ++kb, ++it) {
                     const uint32_t st = it % kGemmStages;
                     const uint32_t ph = (it / kGemmStages) & 1u;
                     if (!mbar_wait(&empty[st], ph ^ 1u, abort)) {
@@ -185,9 +224,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         constexpr uint32_t idesc = umma_idesc_f16(kBM, BN);
         uint32_t it = 0, ci = 0;
         bool issued = false;
-        for (uint32_t t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
+        PieceIter pit(tiles, dp_tiles, nchunks);
+        Piece pc;
+        while (!failed && pit.next(pc, dp_tiles, nchunks)) {
+            const uint32_t kb0 = pc.c0 * CKB, kb1 = pc.c1 * CKB < KB ? pc.c1 * CKB : KB;
             uint32_t d_tmem = tmem_base;
-            for (uint32_t kb = 0; kb < KB; ++kb, ++it) {
+            for (uint32_t kb = kb0; kb < kb1; ++kb, ++it) {
                 if (kb % CKB == 0) {
                     const uint32_t buf = ci & 1u;
                     const bool ok = mbar_wait(&acc_empty[buf], ((ci >> 1) & 1u) ^ 1u, abort);
@@ -228,11 +270,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                         }
                     }
                     umma_commit(&empty[st]);
-                    if (kb % CKB == CKB - 1 || kb == KB - 1) umma_commit(&acc_full[ci & 1u]);
+                    if (kb % CKB == CKB - 1 || kb == kb1 - 1) umma_commit(&acc_full[ci & 1u]);
                 }
                 __syncwarp();
                 issued = true;
-                if (kb % CKB == CKB - 1 || kb == KB - 1) ++ci;
+                if (kb % CKB == CKB - 1 || kb == kb1 - 1) ++ci;
             }
         }
         // every MMA this warp issued must finish before TMEM is released
@@ -246,14 +288,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         const uint32_t quarter = static_cast<uint32_t>(warp & 3);
         const uint32_t lane_addr = (quarter * 32u) << 16;
         uint32_t ci = 0;
-        for (uint32_t t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
+        PieceIter pit(tiles, dp_tiles, nchunks);
+        Piece pc;
+        while (!failed && pit.next(pc, dp_tiles, nchunks)) {
+            const uint32_t t = pc.t;
             const uint32_t m0 = (t / n_tiles) * kBM;
             const uint32_t v0 = (t % n_tiles) * QPT;
             uint32_t run[RUN];
 #pragma unroll
             for (int q = 0; q < RUN; ++q) run[q] = 0u;
-            const uint32_t nchunks = (KB + CKB - 1) / CKB;
-            for (uint32_t c = 0; c < nchunks; ++c, ++ci) {
+            for (uint32_t c = pc.c0; c < pc.c1; ++c, ++ci) {
                 const uint32_t buf = ci & 1u;
                 if (!mbar_wait(&acc_full[buf], (ci >> 1) & 1u, abort)) {
                     failed = true;
@@ -387,6 +431,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             if (failed) break;
             if constexpr (TMEMSUM) continue;   // the last chunk already wrote the tile
             const uint32_t row = m0 + quarter * 32u + static_cast<uint32_t>(lane);
+            if constexpr (kSplit) {
+                if (row < M && !(pc.c0 == 0 && pc.c1 == nchunks)) {
+                    // part of a split tile: exact, since addition mod 2^32 commutes
+#pragma unroll
+                    for (int q = 0; q < QPT; ++q)
+                        if (v0 + q < NV) epi.add(row, v0 + q, run[q]);
+                    continue;
+                }
+            }
             if (row < M) {
                 // groups of up to 16 outputs: all their loads first, then all their stores
                 constexpr int G = QPT < 16 ? QPT : 16;
@@ -630,9 +683,37 @@ int limb_gemm_bn_for(uint32_t nv) {
 
 template <int BN, class Epi, bool PLANED>
 static void launch_one(int grid, const CUtensorMap &a_map, const CUtensorMap &b_map, const Epi &epi, uint32_t M,
-                       uint32_t NV, uint32_t KB, uint32_t plane_chunks, int *status, cudaStream_t stream) {
+                       uint32_t NV, uint32_t KB, uint32_t plane_chunks, int *status, cudaStream_t stream,
+                       uint32_t dp_tiles = 0xffffffffu) {
     limb_gemm_kernel<BN, Epi, PLANED><<<grid, kGemmThreads, GemmCfg<BN>::kSmemBytes, stream>>>(
-        a_map, b_map, epi, M, NV, KB, plane_chunks, status);
+        a_map, b_map, epi, M, NV, KB, plane_chunks, dp_tiles, status);
+}
+
+// Schedule of a plain-store GEMM over `tiles` tiles (n_tiles per row tile) on
+// `num_sms` SMs: the grid and the number of whole (data-parallel) tiles; the
+// rest are split stream-K style.  Whole waves stay whole except the last full
+// one, which joins the remainder so that every CTA ends with about the same
+// share.  Whole tiles dealt round-robin let the CTAs on the n_tiles tiles of a
+// row tile share its rows of D through L2; split pieces run at different K
+// offsets and lose that sharing, which measured slower on the 1 GiB database
+// once a row tile spans 4 or more tiles.  So splitting is used when there are
+// fewer tiles than SMs, or for at most 3 tiles per row tile.  Returns false
+// when no tile is split.
+static bool store_schedule(uint64_t tiles, uint64_t n_tiles, uint32_t nchunks, int num_sms, int *grid,
+                           uint32_t *dp_tiles) {
+    const uint64_t G = static_cast<uint64_t>(num_sms);
+    *grid = static_cast<int>(tiles < G ? tiles : G);
+    *dp_tiles = static_cast<uint32_t>(tiles);
+    if (tiles % G == 0 || nchunks < 2) return false;
+    if (tiles > G) {
+        if (n_tiles > 3) return false;
+        *dp_tiles = static_cast<uint32_t>((tiles / G - 1) * G);
+    } else {
+        *dp_tiles = 0;
+        const uint64_t units = tiles * nchunks;
+        *grid = static_cast<int>(units < G ? units : G);
+    }
+    return true;
 }
 
 // plane_chunks > 0 selects planed mode (then bn >= 64 and K = 4 * 512 * plane_chunks).
@@ -653,13 +734,28 @@ static cudaError_t launch_epi(int bn, const CUtensorMap &a_map, const CUtensorMa
         }
         return cudaGetLastError();
     } else {
-    const int grid = static_cast<int>(tiles < (uint64_t)num_sms ? tiles : (uint64_t)num_sms);
+    int grid = static_cast<int>(tiles < (uint64_t)num_sms ? tiles : (uint64_t)num_sms);
+    uint32_t dp = 0xffffffffu;
+    if constexpr (std::is_same<Epi, StoreEpi>::value) {
+        // split tiles add into the output, so it is zeroed first; only a dense output
+        // (every element of the M x NV block, in either order) can be zeroed in one piece
+        const bool dense = (epi.ld_m == 1 && epi.ld_b == M) || (epi.ld_b == 1 && epi.ld_m == NV);
+        int g2 = grid;
+        uint32_t dp2 = 0;
+        const uint64_t n_tiles = ((uint64_t)Epi::kLimbs * NV + bn - 1) / bn;
+        if (dense && store_schedule(tiles, n_tiles, (KB + kChunkKB - 1) / kChunkKB, num_sms, &g2, &dp2)) {
+            cudaError_t e = cudaMemsetAsync(epi.out, 0, 4ull * M * NV, stream);
+            if (e != cudaSuccess) return e;
+            grid = g2;
+            dp = dp2;
+        }
+    }
     if (plane_chunks == 0) {
         switch (bn) {
-            case 32: launch_one<32, Epi, false>(grid, a_map, b_map, epi, M, NV, KB, 1, status, stream); break;
-            case 64: launch_one<64, Epi, false>(grid, a_map, b_map, epi, M, NV, KB, 1, status, stream); break;
-            case 128: launch_one<128, Epi, false>(grid, a_map, b_map, epi, M, NV, KB, 1, status, stream); break;
-            case 256: launch_one<256, Epi, false>(grid, a_map, b_map, epi, M, NV, KB, 1, status, stream); break;
+            case 32: launch_one<32, Epi, false>(grid, a_map, b_map, epi, M, NV, KB, 1, status, stream, dp); break;
+            case 64: launch_one<64, Epi, false>(grid, a_map, b_map, epi, M, NV, KB, 1, status, stream, dp); break;
+            case 128: launch_one<128, Epi, false>(grid, a_map, b_map, epi, M, NV, KB, 1, status, stream, dp); break;
+            case 256: launch_one<256, Epi, false>(grid, a_map, b_map, epi, M, NV, KB, 1, status, stream, dp); break;
             default: return cudaErrorInvalidValue;
         }
     } else {

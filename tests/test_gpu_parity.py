@@ -183,6 +183,17 @@ def test_answer_batch_many_tiles_per_cta(B, kstep):
     assert np.array_equal(got, oracle.answer_batch(D, Q, threads=oracle.max_threads()))
 
 
+@pytest.mark.parametrize("R,C,B", [(40000, 2100, 70), (20000, 1100, 64), (128, 600, 1024)])
+def test_answer_batch_split_tiles(R, C, B):
+    # the fp16-copy GEMM deals whole tiles round-robin and splits the last waves' tiles over
+    # all SMs (pieces add into a zeroed output): 626 tiles of 5 chunks (the last one 64 deep),
+    # 157 tiles of 3 chunks, and 16 tiles of 2 chunks spread over more SMs than tiles
+    prm, D, db = _setup(R, C, seed=R + C)
+    Q = inputs.uniform_u32(B * C, seed=B + 5, tag=inputs.TAG_MISC).reshape(B, C)
+    got = _answers(db, Q, path=1)
+    assert np.array_equal(got, oracle.answer_batch(D, Q, threads=oracle.max_threads()))
+
+
 def test_answer_batch_linearity_on_device():
     R, C, B = 256, 2048, 8
     prm, D, db = _setup(R, C, seed=3)
@@ -208,7 +219,8 @@ def test_small_plaintext_modulus_and_digit_check():
 
 
 # ------------------------------------------------------------------ Hint
-@pytest.mark.parametrize("R,C,n", [(1024, 1024, 512), (100, 1000, 17), (129, 520, 1), (300, 64, 70)])
+@pytest.mark.parametrize("R,C,n", [(1024, 1024, 512), (100, 1000, 17), (129, 520, 1), (300, 64, 70),
+                                   (40000, 700, 64)])   # 313 row tiles: whole waves, then a split last wave
 def test_hint_matches_oracle(R, C, n):
     prm, D, db = _setup(R, C, n=n, seed=n)
     A = torch.empty(C * n, dtype=torch.int32, device="cuda")
