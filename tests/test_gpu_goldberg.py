@@ -53,6 +53,19 @@ def test_goldberg_matches_oracle(cuda, R, C, p, B, gemm_min, u8max):
     h.close()
 
 
+@pytest.mark.parametrize("B", [40, 100])
+def test_many_row_tiles(cuda, B):
+    # 313 row tiles: every persistent CTA of the one-limb GEMM (register sums at 40 queries,
+    # TMEM-resident residues at 100) walks two or three tiles
+    R, C, p = 40000, 1100, 257
+    D = _db(R, C, p, seed=B)
+    Q = (inputs.uniform_u32(B * C, seed=B + 9, tag=inputs.TAG_MISC) % p).reshape(B, C)
+    h = pir.qpadl_goldberg_setup(R, C, p, torch.from_numpy(D).cuda())
+    got = _answer(h, Q, 1, 0)
+    assert np.array_equal(got, oracle.goldberg_answer(D, Q, p, threads=oracle.max_threads()))
+    h.close()
+
+
 @pytest.mark.parametrize("gemm_min,u8max,B", [(1, 32, 6), (1, 0, 6), (1 << 30, 32, 6), (1, 0, 70)])
 @pytest.mark.parametrize("qval", [256, 128, 129])
 def test_exact_sum_bounds(cuda, gemm_min, u8max, B, qval):
