@@ -422,11 +422,15 @@ def goldberg_measure(torch, pir, inputs, seed=41):
             raise SystemExit("bench: Goldberg answer differs from the host dot product")
         qps = B / (ms * 1e-3)
         one_qps = one_qps or qps
+        # the handle's defaults: streaming below 5 queries, the four-limb uint8-digit GEMM up to 32,
+        # the one-limb fp16 GEMM above
+        path = "streaming + mod p" if B < 5 else ("uint8-digit GEMM + mod p" if B <= 32 else "one-limb GEMM")
         ent = {"ms": round(ms, 4), "queries_per_s": round(qps, 1),
                "db_scan_gbs": round(B * R * C / (ms * 1e-3) / 1e9, 1), "x_vs_one_at_a_time": round(qps / one_qps, 2),
-               "path": "one-limb GEMM" if B >= 5 else "streaming + mod p"}
+               "path": path}
         if B >= 5:
-            ent["fp16_tflops"] = round(2 * R * C * B / (ms * 1e-3) / 1e12, 1)
+            limbs = 4 if B <= 32 else 1
+            ent["fp16_tflops"] = round(2 * R * C * limbs * B / (ms * 1e-3) / 1e12, 1)
         res["batches"][str(B)] = ent
         del Q, out
     h.close()
