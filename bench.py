@@ -254,7 +254,7 @@ def serving_measure(torch, pir, inputs, rates, duration_s, single_db_one_ms, see
 
     def make_server(dbs, max_batch):
         srv = pir.qpadl_server_create(pir.server_config(host_budget_bytes=2 << 30, device_budget_bytes=2 << 30,
-                                                        max_inflight=16384, max_batch=max_batch, num_streams=2))
+                                                        max_inflight=16384, max_batch=max_batch, num_streams=4))
         ids = [pir.qpadl_server_add_db(srv, h) for h in dbs]
         pir.qpadl_server_start(srv)
         return srv, ids
@@ -329,7 +329,7 @@ def serving_measure(torch, pir, inputs, rates, duration_s, single_db_one_ms, see
         h.close()
     return {
         "databases": [f"{R}x{C}" for R, C in shapes], "skew": list(skew), "n_lwe": n_lwe,
-        "answers_checked_in_mix": n0, "streams": 2, "max_batch": 256, "group_size_ratio": 2.0,
+        "answers_checked_in_mix": n0, "streams": 4, "max_batch": 256, "group_size_ratio": 2.0,
         "rates": runs,
         "mean_enqueue_us_per_launch": round(enq_us, 2),
         "single_1gib_saturation": {

@@ -155,6 +155,7 @@ struct Launch {
     uint64_t dev_off = 0, dev_bytes = 0;
     bool failed_by_watchdog = false;
     bool gpu_done = false;
+    bool gemm = false;              // carries a batch of 3 or more (tensor-core GEMM)
     bool drop_completion = false;   // test hook: the completion is not reported to requests
 };
 
@@ -188,6 +189,7 @@ struct qpadl_server {
     bool started = false;
     // counters
     uint64_t n_launches = 0, n_done = 0, n_failed = 0, n_busy = 0, n_grouped = 0;
+    uint32_t active_gemm = 0;    // launches in flight that carry a GEMM
     double busy_batch_sum = 0;
     double enqueue_s = 0;   // host time spent enqueueing launches
 
@@ -227,6 +229,7 @@ void qpadl_server::finalize(Launch *L) {
         n_done += L->reqs.size();
     }
     dev_alloc.release(L->dev_off, L->dev_bytes);
+    if (L->gemm) --active_gemm;
     slots[L->slot].busy = nullptr;
     active.erase(std::remove(active.begin(), active.end(), L), active.end());
     // requests failed by the watchdog and already polled kept their host
@@ -243,6 +246,7 @@ void qpadl_server::finalize(Launch *L) {
 
 namespace {
 constexpr uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+constexpr size_t kMaxGemmLaunches = 2;   // launches in flight at once while a GEMM is among them
 
 // Device workspace of one group of `take` requests: queries, answers and,
 // for the GEMM paths, the byte limbs of the queries.
@@ -291,6 +295,13 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
         groups.push_back(g);
     }
     if (groups.empty()) return false;
+    // A batch of 3 or more runs a tensor-core GEMM whose grid fills every SM.  While one runs,
+    // at most kMaxGemmLaunches launches of any kind are in flight: more would only split the
+    // SMs and shrink each batch.  With no GEMM in flight, one- and two-query streaming
+    // launches may take every free stream, so a lone query does not queue behind another.
+    bool gemm = false;
+    for (const Group &g : groups) gemm = gemm || g.count >= 3;
+    if ((gemm || active_gemm > 0) && active.size() >= kMaxGemmLaunches) return false;
     uint64_t off = 0;
     if (!dev_alloc.alloc(need, &off)) return false;   // wait for a launch to free device memory
     Launch *L = new Launch();
@@ -300,6 +311,8 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
     L->dev_off = off;
     L->dev_bytes = need;
     L->groups = groups;
+    L->gemm = gemm;
+    if (gemm) ++active_gemm;
     for (const Group &g : groups) {
         DbEntry &e = dbs[g.db];
         for (uint32_t i = 0; i < g.count; ++i) {

@@ -568,7 +568,7 @@ class qpadl_server_stats_t(ctypes.Structure):
 
 
 def server_config(host_budget_bytes=1 << 30, device_budget_bytes=1 << 30, max_inflight=4096, max_batch=256,
-                  num_streams=2, hold_us=0.0, watchdog_ms=10000.0, test_drop_completion_launch=0,
+                  num_streams=4, hold_us=0.0, watchdog_ms=10000.0, test_drop_completion_launch=0,
                   group_size_ratio=2.0):
     return qpadl_server_config(host_budget_bytes, device_budget_bytes, max_inflight, max_batch, num_streams,
                                test_drop_completion_launch, hold_us, watchdog_ms, group_size_ratio)
