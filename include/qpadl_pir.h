@@ -484,7 +484,9 @@ typedef struct qpadl_server_config {
     uint32_t max_inflight;        /* requests admitted and not yet polled */
     uint32_t max_batch;           /* requests of one database per launch (1..65535); a launch holds
                                      at most min(max_inflight, 65535) requests in all */
-    uint32_t num_streams;         /* launches in flight at once (1..8) */
+    uint32_t num_streams;         /* launches in flight at once (1..8); while a launch that
+                                     carries a batched GEMM (3 or more requests of a database)
+                                     is in flight, at most 2 launches run */
     uint32_t test_drop_completion_launch; /* test hook: 0 = off; k = the k-th launch's completion
                                              is not reported, so its requests run into the watchdog */
     double hold_us;               /* a lone request may wait this long for company while other
