@@ -743,7 +743,7 @@ def run_ours(args):
         del D
         torch.cuda.empty_cache()
         serving = serving_measure(torch, pir, inputs, rates=(1000, 5000, 10000, 20000, 50000),
-                                  duration_s=1.0, single_db_one_ms=resp_ms_avg)
+                                  duration_s=3.0, single_db_one_ms=resp_ms_avg)
         torch.cuda.empty_cache()
         chor = chor_measure(torch, pir, inputs)
         torch.cuda.empty_cache()
