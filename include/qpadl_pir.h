@@ -377,17 +377,18 @@ int qpadl_goldberg_setup(uint64_t rows, uint64_t cols, uint32_t p, const uint8_t
 /* Answers B queries: Q_dev B x cols field elements (uint32, each < p; larger
  * values give unspecified answers), out_dev B x rows elements in [0, p).
  * Below the GEMM threshold the streaming kernel computes the exact integer
- * sums and a second kernel reduces them mod p; up to 32 queries the
- * uint8-digit GEMM does the same (builds the blocked digit copy on first
- * use); above, one exact tcgen05 GEMM with each query as a single centred
- * fp16 row and a mod-p epilogue (builds the fp16 operand copy on first use). */
+ * sums and a second kernel reduces them mod p; up to 64 queries the
+ * uint8-digit GEMM does the same with each query as one centred fp16 row
+ * (builds the blocked digit copy on first use); above, one exact tcgen05 GEMM
+ * over the fp16 operand copy with the same rows and a mod-p epilogue (builds
+ * that copy on first use). */
 int qpadl_goldberg_answer_batch(qpadl_goldberg *h, const uint32_t *Q_dev, uint32_t B, uint32_t *out_dev,
                                 qpadl_stream_t stream);
 
 /* QPADL_GOLDBERG_OPT_GEMM_MIN_BATCH (default 5): smallest batch on a GEMM.
- * QPADL_GOLDBERG_OPT_U8_MAX_BATCH (0..32, default 32): largest batch on the
- *   uint8-digit GEMM (four limbs, exact integer sums, then mod p); larger
- *   batches take the one-limb fp16 GEMM. */
+ * QPADL_GOLDBERG_OPT_U8_MAX_BATCH (0..64, default 64): largest batch on the
+ *   uint8-digit GEMM (one centred fp16 row per query, exact signed sums, then
+ *   mod p); larger batches take the one-limb fp16 GEMM. */
 #define QPADL_GOLDBERG_OPT_GEMM_MIN_BATCH 1
 #define QPADL_GOLDBERG_OPT_U8_MAX_BATCH 2
 int qpadl_goldberg_set_option(qpadl_goldberg *h, int option, int64_t value);

@@ -868,6 +868,20 @@ __global__ void mod_p_kernel(uint32_t *__restrict__ x, uint64_t n, uint32_t p) {
         x[e] %= p;
 }
 
+// x[i] = x[i] mod p in [0, p) for n words holding exact signed 32-bit sums.
+__global__ void mod_p_signed_kernel(uint32_t *__restrict__ x, uint64_t n, int32_t p) {
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (uint64_t)gridDim.x * blockDim.x) {
+        int32_t r = static_cast<int32_t>(x[e]) % p;
+        if (r < 0) r += p;
+        x[e] = static_cast<uint32_t>(r);
+    }
+}
+
+cudaError_t launch_mod_p_signed(uint32_t *x, uint64_t n, uint32_t p, int num_sms, cudaStream_t stream) {
+    mod_p_signed_kernel<<<num_sms * 4, 256, 0, stream>>>(x, n, static_cast<int32_t>(p));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_centred_rows(const uint32_t *Q, uint32_t B, uint64_t C, uint32_t p, __half *L, uint64_t pitch,
                                 int num_sms, cudaStream_t stream) {
     centred_rows_kernel<<<num_sms * 4, 256, 0, stream>>>(Q, B, C, p, L, pitch);

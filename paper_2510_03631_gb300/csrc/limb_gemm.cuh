@@ -42,6 +42,8 @@ cudaError_t launch_limb_gemm_modp(int bn, const CUtensorMap &a_map, const CUtens
 cudaError_t launch_centred_rows(const uint32_t *Q, uint32_t B, uint64_t C, uint32_t p, __half *L, uint64_t pitch,
                                 int num_sms, cudaStream_t stream);
 cudaError_t launch_mod_p(uint32_t *x, uint64_t n, uint32_t p, int num_sms, cudaStream_t stream);
+// x[i] = (x[i] as a signed 32-bit integer) mod p, in [0, p).
+cudaError_t launch_mod_p_signed(uint32_t *x, uint64_t n, uint32_t p, int num_sms, cudaStream_t stream);
 
 cudaError_t launch_db_to_f16(const uint8_t *D, uint64_t R, uint64_t C, __half *D16, uint64_t pitch, int num_sms,
                              cudaStream_t stream);

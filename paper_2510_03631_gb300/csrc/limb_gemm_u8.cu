@@ -74,7 +74,6 @@ struct U8Cfg {
     static constexpr int kSmemUsed = kBarBase + (2 * kSD + 2 * kSL + 2 * kSA + 5) * 8 + 16 + 1024;
     // padded so that only one CTA fits per SM (it allocates all of TMEM)
     static constexpr int kSmemBytes = kSmemUsed > 120 * 1024 ? kSmemUsed : 120 * 1024;
-    static constexpr int kQPT = BN / 4;
     static_assert(kSA >= 2 && kSD >= 2 && kSD % 2 == 0 && kSL >= 2, "ring sizes");
     static_assert(KS % 128 == 0 && 512 % KS == 0, "stage depth must divide the exact chunk");
     static_assert(kSmemUsed <= 227 * 1024, "shared memory");
@@ -115,11 +114,15 @@ __device__ __forceinline__ bool next_seg(const GroupedGemmArgs &a, uint32_t &u, 
 
 }  // namespace
 
-template <int BN, int KS>
+// LPV: vector-operand rows per vector.  4 = the four byte limbs of 32-bit vectors, recombined
+// mod 2^32; 1 = one row per vector (small signed integers, e.g. centred field elements), whose
+// exact 32-bit signed sums are stored.
+template <int BN, int KS, int LPV = 4>
 __global__ void __launch_bounds__(kThreads, 1)
     limb_gemm_u8_kernel(const __grid_constant__ GroupedGemmArgs args, int *__restrict__ status) {
     using Cfg = U8Cfg<BN, KS>;
-    constexpr int QPT = Cfg::kQPT;
+    static_assert(LPV == 4 || (LPV == 1 && BN <= 64), "one-row vectors: at most 64 running sums per thread");
+    constexpr int QPT = BN / LPV;
     constexpr int SD = Cfg::kSD, SL = Cfg::kSL, SA = Cfg::kSA;
     constexpr int CS = Cfg::kChunkStages;
     extern __shared__ uint8_t smem_raw[];
@@ -318,13 +321,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                     uint32_t v[16];
                     tmem_ld16(tmem_base + lane_addr + buf * BN + 16u * j, v);
                     tmem_wait_ld();
+                    if constexpr (LPV == 1) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const uint32_t s0 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 0])));
-                        const uint32_t s1 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 1])));
-                        const uint32_t s2 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 2])));
-                        const uint32_t s3 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 3])));
-                        run[4 * j + q] += s0 + (s1 << 8) + (s2 << 16) + (s3 << 24);
+                        for (int q = 0; q < 16; ++q)
+                            run[16 * j + q] += static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[q])));
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const uint32_t s0 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 0])));
+                            const uint32_t s1 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 1])));
+                            const uint32_t s2 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 2])));
+                            const uint32_t s3 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 3])));
+                            run[4 * j + q] += s0 + (s1 << 8) + (s2 << 16) + (s3 << 24);
+                        }
                     }
                 }
                 tc_fence_before();
@@ -335,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t row = tr.m0 + quarter * 32u + static_cast<uint32_t>(lane);
             const bool whole = tr.ks0 == 0 && tr.ks1 == tr.ns;   // no other CTA touches this tile
             if (row < gd.M) {
-                const uint32_t v0 = tr.n0 / 4;
+                const uint32_t v0 = tr.n0 / LPV;
 #pragma unroll
                 for (int q = 0; q < QPT; ++q) {
                     const uint32_t vi = v0 + q;
@@ -446,9 +455,9 @@ cudaError_t launch_block_digits(const uint8_t *D, uint64_t R, uint64_t C, uint8_
 }
 
 // ------------------------------------------------------------------ host side
-template <int BN, int KS>
+template <int BN, int KS, int LPV = 4>
 static cudaError_t set_attr() {
-    return cudaFuncSetAttribute(limb_gemm_u8_kernel<BN, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(limb_gemm_u8_kernel<BN, KS, LPV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 U8Cfg<BN, KS>::kSmemBytes);
 }
 
@@ -459,15 +468,17 @@ cudaError_t prepare_limb_gemm_u8_kernels() {
     if ((e = set_attr<64, 128>()) != cudaSuccess) return e;
     if ((e = set_attr<64, 256>()) != cudaSuccess) return e;
     if ((e = set_attr<128, 128>()) != cudaSuccess) return e;
-    return set_attr<128, 256>();
+    if ((e = set_attr<128, 256>()) != cudaSuccess) return e;
+    if ((e = set_attr<32, 128, 1>()) != cudaSuccess) return e;
+    return set_attr<64, 128, 1>();
 }
 
 // 128-digit stages for every tile width: with 256 the TMEM A slots allow only two stages in flight
 int limb_gemm_u8_default_ks(int) { return 128; }
 
-template <int BN, int KS>
+template <int BN, int KS, int LPV = 4>
 static cudaError_t launch_u8(const GroupedGemmArgs &args, int grid, int *status, cudaStream_t stream) {
-    limb_gemm_u8_kernel<BN, KS><<<grid, kThreads, U8Cfg<BN, KS>::kSmemBytes, stream>>>(args, status);
+    limb_gemm_u8_kernel<BN, KS, LPV><<<grid, kThreads, U8Cfg<BN, KS>::kSmemBytes, stream>>>(args, status);
     return cudaGetLastError();
 }
 
@@ -481,6 +492,15 @@ cudaError_t launch_limb_gemm_u8(int bn, int ks, const GroupedGemmArgs &args, int
     if (bn == 64 && ks == 256) return launch_u8<64, 256>(args, grid, status, stream);
     if (bn == 128 && ks == 128) return launch_u8<128, 128>(args, grid, status, stream);
     if (bn == 128 && ks == 256) return launch_u8<128, 256>(args, grid, status, stream);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_limb_gemm_u8_rows(int bn, const GroupedGemmArgs &args, int num_sms, int *status,
+                                     cudaStream_t stream) {
+    const int grid = static_cast<int>(args.total_units < (uint32_t)num_sms ? args.total_units : (uint32_t)num_sms);
+    if (grid <= 0) return cudaSuccess;
+    if (bn == 32) return launch_u8<32, 128, 1>(args, grid, status, stream);
+    if (bn == 64) return launch_u8<64, 128, 1>(args, grid, status, stream);
     return cudaErrorInvalidValue;
 }
 

@@ -21,7 +21,8 @@ struct GroupDesc {
 struct GroupedGemmArgs {
     CUtensorMap a[kMaxGemmGroups];   // blocked uint8 digits: 4-D {128, 128, C/128, R/128},
                                      // box {128, 128, ks/128, 1}, 128-byte swizzle
-    CUtensorMap b[kMaxGemmGroups];   // fp16 limbs, 2-D {C, 4 NV}, box {64, BN}, 128-byte swizzle
+    CUtensorMap b[kMaxGemmGroups];   // fp16 limbs, 2-D {C, 4 NV} ({C, NV} for one row per vector),
+                                     // box {64, BN}, 128-byte swizzle
     GroupDesc g[kMaxGemmGroups];
     uint32_t ngroups, total_units;   // units = sum over groups of tiles x stages
 };
@@ -41,5 +42,13 @@ cudaError_t launch_block_digits(const uint8_t *D, uint64_t R, uint64_t C, uint8_
 int limb_gemm_u8_default_ks(int bn);
 cudaError_t launch_limb_gemm_u8(int bn, int ks, const GroupedGemmArgs &args, int num_sms, int *status,
                                 cudaStream_t stream);
+
+// The same GEMM with one vector-operand row per vector (b maps {C, NV}): each
+// output is the exact signed sum sum_j D[i][j] x_b[j] stored as 32 bits, for
+// |x_b[j]| <= 128 (so every 512-deep chunk stays below 2^24 in fp32 and the
+// whole sum below 2^31 for fewer than 65793 columns).  bn in {32, 64}, 128-digit
+// stages; output zeroed before the launch as above.
+cudaError_t launch_limb_gemm_u8_rows(int bn, const GroupedGemmArgs &args, int num_sms, int *status,
+                                     cudaStream_t stream);
 
 }  // namespace qpadl

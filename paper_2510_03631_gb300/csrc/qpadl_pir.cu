@@ -80,7 +80,7 @@ struct qpadl_goldberg {
     qpadl_db *db = nullptr;
     uint32_t p = 0;
     uint32_t gemm_min_batch = 5;     // batches from this size take a tensor-core GEMM
-    uint32_t u8_max_batch = 32;      // ... the uint8-digit one up to this size, the one-limb fp16 one above
+    uint32_t u8_max_batch = 64;      // ... the uint8-digit one up to this size, the one-limb fp16 one above
 };
 
 // Chor-style GF(2) database handle.
@@ -1203,12 +1203,36 @@ int qpadl_goldberg_answer_batch(qpadl_goldberg *h, const uint32_t *Q_dev, uint32
         QPADL_CU(launch_mod_p(out_dev, (uint64_t)B * R, h->p, db->num_sms, s));
         return QPADL_OK;
     }
-    if (B <= h->u8_max_batch && db->u8_ok && 4 * B <= 128) {
-        // the four-limb uint8-digit GEMM gives the exact integer sums (no wrap below
-        // kGoldbergMaxCols columns), then mod p
-        int rc = answer_tensor_u8(db, Q_dev, B, out_dev, s);
+    if (B <= h->u8_max_batch && db->u8_ok && B <= 64) {
+        // the uint8-digit GEMM with one centred row per query gives the exact signed sums
+        // (below 2^31 in magnitude for at most kGoldbergMaxCols columns), then mod p
+        int rc = ensure_blocked(db, s);
         if (rc != QPADL_OK) return rc;
-        QPADL_CU(launch_mod_p(out_dev, (uint64_t)B * R, h->p, db->num_sms, s));
+        if ((rc = ensure_limbs(db, 2ull * B * db->pitch)) != QPADL_OK) return rc;
+        QPADL_CU(launch_centred_rows(Q_dev, B, C, h->p, db->limbs, db->pitch, db->num_sms, s));
+        const int bn = B <= 32 ? 32 : 64;
+        constexpr int ks = 128;
+        GroupedGemmArgs args;
+        std::memset(&args, 0, sizeof(args));
+        args.a[0] = db->u8_map[ks / 128 - 1];
+        if (!encode_2d(&args.b[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, db->limbs, C, B, db->pitch * 2, kLimbBoxK,
+                       static_cast<uint32_t>(bn), CU_TENSOR_MAP_SWIZZLE_128B))
+            return QPADL_ECUDA;
+        GroupDesc &g = args.g[0];
+        g.out = out_dev;
+        g.ld_m = 1;
+        g.ld_b = R;
+        g.M = static_cast<uint32_t>(R);
+        g.NV = B;
+        g.KB = static_cast<uint32_t>((C + ks - 1) / ks);
+        g.unit_begin = 0;
+        g.n_tiles = (B + bn - 1) / bn;
+        args.ngroups = 1;
+        args.total_units = static_cast<uint32_t>((R + kLimbBoxM - 1) / kLimbBoxM) * g.n_tiles * g.KB;
+        // tiles split between CTAs are accumulated with atomic adds into zeros
+        QPADL_CU(cudaMemsetAsync(out_dev, 0, 4ull * B * R, s));
+        QPADL_CU(launch_limb_gemm_u8_rows(bn, args, db->num_sms, db->d_status, s));
+        QPADL_CU(launch_mod_p_signed(out_dev, (uint64_t)B * R, h->p, db->num_sms, s));
         return QPADL_OK;
     }
     int rc = ensure_tensor_copy(db, s);
@@ -1240,7 +1264,7 @@ int qpadl_goldberg_set_option(qpadl_goldberg *h, int option, int64_t value) {
             h->gemm_min_batch = static_cast<uint32_t>(value);
             return QPADL_OK;
         case QPADL_GOLDBERG_OPT_U8_MAX_BATCH:
-            if (value < 0 || value > 32) return QPADL_EINVAL;
+            if (value < 0 || value > 64) return QPADL_EINVAL;
             h->u8_max_batch = static_cast<uint32_t>(value);
             return QPADL_OK;
         default: return QPADL_EINVAL;

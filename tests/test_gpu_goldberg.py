@@ -43,7 +43,8 @@ CASES = [(300, 1000, 257, 1), (257, 513, 251, 4), (1000, 2048, 257, 5), (700, 40
 
 
 @pytest.mark.parametrize("R,C,p,B", CASES)
-@pytest.mark.parametrize("gemm_min,u8max", [(1, 32), (1, 0), (1 << 30, 32)])   # u8 GEMM / one-limb GEMM / streaming
+# uint8-digit GEMM up to 32 or 64 queries / fp16-copy GEMM / streaming
+@pytest.mark.parametrize("gemm_min,u8max", [(1, 32), (1, 64), (1, 0), (1 << 30, 32)])
 def test_goldberg_matches_oracle(cuda, R, C, p, B, gemm_min, u8max):
     D = _db(R, C, p, seed=R + C)
     Q = (inputs.uniform_u32(B * C, seed=B + p, tag=inputs.TAG_MISC) % p).reshape(B, C)
@@ -66,12 +67,13 @@ def test_many_row_tiles(cuda, B):
     h.close()
 
 
-@pytest.mark.parametrize("gemm_min,u8max,B", [(1, 32, 6), (1, 0, 6), (1 << 30, 32, 6), (1, 0, 70)])
+@pytest.mark.parametrize("gemm_min,u8max,B", [(1, 32, 6), (1, 64, 40), (1, 0, 6), (1 << 30, 32, 6), (1, 0, 70)])
 @pytest.mark.parametrize("qval", [256, 128, 129])
 def test_exact_sum_bounds(cuda, gemm_min, u8max, B, qval):
     # the largest allowed record count with every byte 255: the unsigned sum of the streaming
-    # path, the four-limb sums of the u8 GEMM, the centred register sums (6 queries) and the
-    # TMEM-resident residues reduced mod p after every chunk (70 queries) all stay exact
+    # path, the signed sums of the uint8-digit GEMM (6 and 40 queries), the centred register
+    # sums of the fp16-copy GEMM (6 queries) and its TMEM-resident residues reduced mod p after
+    # every chunk (70 queries) all stay exact
     R, C, p = 128, 65792, 257
     D = np.full((R, C), 255, dtype=np.uint8)
     D[::3, ::7] = 0
