@@ -422,13 +422,13 @@ def goldberg_measure(torch, pir, inputs, seed=41):
             raise SystemExit("bench: Goldberg answer differs from the host dot product")
         qps = B / (ms * 1e-3)
         one_qps = one_qps or qps
-        # the handle's defaults: streaming below 5 queries, the uint8-digit GEMM (one centred row
+        # the handle's defaults: streaming below 3 queries, the uint8-digit GEMM (one centred row
         # per query) up to 64, the one-limb fp16-copy GEMM above
-        path = "streaming + mod p" if B < 5 else ("uint8-digit GEMM + mod p" if B <= 64 else "one-limb fp16 GEMM")
+        path = "streaming + mod p" if B < 3 else ("uint8-digit GEMM + mod p" if B <= 64 else "one-limb fp16 GEMM")
         ent = {"ms": round(ms, 4), "queries_per_s": round(qps, 1),
                "db_scan_gbs": round(B * R * C / (ms * 1e-3) / 1e9, 1), "x_vs_one_at_a_time": round(qps / one_qps, 2),
                "path": path}
-        if B >= 5:
+        if B >= 3:
             ent["fp16_tflops"] = round(2 * R * C * B / (ms * 1e-3) / 1e12, 1)
         res["batches"][str(B)] = ent
         del Q, out

@@ -385,7 +385,7 @@ int qpadl_goldberg_setup(uint64_t rows, uint64_t cols, uint32_t p, const uint8_t
 int qpadl_goldberg_answer_batch(qpadl_goldberg *h, const uint32_t *Q_dev, uint32_t B, uint32_t *out_dev,
                                 qpadl_stream_t stream);
 
-/* QPADL_GOLDBERG_OPT_GEMM_MIN_BATCH (default 5): smallest batch on a GEMM.
+/* QPADL_GOLDBERG_OPT_GEMM_MIN_BATCH (default 3): smallest batch on a GEMM.
  * QPADL_GOLDBERG_OPT_U8_MAX_BATCH (0..64, default 64): largest batch on the
  *   uint8-digit GEMM (one centred fp16 row per query, exact signed sums, then
  *   mod p); larger batches take the one-limb fp16 GEMM. */

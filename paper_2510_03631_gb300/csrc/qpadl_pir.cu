@@ -79,7 +79,7 @@ struct qpadl_client {
 struct qpadl_goldberg {
     qpadl_db *db = nullptr;
     uint32_t p = 0;
-    uint32_t gemm_min_batch = 5;     // batches from this size take a tensor-core GEMM
+    uint32_t gemm_min_batch = 3;     // batches from this size take a tensor-core GEMM
     uint32_t u8_max_batch = 64;      // ... the uint8-digit one up to this size, the one-limb fp16 one above
 };
 
