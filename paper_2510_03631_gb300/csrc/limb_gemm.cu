@@ -297,6 +297,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             uint32_t run[RUN];
 #pragma unroll
             for (int q = 0; q < RUN; ++q) run[q] = 0u;
+            // planed (client) tiles are short in K: their epilogue inputs (Query noise, Recover
+            // answers) are loaded when the tile starts, so the loads overlap its MMAs
+            constexpr int EARLY = PLANED ? QPT : 1;
+            uint32_t early[EARLY];
+            if constexpr (PLANED) {
+                const uint32_t erow = m0 + quarter * 32u + static_cast<uint32_t>(lane);
+#pragma unroll
+                for (int q = 0; q < QPT; ++q) early[q] = (erow < M && v0 + q < NV) ? epi.pre(erow, v0 + q) : 0u;
+            }
             for (uint32_t c = pc.c0; c < pc.c1; ++c, ++ci) {
                 const uint32_t buf = ci & 1u;
                 if (!mbar_wait(&acc_full[buf], (ci >> 1) & 1u, abort)) {
@@ -439,6 +448,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                         if (v0 + q < NV) epi.add(row, v0 + q, run[q]);
                     continue;
                 }
+            }
+            if constexpr (PLANED) {
+                if (row < M) {
+#pragma unroll
+                    for (int q = 0; q < QPT; ++q)
+                        if (v0 + q < NV) epi.put(row, v0 + q, run[q], early[q]);
+                }
+                continue;
             }
             if (row < M) {
                 // groups of up to 16 outputs: all their loads first, then all their stores
