@@ -58,6 +58,10 @@ def _load():
             lib.oracle_chor_query.argtypes = [P, u64, u64, u64, P]
             lib.oracle_chor_reconstruct.argtypes = [P, u64, u64, P]
             lib.oracle_goldberg_answer.argtypes = [P, u64, u64, P, u64, u32, P, i32]
+            lib.oracle_delta_width.argtypes = [P, u64, u64]
+            lib.oracle_delta_width.restype = u32
+            lib.oracle_delta_encode.argtypes = [P, u64, u64, u32, P]
+            lib.oracle_delta_decode.argtypes = [P, u64, u32, P]
             lib.oracle_goldberg_query.argtypes = [P, u64, u64, u64, P, u64, u32, P]
             lib.oracle_goldberg_reconstruct.argtypes = [P, P, u64, u64, u32, P]
             lib.oracle_max_threads.restype = i32
@@ -242,4 +246,33 @@ def goldberg_reconstruct(responses: np.ndarray, alpha: np.ndarray, p: int) -> np
     k, R = responses.shape
     out = np.empty(R, dtype=np.uint32)
     _load().oracle_goldberg_reconstruct(_p(responses), _p(alpha), k, R, p, _p(out))
+    return out
+
+
+def delta_width(x: np.ndarray, E: int) -> int:
+    """Bytes per stored difference for entries x grouped in blocks of E (Sec. 5.3)."""
+    x = _c(x, np.uint32)
+    if x.ndim != 1 or x.size == 0 or E < 1:
+        raise ValueError("x: non-empty 1-D entries; E >= 1")
+    return int(_load().oracle_delta_width(_p(x), x.size, E))
+
+
+def delta_encode(x: np.ndarray, E: int, w: int) -> np.ndarray:
+    """Compressed database (R' x C digits, record j = column j) of entries x (Sec. 5.3)."""
+    x = _c(x, np.uint32)
+    if x.ndim != 1 or x.size == 0 or E < 1 or not 1 <= w <= 4:
+        raise ValueError("x: non-empty 1-D entries; E >= 1; w in 1..4")
+    C = (x.size + E - 1) // E
+    db = np.empty((4 + w * (E - 1), C), dtype=np.uint8)
+    _load().oracle_delta_encode(_p(x), x.size, E, w, _p(db))
+    return db
+
+
+def delta_decode(digits: np.ndarray, E: int, w: int) -> np.ndarray:
+    """The E entries of one block from its R' = 4 + w (E - 1) digits (Sec. 5.3)."""
+    digits = _c(digits, np.uint8)
+    if digits.shape != (4 + w * (E - 1),):
+        raise ValueError("digits: one block of 4 + w (E - 1) digits")
+    out = np.empty(E, dtype=np.uint32)
+    _load().oracle_delta_decode(_p(digits), E, w, _p(out))
     return out

@@ -282,6 +282,74 @@ void oracle_goldberg_reconstruct(const uint32_t *responses, const uint32_t *alph
     }
 }
 
+/* ---------------------------------------------------------------------
+ * Database compression (Sec. 5.3, "Database Compression Techniques"): the
+ * DB entries are sorted and each is stored as its difference from the entry
+ * before it, so that close entries take fewer bits.  Reading taken here: the
+ * entries are 32-bit unsigned integers x_0 <= x_1 <= ... <= x_{N-1}; block j
+ * (one PIR record, a column of the database) holds entries jE .. jE + E - 1,
+ * positions past N - 1 repeating x_{N-1}; a block is stored as the first
+ * entry in full (4 little-endian bytes) followed by the E - 1 differences
+ * x_{jE+i} - x_{jE+i-1} (mod 2^32), each in w little-endian bytes, w the
+ * fewest bytes that hold every such difference in the database.  A block is
+ * therefore R' = 4 + w (E - 1) digits and decodes on its own by prefix sums.
+ * ------------------------------------------------------------------- */
+
+/* Entry k of the padded sequence (positions past n - 1 repeat the last entry). */
+static uint32_t oracle_entry(const uint32_t *x, uint64_t n, uint64_t k)
+{
+    return k < n ? x[k] : x[n - 1];
+}
+
+/* The byte width w in 1..4 of the largest within-block difference. */
+uint32_t oracle_delta_width(const uint32_t *x, uint64_t n, uint64_t E)
+{
+    uint32_t dmax = 0;
+    const uint64_t blocks = (n + E - 1) / E;
+    for (uint64_t j = 0; j < blocks; ++j)
+        for (uint64_t i = 1; i < E; ++i) {
+            const uint32_t d = oracle_entry(x, n, j * E + i) - oracle_entry(x, n, j * E + i - 1);
+            if (d > dmax)
+                dmax = d;
+        }
+    uint32_t w = 1;
+    while (w < 4 && dmax >= (1u << (8 * w)))
+        ++w;
+    return w;
+}
+
+/* Compressed database: R' x C digits, row-major (digit k of block j at k * C + j). */
+void oracle_delta_encode(const uint32_t *x, uint64_t n, uint64_t E, uint32_t w, uint8_t *db)
+{
+    const uint64_t C = (n + E - 1) / E;
+    for (uint64_t j = 0; j < C; ++j) {
+        const uint32_t first = oracle_entry(x, n, j * E);
+        for (uint32_t b = 0; b < 4; ++b)
+            db[b * C + j] = (uint8_t)(first >> (8 * b));
+        for (uint64_t i = 1; i < E; ++i) {
+            const uint32_t d = oracle_entry(x, n, j * E + i) - oracle_entry(x, n, j * E + i - 1);
+            for (uint32_t b = 0; b < w; ++b)
+                db[(4 + (i - 1) * w + b) * C + j] = (uint8_t)(d >> (8 * b));
+        }
+    }
+}
+
+/* One block's E entries from its R' digits (prefix sums of the differences, mod 2^32). */
+void oracle_delta_decode(const uint8_t *digits, uint64_t E, uint32_t w, uint32_t *out)
+{
+    uint32_t v = 0;
+    for (uint32_t b = 0; b < 4; ++b)
+        v |= (uint32_t)digits[b] << (8 * b);
+    out[0] = v;
+    for (uint64_t i = 1; i < E; ++i) {
+        uint32_t d = 0;
+        for (uint32_t b = 0; b < w; ++b)
+            d |= (uint32_t)digits[4 + (i - 1) * w + b] << (8 * b);
+        v += d;
+        out[i] = v;
+    }
+}
+
 int oracle_max_threads(void)
 {
 #ifdef _OPENMP

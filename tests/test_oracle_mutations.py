@@ -60,6 +60,14 @@ MUTATIONS = [
     ("goldberg Lagrange denominator sign", "den = den * ((alpha[m] + p - alpha[s]) % p) % p;",
      "den = den * ((alpha[s] + p - alpha[m]) % p) % p;"),
     ("goldberg Lagrange numerator point", "num = num * alpha[m] % p;", "num = num * alpha[s] % p;"),
+    ("delta first entry big-endian", "db[b * C + j] = (uint8_t)(first >> (8 * b));",
+     "db[b * C + j] = (uint8_t)(first >> (8 * (3 - b)));"),
+    ("delta width one byte short", "while (w < 4 && dmax >= (1u << (8 * w)))", "while (w < 4 && dmax > (1u << (8 * w)))"),
+    ("delta difference two back", "- oracle_entry(x, n, j * E + i - 1);\n            for (uint32_t b = 0; b < w; ++b)",
+     "- oracle_entry(x, n, j * E + (i >= 2 ? i - 2 : 0));\n            for (uint32_t b = 0; b < w; ++b)"),
+    ("delta decode byte order", "d |= (uint32_t)digits[4 + (i - 1) * w + b] << (8 * b);",
+     "d |= (uint32_t)digits[4 + (i - 1) * w + b] << (8 * (w - 1 - b));"),
+    ("delta padding with zeros", "return k < n ? x[k] : x[n - 1];", "return k < n ? x[k] : 0u;"),
 ]
 
 

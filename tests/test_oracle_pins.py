@@ -434,3 +434,61 @@ def test_goldberg_ftr_protocol_recovers_the_record(p, t, ell):
         for sub in (list(range(t + 1)), list(range(ell - t - 1, ell))):
             rec = oracle.goldberg_reconstruct(responses[sub], alpha[sub], p)
             assert np.array_equal(rec, D[:, theta].astype(np.uint32))
+
+
+# ---------------------------------------------------------------- database compression (Sec. 5.3)
+def test_delta_hand_example():
+    # entries 5, 7, 300, 301 in blocks of two: differences 2 and 1 fit one byte; each block is its
+    # first entry in four little-endian bytes (300 = 1 * 256 + 44), then the difference
+    x = np.array([5, 7, 300, 301], dtype=np.uint32)
+    assert oracle.delta_width(x, 2) == 1
+    db = oracle.delta_encode(x, 2, 1)
+    assert db.shape == (5, 2)
+    assert db[:, 0].tolist() == [5, 0, 0, 0, 2]
+    assert db[:, 1].tolist() == [44, 1, 0, 0, 1]
+    assert oracle.delta_decode(db[:, 1], 2, 1).tolist() == [300, 301]
+    # a difference of exactly 256 needs a second byte; 255 does not
+    assert oracle.delta_width(np.array([0, 256], dtype=np.uint32), 2) == 2
+    assert oracle.delta_width(np.array([0, 255], dtype=np.uint32), 2) == 1
+
+
+def _delta_brute(x, E, w):
+    """Independent restatement in Python integers: padded blocks, first entry, differences."""
+    n = len(x)
+    C = (n + E - 1) // E
+    pad = [int(v) for v in x] + [int(x[-1])] * (C * E - n)
+    cols = []
+    for j in range(C):
+        blk = pad[j * E:(j + 1) * E]
+        digits = [(blk[0] >> (8 * b)) & 255 for b in range(4)]
+        for i in range(1, E):
+            d = (blk[i] - blk[i - 1]) % (1 << 32)
+            digits += [(d >> (8 * b)) & 255 for b in range(w)]
+        cols.append(digits)
+    return np.array(cols, dtype=np.uint8).T, pad
+
+
+@pytest.mark.parametrize("n,E,gap", [(1000, 16, 40), (1000, 7, 300), (37, 5, 70000), (8, 1, 3), (5, 8, 9)])
+def test_delta_round_trip_width_and_size(n, E, gap):
+    rng = np.random.default_rng(n + E)
+    x = np.cumsum(rng.integers(0, gap, n, dtype=np.uint64)).astype(np.uint32)   # sorted unless it wraps
+    w = oracle.delta_width(x, E)
+    C = (n + E - 1) // E
+    _, pad = _delta_brute(x, E, 4)
+    diffs = [(pad[j * E + i] - pad[j * E + i - 1]) % (1 << 32) for j in range(C) for i in range(1, E)]
+    dmax = max(diffs) if diffs else 0
+    assert dmax < 256 ** w and (w == 1 or dmax >= 256 ** (w - 1))   # the fewest bytes that hold them
+    db = oracle.delta_encode(x, E, w)
+    exp, pad = _delta_brute(x, E, w)
+    assert db.shape == (4 + w * (E - 1), C)
+    assert np.array_equal(db, exp)
+    for j in range(C):
+        assert oracle.delta_decode(db[:, j], E, w).tolist() == pad[j * E:(j + 1) * E]
+
+
+def test_delta_unsorted_entries_wrap():
+    # a decreasing pair stores its difference mod 2^32 (four bytes) and still decodes exactly
+    x = np.array([10, 3, 2 ** 32 - 1, 0], dtype=np.uint32)
+    w = oracle.delta_width(x, 4)
+    assert w == 4
+    assert oracle.delta_decode(oracle.delta_encode(x, 4, w)[:, 0], 4, w).tolist() == x.tolist()
