@@ -289,6 +289,40 @@ int qpadl_pir_recover_batch(const qpadl_params *prm, const uint32_t *ans_dev,
                             const uint32_t *H_dev, const uint32_t *S_dev, uint32_t B,
                             uint8_t *out_dev, qpadl_stream_t stream);
 
+/* ======================================================================
+ * Database compression (Sec. 5.3, "Database Compression Techniques"): the
+ * DB entries are sorted and stored as differences between successive
+ * entries, so that close entries take fewer bits and each Response scans
+ * fewer bytes.  Layout: entries are uint32 x_0 <= ... <= x_{n-1} (device);
+ * block j (one record = one column of the database) holds entries
+ * jE .. jE + E - 1, positions past n - 1 repeating x_{n-1}.  A block is its
+ * first entry (4 little-endian bytes) followed by its E - 1 differences
+ * x_{jE+i} - x_{jE+i-1} mod 2^32 in w little-endian bytes each, so the
+ * compressed database is R' = 4 + w (E - 1) rows by C = ceil(n / E) columns
+ * of digits (row-major uint8, p = 256), on which qpadl_pir_setup, hint,
+ * Query, Answer and Recover run unchanged.  Unsorted entries still round-trip
+ * exactly (the differences wrap mod 2^32) but need a larger w.
+ * All three calls: QPADL_EINVAL for a NULL pointer, n or E of 0, w outside
+ * 1..4, or R' or C at or above 2^31.
+ * ==================================================================== */
+
+/* The fewest bytes w (1..4) holding every within-block difference of the n
+ * entries.  Synchronises `stream` (the result is returned on the host);
+ * allocates one word of stream-ordered device memory for the reduction. */
+int qpadl_pir_delta_width(const uint32_t *entries_dev, uint64_t n, uint32_t E, uint32_t *w_out,
+                          qpadl_stream_t stream);
+
+/* Writes the compressed database: db_dev receives R' x C digits (caller-
+ * owned, R' * C bytes).  Asynchronous on `stream`; allocates nothing. */
+int qpadl_pir_delta_encode(const uint32_t *entries_dev, uint64_t n, uint32_t E, uint32_t w,
+                           uint8_t *db_dev, qpadl_stream_t stream);
+
+/* Decodes B recovered blocks: digits_dev B x R' (block b's digits at
+ * b * R', as qpadl_pir_recover[_batch] writes them), entries_dev B x E
+ * (entry i of block b at b * E + i).  Asynchronous; allocates nothing. */
+int qpadl_pir_delta_decode(const uint8_t *digits_dev, uint32_t B, uint32_t E, uint32_t w,
+                           uint32_t *entries_dev, qpadl_stream_t stream);
+
 /*
  * Status of the handle-free single-vector Query and Recover kernels.  For
  * n in {512, 1024, 2048} (with 16-byte aligned matrix and secret) those two

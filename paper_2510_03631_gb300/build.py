@@ -20,7 +20,7 @@ LIB = os.path.join(BUILD, "libqpadl_pir.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["qpadl_pir.cu", "stream_answer.cu", "limb_gemm.cu", "limb_gemm_u8.cu", "client.cu", "noalloc.cu",
-           "server.cu", "chor.cu", "selftest.cu"]
+           "server.cu", "chor.cu", "selftest.cu", "delta.cu"]
 
 
 def _nvcc() -> str:

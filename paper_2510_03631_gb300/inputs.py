@@ -192,6 +192,16 @@ def chor_queries(batch: int, rows: int, seed: int) -> np.ndarray:
     return Q
 
 
+def sorted_entries(n: int, seed: int, max_gap: int) -> np.ndarray:
+    """n sorted 32-bit entries (uint32): a seeded start plus cumulative gaps uniform in
+    [0, max_gap], the shape of sorted spectrum records (frequencies, times) whose
+    neighbours are close.  The sums wrap mod 2^32 only if n * max_gap exceeds it."""
+    u = stream_u64(seed, TAG_MISC, 0, n + 1)
+    gaps = (u[1:] >> np.uint64(32)) * np.uint64(max_gap + 1) >> np.uint64(32)
+    start = u[0] >> np.uint64(40)   # below 2^24
+    return ((start + np.cumsum(gaps, dtype=np.uint64)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+
+
 WORKLOADS = {
     "tiny": dict(rows=1024, cols=1024, n=512, p=256, sigma=6.4),
     "single_1gib": dict(rows=32768, cols=32768, n=1024, p=256, sigma=6.4),
@@ -201,4 +211,7 @@ WORKLOADS = {
                     n=1024, p=256, sigma=6.4, skew=(0.60, 0.25, 0.10, 0.05)),
     # Chor Response over GF(2): 1 GiB of bits, 32768 records of 32 KiB (262144 bits)
     "chor_1gib": dict(rows=32768, bits=262144, batches=(1, 8, 32, 128, 256, 1024)),
+    # Sec. 5.3 compression: 2^28 sorted 32-bit entries (1 GiB as plain blocks of 8192 entries,
+    # i.e. the 32768 x 32768 database) with gaps uniform in [0, 31], so differences fit one byte
+    "delta_1gib": dict(entries=1 << 28, block=8192, max_gap=31, n=1024, p=256, sigma=6.4),
 }

@@ -114,6 +114,9 @@ _SIGS = {
     "qpadl_server_replay": ([_P, ctypes.c_uint64, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "qpadl_pir_recover_batch": ([_P, _P, _P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
     "qpadl_pir_client_status": ([], ctypes.c_int),
+    "qpadl_pir_delta_width": ([_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32), _P], ctypes.c_int),
+    "qpadl_pir_delta_encode": ([_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _P, _P], ctypes.c_int),
+    "qpadl_pir_delta_decode": ([_P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _P, _P], ctypes.c_int),
 }
 
 
@@ -332,6 +335,38 @@ def qpadl_pir_recover_batch(prm: qpadl_params, ans: torch.Tensor, H: torch.Tenso
         ctypes.byref(prm), _dev(ans, torch.int32, B * R, "ans"), _dev(H, torch.int32, R * n, "H"),
         _dev(S, torch.int32, B * n, "S"), B, _dev(out, torch.uint8, B * R, "out"), _stream(stream)),
         "qpadl_pir_recover_batch")
+    return out
+
+
+def delta_rows(E: int, w: int) -> int:
+    """Rows R' = 4 + w (E - 1) of a compressed database (Sec. 5.3)."""
+    return 4 + w * (E - 1)
+
+
+def qpadl_pir_delta_width(entries: torch.Tensor, E: int, stream=None) -> int:
+    """Bytes per stored difference for the entries in blocks of E (synchronises the stream)."""
+    w = ctypes.c_uint32(0)
+    _check(load().qpadl_pir_delta_width(_dev(entries, torch.int32, entries.numel(), "entries"), entries.numel(), E,
+                                        ctypes.byref(w), _stream(stream)), "qpadl_pir_delta_width")
+    return int(w.value)
+
+
+def qpadl_pir_delta_encode(entries: torch.Tensor, E: int, w: int, db: torch.Tensor, stream=None) -> torch.Tensor:
+    """Compressed database (R' x C uint8 digits) of the entries (Sec. 5.3)."""
+    n = entries.numel()
+    C = (n + E - 1) // E
+    _check(load().qpadl_pir_delta_encode(_dev(entries, torch.int32, n, "entries"), n, E, w,
+                                         _dev(db, torch.uint8, delta_rows(E, w) * C, "db"), _stream(stream)),
+           "qpadl_pir_delta_encode")
+    return db
+
+
+def qpadl_pir_delta_decode(digits: torch.Tensor, B: int, E: int, w: int, out: torch.Tensor,
+                           stream=None) -> torch.Tensor:
+    """Entries (B x E) of B recovered blocks (B x R' digits)."""
+    _check(load().qpadl_pir_delta_decode(_dev(digits, torch.uint8, B * delta_rows(E, w), "digits"), B, E, w,
+                                         _dev(out, torch.int32, B * E, "out"), _stream(stream)),
+           "qpadl_pir_delta_decode")
     return out
 
 

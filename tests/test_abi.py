@@ -98,3 +98,20 @@ def test_invalid_server_config_rejected_before_any_allocation(lib, field, value)
 def test_replay_rejects_a_null_server(lib):
     from paper_2510_03631_gb300 import pir
     assert lib.qpadl_server_replay(None, 0, None, None, None, None, None, None, None) == pir.QPADL_EINVAL
+
+
+def test_delta_compression_calls_reject_bad_arguments(lib):
+    # NULL pointers, an empty entry list, empty blocks and byte widths outside 1..4 fail before any
+    # device work
+    from paper_2510_03631_gb300 import pir
+    w = ctypes.c_uint32(0)
+    buf = ctypes.c_void_p(16)   # never dereferenced: every call below fails validation first
+    assert lib.qpadl_pir_delta_width(None, 10, 4, ctypes.byref(w), None) == pir.QPADL_EINVAL
+    assert lib.qpadl_pir_delta_width(buf, 0, 4, ctypes.byref(w), None) == pir.QPADL_EINVAL
+    assert lib.qpadl_pir_delta_width(buf, 10, 0, ctypes.byref(w), None) == pir.QPADL_EINVAL
+    for E, wd in ((0, 1), (4, 0), (4, 5)):
+        assert lib.qpadl_pir_delta_encode(buf, 10, E, wd, buf, None) == pir.QPADL_EINVAL
+        assert lib.qpadl_pir_delta_decode(buf, 1, E, wd, buf, None) == pir.QPADL_EINVAL
+    assert lib.qpadl_pir_delta_encode(None, 10, 4, 1, buf, None) == pir.QPADL_EINVAL
+    assert lib.qpadl_pir_delta_decode(buf, 0, 4, 1, buf, None) == pir.QPADL_EINVAL
+    assert lib.qpadl_pir_delta_decode(buf, 1, 1 << 30, 4, buf, None) == pir.QPADL_EINVAL   # R' >= 2^31
