@@ -436,6 +436,89 @@ def goldberg_measure(torch, pir, inputs, seed=41):
     return res
 
 
+def delta_measure(torch, pir, inputs, plain_ms, seed=51):
+    """Sec. 5.3 database compression on 2^28 sorted 32-bit entries (1 GiB as plain
+    8192-entry blocks, the 32768 x 32768 database): width and encoding at setup, the
+    single-query Response on the compressed R' x C database against the plain one, and
+    a checked private retrieval of blocks (Query -> Answer -> Recover -> decode)."""
+    w_ = inputs.WORKLOADS["delta_1gib"]
+    N, E, gap, n_lwe = w_["entries"], w_["block"], w_["max_gap"], w_["n"]
+    x_np = inputs.sorted_entries(N, seed=seed, max_gap=gap)
+    x = torch.from_numpy(x_np.view(np.int32)).cuda()
+    C = (N + E - 1) // E
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t0 = time.perf_counter()
+    w = pir.qpadl_pir_delta_width(x, E)
+    width_ms = (time.perf_counter() - t0) * 1e3
+    Rp = pir.delta_rows(E, w)
+    db = torch.empty(Rp * C, dtype=torch.uint8, device="cuda")
+    encode_ms = timed(lambda: pir.qpadl_pir_delta_encode(x, E, w, db), 3)
+    prm = pir.params(Rp, C, n_lwe, seed=seed)
+    h = pir.qpadl_pir_setup(prm, db)
+    pir.qpadl_pir_autotune(h, 64)
+    A = torch.empty(C * n_lwe, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_gen_a(prm, A)
+    H = torch.empty(Rp * n_lwe, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_hint(h, A, H)
+    # single-query Response, 64 back-to-back launches over distinct queries per replay
+    P = 64
+    Qs = pir.from_u32(inputs.uniform_u32(P * C, seed=seed + 1, tag=inputs.TAG_MISC))
+    ans = torch.empty(P * Rp, dtype=torch.int32, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for i in range(P):
+            pir.qpadl_pir_answer(h, Qs[i * C:(i + 1) * C], ans[i * Rp:(i + 1) * Rp])
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for i in range(P):
+            pir.qpadl_pir_answer(h, Qs[i * C:(i + 1) * C], ans[i * Rp:(i + 1) * Rp])
+    resp_ms = timed(g.replay, 20) / P
+    # private retrieval of B blocks, checked against the entries
+    B = 8
+    cols = inputs.target_columns(B, C, seed=seed + 2)
+    S = pir.from_u32(inputs.secrets(B, n_lwe, seed=seed + 3).reshape(-1))
+    Eq = torch.from_numpy(inputs.noise_batch(B, C, seed=seed + 4).reshape(-1)).cuda()
+    Q = torch.empty(B * C, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_query_batch(prm, A, S, Eq, torch.from_numpy(cols.astype(np.int32)).cuda(), Q)
+    ansB = torch.empty(B * Rp, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_answer_batch(h, Q, ansB)
+    digits = torch.empty(B * Rp, dtype=torch.uint8, device="cuda")
+    pir.qpadl_pir_recover_batch(prm, ansB, H, S, digits)
+    entries = torch.empty(B * E, dtype=torch.int32, device="cuda")
+    pir.qpadl_pir_delta_decode(digits, B, E, w, entries)
+    decode_ms = timed(lambda: pir.qpadl_pir_delta_decode(digits, B, E, w, entries), 10)
+    got = pir.as_u32(entries).reshape(B, E)
+    exp = np.stack([x_np[c * E:(c + 1) * E] for c in cols])   # N is a multiple of E here
+    if not np.array_equal(got, exp) or pir.qpadl_pir_status(h) != 0:
+        raise SystemExit("bench: entries retrieved from the compressed database differ")
+    h.close()
+    plain_bytes, comp_bytes = 4 * N, Rp * C
+    return {"workload": f"{N} sorted 32-bit entries, blocks of {E} (plain: {E * 4} x {C} digits = 1 GiB), "
+                        f"gaps uniform in [0, {gap}]",
+            "width_bytes": w, "rows_compressed": Rp, "compressed_bytes": comp_bytes,
+            "ratio": round(plain_bytes / comp_bytes, 3),
+            "width_ms": round(width_ms, 3), "encode_ms": round(encode_ms, 3),
+            "response_ms": round(resp_ms, 4), "response_plain_ms": round(plain_ms, 4),
+            "speedup_vs_plain": round(plain_ms / resp_ms, 2),
+            "scan_gbs": round(comp_bytes / (resp_ms * 1e-3) / 1e9, 1),
+            "logical_gbs": round(plain_bytes / (resp_ms * 1e-3) / 1e9, 1),
+            "decode_ms_8_blocks": round(decode_ms, 4), "retrieval_checked_blocks": B}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_ours(args):
     import torch
@@ -736,7 +819,7 @@ def run_ours(args):
     e2e_check()
 
     serving = None
-    chor = goldberg = None
+    chor = goldberg = delta = None
     if extras:
         db.close()
         del D
@@ -747,6 +830,8 @@ def run_ours(args):
         chor = chor_measure(torch, pir, inputs)
         torch.cuda.empty_cache()
         goldberg = goldberg_measure(torch, pir, inputs)
+        torch.cuda.empty_cache()
+        delta = delta_measure(torch, pir, inputs, resp_ms_avg)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -790,6 +875,7 @@ def run_ours(args):
         "serving": serving,
         "chor_gf2": chor,
         "goldberg_zp": goldberg,
+        "compressed_db": delta,
         "gpu_launches": (3 if raw else 4) * K,
         "autotune": tune,
         "timing": f"CUDA events around K steps replayed as CUDA graphs of {P} consecutive steps (distinct queries)",
