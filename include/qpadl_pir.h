@@ -313,7 +313,8 @@ int qpadl_pir_delta_width(const uint32_t *entries_dev, uint64_t n, uint32_t E, u
                           qpadl_stream_t stream);
 
 /* Writes the compressed database: db_dev receives R' x C digits (caller-
- * owned, R' * C bytes).  Asynchronous on `stream`; allocates nothing. */
+ * owned, R' * C bytes).  Asynchronous on `stream`; allocates nothing.  Also
+ * QPADL_EINVAL for blocks of more than 4,194,241 entries (E - 1 > 64 * 65535). */
 int qpadl_pir_delta_encode(const uint32_t *entries_dev, uint64_t n, uint32_t E, uint32_t w,
                            uint8_t *db_dev, qpadl_stream_t stream);
 

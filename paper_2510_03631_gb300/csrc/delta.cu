@@ -15,8 +15,9 @@
 // block j decodes it on its own by prefix sums.
 //
 //   delta_width_kernel   largest within-block difference (atomic max)
-//   delta_encode_kernel  one thread per database byte, columns fastest, so
-//                        every row of the database is written coalesced
+//   delta_encode_kernel  a CTA per 128 blocks x 64 differences: the entries
+//                        staged in shared memory (read block by block), the
+//                        database rows written 128 bytes at a time
 //   delta_decode_kernel  one CTA per recovered block: per-thread runs of
 //                        differences, a CTA-wide exclusive scan of the run
 //                        totals, then each run's prefix sums
@@ -48,24 +49,46 @@ __global__ void delta_width_kernel(const uint32_t *__restrict__ x, uint64_t n, u
     if ((threadIdx.x & 31) == 0 && m) atomicMax(dmax, m);
 }
 
-// Byte (row k, column j) of the compressed database.
-__global__ void delta_encode_kernel(const uint32_t *__restrict__ x, uint64_t n, uint64_t E, uint32_t w, uint64_t C,
-                                    uint64_t Rp, uint8_t *__restrict__ db) {
-    const uint64_t total = Rp * C;
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t k = t / C, j = t - k * C;
-        uint32_t v;
-        uint32_t byte;
-        if (k < 4) {
-            v = entry_at(x, n, j * E);
-            byte = static_cast<uint32_t>(k);
-        } else {
-            const uint64_t i = 1 + (k - 4) / w;
-            byte = static_cast<uint32_t>((k - 4) % w);
-            v = entry_at(x, n, j * E + i) - entry_at(x, n, j * E + i - 1);
+// A CTA writes the rows of kEncCols consecutive blocks (columns) that hold
+// differences kEncEntries * blockIdx.y + 1 .. + kEncEntries (and the CTAs with
+// blockIdx.y == 0 also the 4 rows of the first entries).  The entries it needs
+// are read block by block (consecutive entries of one block are contiguous)
+// into shared memory, so both the reads and the row writes are coalesced.
+constexpr int kEncCols = 128;     // columns per CTA: each database row segment is 128 bytes
+constexpr int kEncEntries = 64;   // differences per block per CTA
+constexpr int kEncThreads = 256;
+
+__global__ void __launch_bounds__(kEncThreads) delta_encode_kernel(const uint32_t *__restrict__ x, uint64_t n,
+                                                                   uint64_t E, uint32_t w, uint64_t C,
+                                                                   uint8_t *__restrict__ db) {
+    __shared__ uint32_t ent[kEncCols][kEncEntries + 1];   // entries i0 - 1 .. i0 + kEncEntries - 1
+    const uint64_t j0 = (uint64_t)blockIdx.x * kEncCols;
+    const uint64_t i0 = 1 + (uint64_t)blockIdx.y * kEncEntries;   // first difference of this CTA
+    const uint64_t ncols = C - j0 < (uint64_t)kEncCols ? C - j0 : (uint64_t)kEncCols;
+    const uint64_t i1 = i0 + kEncEntries < E ? i0 + kEncEntries : E;   // differences [i0, i1)
+    // stage entries (block j0 + c, positions i0 - 1 .. i1 - 1): a warp reads one block's run
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint64_t c = warp; c < ncols; c += kEncThreads / 32)
+        for (uint64_t t = lane; t <= i1 - i0; t += 32)
+            ent[c][t] = entry_at(x, n, (j0 + c) * E + i0 - 1 + t);
+    __syncthreads();
+    // rows of this CTA's differences: row 4 + (i - 1) w + b, column j0 + c; threads run over
+    // (row, column) with the column fastest
+    const uint64_t rows = (i1 - i0) * w;
+    const uint64_t row0 = 4 + (i0 - 1) * w;
+    for (uint64_t t = threadIdx.x; t < rows * kEncCols; t += kEncThreads) {
+        const uint64_t r = t / kEncCols, c = t % kEncCols;
+        if (c >= ncols) continue;
+        const uint64_t di = r / w;   // difference i0 + di
+        const uint32_t b = static_cast<uint32_t>(r % w);
+        const uint32_t d = ent[c][di + 1] - ent[c][di];
+        db[(row0 + r) * C + j0 + c] = static_cast<uint8_t>(d >> (8u * b));
+    }
+    if (blockIdx.y == 0) {   // the first entry of each block in full
+        for (uint64_t t = threadIdx.x; t < 4 * (uint64_t)kEncCols; t += kEncThreads) {
+            const uint64_t r = t / kEncCols, c = t % kEncCols;
+            if (c < ncols) db[r * C + j0 + c] = static_cast<uint8_t>(ent[c][0] >> (8u * r));
         }
-        db[t] = static_cast<uint8_t>(v >> (8u * byte));
     }
 }
 
@@ -157,10 +180,13 @@ int qpadl_pir_delta_encode(const uint32_t *entries_dev, uint64_t n, uint32_t E, 
     if (!entries_dev || !db_dev || !delta_shape_ok(n, E, w)) return QPADL_EINVAL;
     const int sms = num_sms_current();
     if (sms <= 0) return QPADL_ECUDA;
+    (void)sms;
     const uint64_t C = (n + E - 1) / E;
-    const uint64_t Rp = 4 + (uint64_t)w * (E - 1);
-    delta_encode_kernel<<<sms * 16, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(entries_dev, n, E, w, C, Rp,
-                                                                                      db_dev);
+    const uint64_t ytiles = E > 1 ? (E - 1 + kEncEntries - 1) / kEncEntries : 1;
+    if (ytiles > 65535) return QPADL_EINVAL;   // blocks of more than 4 million entries
+    const dim3 grid(static_cast<unsigned>((C + kEncCols - 1) / kEncCols), static_cast<unsigned>(ytiles));
+    delta_encode_kernel<<<grid, kEncThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(entries_dev, n, E, w, C,
+                                                                                          db_dev);
     return cudaGetLastError() == cudaSuccess ? QPADL_OK : QPADL_ECUDA;
 }
 

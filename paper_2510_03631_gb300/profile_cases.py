@@ -103,10 +103,46 @@ def _goldberg_case(a):
     h.close()
 
 
+def _delta_case(a):
+    """Sec. 5.3 compression: width, encoding of rows x 8192 sorted entries (blocks of E = 8192), and
+    decoding of `batch` blocks taken from the encoded database; checked by host prefix sums."""
+    E, C = 8192, a.rows
+    n = C * E
+    x_np = inputs.sorted_entries(n, seed=5, max_gap=31)
+    x = torch.from_numpy(x_np.view(np.int32)).cuda()
+    w = pir.qpadl_pir_delta_width(x, E)
+    Rp = pir.delta_rows(E, w)
+    db = torch.empty(Rp * C, dtype=torch.uint8, device="cuda")
+    B = min(a.batch, C)
+    blocks = torch.empty(B * Rp, dtype=torch.uint8, device="cuda")
+    out = torch.empty(B * E, dtype=torch.int32, device="cuda")
+
+    def fn():
+        pir.qpadl_pir_delta_encode(x, E, w, db)
+        blocks.copy_(db.view(Rp, C)[:, :B].t().reshape(-1))
+        pir.qpadl_pir_delta_decode(blocks, B, E, w, out)
+
+    fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(a.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    got = pir.as_u32(out).reshape(B, E)
+    if not np.array_equal(got, x_np[:B * E].reshape(B, E)):
+        raise SystemExit("profile case: decoded blocks differ from the entries")
+    print(json.dumps({"case": "delta", "blocks": C, "block_entries": E, "width": w, "rows_compressed": Rp,
+                      "decoded_blocks": B, "ms": times, "entry_bytes": 4 * n, "db_bytes": Rp * C}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["stream", "gemm", "hint", "query", "recover", "qbatch", "rbatch", "chor",
-                                     "goldberg"])
+                                     "goldberg", "delta"])
     ap.add_argument("--rows", type=int, default=8192)
     ap.add_argument("--cols", type=int, default=32768)
     ap.add_argument("--bits", type=int, default=262144, help="chor: bits per record")
@@ -126,6 +162,8 @@ def main():
         return _chor_case(a)
     if a.case == "goldberg":
         return _goldberg_case(a)
+    if a.case == "delta":
+        return _delta_case(a)
     R, C = a.rows, a.cols
     D_np = inputs.db_digits(R, C, 256, seed=1)
     prm = pir.params(R, C, a.n, seed=1)
