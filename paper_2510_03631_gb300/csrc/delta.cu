@@ -14,9 +14,10 @@
 // Response, Recover and hint run on it unchanged.  A client that recovers
 // block j decodes it on its own by prefix sums.
 //
-//   delta_width_kernel   largest within-block difference (atomic max)
+//   delta_width_kernel   largest within-block difference: a warp per block,
+//                        a warp max, one atomic max per warp
 //   delta_encode_kernel  a CTA per 128 blocks x 64 differences: the entries
-//                        staged in shared memory (read block by block), the
+//                        staged in shared memory (read run by run), the
 //                        database rows written 128 bytes at a time
 //   delta_decode_kernel  one CTA per recovered block: per-thread runs of
 //                        differences, a CTA-wide exclusive scan of the run
@@ -32,28 +33,30 @@ __device__ __forceinline__ uint32_t entry_at(const uint32_t *__restrict__ x, uin
     return x[k < n ? k : n - 1];
 }
 
-__global__ void delta_width_kernel(const uint32_t *__restrict__ x, uint64_t n, uint64_t E, uint64_t total,
+// One warp per block (grid-stride over blocks), lanes striding over its differences.
+__global__ void delta_width_kernel(const uint32_t *__restrict__ x, uint64_t n, uint64_t E, uint64_t C,
                                    uint32_t *__restrict__ dmax) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     uint32_t m = 0;
-    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
-         k += (uint64_t)gridDim.x * blockDim.x) {
-        if (k % E == 0) continue;
-        const uint32_t d = entry_at(x, n, k) - entry_at(x, n, k - 1);
-        m = d > m ? d : m;
-    }
+    for (uint64_t j = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < C; j += warps)
+        for (uint64_t i = 1 + lane; i < E; i += 32) {
+            const uint32_t d = entry_at(x, n, j * E + i) - entry_at(x, n, j * E + i - 1);
+            m = d > m ? d : m;
+        }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const uint32_t other = __shfl_xor_sync(0xffffffffu, m, o);
         m = other > m ? other : m;
     }
-    if ((threadIdx.x & 31) == 0 && m) atomicMax(dmax, m);
+    if (lane == 0 && m) atomicMax(dmax, m);
 }
 
 // A CTA writes the rows of kEncCols consecutive blocks (columns) that hold
 // differences kEncEntries * blockIdx.y + 1 .. + kEncEntries (and the CTAs with
 // blockIdx.y == 0 also the 4 rows of the first entries).  The entries it needs
-// are read block by block (consecutive entries of one block are contiguous)
-// into shared memory, so both the reads and the row writes are coalesced.
+// are read run by run (consecutive entries of one block are contiguous) into
+// shared memory, so both the reads and the row writes are coalesced.
 constexpr int kEncCols = 128;     // columns per CTA: each database row segment is 128 bytes
 constexpr int kEncEntries = 64;   // differences per block per CTA
 constexpr int kEncThreads = 256;
@@ -66,21 +69,25 @@ __global__ void __launch_bounds__(kEncThreads) delta_encode_kernel(const uint32_
     const uint64_t i0 = 1 + (uint64_t)blockIdx.y * kEncEntries;   // first difference of this CTA
     const uint64_t ncols = C - j0 < (uint64_t)kEncCols ? C - j0 : (uint64_t)kEncCols;
     const uint64_t i1 = i0 + kEncEntries < E ? i0 + kEncEntries : E;   // differences [i0, i1)
-    // stage entries (block j0 + c, positions i0 - 1 .. i1 - 1): a warp reads one block's run
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint64_t c = warp; c < ncols; c += kEncThreads / 32)
-        for (uint64_t t = lane; t <= i1 - i0; t += 32)
-            ent[c][t] = entry_at(x, n, (j0 + c) * E + i0 - 1 + t);
+    // stage entries (block j0 + c, positions i0 - 1 .. i1 - 1): consecutive threads take
+    // consecutive entries of one block's run, and each thread issues its loads independently
+    const uint32_t nt = static_cast<uint32_t>(i1 - i0) + 1;
+    const uint32_t nload = static_cast<uint32_t>(ncols) * nt;
+#pragma unroll 4
+    for (uint32_t f = threadIdx.x; f < nload; f += kEncThreads) {
+        const uint32_t c = f / nt, t = f - c * nt;
+        ent[c][t] = entry_at(x, n, (j0 + c) * E + i0 - 1 + t);
+    }
     __syncthreads();
     // rows of this CTA's differences: row 4 + (i - 1) w + b, column j0 + c; threads run over
     // (row, column) with the column fastest
-    const uint64_t rows = (i1 - i0) * w;
+    const uint32_t rows = (nt - 1) * w;   // at most 64 x 4 rows: 32-bit index math below
     const uint64_t row0 = 4 + (i0 - 1) * w;
-    for (uint64_t t = threadIdx.x; t < rows * kEncCols; t += kEncThreads) {
-        const uint64_t r = t / kEncCols, c = t % kEncCols;
+    for (uint32_t t = threadIdx.x; t < rows * kEncCols; t += kEncThreads) {
+        const uint32_t r = t / kEncCols, c = t % kEncCols;
         if (c >= ncols) continue;
-        const uint64_t di = r / w;   // difference i0 + di
-        const uint32_t b = static_cast<uint32_t>(r % w);
+        const uint32_t di = r / w;   // difference i0 + di
+        const uint32_t b = r - di * w;
         const uint32_t d = ent[c][di + 1] - ent[c][di];
         db[(row0 + r) * C + j0 + c] = static_cast<uint8_t>(d >> (8u * b));
     }
@@ -156,13 +163,13 @@ int qpadl_pir_delta_width(const uint32_t *entries_dev, uint64_t n, uint32_t E, u
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int sms = num_sms_current();
     if (sms <= 0) return QPADL_ECUDA;
-    const uint64_t total = (n + E - 1) / E * E;
+    const uint64_t C = (n + E - 1) / E;
     uint32_t *dmax = nullptr;
     if (cudaMallocAsync(reinterpret_cast<void **>(&dmax), sizeof(uint32_t), s) != cudaSuccess) return QPADL_ENOMEM;
     uint32_t h = 0;
     bool ok = cudaMemsetAsync(dmax, 0, sizeof(uint32_t), s) == cudaSuccess;
     if (ok) {
-        delta_width_kernel<<<sms * 8, 256, 0, s>>>(entries_dev, n, E, total, dmax);
+        delta_width_kernel<<<sms * 8, 256, 0, s>>>(entries_dev, n, E, C, dmax);
         ok = cudaGetLastError() == cudaSuccess;
     }
     ok = ok && cudaMemcpyAsync(&h, dmax, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) == cudaSuccess;
