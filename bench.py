@@ -868,7 +868,9 @@ def run_ours(args):
                      "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": ("qpadl_pir_answer (stream_answer, query packed in-kernel)" if raw
                                 else "qpadl_pir_answer (pack_query + stream_answer)"),
-                     "alg_bytes_per_launch": alg_bytes},
+                     "alg_bytes_per_launch": alg_bytes,
+                     "frac_of_nominal_7900_gbs": round(achieved / 7900.0, 4),
+                     "isolated_launch_frac": round(alg_bytes / (resp_isolated_ms * 1e-3) / 1e9 / peak, 4)},
         "batched": {"one_at_a_time_qps": round(one_qps, 1), "sweep": sweep},
         "hint_ms": round(min(hint_ms), 3),
         "client_batch_1024": client,
