@@ -307,8 +307,9 @@ int qpadl_pir_recover_batch(const qpadl_params *prm, const uint32_t *ans_dev,
  * ==================================================================== */
 
 /* The fewest bytes w (1..4) holding every within-block difference of the n
- * entries.  Synchronises `stream` (the result is returned on the host);
- * allocates one word of stream-ordered device memory for the reduction. */
+ * entries.  Synchronises `stream` (the result is returned on the host) and
+ * allocates nothing: the reduction uses one library word per device, and
+ * concurrent calls take turns on a host lock. */
 int qpadl_pir_delta_width(const uint32_t *entries_dev, uint64_t n, uint32_t E, uint32_t *w_out,
                           qpadl_stream_t stream);
 

@@ -23,6 +23,8 @@
 //                        differences, a CTA-wide exclusive scan of the run
 //                        totals, then each run's prefix sums
 #include <cstdint>
+#include <mutex>
+
 #include <cuda_runtime.h>
 
 #include "qpadl_pir.h"
@@ -139,6 +141,11 @@ __global__ void __launch_bounds__(kDecodeThreads) delta_decode_kernel(const uint
     }
 }
 
+// The width reduction's result word: one per device, used under g_width_mu for
+// the whole (synchronous) call, so the call allocates nothing.
+__device__ uint32_t g_width_word;
+std::mutex g_width_mu;
+
 int num_sms_current() {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return -1;
@@ -164,8 +171,9 @@ int qpadl_pir_delta_width(const uint32_t *entries_dev, uint64_t n, uint32_t E, u
     const int sms = num_sms_current();
     if (sms <= 0) return QPADL_ECUDA;
     const uint64_t C = (n + E - 1) / E;
+    std::lock_guard<std::mutex> guard(g_width_mu);
     uint32_t *dmax = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&dmax), sizeof(uint32_t), s) != cudaSuccess) return QPADL_ENOMEM;
+    if (cudaGetSymbolAddress(reinterpret_cast<void **>(&dmax), g_width_word) != cudaSuccess) return QPADL_ECUDA;
     uint32_t h = 0;
     bool ok = cudaMemsetAsync(dmax, 0, sizeof(uint32_t), s) == cudaSuccess;
     if (ok) {
@@ -173,7 +181,6 @@ int qpadl_pir_delta_width(const uint32_t *entries_dev, uint64_t n, uint32_t E, u
         ok = cudaGetLastError() == cudaSuccess;
     }
     ok = ok && cudaMemcpyAsync(&h, dmax, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) == cudaSuccess;
-    ok = (cudaFreeAsync(dmax, s) == cudaSuccess) && ok;
     ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
     if (!ok) return QPADL_ECUDA;
     uint32_t w = 1;
