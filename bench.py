@@ -10,9 +10,14 @@ database bytes scanned per second over whole steps.
 
 Also measured in the same run and reported beside the headline:
   - the Response kernel alone and its fraction of the measured HBM roofline;
-  - the batched Response (exact byte-limb tensor-core GEMM) over a batch
+  - the end-to-end rate through the ABI with pinned host buffers (e2e);
+  - the batched Response (exact byte-limb tensor-core GEMMs) over a batch
     sweep, as queries/s against one-query-at-a-time on the same database;
-  - the hint time;
+  - the hint time and the tensor-core client batches (1024 Queries/Recovers);
+  - the serving loop under Poisson load over four databases (p50/p99) and
+    at saturation on the 1 GiB database;
+  - the Chor (GF(2)) and Goldberg (Z_257) Responses and the compressed
+    database of Sec. 5.3;
   - the CPU oracle on a bounded sample (cpu_baseline).
 
 `--impl reference` times the CPU oracle itself as the reference arm.
