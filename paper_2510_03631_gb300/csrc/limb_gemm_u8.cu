@@ -1,6 +1,9 @@
 // Exact mod-2^32 product of one or several databases with batches of Z_q
 // vectors, reading the databases as stored (uint8 digits):
 //     OUT_g[i][b] = sum_j D_g[i][j] * X_g[b][j]   (mod 2^32), g < ngroups.
+// A one-row mode (LPV = 1) takes vectors of small signed integers (|x| <=
+// 128, e.g. centred Z_p elements) as single fp16 rows and stores their exact
+// signed sums; the Goldberg Response over Z_p uses it.
 //
 // Same exact byte-limb algebra as limb_gemm.cu (balanced limbs in fp16,
 // fp32 accumulation over 512-deep K-chunks, int32 recombination; see there),
