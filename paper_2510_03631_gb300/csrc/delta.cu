@@ -18,7 +18,8 @@
 //                        a warp max, one atomic max per warp
 //   delta_encode_kernel  a CTA per 128 blocks x 64 differences: the entries
 //                        staged in shared memory (read run by run), the
-//                        database rows written 128 bytes at a time
+//                        database rows written 128 bytes at a time (four
+//                        columns per 32-bit store when aligned)
 //   delta_decode_kernel  one CTA per recovered block: per-thread runs of
 //                        differences, a CTA-wide exclusive scan of the run
 //                        totals, then each run's prefix sums
@@ -85,13 +86,30 @@ __global__ void __launch_bounds__(kEncThreads) delta_encode_kernel(const uint32_
     // (row, column) with the column fastest
     const uint32_t rows = (nt - 1) * w;   // at most 64 x 4 rows: 32-bit index math below
     const uint64_t row0 = 4 + (i0 - 1) * w;
-    for (uint32_t t = threadIdx.x; t < rows * kEncCols; t += kEncThreads) {
-        const uint32_t r = t / kEncCols, c = t % kEncCols;
-        if (c >= ncols) continue;
-        const uint32_t di = r / w;   // difference i0 + di
-        const uint32_t b = r - di * w;
-        const uint32_t d = ent[c][di + 1] - ent[c][di];
-        db[(row0 + r) * C + j0 + c] = static_cast<uint8_t>(d >> (8u * b));
+    // four columns per thread in one 32-bit store when every row segment is 4-byte aligned
+    const bool quad = (C % 4 == 0) && (ncols % 4 == 0) && ((reinterpret_cast<uintptr_t>(db) & 3u) == 0);
+    if (quad) {
+        constexpr uint32_t kQuads = kEncCols / 4;
+        for (uint32_t t = threadIdx.x; t < rows * kQuads; t += kEncThreads) {
+            const uint32_t r = t / kQuads, c = 4 * (t % kQuads);
+            if (c >= ncols) continue;
+            const uint32_t di = r / w;   // difference i0 + di
+            const uint32_t sh = 8u * (r - di * w);
+            uint32_t v = 0;
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k)
+                v |= (((ent[c + k][di + 1] - ent[c + k][di]) >> sh) & 255u) << (8u * k);
+            *reinterpret_cast<uint32_t *>(db + (row0 + r) * C + j0 + c) = v;
+        }
+    } else {
+        for (uint32_t t = threadIdx.x; t < rows * kEncCols; t += kEncThreads) {
+            const uint32_t r = t / kEncCols, c = t % kEncCols;
+            if (c >= ncols) continue;
+            const uint32_t di = r / w;   // difference i0 + di
+            const uint32_t b = r - di * w;
+            const uint32_t d = ent[c][di + 1] - ent[c][di];
+            db[(row0 + r) * C + j0 + c] = static_cast<uint8_t>(d >> (8u * b));
+        }
     }
     if (blockIdx.y == 0) {   // the first entry of each block in full
         for (uint64_t t = threadIdx.x; t < 4 * (uint64_t)kEncCols; t += kEncThreads) {
