@@ -248,10 +248,10 @@ int qpadl_pir_answer_host(qpadl_db *db, const uint32_t *q_host, uint32_t *ans_ho
 /*
  * Allocation-free Response.  The paper has no counterpart: this is a
  * deployment variant of qpadl_pir_answer for callers that cannot allocate
- * device memory at the moment they answer - a stream being captured into a
- * CUDA graph (allocation cannot be recorded in a capture), a runtime whose
- * own allocator owns all device memory, or a serving loop that must not take
- * the device-wide synchronisation that cudaMalloc/cudaFree imply.
+ * device memory at the moment they answer - a runtime whose own allocator
+ * owns all device memory and forbids side allocations, or a serving loop
+ * that must not take the device-wide synchronisation that cudaMalloc and
+ * cudaFree imply.
  *
  * Computes ans_dev[i] = sum_j D[i][j] q_dev[j] mod 2^32 for the caller's
  * resident database db_dev (rows x cols digits, row-major uint8) with no
@@ -267,12 +267,24 @@ int qpadl_pir_answer_host(qpadl_db *db, const uint32_t *q_host, uint32_t *ans_ho
  *    contents: calls whose work overlaps on the GPU (e.g. on two streams)
  *    race and can return wrong answers.  Serialise them.
  *  - Asynchronous on `stream`.  If a kernel's bounded wait runs out, ans_dev
- *    is incomplete and the failure is recorded only in the array's status
- *    word (cleared by the next call).
+ *    is incomplete and the array's status word is set; it stays set across
+ *    later calls until qpadl_pir_noalloc_status reads it.
  */
 #define QPADL_NOALLOC_MAX_COLS 262144u
 int qpadl_pir_answer_noalloc(const uint8_t *db_dev, uint64_t rows, uint64_t cols,
                              const uint32_t *q_dev, uint32_t *ans_dev, qpadl_stream_t stream);
+
+/*
+ * Status of the allocation-free Response on the current device (no paper
+ * counterpart; see qpadl_pir_answer_noalloc).  Waits for all work on the
+ * device (cudaDeviceSynchronize), then reads the fixed array's status word:
+ * QPADL_OK if no call since the last read gave up on a bounded wait,
+ * QPADL_ETIMEOUT if one did (some answer since the last read is incomplete;
+ * the word is cleared), QPADL_ECUDA if the device cannot be read.  Returns
+ * QPADL_OK when no allocation-free call has run on the device.  Allocates
+ * nothing.
+ */
+int qpadl_pir_noalloc_status(void);
 
 /*
  * Recover (Def. 1, Client.BlockReconst): out_dev[i] = ((ans[i] - sum_k

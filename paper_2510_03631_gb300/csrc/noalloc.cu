@@ -1,20 +1,28 @@
-// Allocation-free single-query Response (qpadl_pir_answer_noalloc).
+// Allocation-free single-query Response (qpadl_pir_answer_noalloc) and the
+// read of its status word (qpadl_pir_noalloc_status).
 //
 // Some callers cannot call cudaMalloc at the moment they need an answer:
-// code running while its stream is being captured into a CUDA graph
-// (allocation is not an operation a capture can record), runtimes whose own
-// memory manager owns all device memory and forbids side allocations, and
-// latency-critical serving loops where the implicit device-wide
-// synchronisation of cudaMalloc/cudaFree would stall every other stream.
-// This entry point answers one query against a caller-resident database
-// with no handle and no allocation of any kind: the packed query limbs and
-// the kernel's status word live in one fixed file-scope device array
-// (g_noalloc_scratch, 1 MiB + 256 bytes), which every GPU that loads the
-// library keeps until the process exits.
+// runtimes whose own memory manager owns all device memory and forbids side
+// allocations, and latency-critical serving loops where the implicit
+// device-wide synchronisation of cudaMalloc/cudaFree would stall every other
+// stream.  This entry point answers one query against a caller-resident
+// database with no handle and no allocation of any kind: the packed query
+// limbs and the kernels' status word live in one fixed file-scope device
+// array (g_noalloc_scratch, 1 MiB + 256 bytes), which every GPU that loads
+// the library keeps until the process exits.
 //
 // The arithmetic is the same streaming Response as qpadl_pir_answer (the
 // same pack and streaming kernels, launched with pointers into the fixed
 // array instead of a handle's buffers).
+//
+// Ordering: the streaming kernel is launched with programmatic dependent
+// launch and its producer issues its first database loads before it waits
+// for its predecessor (a handle's database is immutable while bound).  Here
+// the database is the caller's and may have just been written on the same
+// stream, so the pack kernel (an ordinary launch, which starts only after
+// everything earlier on the stream has finished and never lets its
+// successor start early) must stay the streaming kernel's immediate
+// predecessor: it is what orders the caller's writes before those loads.
 #include <cstdint>
 #include <cstdio>
 #include <mutex>
@@ -37,6 +45,7 @@ static __device__ __align__(256) uint32_t g_noalloc_scratch[kScratchWords];
 std::mutex g_mu;
 uint32_t *g_scratch_ptr[64];   // device address of g_noalloc_scratch, per device
 int g_num_sms[64];
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;   // resolved at the first set-up
 
 // Once per device, with that device current: resolve the array's device
 // address (the host-side name is only a stand-in) and set the kernels'
@@ -52,6 +61,14 @@ int device_setup(int dev, uint32_t **scratch, int *num_sms) {
             return QPADL_ECUDA;
         }
         if (qpadl::prepare_stream_kernels() != cudaSuccess) return QPADL_ECUDA;
+        if (!g_encode) {
+            void *fp = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fp, 12000, cudaEnableDefault, &q) ==
+                    cudaSuccess &&
+                q == cudaDriverEntryPointSuccess)
+                g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fp);
+        }
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QPADL_ECUDA;
         g_num_sms[dev] = sms;
@@ -63,20 +80,14 @@ int device_setup(int dev, uint32_t **scratch, int *num_sms) {
 }
 
 bool encode_db_map(CUtensorMap *map, const uint8_t *db, uint64_t R, uint64_t C) {
-    void *fp = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fp, 12000, cudaEnableDefault, &q) !=
-            cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-        return false;
-    auto fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fp);
+    if (!g_encode) return false;   // the bulk-copy form is used instead
     cuuint64_t dims[3] = {256, C / 256, R};
     cuuint64_t strides[2] = {256, C};
     cuuint32_t box[3] = {256, kChunk / 256, 8};
     cuuint32_t estr[3] = {1, 1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(db), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(db), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -109,8 +120,8 @@ extern "C" int qpadl_pir_answer_noalloc(const uint8_t *db_dev, uint64_t rows, ui
     uint32_t *pack = scratch;
     int *status = reinterpret_cast<int *>(scratch + kMaxCols);
     const uint64_t pack_words = qpadl::stream_pack_words(cols);   // <= kMaxCols for cols <= kMaxCols
-    // the status word must start each call at zero; the packed limbs are fully rewritten
-    if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return QPADL_ECUDA;
+    // the packed limbs are fully rewritten by every call; the status word is only ever set (a
+    // bounded wait that gave up) and stays set until qpadl_pir_noalloc_status reads it
     CUtensorMap map;
     const bool use_map = (cols % 256 == 0) && encode_db_map(&map, db_dev, rows, cols);
     if (qpadl::launch_pack_query(q_dev, cols, C, kChunk, 1, pack, pack_words, s) != cudaSuccess) return QPADL_ECUDA;
@@ -118,4 +129,23 @@ extern "C" int qpadl_pir_answer_noalloc(const uint8_t *db_dev, uint64_t rows, ui
                                     rows, sms, status, s) != cudaSuccess)
         return QPADL_ECUDA;
     return QPADL_OK;
+}
+
+extern "C" int qpadl_pir_noalloc_status(void) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return QPADL_ECUDA;
+    if (dev < 0 || dev >= 64) return QPADL_EINVAL;
+    uint32_t *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        scratch = g_scratch_ptr[dev];
+    }
+    if (!scratch) return QPADL_OK;   // no call has run on this device yet
+    int *status = reinterpret_cast<int *>(scratch + kMaxCols);
+    if (cudaDeviceSynchronize() != cudaSuccess) return QPADL_ECUDA;
+    int word = 0;
+    if (cudaMemcpy(&word, status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return QPADL_ECUDA;
+    if (word == 0) return QPADL_OK;
+    if (cudaMemset(status, 0, sizeof(int)) != cudaSuccess) return QPADL_ECUDA;
+    return QPADL_ETIMEOUT;
 }

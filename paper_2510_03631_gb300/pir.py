@@ -78,6 +78,7 @@ _SIGS = {
     "qpadl_pir_answer_batch_path": ([_P, _P, ctypes.c_uint32, _P, ctypes.c_int, _P], ctypes.c_int),
     "qpadl_pir_answer_host": ([_P, _P, _P, _P], ctypes.c_int),
     "qpadl_pir_answer_noalloc": ([_P, ctypes.c_uint64, ctypes.c_uint64, _P, _P, _P], ctypes.c_int),
+    "qpadl_pir_noalloc_status": ([], ctypes.c_int),
     "qpadl_pir_recover": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
     "qpadl_pir_shape": ([_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "qpadl_pir_reserve": ([_P, ctypes.c_uint32, _P], ctypes.c_int),
@@ -316,6 +317,12 @@ def qpadl_pir_answer_noalloc(db: torch.Tensor, rows: int, cols: int, q: torch.Te
                                            _dev(q, torch.int32, cols, "q"), _dev(ans, torch.int32, rows, "ans"),
                                            _stream(stream)), "qpadl_pir_answer_noalloc")
     return ans
+
+
+def qpadl_pir_noalloc_status() -> int:
+    """Waits for the current device; returns and clears the status word of the
+    allocation-free Response (QPADL_OK or QPADL_ETIMEOUT)."""
+    return int(load().qpadl_pir_noalloc_status())
 
 
 def qpadl_pir_recover(prm: qpadl_params, ans: torch.Tensor, H: torch.Tensor, s: torch.Tensor,

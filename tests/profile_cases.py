@@ -1,37 +1,39 @@
-"""Small, self-checking launch cases for profiling one kernel at a time.
+"""Small, self-checking launch cases for profiling one kernel at a time
+(test infrastructure, like the oracle it checks against).
 
-    python -m paper_2510_03631_gb300.profile_cases stream --rows 8192 --cols 32768 --reps 3
-    python -m paper_2510_03631_gb300.profile_cases gemm   --rows 8192 --cols 32768 --batch 256 --reps 2
-    python -m paper_2510_03631_gb300.profile_cases hint   --rows 8192 --cols 32768 --n 1024 --reps 1
-    python -m paper_2510_03631_gb300.profile_cases qbatch --cols 32768 --n 1024 --batch 1024 --client 1
+    python tests/profile_cases.py stream --rows 8192 --cols 32768 --reps 3
+    python tests/profile_cases.py gemm   --rows 8192 --cols 32768 --batch 256 --reps 2
+    python tests/profile_cases.py hint   --rows 8192 --cols 32768 --n 1024 --reps 1
+    python tests/profile_cases.py qbatch --cols 32768 --n 1024 --batch 1024 --client 1
 
 Each case builds one database of the given size on cuda:0 (uniform digits,
 seed 1), runs the chosen entry point `reps` times after one warm-up call,
 prints the CUDA-event time per call and the bytes/flops it implies, and
-checks one output row against a plain host recomputation so a profile is
-never taken of a wrong kernel.  Sizes default to inputs larger than L2
-(129 MB) with a few GB on the device at most.
+checks sampled outputs against the CPU oracle so a profile is never taken of
+a wrong kernel.  Sizes default to inputs larger than L2 (129 MB) with a few
+GB on the device at most.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import os
+import sys
 
 import numpy as np
 import torch
 
-from . import inputs, pir
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
-
-def _dots(X: np.ndarray, s: np.ndarray) -> np.ndarray:
-    """Row dot products X s mod 2^32 (uint64 products wrap mod 2^64, which keeps the low 32 bits)."""
-    return ((X.astype(np.uint64) * s.astype(np.uint64)[None, :]).sum(axis=1) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+import oracle  # noqa: E402
+from paper_2510_03631_gb300 import inputs, pir  # noqa: E402
 
 
 def _row_check(D_row: np.ndarray, X: np.ndarray, got: np.ndarray):
-    exp = (X.astype(np.uint64) * D_row.astype(np.uint64)[None, :]).sum(axis=1) & np.uint64(0xFFFFFFFF)
-    if not np.array_equal(exp.astype(np.uint32), got):
-        raise SystemExit("profile case: output row differs from the host recomputation")
+    """One database row against every vector of X (B x C): the oracle's batched Response."""
+    exp = oracle.answer_batch(D_row[None, :], X, threads=oracle.max_threads())[:, 0]
+    if not np.array_equal(exp, got):
+        raise SystemExit("profile case: output row differs from the oracle")
 
 
 def _chor_case(a):
@@ -58,11 +60,10 @@ def _chor_case(a):
         times.append(e0.elapsed_time(e1))
     if pir.qpadl_chor_status(h) != 0:
         raise SystemExit("profile case: device status word set")
-    # host recomputation of query 0 on the first 64 words: XOR of the selected rows
-    sel = ((Q_np[0][np.arange(rows) // 32] >> (np.arange(rows) % 32).astype(np.uint32)) & 1).astype(bool)
-    exp = np.bitwise_xor.reduce(DB_np[sel, :64], axis=0) if sel.any() else np.zeros(64, np.uint32)
+    # query 0 on the first 64 words against the oracle
+    exp = oracle.chor_answer(np.ascontiguousarray(DB_np[:, :64]), rows, Q_np[:1], threads=oracle.max_threads())[0]
     if not np.array_equal(pir.as_u32(out)[:64], exp):
-        raise SystemExit("profile case: output differs from the host recomputation")
+        raise SystemExit("profile case: output differs from the oracle")
     ms = min(times)
     alg = rows * W * 4 + B * ((rows + 31) // 32) * 4 + B * W * 4
     print(json.dumps({"case": "chor", "rows": rows, "bits": bits, "batch": B, "ms": times, "alg_bytes": alg,
@@ -93,9 +94,9 @@ def _goldberg_case(a):
         times.append(e0.elapsed_time(e1))
     if pir.qpadl_goldberg_status(h) != 0:
         raise SystemExit("profile case: device status word set")
-    exp = (Q_np[:, :].astype(np.int64) @ D_np[R // 2].astype(np.int64)) % p
-    if not np.array_equal(pir.as_u32(out).reshape(B, R)[:, R // 2], exp.astype(np.uint32)):
-        raise SystemExit("profile case: output differs from the host recomputation")
+    exp = oracle.goldberg_answer(D_np[R // 2][None, :], Q_np, p, threads=oracle.max_threads())[:, 0]
+    if not np.array_equal(pir.as_u32(out).reshape(B, R)[:, R // 2], exp):
+        raise SystemExit("profile case: output differs from the oracle")
     ms = min(times)
     print(json.dumps({"case": "goldberg", "rows": R, "cols": C, "batch": B, "ms": times,
                       "fp16_mma_flops": 2 * R * C * B, "tflops": 2 * R * C * B / (ms * 1e-3) / 1e12,
@@ -135,6 +136,9 @@ def _delta_case(a):
     got = pir.as_u32(out).reshape(B, E)
     if not np.array_equal(got, x_np[:B * E].reshape(B, E)):
         raise SystemExit("profile case: decoded blocks differ from the entries")
+    exp_db = oracle.delta_encode(x_np[:B * E], E, w)
+    if not np.array_equal(blocks.cpu().numpy().reshape(B, Rp), exp_db.T):
+        raise SystemExit("profile case: encoded blocks differ from the oracle")
     print(json.dumps({"case": "delta", "blocks": C, "block_entries": E, "width": w, "rows_compressed": Rp,
                       "decoded_blocks": B, "ms": times, "entry_bytes": 4 * n, "db_bytes": Rp * C}))
 
@@ -236,11 +240,10 @@ def main():
             else:
                 fn = lambda: pir.qpadl_pir_query_batch(cprm, X, S, E, cols_t, Q)
             def check():
-                # first query, sampled rows: dot + e + Delta at the target column
-                idx = np.unique(np.r_[0:64, rows - 64:rows, int(cols[0])].clip(0, rows - 1))
-                exp = _dots(pir.as_u32(X).reshape(rows, n)[idx], S_np[0]) + E_np[0][idx].astype(np.uint32)
-                exp = exp + np.where(idx == int(cols[0]), np.uint32(1 << 24), np.uint32(0))
-                return np.array_equal(pir.as_u32(Q)[:rows][idx], exp.astype(np.uint32))
+                # first query against the oracle's Query
+                exp = oracle.query(pir.as_u32(X).reshape(rows, n), S_np[0], E_np[0], int(cols[0]),
+                                   oracle.delta_for(256))
+                return np.array_equal(pir.as_u32(Q)[:rows], exp)
         else:
             ans_np = inputs.uniform_u32(B * rows, seed=6, tag=inputs.TAG_MISC)
             ans = pir.from_u32(ans_np)
@@ -253,11 +256,9 @@ def main():
             else:
                 fn = lambda: pir.qpadl_pir_recover_batch(cprm, ans, Xr, S, out)
             def check():
-                # first recovery, sampled rows: (ans - dot + Delta/2) >> 24
-                idx = np.unique(np.r_[0:64, rows - 64:rows].clip(0, rows - 1))
-                x = (ans_np[:rows][idx] - _dots(pir.as_u32(X).reshape(rows, n)[idx], S_np[0])).astype(np.uint32)
-                exp = ((x.astype(np.uint64) + (1 << 23)) & 0xFFFFFFFF) >> 24
-                return np.array_equal(out.cpu().numpy()[:rows][idx], exp.astype(np.uint8))
+                # first recovery against the oracle's Recover
+                exp = oracle.recover(ans_np[:rows], pir.as_u32(X).reshape(rows, n), S_np[0], 256)
+                return np.array_equal(out.cpu().numpy()[:rows], exp)
         out_row = None
         res.update(n=n, batch=B, client=a.client, u32_macs=rows * n * B, fp16_mma_flops=2 * rows * 4 * n * 4 * B)
     else:
@@ -286,7 +287,7 @@ def main():
         _row_check(D_np[R // 2], X_chk, out_row())
     if a.case in ("qbatch", "rbatch"):
         if not check():
-            raise SystemExit("profile case: first vector differs from the host recomputation")
+            raise SystemExit("profile case: first vector differs from the oracle")
         if cl is not None and pir.qpadl_client_status(cl) != 0:
             raise SystemExit("profile case: client status word set")
     res["ms"] = times
