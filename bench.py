@@ -167,6 +167,81 @@ def cpu_oracle_sample(D, A_np, H_np, budget_s: float = 12.0, threads: int | None
                       f"{el:.1f} s"}
 
 
+def _time_rows(fn, rows_total: int, r0: int, min_s: float = 0.25):
+    """Time fn(r) on r rows, growing r (x4) until one call takes min_s or r reaches
+    rows_total; returns (seconds for all rows_total rows by linear extrapolation, r)."""
+    r = min(r0, rows_total)
+    while True:
+        t0 = time.perf_counter()
+        fn(r)
+        dt = time.perf_counter() - t0
+        if dt >= min_s or r >= rows_total:
+            return dt * rows_total / r, r
+        r = min(rows_total, r * 4)
+
+
+def cpu_oracle_blocks(D, A_np, H_np, threads: int):
+    """The oracle beside every GPU block of the bench line (each on a bounded row or
+    call sample, extrapolated linearly to the full size; the sample is stated)."""
+    import oracle
+    from paper_2510_03631_gb300 import inputs
+    R, C = D.shape
+    n = A_np.shape[1]
+    out = {"cores": threads, "kind": "oracle"}
+    # the batched Response, B queries (linear in the answered rows)
+    sweep = {}
+    for B in (1, 8, 32, 128, 256, 1024):
+        Q = inputs.uniform_u32(B * C, seed=900 + B, tag=inputs.TAG_MISC).reshape(B, C)
+        r0 = max(2 * threads, 4096 // B)
+        full_s, r = _time_rows(lambda r: oracle.answer_batch(np.ascontiguousarray(D[:r]), Q, threads=threads), R, r0)
+        sweep[str(B)] = {"ms": round(full_s * 1e3, 1), "sample_rows": r}
+    out["batched_sweep"] = sweep
+    # the offline hint D A (linear in rows)
+    full_s, r = _time_rows(lambda r: oracle.hint(np.ascontiguousarray(D[:r]), A_np, threads=threads), R,
+                           2 * threads)
+    out["hint"] = {"ms": round(full_s * 1e3, 1), "sample_rows": r}
+    # 1024 Queries and 1024 Recovers (the oracle's Query and Recover are single calls per vector)
+    S = inputs.secrets(8, n, seed=77)
+    E = inputs.noise_batch(8, C, seed=78)
+    t0 = time.perf_counter()
+    for b in range(8):
+        oracle.query(A_np, S[b], E[b], b, oracle.delta_for(256))
+    tq = (time.perf_counter() - t0) / 8
+    ans = inputs.uniform_u32(R, seed=79, tag=inputs.TAG_MISC)
+    t0 = time.perf_counter()
+    for b in range(8):
+        oracle.recover(ans, H_np, S[b])
+    tr = (time.perf_counter() - t0) / 8
+    out["client_batch_1024"] = {"query_ms": round(tq * 1024 * 1e3, 1), "recover_ms": round(tr * 1024 * 1e3, 1),
+                                "sample": "8 calls each (one thread: the oracle's Query and Recover are single loops), x 128"}
+    out["sample"] = ("row samples of the 1 GiB database grown until one call takes 0.25 s, extrapolated "
+                     "linearly to all rows")
+    return out
+
+
+def cpu_oracle_tiny(threads: int):
+    """The tiny workload (1024 x 1024, n = 512) in full: Setup's A, Hint, Query, Answer, Recover."""
+    import oracle
+    from paper_2510_03631_gb300 import inputs
+    w = inputs.WORKLOADS["tiny"]
+    R, C, n = w["rows"], w["cols"], w["n"]
+    D = inputs.db_digits(R, C, 256, seed=1)
+    t0 = time.perf_counter()
+    A = oracle.gen_a(1, C, n)
+    H = oracle.hint(D, A, threads=threads)
+    s = inputs.secrets(1, n, seed=2)[0]
+    e = inputs.noise(C, seed=3)
+    col = int(inputs.target_columns(1, C, seed=4)[0])
+    qu = oracle.query(A, s, e, col, oracle.delta_for(256))
+    ans = oracle.answer(D, qu, threads=threads)
+    rec = oracle.recover(ans, H, s)
+    dt = time.perf_counter() - t0
+    if not np.array_equal(rec, D[:, col]):
+        raise SystemExit("bench: oracle tiny round trip failed")
+    return {"ms": round(dt * 1e3, 1), "cores": threads,
+            "sample": "full: A, hint 1024 x 1024 x 512, Query, Answer, Recover (checked)"}
+
+
 def run_reference(args, budget_s: float = 150.0):
     """The CPU oracle as the reference arm, on the same workload and metric.
 
@@ -831,7 +906,7 @@ def run_ours(args):
         del D
         torch.cuda.empty_cache()
         serving = serving_measure(torch, pir, inputs, rates=(1000, 5000, 10000, 20000, 50000),
-                                  duration_s=3.0, single_db_one_ms=resp_ms_avg)
+                                  duration_s=args.serve_s, single_db_one_ms=resp_ms_avg)
         torch.cuda.empty_cache()
         chor = chor_measure(torch, pir, inputs)
         torch.cuda.empty_cache()
@@ -847,6 +922,11 @@ def run_ours(args):
         cpu = cpu_oracle_sample(D_np, A_np, H_np, budget_s=args.cpu_budget)
         one = cpu_oracle_sample(D_np, A_np, H_np, budget_s=args.cpu_budget / 3, threads=1)
         cpu["single_thread"] = {"value": one["value"], "unit": one["unit"], "sample": one["sample"]}
+        if extras:
+            ncores = os.cpu_count() or 1
+            cpu["blocks"] = {"all_cores": cpu_oracle_blocks(D_np, A_np, H_np, ncores),
+                             "single_thread": cpu_oracle_blocks(D_np, A_np, H_np, 1),
+                             "tiny_all_cores": cpu_oracle_tiny(ncores), "tiny_single_thread": cpu_oracle_tiny(1)}
 
     gbs = replicas.job_rate(R * C, world, step_ms * 1e-3) / 1e9
     line = {
@@ -912,6 +992,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the batch sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--serve-s", type=float, default=10.0, help="seconds of open-loop load per offered rate")
     ap.add_argument("--stream-chunk", type=int, default=0,
                     help="pin the single-query streaming chunk width after tuning (profiling runs)")
     ap.add_argument("--stream-raw", type=int, default=-1,

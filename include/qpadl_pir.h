@@ -89,9 +89,10 @@ int qpadl_version(void);
                                         Response: 512, 1024, 2048 (default) or 4096 */
 #define QPADL_OPT_TENSOR_MIN_BATCH 2 /* smallest batch that qpadl_pir_answer_batch sends to
                                         the tensor-core GEMM (>= 1; default 3) */
-#define QPADL_OPT_STREAM_RAW 3       /* 1: a single query is packed inside the streaming kernel
-                                        (one launch, no scratch); 0 (default): a separate
-                                        packing launch first */
+#define QPADL_OPT_STREAM_RAW 3       /* 1: one or two queries are packed inside the streaming
+                                        kernel (one launch, no scratch; two queries share one
+                                        pass over D); 0 (default): a separate packing launch
+                                        first */
 #define QPADL_OPT_U8_MAX_BATCH 4     /* batches of up to this many queries (0..32, default 32)
                                         run the tensor-core GEMM on the uint8 digits as stored;
                                         larger ones use the handle's fp16 operand copy */
@@ -557,6 +558,9 @@ typedef struct qpadl_server_stats_t {
     uint64_t host_bytes_used, device_bytes_used;
     uint64_t grouped_launches;    /* launches that answered two or more databases */
     double mean_enqueue_us;       /* host time per launch spent enqueueing its kernels */
+    uint64_t stream_kernels;      /* streaming Response kernels enqueued (one pass over a
+                                     database answers its 1 or 2 queries of a launch) */
+    uint64_t gemm_kernels;        /* batched-GEMM Response kernels enqueued */
 } qpadl_server_stats_t;
 
 /* Creates a server on the current device (allocates both arenas and the

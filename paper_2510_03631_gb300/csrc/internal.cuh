@@ -35,4 +35,9 @@ int db_answer_f16_ws(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans,
 // falls back to the row-wise kernel for shapes the streaming kernel cannot take.
 int db_answer_one_noscratch(qpadl_db *db, const uint32_t *q, uint32_t *ans, cudaStream_t stream);
 
+// Two queries (q, q + q_ld) in one pass over the database without any scratch (both packed
+// in-kernel); answers to ans and ans + ans_ld.  Falls back to the row-wise kernel likewise.
+int db_answer_two_noscratch(qpadl_db *db, const uint32_t *q, uint64_t q_ld, uint32_t *ans, uint64_t ans_ld,
+                            cudaStream_t stream);
+
 }  // namespace qpadl

@@ -268,8 +268,26 @@ int answer_stream_group(qpadl_db *db, const uint32_t *Q, uint32_t nq, uint32_t *
     return QPADL_OK;
 }
 
+// Chunk width of the two-query in-kernel-packing form: the handle's single-query width where
+// that form has it (1024 or 2048), else 1024.
+int raw2_chunk(const qpadl_db *db) { return db->stream_chunk == 2048 ? 2048 : 1024; }
+
+int answer_two_raw(qpadl_db *db, const uint32_t *Q, uint64_t q_ld, uint32_t *ans, uint64_t ans_ld,
+                   cudaStream_t stream) {
+    const uint64_t C = db->prm.cols, R = db->prm.rows;
+    const int cch = raw2_chunk(db);
+    int mi = 0;
+    while ((512 << mi) < cch) ++mi;
+    const CUtensorMap *map = db->stream_maps ? &db->stream_map[mi] : nullptr;
+    QPADL_CU(launch_stream_answer_raw2(cch, map, db->db, static_cast<uint32_t>(R), static_cast<uint32_t>(C), Q, q_ld,
+                                       ans, ans_ld, db->num_sms, db->d_status, stream));
+    return QPADL_OK;
+}
+
 int answer_streaming(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, cudaStream_t stream) {
     const uint64_t C = db->prm.cols, R = db->prm.rows;
+    if (db->stream_ok && B == 2 && db->stream_raw && aligned16(Q))
+        return answer_two_raw(db, Q, C, ans, R, stream);   // both queries in one pass, no scratch
     if (db->stream_ok && B == 1 && db->stream_raw && aligned16(Q)) {
         // one query: the streaming kernel packs its limbs itself (one launch, no scratch)
         int mi = 0;
@@ -427,6 +445,14 @@ int db_answer_one_noscratch(qpadl_db *db, const uint32_t *q, uint32_t *ans, cuda
         return QPADL_OK;
     }
     QPADL_CU(launch_rowwise_answer(db->db, R, C, q, C, 1, ans, R, db->num_sms, stream));
+    return QPADL_OK;
+}
+
+int db_answer_two_noscratch(qpadl_db *db, const uint32_t *q, uint64_t q_ld, uint32_t *ans, uint64_t ans_ld,
+                            cudaStream_t stream) {
+    if (db->stream_ok && aligned16(q) && q_ld % 4 == 0) return answer_two_raw(db, q, q_ld, ans, ans_ld, stream);
+    const uint64_t C = db->prm.cols, R = db->prm.rows;
+    QPADL_CU(launch_rowwise_answer(db->db, R, C, q, q_ld, 2, ans, ans_ld, db->num_sms, stream));
     return QPADL_OK;
 }
 

@@ -14,7 +14,7 @@
 //    query straight from pinned host memory; one grouped exact byte-limb
 //    GEMM over all databases with 3..32 queued queries (the tiles of every
 //    database form one work list split evenly over the SMs); the streaming
-//    kernel for databases with 1 or 2 queries; the fp16-copy GEMM for
+//    kernel for databases with 1 or 2 queries (two in one pass); the fp16-copy GEMM for
 //    batches above 32; and a scatter kernel that writes every answer
 //    straight into its request's pinned buffer.  A host callback at the end
 //    of the stream marks the requests done and frees the workspace.
@@ -192,6 +192,7 @@ struct qpadl_server {
     uint32_t active_gemm = 0;    // launches in flight that carry a GEMM
     double busy_batch_sum = 0;
     double enqueue_s = 0;   // host time spent enqueueing launches
+    uint64_t stream_kernels = 0, gemm_kernels = 0;   // Response kernels enqueued, by kind
 
     void run();
     bool form_launch(int slot_idx, std::unique_lock<std::mutex> &lk);
@@ -349,6 +350,7 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
         }
     }
     bool ok = true;
+    uint64_t n_stream_k = 0, n_gemm_k = 0;   // Response kernels this launch enqueues
     const unsigned gx = static_cast<unsigned>(std::min<uint64_t>((maxC + 1023) / 1024, 32));
     copy_jobs_kernel<<<dim3(gx, total), 256, 0, S.stream>>>(S.q_jobs);
     ok = ok && cudaGetLastError() == cudaSuccess;
@@ -359,9 +361,13 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
         uint32_t *dq = reinterpret_cast<uint32_t *>(base + g.dq_off);
         uint32_t *da = reinterpret_cast<uint32_t *>(base + g.da_off);
         __half *dl = reinterpret_cast<__half *>(base + g.dl_off);
-        if (g.count <= 2) {
-            for (uint32_t i = 0; i < g.count && ok; ++i)
-                ok = qpadl::db_answer_one_noscratch(e.db, dq + i * e.C, da + i * e.R, S.stream) == QPADL_OK;
+        if (g.count == 1) {
+            ok = ok && qpadl::db_answer_one_noscratch(e.db, dq, da, S.stream) == QPADL_OK;
+            ++n_stream_k;
+        } else if (g.count == 2) {
+            // both queries in one pass over the database
+            ok = ok && qpadl::db_answer_two_noscratch(e.db, dq, e.C, da, e.R, S.stream) == QPADL_OK;
+            ++n_stream_k;
         } else if (g.count <= 32) {
             ok = ok && qpadl::launch_vec_limbs(dq, e.C, g.count, e.C, dl, e.pitch, qpadl::db_num_sms(e.db),
                                                S.stream) == cudaSuccess;
@@ -369,6 +375,7 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
             small.push_back(&g);
         } else {
             ok = ok && qpadl::db_answer_f16_ws(e.db, dq, g.count, da, dl, S.stream) == QPADL_OK;
+            ++n_gemm_k;
         }
     }
     for (size_t k0 = 0; k0 < small.size() && ok; k0 += qpadl::kMaxGemmGroups) {
@@ -393,6 +400,7 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
         args.total_units = units;
         ok = ok && qpadl::launch_limb_gemm_u8(bn, ks, args, qpadl::db_num_sms(dbs[small[k0]->db].db),
                                               qpadl::db_status_word(dbs[small[k0]->db].db), S.stream) == cudaSuccess;
+        ++n_gemm_k;
     }
     if (ok) {
         const unsigned gy = static_cast<unsigned>(std::min<uint64_t>((maxR + 1023) / 1024, 32));
@@ -417,6 +425,8 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
     const double t_enq = now_s() - t_enq0;
     lk.lock();
     enqueue_s += t_enq;
+    stream_kernels += n_stream_k;
+    gemm_kernels += n_gemm_k;
     return true;
 }
 
@@ -643,6 +653,8 @@ int qpadl_server_stats(qpadl_server *s, qpadl_server_stats_t *st) {
     st->device_bytes_used = s->dev_alloc.used();
     st->grouped_launches = s->n_grouped;
     st->mean_enqueue_us = s->n_launches ? 1e6 * s->enqueue_s / static_cast<double>(s->n_launches) : 0.0;
+    st->stream_kernels = s->stream_kernels;
+    st->gemm_kernels = s->gemm_kernels;
     return QPADL_OK;
 }
 

@@ -36,7 +36,7 @@ namespace qpadl {
 
 // Where a stage's query operand comes from.
 constexpr int kQPacked = 0;   // NQ queries pre-packed into byte-limb planes (pack_query_kernel)
-constexpr int kQRaw = 1;      // one raw query (uint32 words); limbs are packed per thread
+constexpr int kQRaw = 1;      // NQ (1 or 2) raw queries (uint32 words); limbs are packed per thread
 
 template <int NQ, int CCH, int QM = kQPacked>
 struct StreamCfg {
@@ -47,7 +47,7 @@ struct StreamCfg {
     static constexpr int kWarpsPerRow = kGroups / 32;
     static constexpr int kBoxRows = 16384 / CCH;                   // every 3-D box moves 16 KB
     static constexpr int kDbStageBytes = kSpan * CCH;
-    // packed limbs of NQ queries (4 bytes per digit), or the raw secret slice (1 byte per digit)
+    // packed limbs or raw words of NQ queries (4 bytes per digit either way)
     static constexpr int kQStageBytes = NQ * CCH * 4;
     static constexpr int kStageBytes = kDbStageBytes + kQStageBytes;
     static constexpr int kStages = (220 * 1024) / kStageBytes > 4 ? 4 : (220 * 1024) / kStageBytes;
@@ -106,8 +106,9 @@ __device__ __forceinline__ void consumer_sync() {
 
 // D: R rows of C digits.
 //  kQPacked: NQ packed queries (pack_ld words apart).
-//  kQRaw:    one raw query; each thread byte-permutes its 16 query words into
-//            the 4 limb words of each 4-digit group.
+//  kQRaw:    NQ (1 or 2) raw queries (pack_ld words apart); each thread
+//            byte-permutes its 16 words of each query into the 4 limb words
+//            of each 4-digit group.
 // Launched with programmatic dependent launch: the kernel lets its successor
 // be scheduled at once and waits (griddepcontrol.wait) for its predecessor
 // before it reads anything the predecessor may have written.  The database
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                          uint32_t R, uint32_t C, const uint32_t *__restrict__ qsrc, uint64_t pack_ld, Epi epi,
                          int *__restrict__ status) {
     using Cfg = StreamCfg<NQ, CCH, QM>;
-    static_assert(QM == kQPacked || NQ == 1, "the raw form serves one query");
+    static_assert(QM == kQPacked || NQ <= 2, "the raw form serves one or two queries");
     constexpr int RPT = Cfg::kRowsPerThread;
     constexpr int SR = Cfg::kSpan;
     constexpr int ST = Cfg::kStages;
@@ -170,7 +171,9 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                 const uint32_t bytes = (C - c0) < (uint32_t)CCH ? (C - c0) : (uint32_t)CCH;
                 uint32_t *qdst = q_st + st * (Cfg::kQStageBytes / 4);
                 if (QM == kQRaw) {
-                    bulk_load(qdst, qsrc + c0, bytes * 4u, &full[st]);
+#pragma unroll
+                    for (int b = 0; b < NQ; ++b)
+                        bulk_load(qdst + b * CCH, qsrc + b * pack_ld + c0, bytes * 4u, &full[st]);
                 } else {
 #pragma unroll
                     for (int b = 0; b < NQ; ++b)
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                     }
                     const uint32_t c0 = c * CCH;
                     const uint32_t bytes = (C - c0) < (uint32_t)CCH ? (C - c0) : (uint32_t)CCH;
-                    const uint32_t qbytes = QM == kQRaw ? bytes * 4u : NQ * CCH * 4u;
+                    const uint32_t qbytes = QM == kQRaw ? NQ * bytes * 4u : NQ * CCH * 4u;
                     mbar_arrive_expect_tx(&full[st], nbox * BR * CCH + (s1 - s0 - BR * nbox) * bytes + qbytes);
                     uint8_t *dst = db_st + st * Cfg::kDbStageBytes;
                     for (uint32_t b = 0; b < nbox; ++b)
@@ -265,7 +268,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         uint4 a = make_uint4(0u, 0u, 0u, 0u);
-                        if (valid) a = *reinterpret_cast<const uint4 *>(qs + cg * 16 + 4 * i);
+                        if (valid) a = *reinterpret_cast<const uint4 *>(qs + b * CCH + cg * 16 + 4 * i);
                         const uint32_t lo01 = __byte_perm(a.x, a.y, 0x5140);
                         const uint32_t lo23 = __byte_perm(a.z, a.w, 0x5140);
                         const uint32_t hi01 = __byte_perm(a.x, a.y, 0x7362);
@@ -373,7 +376,9 @@ cudaError_t prepare_stream_kernels() {
     if ((e = set_stream_attr<1, 512, kQRaw, AnswerEpi>()) != cudaSuccess) return e;
     if ((e = set_stream_attr<1, 1024, kQRaw, AnswerEpi>()) != cudaSuccess) return e;
     if ((e = set_stream_attr<1, 2048, kQRaw, AnswerEpi>()) != cudaSuccess) return e;
-    return set_stream_attr<1, 4096, kQRaw, AnswerEpi>();
+    if ((e = set_stream_attr<1, 4096, kQRaw, AnswerEpi>()) != cudaSuccess) return e;
+    if ((e = set_stream_attr<2, 1024, kQRaw, AnswerEpi>()) != cudaSuccess) return e;
+    return set_stream_attr<2, 2048, kQRaw, AnswerEpi>();
 }
 
 bool stream_config_valid(int nq, int cch) {
@@ -444,6 +449,18 @@ cudaError_t launch_stream_answer_raw(int cch, const CUtensorMap *map, const uint
         case 1024: return launch_cfg<1, 1024, kQRaw>(map, D, R, C, q, 0, epi, grid, status, stream);
         case 2048: return launch_cfg<1, 2048, kQRaw>(map, D, R, C, q, 0, epi, grid, status, stream);
         case 4096: return launch_cfg<1, 4096, kQRaw>(map, D, R, C, q, 0, epi, grid, status, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_stream_answer_raw2(int cch, const CUtensorMap *map, const uint8_t *D, uint32_t R, uint32_t C,
+                                      const uint32_t *q, uint64_t q_ld, uint32_t *ans, uint64_t ans_ld, int num_sms,
+                                      int *status, cudaStream_t stream) {
+    const int grid = stream_grid(R, num_sms);
+    const AnswerEpi epi{ans, ans_ld};
+    switch (cch) {
+        case 1024: return launch_cfg<2, 1024, kQRaw>(map, D, R, C, q, q_ld, epi, grid, status, stream);
+        case 2048: return launch_cfg<2, 2048, kQRaw>(map, D, R, C, q, q_ld, epi, grid, status, stream);
         default: return cudaErrorInvalidValue;
     }
 }

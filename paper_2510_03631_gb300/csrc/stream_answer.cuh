@@ -35,6 +35,13 @@ cudaError_t launch_stream_answer_raw(int cch, const CUtensorMap *map, const uint
                                      const uint32_t *q, uint32_t *ans, int num_sms, int *status,
                                      cudaStream_t stream);
 
+// Two queries, raw: one pass over D answers both (query b at q + b * q_ld,
+// answer b at ans + b * ans_ld).  cch in {1024, 2048}; q and q + q_ld must be
+// 16-byte aligned (q_ld a multiple of 4).
+cudaError_t launch_stream_answer_raw2(int cch, const CUtensorMap *map, const uint8_t *D, uint32_t R, uint32_t C,
+                                      const uint32_t *q, uint64_t q_ld, uint32_t *ans, uint64_t ans_ld, int num_sms,
+                                      int *status, cudaStream_t stream);
+
 cudaError_t launch_rowwise_answer(const uint8_t *D, uint64_t R, uint64_t C, const uint32_t *Q, uint64_t q_ld,
                                   uint32_t B, uint32_t *ans, uint64_t ans_ld, int num_sms, cudaStream_t stream);
 

@@ -605,7 +605,8 @@ class qpadl_server_stats_t(ctypes.Structure):
         ("refused", ctypes.c_uint64), ("inflight", ctypes.c_uint32), ("queued", ctypes.c_uint32),
         ("mean_launch_requests", ctypes.c_double), ("host_bytes_used", ctypes.c_uint64),
         ("device_bytes_used", ctypes.c_uint64), ("grouped_launches", ctypes.c_uint64),
-        ("mean_enqueue_us", ctypes.c_double),
+        ("mean_enqueue_us", ctypes.c_double), ("stream_kernels", ctypes.c_uint64),
+        ("gemm_kernels", ctypes.c_uint64),
     ]
 
 

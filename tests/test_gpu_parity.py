@@ -95,6 +95,29 @@ def test_answer_single_every_chunk_width(R, C, chunk):
         assert np.array_equal(_answers(db, q[None, :])[0], exp), f"raw={raw}"
 
 
+@pytest.mark.parametrize("chunk", [1024, 2048, 4096])
+@pytest.mark.parametrize("R,C", [
+    (1000, 1008), (153, 4096 + 16), (2, 9000 - 8),     # per-row bulk copies
+    (640, 512), (1000, 4096), (9, 33024),               # 3-D boxes, remainder rows, partial last chunk
+    (300, 2048 + 48), (17, 4096 + 4080),
+])
+def test_answer_two_queries_one_pass(R, C, chunk):
+    # two queries: one streaming pass with both packed in-kernel (raw = 1), or the pack launch first
+    prm, D, db = _setup(R, C, seed=chunk + 3 * R)
+    pir.qpadl_pir_set_option(db, pir.QPADL_OPT_STREAM_CHUNK, chunk)
+    Q = inputs.uniform_u32(2 * C, seed=chunk + C, tag=inputs.TAG_MISC).reshape(2, C)
+    exp = oracle.answer_batch(D, Q)
+    for raw in (0, 1):
+        pir.qpadl_pir_set_option(db, pir.QPADL_OPT_STREAM_RAW, raw)
+        assert np.array_equal(_answers(db, Q, path=0), exp), f"raw={raw}"
+    # the largest limb magnitudes in both queries
+    Dx = np.full((R, C), 255, dtype=np.uint8)
+    prm, Dx, dbx = _setup(R, C, D=Dx)
+    pir.qpadl_pir_set_option(dbx, pir.QPADL_OPT_STREAM_RAW, 1)
+    Qx = np.stack([np.full(C, 0x7F7F7F80, dtype=np.uint32), np.full(C, 0xFFFFFFFF, dtype=np.uint32)])
+    assert np.array_equal(_answers(dbx, Qx, path=0), oracle.answer_batch(Dx, Qx))
+
+
 def test_options_reject_bad_values():
     prm, D, db = _setup(64, 64, seed=1)
     for opt, val in ((pir.QPADL_OPT_STREAM_CHUNK, 256), (pir.QPADL_OPT_STREAM_CHUNK, 3000),

@@ -247,3 +247,25 @@ def test_replay_rejects_unsorted_arrivals(dbs):
         pir.qpadl_server_replay(srv, np.array([0.0, 2e-3, 1e-3]), [ids[0]] * 3, qs)
     assert e.value.code == pir.QPADL_EINVAL
     srv.close()
+
+
+@pytest.mark.parametrize("d", range(len(SHAPES)))
+def test_two_queued_queries_share_one_scan(dbs, d):
+    # two requests for one database, queued before start, form one launch whose
+    # streaming kernel answers both in a single pass over the database
+    srv = pir.qpadl_server_create(pir.server_config(max_batch=64, num_streams=1))
+    ids = [pir.qpadl_server_add_db(srv, h) for _, h in dbs]
+    R, C = SHAPES[d]
+    tickets = []
+    for i in range(2):
+        q = inputs.uniform_u32(C, seed=4200 + 10 * d + i, tag=inputs.TAG_MISC)
+        tickets.append((q, pir.qpadl_server_submit(srv, ids[d], q)))
+    pir.qpadl_server_start(srv)
+    for q, t in tickets:
+        rc, ans, _ = _wait(srv, t, R)
+        assert rc == pir.QPADL_OK
+        assert np.array_equal(ans, oracle.answer(dbs[d][0], q))
+    st = pir.qpadl_server_stats(srv)
+    assert st["launches"] == 1 and st["completed"] == 2
+    assert st["stream_kernels"] == 1 and st["gemm_kernels"] == 0
+    srv.close()
