@@ -98,6 +98,11 @@ int qpadl_version(void);
                                         larger ones use the handle's fp16 operand copy */
 #define QPADL_OPT_U8_KSTEP 5         /* digits per row per pipeline stage of that GEMM: 128 or 256;
                                         0 (default) = 128 */
+#define QPADL_OPT_PAIR_GEMM 6        /* batches on the fp16 operand copy and the hint: 1 (default)
+                                        = tiles of 256 rows over pairs of SMs (tcgen05
+                                        cta_group::2, each SM loads half of the vector tile);
+                                        0 = tiles of 128 rows on one SM each (stream-K split
+                                        of the last wave) */
 
 /*
  * Setup (server side; Def. 1's server holds D).  Validates `prm`, records
@@ -399,6 +404,10 @@ uint64_t qpadl_client_device_bytes(const qpadl_client *c);
  *   blocks with u > t, whose secret limbs are zero (10 of 16 blocks run);
  *   0 runs all 16.  QPADL_EINVAL for an unknown option or value. */
 #define QPADL_CLIENT_OPT_SKIP_ZERO_BLOCKS 1
+/* QPADL_CLIENT_OPT_PAIR_GEMM (default 1): run the batches on tiles of 256 rows
+ *   over pairs of SMs (tcgen05 cta_group::2: each SM loads its own matrix
+ *   rows and half of the secret rows); 0: tiles of 128 rows on one SM each. */
+#define QPADL_CLIENT_OPT_PAIR_GEMM 2
 int qpadl_client_set_option(qpadl_client *c, int option, int64_t value);
 
 /* Waits for the device and frees the context (NULL is fine). */

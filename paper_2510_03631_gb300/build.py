@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqpadl_pir.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["qpadl_pir.cu", "stream_answer.cu", "limb_gemm.cu", "limb_gemm_u8.cu", "client.cu", "noalloc.cu",
+SOURCES = ["qpadl_pir.cu", "stream_answer.cu", "limb_gemm.cu", "limb_gemm_pair.cu", "limb_gemm_u8.cu", "client.cu", "noalloc.cu",
            "server.cu", "chor.cu", "selftest.cu", "delta.cu"]
 
 

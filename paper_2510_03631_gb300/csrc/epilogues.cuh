@@ -63,6 +63,31 @@ struct QueryEpi {
     }
 };
 
+// Query without its unit vector: q_b[j] = (A s_b)[j] + e_b[j] mod 2^32.  Delta at the target
+// column (one element per vector) is added afterwards by launch_add_delta, so an element's
+// epilogue depends on no other load (a compare against a loaded target column would hold up
+// every load behind it).
+struct QueryNoiseEpi {
+    static constexpr int kLimbs = 4;
+    const int32_t *e;        // noise, row b at e + b * e_ld
+    uint64_t e_ld;
+    uint32_t *q;             // output, vector b at q + b * q_ld
+    uint64_t q_ld;
+    __device__ __forceinline__ void prefetch(uint64_t j0, uint32_t b0, uint32_t nb) const {
+        for (uint32_t b = b0; b < b0 + nb; ++b)
+            for (uint32_t l = 0; l < 4; ++l) prefetch_l2(e + b * e_ld + j0 + 32u * l);   // 128 rows x 4 B
+    }
+    __device__ __forceinline__ uint32_t pre(uint64_t j, uint32_t b) const {
+        return static_cast<uint32_t>(e[b * e_ld + j]);
+    }
+    __device__ __forceinline__ void put(uint64_t j, uint32_t b, uint32_t dot, uint32_t pre_v) const {
+        q[b * q_ld + j] = dot + pre_v;
+    }
+    __device__ __forceinline__ void operator()(uint64_t j, uint32_t b, uint32_t dot) const {
+        put(j, b, dot, pre(j, b));
+    }
+};
+
 // Recover (Def. 1 Client.BlockReconst): d_b[i] = round((ans_b[i] - (H s_b)[i]) / Delta) mod p,
 // as (x + Delta/2) >> (32 - log2 p) in uint32 arithmetic.
 struct RecoverEpi {

@@ -681,9 +681,9 @@ static cudaError_t set_planed_attrs() {
 cudaError_t prepare_limb_gemm_kernels() {
     cudaError_t e;
     if ((e = set_gemm_attrs<StoreEpi>()) != cudaSuccess) return e;
-    if ((e = set_gemm_attrs<QueryEpi>()) != cudaSuccess) return e;
+    if ((e = set_gemm_attrs<QueryNoiseEpi>()) != cudaSuccess) return e;
     if ((e = set_gemm_attrs<RecoverEpi>()) != cudaSuccess) return e;
-    if ((e = set_planed_attrs<QueryEpi>()) != cudaSuccess) return e;
+    if ((e = set_planed_attrs<QueryNoiseEpi>()) != cudaSuccess) return e;
     if ((e = set_planed_attrs<RecoverEpi>()) != cudaSuccess) return e;
     if ((e = set_gemm_attr<32, ModPEpi, false>()) != cudaSuccess) return e;
     if ((e = set_gemm_attr<64, ModPEpi, false>()) != cudaSuccess) return e;
@@ -802,10 +802,23 @@ cudaError_t launch_limb_gemm(int bn, const CUtensorMap &a_map, const CUtensorMap
     return launch_epi(bn, a_map, b_map, StoreEpi{out, ld_m, ld_b}, M, NV, K, 0, num_sms, status, stream);
 }
 
-cudaError_t launch_limb_gemm_query(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, const QueryEpi &epi,
+cudaError_t launch_limb_gemm_query(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, const QueryNoiseEpi &epi,
                                    uint32_t M, uint32_t NV, uint64_t K, uint32_t plane_chunks, int num_sms,
                                    int *status, cudaStream_t stream) {
     return launch_epi(bn, a_map, b_map, epi, M, NV, K, plane_chunks, num_sms, status, stream);
+}
+
+__global__ void add_delta_kernel(uint32_t *__restrict__ Q, uint64_t q_ld, const uint32_t *__restrict__ cols,
+                                 uint32_t B, uint32_t delta) {
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) Q[b * q_ld + cols[b]] += delta;
+}
+
+cudaError_t launch_add_delta(uint32_t *Q, uint64_t q_ld, const uint32_t *cols, uint32_t B, uint32_t delta,
+                             cudaStream_t stream) {
+    if (B == 0) return cudaSuccess;
+    add_delta_kernel<<<(B + 255) / 256, 256, 0, stream>>>(Q, q_ld, cols, B, delta);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_limb_gemm_recover(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map,
@@ -859,8 +872,9 @@ cudaError_t launch_secret_limbs(const uint32_t *S, uint32_t B, uint32_t n, __hal
 }
 
 cudaError_t launch_secret_limbs_planed(const uint32_t *S, uint32_t B, uint32_t n, uint32_t qpt, __half *V,
-                                       uint64_t pitch, int num_sms, cudaStream_t stream) {
-    const uint32_t Bp = (B + qpt - 1) / qpt * qpt;
+                                       uint64_t pitch, int num_sms, cudaStream_t stream, uint32_t Bp) {
+    if (Bp == 0) Bp = (B + qpt - 1) / qpt * qpt;
+    if (Bp < B || Bp % qpt != 0) return cudaErrorInvalidValue;
     secret_limbs_planed_kernel<<<num_sms * 4, 256, 0, stream>>>(S, B, Bp, n, qpt, V, pitch);
     return cudaGetLastError();
 }

@@ -27,9 +27,12 @@ cudaError_t launch_limb_gemm(int bn, const CUtensorMap &a_map, const CUtensorMap
 // covers the limb planes of A or H, b_map the shifted secret limb rows).
 // plane_chunks = n / 512 selects the planed mode (bn >= 64, K = 4n, rows of
 // b_map in the planed layout); 0 the plain one.
-cudaError_t launch_limb_gemm_query(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, const QueryEpi &epi,
+cudaError_t launch_limb_gemm_query(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, const QueryNoiseEpi &epi,
                                    uint32_t M, uint32_t NV, uint64_t K, uint32_t plane_chunks, int num_sms,
                                    int *status, cudaStream_t stream);
+// Q[b * q_ld + cols[b]] += delta for b < B (the unit-vector term of a batch of Queries).
+cudaError_t launch_add_delta(uint32_t *Q, uint64_t q_ld, const uint32_t *cols, uint32_t B, uint32_t delta,
+                             cudaStream_t stream);
 cudaError_t launch_limb_gemm_recover(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map,
                                      const RecoverEpi &epi, uint32_t M, uint32_t NV, uint64_t K,
                                      uint32_t plane_chunks, int num_sms, int *status, cudaStream_t stream);
@@ -55,8 +58,9 @@ cudaError_t launch_mat_row_limbs(const uint32_t *X, uint64_t rows, uint32_t n, _
                                  cudaStream_t stream);
 cudaError_t launch_secret_limbs(const uint32_t *S, uint32_t B, uint32_t n, __half *V, uint64_t pitch, int num_sms,
                                 cudaStream_t stream);
-// Planed layout for tiles of 4 * qpt rows; writes 4 * roundup(B, qpt) rows (zeros past B).
+// Planed layout for tiles of 4 * qpt rows; writes 4 * Bp rows (zeros past B), Bp = roundup(B, qpt)
+// unless given (then a multiple of qpt, >= B).
 cudaError_t launch_secret_limbs_planed(const uint32_t *S, uint32_t B, uint32_t n, uint32_t qpt, __half *V,
-                                       uint64_t pitch, int num_sms, cudaStream_t stream);
+                                       uint64_t pitch, int num_sms, cudaStream_t stream, uint32_t Bp = 0);
 
 }  // namespace qpadl

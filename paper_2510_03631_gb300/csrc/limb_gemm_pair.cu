@@ -1,0 +1,499 @@
+// Exact mod-2^32 limb GEMM on CTA pairs: the same product as limb_gemm.cu,
+//     OUT[i][b] = sum_j X[i][j] * V[b][j]   (mod 2^32),
+// with one tile of 256 matrix rows per pair of SMs (tcgen05 cta_group::2).
+//
+// Why pairs.  A 128 x BN tile on one SM moves 128 + BN operand rows from L2
+// into shared memory per k-step.  A pair tile of 256 x BN lets each SM load
+// its own 128 matrix rows but only half of the BN vector rows: the pair MMA
+// (M = 256) reads the other half from the peer's shared memory.  At BN = 256
+// each SM receives 32 KB per 64-deep k-step instead of 48 KB for the same
+// tensor work, which is what bounds the short-K client batches (Query over A,
+// Recover over H: K = 4n) and the long-K batched Response and hint.
+//
+// Exactness is that of limb_gemm.cu: balanced byte limbs in fp16, products of
+// magnitude <= 2^14 (Query/Recover) or 255 * 128 (Response, hint), 512-deep
+// chunks whose fp32 sums stay below 2^24, drained to int32 after every chunk
+// and recombined as sum_k 2^{8k} s_k in uint32 arithmetic.
+//
+// Pair protocol (cluster of 2 CTAs; rank 0 leads):
+//   producer (warp 0 of each CTA)  waits its own `empty` slot, loads its A
+//       rows and its half of the vector rows with TMA; both CTAs' copies
+//       complete on the leader's `full` barrier (the leader expects the bytes
+//       of both).
+//   MMA (warp 1 of the leader)  waits `full`, issues the pair MMAs, and
+//       commits to `empty` of both CTAs (the stage may be refilled) and, at
+//       the end of a chunk, to `acc_full` of both CTAs.
+//   epilogue (warps 2..5 of each CTA)  drains its own TMEM (its 128 rows x
+//       all N columns of the pair tile) and arrives on the leader's
+//       `acc_empty` (count 8: four warps of each CTA).
+// TMEM is allocated and freed by warp 1 of both CTAs together.  A CTA that
+// gives up on a bounded wait raises its own and its peer's abort flag; both
+// leave their loops, the leader's producer waits (bounded) for copies in
+// flight, and a cluster barrier keeps either CTA from exiting while the other
+// may still touch its shared memory.
+//
+// Column order.  The pair MMA's N columns take the leader's N/2 vector rows
+// first, then the peer's.  Plain mode: the vector rows of a tile are
+// consecutive (row n0 + n is column n).  Planed mode (client batches, n a
+// multiple of 512): a tile holds QPT = bn/4 secrets; the leader holds secrets
+// 0..QPT/2-1 of the tile and the peer the rest, each as 4 shift groups in
+// descending shift order (launch_secret_limbs_planed with qpt = QPT/2).  A
+// chunk of limb plane u needs shifts t >= u only: each CTA loads the first
+// (4 - u) QPT/2 rows of its block and the MMA runs N = (4 - u) QPT; column
+// (3 - t) QPT/2 + q is shift t of leader secret q and column N/2 + (3 - t)
+// QPT/2 + q shift t of peer secret q.
+#include <cstdint>
+#include <type_traits>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "epilogues.cuh"
+#include "limb_gemm_pair.cuh"
+#include "ptx.cuh"
+
+namespace qpadl {
+
+namespace {
+
+constexpr int kPM = 128;          // matrix rows per CTA (256 per pair)
+constexpr int kPK = 64;           // fp16 elements per 128-byte swizzled row
+constexpr uint32_t kPChunkKB = 8; // 8 x 64 = 512-deep exact chunks
+constexpr int kPThreads = 192;
+
+template <int BN>
+struct PairCfg {
+    static constexpr uint32_t kABytes = kPM * kPK * 2;           // 16 KB
+    static constexpr uint32_t kBBytes = (BN / 2) * kPK * 2;      // this CTA's half of the vector rows
+    static constexpr uint32_t kStageBytes = kABytes + kBBytes;
+    // as many stages as the 227 KB of shared memory hold (7 at 32 KB): the ring is bound by
+    // bytes in flight over the round trip of a stage, not by bandwidth
+    static constexpr int kFit = (227 * 1024 - 2048) / kStageBytes;
+    static constexpr int kStages = kFit < 8 ? kFit : 8;
+    static constexpr uint32_t kTmemCols = 2 * BN;                 // two accumulators
+    static constexpr int kSmemBytes = kStages * kStageBytes + 256 + 1024;
+    static constexpr int kQPT = BN / 4;                           // vectors per pair tile
+    static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+    static_assert(kStages >= 4, "pipeline depth");
+};
+
+__device__ __forceinline__ bool drain_wait_p(uint64_t *bar, uint32_t parity) {
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_test(bar, parity)) {
+        if (global_ns() - t0 > QPADL_WAIT_NS) return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+template <int BN, class Epi, bool PLANED>
+__global__ void __launch_bounds__(kPThreads, 1)
+    limb_gemm_pair_kernel(const __grid_constant__ CUtensorMap a_map, const __grid_constant__ PairBMaps bm, Epi epi,
+                          uint32_t M, uint32_t NV, uint32_t KB, uint32_t plane_chunks, int *__restrict__ status) {
+    using Cfg = PairCfg<BN>;
+    static_assert(Epi::kLimbs == 4, "four byte limbs per vector");
+    static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
+    static_assert(!PLANED || BN >= 128, "a planed shift group needs N/2 >= 16 rows per CTA");
+    constexpr int ST = Cfg::kStages;
+    constexpr int QPT = Cfg::kQPT;
+    constexpr int HQ = QPT / 2;   // planed: secrets per CTA block
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + ST * Cfg::kStageBytes);   // [ST], leader's counts
+    uint64_t *empty = full + ST;                                                     // [ST], own
+    uint64_t *acc_full = empty + ST;                                                 // [2], own
+    uint64_t *acc_empty = acc_full + 2;                                              // [2], leader's counts
+    uint64_t *mma_done = acc_empty + 2;                                              // [1], leader
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 8);
+        }
+        mbar_init(mma_done, 1);
+        *abort = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(tmem_slot, Cfg::kTmemCols);
+        tmem_relinquish_pair();
+    }
+    // both CTAs' barriers exist before either touches the other's
+    tc_fence_before();
+    cluster_sync();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const uint32_t full_c = cluster_addr(full, 0);          // the leader's full barriers
+    const uint32_t acc_empty_c = cluster_addr(acc_empty, 0);
+    const uint32_t peer_abort = cluster_addr(const_cast<int *>(abort), rank ^ 1u);
+
+    const uint32_t m_tiles = (M + 2 * kPM - 1) / (2 * kPM);
+    const uint32_t n_tiles = (NV + QPT - 1) / QPT;
+    const uint32_t tiles = m_tiles * n_tiles;
+    const uint32_t cluster = blockIdx.x >> 1, nclusters = gridDim.x >> 1;   // clusters are CTAs 2c, 2c + 1
+    const uint32_t nchunks = (KB + kPChunkKB - 1) / kPChunkKB;
+    bool failed = false;
+    auto fail_both = [&]() {
+        failed = true;
+        *abort = 1;
+        st_cluster_u32(peer_abort, 1u);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer (both CTAs)
+            tma_prefetch_desc(&a_map);
+#pragma unroll
+            for (int u = 0; u < (PLANED ? 4 : 1); ++u) tma_prefetch_desc(&bm.m[u]);
+            uint32_t it = 0;
+            for (uint32_t t = cluster; t < tiles && !failed; t += nclusters) {
+                const int32_t m0 = static_cast<int32_t>((t / n_tiles) * 2 * kPM + rank * kPM);
+                const int32_t r0 = static_cast<int32_t>((t % n_tiles) * BN + rank * (BN / 2));
+                {
+                    const uint32_t v0 = (t % n_tiles) * QPT;
+                    const uint32_t nv = v0 < NV ? (NV - v0 < (uint32_t)QPT ? NV - v0 : (uint32_t)QPT) : 0u;
+                    if (static_cast<uint32_t>(m0) + kPM <= M) epi.prefetch(static_cast<uint64_t>(m0), v0, nv);
+                }
+                for (uint32_t kb = 0; kb < KB; ++kb, ++it) {
+                    const uint32_t st = it % ST;
+                    const uint32_t ph = (it / ST) & 1u;
+                    if (!mbar_wait(&empty[st], ph ^ 1u, abort)) {
+                        fail_both();
+                        break;
+                    }
+                    const uint32_t u = PLANED ? (kb / kPChunkKB) / plane_chunks : 0u;
+                    const uint32_t brows = pair_b_box_rows(BN, PLANED, static_cast<int>(u));
+                    uint8_t *sa = smem + st * Cfg::kStageBytes;
+                    if (leader) mbar_arrive_expect_tx(&full[st], 2u * (Cfg::kABytes + brows * kPK * 2u));
+                    tma_load_2d_pair(sa, &a_map, full_c + 8u * st, static_cast<int32_t>(kb * kPK), m0);
+                    tma_load_2d_pair(sa + Cfg::kABytes, &bm.m[u], full_c + 8u * st, static_cast<int32_t>(kb * kPK),
+                                     r0);
+                }
+            }
+            if (leader) {
+                // the stages still owed bytes (this CTA's and the peer's copies) must land before exit
+                const uint32_t inflight = it < (uint32_t)ST ? it : (uint32_t)ST;
+                for (uint32_t j = it - inflight; j < it; ++j)
+                    if (!drain_wait_p(&full[j % ST], (j / ST) & 1u)) failed = true;
+            }
+        }
+    } else if (warp == 1) {
+        if (leader) {
+            // ---------------- MMA issuer (leader only): the whole warp walks the loop, one lane issues
+            uint32_t it = 0, ci = 0;
+            bool issued = false;
+            for (uint32_t t = cluster; t < tiles && !failed; t += nclusters) {
+                uint32_t d_tmem = tmem_base;
+                for (uint32_t kb = 0; kb < KB; ++kb, ++it) {
+                    if (kb % kPChunkKB == 0) {
+                        const uint32_t buf = ci & 1u;
+                        const bool ok = mbar_wait(&acc_empty[buf], ((ci >> 1) & 1u) ^ 1u, abort);
+                        if (__any_sync(0xffffffffu, !ok)) {
+                            fail_both();
+                            break;
+                        }
+                        tc_fence_after();
+                        d_tmem = tmem_base + buf * BN;
+                    }
+                    const uint32_t st = it % ST;
+                    const uint32_t ph = (it / ST) & 1u;
+                    const bool ok = mbar_wait(&full[st], ph, abort);
+                    if (__any_sync(0xffffffffu, !ok)) {
+                        fail_both();
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_addr(smem + st * Cfg::kStageBytes);
+                    const uint64_t adesc = umma_desc_sw128(sa);
+                    const uint64_t bdesc = umma_desc_sw128(sa + Cfg::kABytes);
+                    const uint32_t u = PLANED ? (kb / kPChunkKB) / plane_chunks : 0u;
+                    const uint32_t idesc = umma_idesc_f16(2 * kPM, PLANED ? (4u - u) * (BN / 4) : BN);
+                    const bool last_of_chunk = kb % kPChunkKB == kPChunkKB - 1 || kb == KB - 1;
+                    if (elect_one()) {
+#pragma unroll
+                        for (int k = 0; k < kPK / 16; ++k)
+                            umma_f16_pair(d_tmem, adesc + 2u * k, bdesc + 2u * k, idesc,
+                                          (kb % kPChunkKB != 0 || k != 0) ? 1u : 0u);
+                        umma_commit_pair(&empty[st], 3);
+                        if (last_of_chunk) umma_commit_pair(&acc_full[ci & 1u], 3);
+                    }
+                    __syncwarp();
+                    issued = true;
+                    if (last_of_chunk) ++ci;
+                }
+            }
+            // every pair MMA must finish before TMEM is released
+            if (issued) {
+                if (elect_one()) umma_commit_pair(mma_done, 1);
+                __syncwarp();
+                if (!drain_wait_p(mma_done, 0)) failed = true;
+            }
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5 of both CTAs; TMEM lane quarter = warp % 4)
+        const uint32_t quarter = static_cast<uint32_t>(warp & 3);
+        const uint32_t lane_addr = (quarter * 32u) << 16;
+        uint32_t ci = 0;
+        for (uint32_t t = cluster; t < tiles && !failed; t += nclusters) {
+            const uint32_t row = (t / n_tiles) * 2 * kPM + rank * kPM + quarter * 32u + static_cast<uint32_t>(lane);
+            const uint32_t v0 = (t % n_tiles) * QPT;
+            uint32_t run[QPT];
+#pragma unroll
+            for (int q = 0; q < QPT; ++q) run[q] = 0u;
+            // client tiles are short in K: their epilogue inputs are loaded as the tile starts
+            constexpr int EARLY = PLANED ? QPT : 1;
+            uint32_t early[EARLY];
+            if constexpr (PLANED) {
+#pragma unroll
+                for (int q = 0; q < QPT; ++q) early[q] = (row < M && v0 + q < NV) ? epi.pre(row, v0 + q) : 0u;
+            }
+            for (uint32_t c = 0; c < nchunks; ++c, ++ci) {
+                const uint32_t buf = ci & 1u;
+                const bool ok = mbar_wait(&acc_full[buf], (ci >> 1) & 1u, abort);
+                if (__any_sync(0xffffffffu, !ok)) {   // the TMEM loads below are warp-collective
+                    fail_both();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc = tmem_base + lane_addr + buf * BN;
+                if constexpr (PLANED) {
+                    const uint32_t u = c / plane_chunks;
+                    const uint32_t half = (4u - u) * HQ;   // N / 2
+                    for (uint32_t s = u; s < 4; ++s) {
+                        const uint32_t col = (3u - s) * HQ;
+                        if constexpr (HQ == 32) {
+                            uint32_t v[2][32];
+                            tmem_ld32(acc + col, v[0]);
+                            tmem_ld32(acc + half + col, v[1]);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                                for (int q = 0; q < 32; ++q)
+                                    run[32 * h + q] += static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[h][q])))
+                                                       << (8u * s);
+                        } else {
+                            uint32_t v[2][16];
+                            tmem_ld16(acc + col, v[0]);
+                            tmem_ld16(acc + half + col, v[1]);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                                for (int q = 0; q < 16; ++q)
+                                    run[16 * h + q] += static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[h][q])))
+                                                       << (8u * s);
+                        }
+                    }
+                } else {
+                    // two 32-column loads per wait; column 4q + k is limb k of vector q
+                    constexpr int NJ = BN / 32;
+                    constexpr int JB = NJ < 2 ? NJ : 2;
+#pragma unroll
+                    for (int j0 = 0; j0 < NJ; j0 += JB) {
+                        uint32_t v[JB][32];
+#pragma unroll
+                        for (int g = 0; g < JB; ++g) tmem_ld32(acc + 32u * (j0 + g), v[g]);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int g = 0; g < JB; ++g)
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                const uint32_t s0 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[g][4 * q + 0])));
+                                const uint32_t s1 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[g][4 * q + 1])));
+                                const uint32_t s2 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[g][4 * q + 2])));
+                                const uint32_t s3 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[g][4 * q + 3])));
+                                run[8 * (j0 + g) + q] += s0 + (s1 << 8) + (s2 << 16) + (s3 << 24);
+                            }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(acc_empty_c + 8u * buf);
+            }
+            if (failed) break;
+            if (row < M) {
+                if constexpr (PLANED) {
+#pragma unroll
+                    for (int q = 0; q < QPT; ++q)
+                        if (v0 + q < NV) epi.put(row, v0 + q, run[q], early[q]);
+                } else {
+                    // groups of up to 16 outputs: all their loads first, then all their stores
+                    constexpr int G = QPT < 16 ? QPT : 16;
+#pragma unroll
+                    for (int g = 0; g < QPT; g += G) {
+                        uint32_t pre_v[G];
+#pragma unroll
+                        for (int q = 0; q < G; ++q) pre_v[q] = (v0 + g + q < NV) ? epi.pre(row, v0 + g + q) : 0u;
+#pragma unroll
+                        for (int q = 0; q < G; ++q)
+                            if (v0 + g + q < NV) epi.put(row, v0 + g + q, run[g + q], pre_v[q]);
+                    }
+                }
+            }
+        }
+    }
+
+    if (failed) {
+        *abort = 1;
+        *status = kDevTimeout;
+        // a copy this CTA issued may still be landing (after an abort its stage is never
+        // consumed): give it a bounded moment before the CTA can exit
+        const uint64_t t0 = global_ns();
+        while (global_ns() - t0 < 200000ull) {
+        }
+    }
+    // no CTA leaves (or frees TMEM) while its peer may still reach its shared memory or TMEM
+    __syncwarp();
+    tc_fence_before();
+    cluster_sync();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, Cfg::kTmemCols);
+    }
+}
+
+// ------------------------------------------------------------------ host side
+template <int BN, class Epi, bool PLANED>
+static cudaError_t set_pair_attr() {
+    return cudaFuncSetAttribute(limb_gemm_pair_kernel<BN, Epi, PLANED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                PairCfg<BN>::kSmemBytes);
+}
+
+cudaError_t prepare_limb_gemm_pair_kernels() {
+    cudaError_t e;
+    if ((e = set_pair_attr<64, StoreEpi, false>()) != cudaSuccess) return e;
+    if ((e = set_pair_attr<128, StoreEpi, false>()) != cudaSuccess) return e;
+    if ((e = set_pair_attr<256, StoreEpi, false>()) != cudaSuccess) return e;
+    if ((e = set_pair_attr<64, QueryNoiseEpi, false>()) != cudaSuccess) return e;
+    if ((e = set_pair_attr<128, QueryNoiseEpi, false>()) != cudaSuccess) return e;
+    if ((e = set_pair_attr<256, QueryNoiseEpi, false>()) != cudaSuccess) return e;
+    if ((e = set_pair_attr<64, RecoverEpi, false>()) != cudaSuccess) return e;
+    if ((e = set_pair_attr<128, RecoverEpi, false>()) != cudaSuccess) return e;
+    if ((e = set_pair_attr<256, RecoverEpi, false>()) != cudaSuccess) return e;
+    if ((e = set_pair_attr<128, QueryNoiseEpi, true>()) != cudaSuccess) return e;
+    if ((e = set_pair_attr<256, QueryNoiseEpi, true>()) != cudaSuccess) return e;
+    if ((e = set_pair_attr<128, RecoverEpi, true>()) != cudaSuccess) return e;
+    return set_pair_attr<256, RecoverEpi, true>();
+}
+
+int limb_gemm_pair_bn_for(uint32_t nv) {
+    const uint32_t cols = 4 * nv;
+    if (cols <= 64) return 64;
+    if (cols <= 128) return 128;
+    return 256;
+}
+
+// Launch configuration of a pair kernel: clusters of 2 CTAs, one CTA per SM.
+template <int BN>
+static cudaLaunchConfig_t pair_config(unsigned clusters, cudaStream_t stream, cudaLaunchAttribute *attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * clusters);
+    cfg.blockDim = dim3(kPThreads);
+    cfg.dynamicSmemBytes = PairCfg<BN>::kSmemBytes;
+    cfg.stream = stream;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// CTA pairs that fit on the GPU at once (a GPC with an odd number of free SMs leaves one
+// idle), per device; the persistent grid is never larger, so no cluster waits for a second wave.
+template <int BN, class Epi, bool PLANED>
+static int resident_pairs(int num_sms) {
+    static int cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return num_sms / 2;
+    if (cache[dev] > 0) return cache[dev];
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = pair_config<BN>(static_cast<unsigned>(num_sms / 2), nullptr, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, limb_gemm_pair_kernel<BN, Epi, PLANED>, &cfg) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        return num_sms / 2;
+    }
+    n = n < num_sms / 2 ? n : num_sms / 2;
+    cache[dev] = n;
+    return n;
+}
+
+template <int BN, class Epi, bool PLANED>
+static cudaError_t launch_pair_t(const CUtensorMap &a_map, const PairBMaps &bm, const Epi &epi, uint32_t M,
+                                 uint32_t NV, uint32_t KB, uint32_t plane_chunks, int num_sms, int *status,
+                                 cudaStream_t stream) {
+    const uint64_t m_tiles = (M + 2ull * kPM - 1) / (2ull * kPM);
+    const uint64_t n_tiles = (NV + PairCfg<BN>::kQPT - 1) / PairCfg<BN>::kQPT;
+    const uint64_t tiles = m_tiles * n_tiles;
+    const uint64_t pairs = static_cast<uint64_t>(resident_pairs<BN, Epi, PLANED>(num_sms));
+    const uint64_t clusters = tiles < pairs ? tiles : pairs;
+    if (clusters == 0) return cudaSuccess;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = pair_config<BN>(static_cast<unsigned>(clusters), stream, attr);
+    return cudaLaunchKernelEx(&cfg, limb_gemm_pair_kernel<BN, Epi, PLANED>, a_map, bm, epi, M, NV, KB, plane_chunks,
+                              status);
+}
+
+template <class Epi>
+static cudaError_t launch_pair_epi(int bn, const CUtensorMap &a_map, const PairBMaps &bm, const Epi &epi, uint32_t M,
+                                   uint32_t NV, uint64_t K, uint32_t plane_chunks, int num_sms, int *status,
+                                   cudaStream_t stream) {
+    if (M == 0 || NV == 0 || K == 0 || num_sms < 2) return cudaErrorInvalidValue;
+    const uint32_t KB = static_cast<uint32_t>((K + kPK - 1) / kPK);
+    if (plane_chunks == 0) {
+        switch (bn) {
+            case 64: return launch_pair_t<64, Epi, false>(a_map, bm, epi, M, NV, KB, 0, num_sms, status, stream);
+            case 128: return launch_pair_t<128, Epi, false>(a_map, bm, epi, M, NV, KB, 0, num_sms, status, stream);
+            case 256: return launch_pair_t<256, Epi, false>(a_map, bm, epi, M, NV, KB, 0, num_sms, status, stream);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if constexpr (std::is_same<Epi, StoreEpi>::value) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (K != 4ull * 512 * plane_chunks) return cudaErrorInvalidValue;
+        switch (bn) {
+            case 128:
+                return launch_pair_t<128, Epi, true>(a_map, bm, epi, M, NV, KB, plane_chunks, num_sms, status, stream);
+            case 256:
+                return launch_pair_t<256, Epi, true>(a_map, bm, epi, M, NV, KB, plane_chunks, num_sms, status, stream);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+}
+
+cudaError_t launch_limb_gemm_pair(int bn, const CUtensorMap &a_map, const PairBMaps &bm, uint32_t *out,
+                                  uint64_t ld_m, uint64_t ld_b, uint32_t M, uint32_t NV, uint64_t K, int num_sms,
+                                  int *status, cudaStream_t stream) {
+    return launch_pair_epi(bn, a_map, bm, StoreEpi{out, ld_m, ld_b}, M, NV, K, 0, num_sms, status, stream);
+}
+
+cudaError_t launch_limb_gemm_pair_query(int bn, const CUtensorMap &a_map, const PairBMaps &bm,
+                                        const QueryNoiseEpi &epi,
+                                        uint32_t M, uint32_t NV, uint64_t K, uint32_t plane_chunks, int num_sms,
+                                        int *status, cudaStream_t stream) {
+    return launch_pair_epi(bn, a_map, bm, epi, M, NV, K, plane_chunks, num_sms, status, stream);
+}
+
+cudaError_t launch_limb_gemm_pair_recover(int bn, const CUtensorMap &a_map, const PairBMaps &bm,
+                                          const RecoverEpi &epi, uint32_t M, uint32_t NV, uint64_t K,
+                                          uint32_t plane_chunks, int num_sms, int *status, cudaStream_t stream) {
+    return launch_pair_epi(bn, a_map, bm, epi, M, NV, K, plane_chunks, num_sms, status, stream);
+}
+
+}  // namespace qpadl

@@ -294,8 +294,12 @@ __device__ __forceinline__ void cluster_sync() {
 }
 
 // Arrive once on an mbarrier given by its shared::cluster address (possibly in the peer CTA).
+// Default (CTA-scope release) semantics: a cluster-scope release would first wait for every
+// global load and store the thread has in flight.  The arrivals this kernel makes order TMEM
+// reads (completed by tcgen05.wait::ld and fenced by tcgen05.fence::before_thread_sync), which
+// needs no wider release.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cbar) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cbar) : "memory");
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cbar) : "memory");
 }
 
 // Store a word into shared memory given by its shared::cluster address (possibly in the peer CTA).

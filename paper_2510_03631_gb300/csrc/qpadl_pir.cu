@@ -18,6 +18,7 @@
 #include "chor.cuh"
 #include "client.cuh"
 #include "limb_gemm.cuh"
+#include "limb_gemm_pair.cuh"
 #include "limb_gemm_u8.cuh"
 #include "internal.cuh"
 #include "qpadl_pir.h"
@@ -47,6 +48,7 @@ struct qpadl_db {
     CUtensorMap u8_map[2];           // over blk: box {128, 128, ks/128, 1} for ks = 128, 256
     uint32_t u8_max_batch = 32;      // QPADL_OPT_U8_MAX_BATCH
     int u8_kstep = 0;                // QPADL_OPT_U8_KSTEP (0 = per tile width default)
+    int pair_gemm = 1;               // QPADL_OPT_PAIR_GEMM
     __half *d16 = nullptr;           // digits as fp16, R x pitch
     uint64_t pitch = 0;              // roundup(C, 8)
     CUtensorMap a_map;
@@ -72,6 +74,7 @@ struct qpadl_client {
     int *d_status = nullptr;
     uint64_t owned_bytes = 0;
     bool planed = true;              // skip the zero (plane, shift) blocks when n % 512 == 0
+    bool pair = true;                // tiles over pairs of SMs (QPADL_CLIENT_OPT_PAIR_GEMM)
 };
 
 // Goldberg-style Z_p database handle: the lattice handle of the same bytes
@@ -153,6 +156,7 @@ int prepare_device(int dev) {
     if (prepared[dev]) return QPADL_OK;
     QPADL_CU(prepare_stream_kernels());
     QPADL_CU(prepare_limb_gemm_kernels());
+    QPADL_CU(prepare_limb_gemm_pair_kernels());
     QPADL_CU(prepare_limb_gemm_u8_kernels());
     QPADL_CU(prepare_client_kernels());
     QPADL_CU(prepare_chor_kernels());
@@ -242,16 +246,33 @@ int set_device(const qpadl_db *db) {
     return QPADL_OK;
 }
 
-// out[i * ld_m + v * ld_b] = D * X[v] for NV vectors given as fp16 limbs in db->limbs
-int run_limb_gemm(qpadl_db *db, uint32_t NV, uint32_t *out, uint64_t ld_m, uint64_t ld_b, cudaStream_t stream) {
+// out[i * ld_m + v * ld_b] = D * X[v] for NV vectors given as fp16 limbs at `limbs`
+// (4 NV rows of db->pitch elements), on CTA pairs or single SMs (QPADL_OPT_PAIR_GEMM)
+int run_limb_gemm_at(qpadl_db *db, const __half *limbs, uint32_t NV, uint32_t *out, uint64_t ld_m, uint64_t ld_b,
+                     cudaStream_t stream) {
+    if (db->pair_gemm && db->num_sms >= 2) {
+        const int bn = limb_gemm_pair_bn_for(NV);
+        PairBMaps bm;
+        std::memset(&bm, 0, sizeof(bm));
+        if (!encode_2d(&bm.m[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, limbs, db->prm.cols, 4ull * NV, db->pitch * 2,
+                       kLimbBoxK, pair_b_box_rows(bn, false, 0), CU_TENSOR_MAP_SWIZZLE_128B))
+            return QPADL_ECUDA;
+        QPADL_CU(launch_limb_gemm_pair(bn, db->a_map, bm, out, ld_m, ld_b, static_cast<uint32_t>(db->prm.rows), NV,
+                                       db->prm.cols, db->num_sms, db->d_status, stream));
+        return QPADL_OK;
+    }
     const int bn = limb_gemm_bn_for(NV);
     CUtensorMap b_map;
-    if (!encode_2d(&b_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, db->limbs, db->prm.cols, 4ull * NV, db->pitch * 2,
+    if (!encode_2d(&b_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, limbs, db->prm.cols, 4ull * NV, db->pitch * 2,
                    kLimbBoxK, static_cast<uint32_t>(bn), CU_TENSOR_MAP_SWIZZLE_128B))
         return QPADL_ECUDA;
     QPADL_CU(launch_limb_gemm(bn, db->a_map, b_map, out, ld_m, ld_b, static_cast<uint32_t>(db->prm.rows), NV,
                               db->prm.cols, db->num_sms, db->d_status, stream));
     return QPADL_OK;
+}
+
+int run_limb_gemm(qpadl_db *db, uint32_t NV, uint32_t *out, uint64_t ld_m, uint64_t ld_b, cudaStream_t stream) {
+    return run_limb_gemm_at(db, db->limbs, NV, out, ld_m, ld_b, stream);
 }
 
 int answer_stream_group(qpadl_db *db, const uint32_t *Q, uint32_t nq, uint32_t *ans, cudaStream_t stream) {
@@ -424,14 +445,7 @@ int db_answer_f16_ws(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans,
     if (!db->d16) return QPADL_EINVAL;
     const uint64_t C = db->prm.cols, R = db->prm.rows;
     QPADL_CU(launch_vec_limbs(Q, C, B, C, limbs, db->pitch, db->num_sms, stream));
-    const int bn = limb_gemm_bn_for(B);
-    CUtensorMap b_map;
-    if (!encode_2d(&b_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, limbs, C, 4ull * B, db->pitch * 2, kLimbBoxK,
-                   static_cast<uint32_t>(bn), CU_TENSOR_MAP_SWIZZLE_128B))
-        return QPADL_ECUDA;
-    QPADL_CU(launch_limb_gemm(bn, db->a_map, b_map, ans, 1, R, static_cast<uint32_t>(R), B, C, db->num_sms,
-                              db->d_status, stream));
-    return QPADL_OK;
+    return run_limb_gemm_at(db, limbs, B, ans, 1, R, stream);
 }
 
 int db_answer_one_noscratch(qpadl_db *db, const uint32_t *q, uint32_t *ans, cudaStream_t stream) {
@@ -733,6 +747,10 @@ int qpadl_pir_set_option(qpadl_db *db, int option, int64_t value) {
             if (value != 0 && value != 128 && value != 256) return QPADL_EINVAL;
             db->u8_kstep = static_cast<int>(value);
             return QPADL_OK;
+        case QPADL_OPT_PAIR_GEMM:
+            if (value != 0 && value != 1) return QPADL_EINVAL;
+            db->pair_gemm = static_cast<int>(value);
+            return QPADL_OK;
         default: return QPADL_EINVAL;
     }
 }
@@ -745,6 +763,7 @@ int qpadl_pir_get_option(const qpadl_db *db, int option, int64_t *value) {
         case QPADL_OPT_STREAM_RAW: *value = db->stream_raw; return QPADL_OK;
         case QPADL_OPT_U8_MAX_BATCH: *value = db->u8_max_batch; return QPADL_OK;
         case QPADL_OPT_U8_KSTEP: *value = db->u8_kstep; return QPADL_OK;
+        case QPADL_OPT_PAIR_GEMM: *value = db->pair_gemm; return QPADL_OK;
         default: return QPADL_EINVAL;
     }
 }
@@ -978,6 +997,33 @@ int client_secret_operand(qpadl_client *c, const uint32_t *S, uint32_t Bc, int b
     return QPADL_OK;
 }
 
+// Pair-tile form of the secret operand: planed rows with qpt = bn / 8 padded to whole
+// pair tiles (bn / 4 secrets), or the plain shifted rows; one map per limb plane.
+int client_secret_operand_pair(qpadl_client *c, const uint32_t *S, uint32_t Bc, int bn, uint32_t plane_chunks,
+                               PairBMaps *bm, cudaStream_t s) {
+    const uint32_t n = c->prm.n;
+    std::memset(bm, 0, sizeof(*bm));
+    uint64_t rows = 4ull * Bc;
+    if (plane_chunks) {
+        const uint32_t qpt = static_cast<uint32_t>(bn / 8), per_tile = static_cast<uint32_t>(bn / 4);
+        const uint32_t Bp = (Bc + per_tile - 1) / per_tile * per_tile;
+        QPADL_CU(launch_secret_limbs_planed(S, Bc, n, qpt, c->v, c->pitch, c->num_sms, s, Bp));
+        rows = 4ull * Bp;
+    } else {
+        QPADL_CU(launch_secret_limbs(S, Bc, n, c->v, c->pitch, c->num_sms, s));
+    }
+    for (int u = 0; u < (plane_chunks ? 4 : 1); ++u)
+        if (!encode_2d(&bm->m[u], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, c->v, 4ull * n, rows, c->pitch * 2, kLimbBoxK,
+                       pair_b_box_rows(bn, plane_chunks != 0, u), CU_TENSOR_MAP_SWIZZLE_128B))
+            return QPADL_ECUDA;
+    return QPADL_OK;
+}
+
+// Planed pair tiles need n a multiple of 512 and at least 16 secret rows per shift group.
+uint32_t client_pair_plane_chunks(const qpadl_client *c, int bn) {
+    return (c->planed && c->prm.n % 512 == 0 && bn >= 128) ? c->prm.n / 512 : 0u;
+}
+
 }  // namespace
 
 int qpadl_client_query_batch(qpadl_client *c, const uint32_t *S_dev, const int32_t *E_dev, const uint32_t *cols_dev,
@@ -989,14 +1035,26 @@ int qpadl_client_query_batch(qpadl_client *c, const uint32_t *S_dev, const int32
     const uint32_t delta = static_cast<uint32_t>((1ull << 32) / c->prm.p);
     for (uint32_t b0 = 0; b0 < B; b0 += c->max_batch) {
         const uint32_t Bc = std::min(B - b0, c->max_batch);
+        const QueryNoiseEpi epi{E_dev + (uint64_t)b0 * C, C, Q_dev + (uint64_t)b0 * C, C};
+        if (c->pair && c->num_sms >= 2) {
+            const int bn = limb_gemm_pair_bn_for(Bc);
+            const uint32_t pc = client_pair_plane_chunks(c, bn);
+            PairBMaps bm;
+            int rc = client_secret_operand_pair(c, S_dev + (uint64_t)b0 * n, Bc, bn, pc, &bm, s);
+            if (rc != QPADL_OK) return rc;
+            QPADL_CU(launch_limb_gemm_pair_query(bn, c->a_map, bm, epi, static_cast<uint32_t>(C), Bc, 4 * n, pc,
+                                                 c->num_sms, c->d_status, s));
+            QPADL_CU(launch_add_delta(Q_dev + (uint64_t)b0 * C, C, cols_dev + b0, Bc, delta, s));
+            continue;
+        }
         const int bn = limb_gemm_bn_for(Bc);
         const uint32_t pc = client_plane_chunks(c, bn);
         CUtensorMap v_map;
         int rc = client_secret_operand(c, S_dev + (uint64_t)b0 * n, Bc, bn, pc, &v_map, s);
         if (rc != QPADL_OK) return rc;
-        const QueryEpi epi{E_dev + (uint64_t)b0 * C, C, cols_dev + b0, 0, delta, Q_dev + (uint64_t)b0 * C, C};
         QPADL_CU(launch_limb_gemm_query(bn, c->a_map, v_map, epi, static_cast<uint32_t>(C), Bc, 4 * n, pc,
                                         c->num_sms, c->d_status, s));
+        QPADL_CU(launch_add_delta(Q_dev + (uint64_t)b0 * C, C, cols_dev + b0, Bc, delta, s));
     }
     return QPADL_OK;
 }
@@ -1010,12 +1068,22 @@ int qpadl_client_recover_batch(qpadl_client *c, const uint32_t *ans_dev, const u
     const uint32_t shift = 32u - static_cast<uint32_t>(log2_exact(c->prm.p));
     for (uint32_t b0 = 0; b0 < B; b0 += c->max_batch) {
         const uint32_t Bc = std::min(B - b0, c->max_batch);
+        const RecoverEpi epi{ans_dev + (uint64_t)b0 * R, R, shift, out_dev + (uint64_t)b0 * R, R};
+        if (c->pair && c->num_sms >= 2) {
+            const int bn = limb_gemm_pair_bn_for(Bc);
+            const uint32_t pc = client_pair_plane_chunks(c, bn);
+            PairBMaps bm;
+            int rc = client_secret_operand_pair(c, S_dev + (uint64_t)b0 * n, Bc, bn, pc, &bm, s);
+            if (rc != QPADL_OK) return rc;
+            QPADL_CU(launch_limb_gemm_pair_recover(bn, c->h_map, bm, epi, static_cast<uint32_t>(R), Bc, 4 * n, pc,
+                                                   c->num_sms, c->d_status, s));
+            continue;
+        }
         const int bn = limb_gemm_bn_for(Bc);
         const uint32_t pc = client_plane_chunks(c, bn);
         CUtensorMap v_map;
         int rc = client_secret_operand(c, S_dev + (uint64_t)b0 * n, Bc, bn, pc, &v_map, s);
         if (rc != QPADL_OK) return rc;
-        const RecoverEpi epi{ans_dev + (uint64_t)b0 * R, R, shift, out_dev + (uint64_t)b0 * R, R};
         QPADL_CU(launch_limb_gemm_recover(bn, c->h_map, v_map, epi, static_cast<uint32_t>(R), Bc, 4 * n, pc,
                                           c->num_sms, c->d_status, s));
     }
@@ -1044,6 +1112,10 @@ int qpadl_client_set_option(qpadl_client *c, int option, int64_t value) {
         case QPADL_CLIENT_OPT_SKIP_ZERO_BLOCKS:
             if (value != 0 && value != 1) return QPADL_EINVAL;
             c->planed = value != 0;
+            return QPADL_OK;
+        case QPADL_CLIENT_OPT_PAIR_GEMM:
+            if (value != 0 && value != 1) return QPADL_EINVAL;
+            c->pair = value != 0;
             return QPADL_OK;
         default: return QPADL_EINVAL;
     }

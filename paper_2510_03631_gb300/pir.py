@@ -30,6 +30,7 @@ QPADL_OPT_TENSOR_MIN_BATCH = 2
 QPADL_OPT_STREAM_RAW = 3
 QPADL_OPT_U8_MAX_BATCH = 4
 QPADL_OPT_U8_KSTEP = 5
+QPADL_OPT_PAIR_GEMM = 6
 
 
 class QpadlError(RuntimeError):
@@ -440,6 +441,7 @@ def qpadl_client_status(c: Client) -> int:
 
 
 QPADL_CLIENT_OPT_SKIP_ZERO_BLOCKS = 1
+QPADL_CLIENT_OPT_PAIR_GEMM = 2
 
 
 def qpadl_client_set_option(c: Client, option: int, value: int):

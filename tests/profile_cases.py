@@ -158,6 +158,7 @@ def main():
     ap.add_argument("--raw", type=int, default=-1, help="1: single query packed inside the kernel")
     ap.add_argument("--u8max", type=int, default=-1, help="largest batch on the uint8-digit GEMM")
     ap.add_argument("--kstep", type=int, default=-1, help="digits per row per stage of that GEMM")
+    ap.add_argument("--pair", type=int, default=-1, help="1: GEMMs on tiles over pairs of SMs, 0: single-SM tiles")
     ap.add_argument("--client", type=int, default=1, help="qbatch/rbatch: 1 = tensor-core client context, "
                                                             "0 = CUDA-core batch entry point")
     a = ap.parse_args()
@@ -180,7 +181,10 @@ def main():
         pir.qpadl_pir_set_option(db, pir.QPADL_OPT_U8_MAX_BATCH, a.u8max)
     if a.kstep >= 0:
         pir.qpadl_pir_set_option(db, pir.QPADL_OPT_U8_KSTEP, a.kstep)
-    res = {"case": a.case, "rows": R, "cols": C, "chunk": pir.qpadl_pir_get_option(db, pir.QPADL_OPT_STREAM_CHUNK)}
+    if a.pair >= 0:
+        pir.qpadl_pir_set_option(db, pir.QPADL_OPT_PAIR_GEMM, a.pair)
+    res = {"case": a.case, "rows": R, "cols": C, "chunk": pir.qpadl_pir_get_option(db, pir.QPADL_OPT_STREAM_CHUNK),
+           "pair": a.pair}
     if a.case == "stream":
         X_np = inputs.uniform_u32(C, seed=2, tag=inputs.TAG_MISC)
         q = pir.from_u32(X_np)
@@ -236,6 +240,8 @@ def main():
             Q = torch.empty(B * rows, dtype=torch.int32, device="cuda")
             if a.client:
                 cl = pir.qpadl_client_create(cprm, X, None, max_batch=B)
+                if a.pair >= 0:
+                    pir.qpadl_client_set_option(cl, pir.QPADL_CLIENT_OPT_PAIR_GEMM, a.pair)
                 fn = lambda: pir.qpadl_client_query_batch(cl, S, E, cols_t, Q)
             else:
                 fn = lambda: pir.qpadl_pir_query_batch(cprm, X, S, E, cols_t, Q)
@@ -252,6 +258,8 @@ def main():
             if a.client:
                 A_dummy = torch.zeros(C * n, dtype=torch.int32, device="cuda")
                 cl = pir.qpadl_client_create(cprm, A_dummy, Xr, max_batch=B)
+                if a.pair >= 0:
+                    pir.qpadl_client_set_option(cl, pir.QPADL_CLIENT_OPT_PAIR_GEMM, a.pair)
                 fn = lambda: pir.qpadl_client_recover_batch(cl, ans, S, out)
             else:
                 fn = lambda: pir.qpadl_pir_recover_batch(cprm, ans, Xr, S, out)

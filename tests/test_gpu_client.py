@@ -27,8 +27,9 @@ CASES = [(1024, 1024, 512, 8, 1024), (700, 1000, 64, 37, 16), (300, 4096 + 48, 9
          (2048, 2048, 1024, 256, 256), (129, 257, 16, 3, 1), (512, 512, 128, 65, 65)]
 
 
+@pytest.mark.parametrize("pair", [1, 0])
 @pytest.mark.parametrize("R,C,n,B,max_batch", CASES)
-def test_query_and_recover_match_oracle(cuda, R, C, n, B, max_batch):
+def test_query_and_recover_match_oracle(cuda, R, C, n, B, max_batch, pair):
     seed = R + C + n + B
     D = inputs.db_digits(R, C, 256, seed=seed)
     A_np = inputs.public_matrix(C, n, seed=seed + 1)
@@ -41,6 +42,7 @@ def test_query_and_recover_match_oracle(cuda, R, C, n, B, max_batch):
     E = torch.from_numpy(np.ascontiguousarray(E_np).reshape(-1)).cuda()
     cols_t = torch.from_numpy(cols.astype(np.int32)).cuda()
     cl = pir.qpadl_client_create(prm, A, H, max_batch=max_batch)
+    pir.qpadl_client_set_option(cl, pir.QPADL_CLIENT_OPT_PAIR_GEMM, pair)
     Q = torch.empty(B * C, dtype=torch.int32, device="cuda")
     pir.qpadl_client_query_batch(cl, S, E, cols_t, Q)
     Q_simt = torch.empty_like(Q)
@@ -67,7 +69,8 @@ def test_query_and_recover_match_oracle(cuda, R, C, n, B, max_batch):
 @pytest.mark.parametrize("R,C,n,B,max_batch", [(1000, 1500, 512, 12, 64), (700, 600, 512, 24, 1024),
                                                (300, 2048 + 40, 1024, 37, 1024), (513, 1000, 1024, 150, 70)])
 @pytest.mark.parametrize("skip", [0, 1])
-def test_zero_block_skipping_on_and_off(cuda, R, C, n, B, max_batch, skip):
+@pytest.mark.parametrize("pair", [1, 0])
+def test_zero_block_skipping_on_and_off(cuda, R, C, n, B, max_batch, skip, pair):
     seed = 3 * R + C + n + B
     D = inputs.db_digits(R, C, 256, seed=seed)
     A_np = inputs.public_matrix(C, n, seed=seed + 1)
@@ -78,6 +81,7 @@ def test_zero_block_skipping_on_and_off(cuda, R, C, n, B, max_batch, skip):
     cl = pir.qpadl_client_create(pir.params(R, C, n, seed=seed), _dev_u32(A_np), _dev_u32(H_np),
                                  max_batch=max_batch)
     pir.qpadl_client_set_option(cl, pir.QPADL_CLIENT_OPT_SKIP_ZERO_BLOCKS, skip)
+    pir.qpadl_client_set_option(cl, pir.QPADL_CLIENT_OPT_PAIR_GEMM, pair)
     Q = torch.empty(B * C, dtype=torch.int32, device="cuda")
     pir.qpadl_client_query_batch(cl, _dev_u32(S_np), torch.from_numpy(E_np.reshape(-1)).cuda(),
                                  torch.from_numpy(cols.astype(np.int32)).cuda(), Q)
@@ -100,14 +104,16 @@ def test_zero_block_skipping_on_and_off(cuda, R, C, n, B, max_batch, skip):
 @pytest.mark.parametrize("a_word,s_word", [(0xFFFFFFFF, 0xFFFFFFFF), (0x80808080, 0x80808080),
                                            (0x7F7F7F7F, 0x80808080), (0x80808080, 0x7F7F7F7F),
                                            (0x7F7F7F7F, 0x7F7F7F7F), (0x00800080, 0xFF7FFF80)])
-def test_limb_boundary_values(cuda, a_word, s_word):
-    # every limb at +-127/-128 pushes each 512-deep chunk to its exactness bound
-    R, C, n, B = 256, 512, 1024, 16   # B = 16: planed mode, shift groups of 16 columns
+@pytest.mark.parametrize("B", [16, 40])
+def test_limb_boundary_values(cuda, a_word, s_word, B):
+    # every limb at +-127/-128 pushes each 512-deep chunk to its exactness bound; B = 16 runs
+    # 64-wide pair tiles (plain), B = 40 planed 256-wide pair tiles
+    R, C, n = 256, 512, 1024
     A_np = np.full((C, n), a_word, dtype=np.uint32)
     S_np = np.full((B, n), s_word, dtype=np.uint32)
     H_np = np.full((R, n), a_word, dtype=np.uint32)
     E_np = np.zeros((B, C), dtype=np.int32)
-    cols = np.array([0, 1, C - 1, 77] * 4, dtype=np.int32)
+    cols = np.array([0, 1, C - 1, 77] * (B // 4), dtype=np.int32)
     prm = pir.params(R, C, n)
     cl = pir.qpadl_client_create(prm, _dev_u32(A_np), _dev_u32(H_np), max_batch=B)
     Q = torch.empty(B * C, dtype=torch.int32, device="cuda")

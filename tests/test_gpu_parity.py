@@ -212,9 +212,46 @@ def test_answer_batch_split_tiles(R, C, B):
     # all SMs (pieces add into a zeroed output): 626 tiles of 5 chunks (the last one 64 deep),
     # 157 tiles of 3 chunks, and 16 tiles of 2 chunks spread over more SMs than tiles
     prm, D, db = _setup(R, C, seed=R + C)
+    pir.qpadl_pir_set_option(db, pir.QPADL_OPT_PAIR_GEMM, 0)   # the single-SM tiles split their last waves
     Q = inputs.uniform_u32(B * C, seed=B + 5, tag=inputs.TAG_MISC).reshape(B, C)
     got = _answers(db, Q, path=1)
     assert np.array_equal(got, oracle.answer_batch(D, Q, threads=oracle.max_threads()))
+
+
+@pytest.mark.parametrize("R,C,B", [
+    (300, 1000 + 8, 33),     # one pair tile row: the peer's rows partly past R; ragged K
+    (257, 640, 64),          # a second pair row of one matrix row
+    (1000, 2048, 100),       # ragged vector tile (400 of 512 limb rows)
+    (4099, 1536, 200),       # many pair tiles, ragged in rows and vectors
+    (128, 64, 40),           # the peer holds no rows at all; K below one k-step
+    (20000, 1100, 300),      # several tiles per CTA pair, rings wrapping
+    (600, 512, 17),          # 68 limb columns: 128-wide pair tiles (u8 GEMM off)
+    (600, 512, 9),           # 36 limb columns: 64-wide pair tiles (u8 GEMM off)
+])
+def test_answer_batch_pair_and_single_sm_gemms(R, C, B):
+    # the fp16-copy GEMM on tiles of 256 rows over pairs of SMs and on 128-row tiles of one SM
+    prm, D, db = _setup(R, C, seed=R + 3 * B)
+    pir.qpadl_pir_set_option(db, pir.QPADL_OPT_U8_MAX_BATCH, 0)
+    Q = inputs.uniform_u32(B * C, seed=C + 7 * B, tag=inputs.TAG_MISC).reshape(B, C)
+    exp = oracle.answer_batch(D, Q, threads=oracle.max_threads())
+    for pair in (1, 0):
+        pir.qpadl_pir_set_option(db, pir.QPADL_OPT_PAIR_GEMM, pair)
+        assert pir.qpadl_pir_get_option(db, pir.QPADL_OPT_PAIR_GEMM) == pair
+        assert np.array_equal(_answers(db, Q, path=1), exp), f"pair {pair}"
+
+
+def test_answer_batch_pair_gemm_extreme_values():
+    # every digit 255 against limb-extreme query words: each 512-deep chunk at its exactness bound
+    R, C, B = 512, 2048, 64
+    D = np.full((R, C), 255, dtype=np.uint8)
+    prm, D, db = _setup(R, C, D=D)
+    pir.qpadl_pir_set_option(db, pir.QPADL_OPT_PAIR_GEMM, 1)
+    words = np.array([0x7F7F7F80, 0x7F7F7F7F, 0xFFFFFFFF, 0x80808080], dtype=np.uint32)
+    Q = np.repeat(words, B // 4)[:, None].repeat(C, axis=1)
+    exp = ((255 * C * Q[:, 0].astype(np.uint64)) & M32).astype(np.uint32)
+    got = _answers(db, Q, path=1)
+    for b in range(B):
+        assert np.all(got[b] == exp[b]), hex(int(Q[b, 0]))
 
 
 def test_answer_batch_linearity_on_device():
@@ -244,8 +281,10 @@ def test_small_plaintext_modulus_and_digit_check():
 # ------------------------------------------------------------------ Hint
 @pytest.mark.parametrize("R,C,n", [(1024, 1024, 512), (100, 1000, 17), (129, 520, 1), (300, 64, 70),
                                    (40000, 700, 64)])   # 313 row tiles: whole waves, then a split last wave
-def test_hint_matches_oracle(R, C, n):
+@pytest.mark.parametrize("pair", [1, 0])
+def test_hint_matches_oracle(R, C, n, pair):
     prm, D, db = _setup(R, C, n=n, seed=n)
+    pir.qpadl_pir_set_option(db, pir.QPADL_OPT_PAIR_GEMM, pair)
     A = torch.empty(C * n, dtype=torch.int32, device="cuda")
     pir.qpadl_pir_gen_a(prm, A)
     H = torch.full((R * n,), -1, dtype=torch.int32, device="cuda")
