@@ -10,16 +10,20 @@
 // tensor work, which is what bounds the short-K client batches (Query over A,
 // Recover over H: K = 4n) and the long-K batched Response and hint.
 //
-// Exactness is that of limb_gemm.cu: balanced byte limbs in fp16, products of
-// magnitude <= 2^14 (Query/Recover) or 255 * 128 (Response, hint), 512-deep
-// chunks whose fp32 sums stay below 2^24, drained to int32 after every chunk
-// and recombined as sum_k 2^{8k} s_k in uint32 arithmetic.
+// Exactness is that of limb_gemm.cu: balanced byte limbs in fp16, drained to
+// int32 after every exact chunk and recombined as sum_k 2^{8k} s_k in uint32
+// arithmetic.  The chunk depth follows the products' bound: digits times limbs
+// (Response, hint; magnitude <= 255 * 128) take 512-deep chunks, whose sums
+// stay below 2^24; limbs times limbs (client Query/Recover; magnitude <= 2^14)
+// take 1024-deep chunks, whose partial sums never exceed 2^24 in magnitude.
+// Every integer of magnitude <= 2^24 is an fp32 value, so no partial sum is
+// ever rounded either way.
 //
 // Pair protocol (cluster of 2 CTAs; rank 0 leads):
-//   producer (warp 0 of each CTA)  waits its own `empty` slot, loads its A
-//       rows and its half of the vector rows with TMA; both CTAs' copies
-//       complete on the leader's `full` barrier (the leader expects the bytes
-//       of both).
+//   producers (warps 0 and 6 of each CTA)  wait their own `empty` slot; warp
+//       0 loads the CTA's A rows and warp 6 its half of the vector rows with
+//       TMA; every copy completes on the leader's `full` barrier (the leader's
+//       warp 0 expects the bytes of both CTAs).
 //   MMA (warp 1 of the leader)  waits `full`, issues the pair MMAs, and
 //       commits to `empty` of both CTAs (the stage may be refilled) and, at
 //       the end of a chunk, to `acc_full` of both CTAs.
@@ -57,8 +61,7 @@ namespace {
 
 constexpr int kPM = 128;          // matrix rows per CTA (256 per pair)
 constexpr int kPK = 64;           // fp16 elements per 128-byte swizzled row
-constexpr uint32_t kPChunkKB = 8; // 8 x 64 = 512-deep exact chunks
-constexpr int kPThreads = 192;
+constexpr int kPThreads = 224;   // warps: 0 matrix-tile producer, 1 MMA, 2..5 epilogue, 6 vector-tile producer
 
 template <int BN>
 struct PairCfg {
@@ -90,7 +93,8 @@ __device__ __forceinline__ bool drain_wait_p(uint64_t *bar, uint32_t parity) {
 template <int BN, class Epi, bool PLANED>
 __global__ void __launch_bounds__(kPThreads, 1)
     limb_gemm_pair_kernel(const __grid_constant__ CUtensorMap a_map, const __grid_constant__ PairBMaps bm, Epi epi,
-                          uint32_t M, uint32_t NV, uint32_t KB, uint32_t plane_chunks, int *__restrict__ status) {
+                          uint32_t M, uint32_t NV, uint32_t KB, uint32_t ckb, uint32_t plane_chunks,
+                          int *__restrict__ status) {
     using Cfg = PairCfg<BN>;
     static_assert(Epi::kLimbs == 4, "four byte limbs per vector");
     static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     const uint32_t n_tiles = (NV + QPT - 1) / QPT;
     const uint32_t tiles = m_tiles * n_tiles;
     const uint32_t cluster = blockIdx.x >> 1, nclusters = gridDim.x >> 1;   // clusters are CTAs 2c, 2c + 1
-    const uint32_t nchunks = (KB + kPChunkKB - 1) / kPChunkKB;
+    const uint32_t nchunks = (KB + ckb - 1) / ckb;
     bool failed = false;
     auto fail_both = [&]() {
         failed = true;
@@ -151,39 +155,56 @@ __global__ void __launch_bounds__(kPThreads, 1)
         st_cluster_u32(peer_abort, 1u);
     };
 
-    if (warp == 0) {
+    if (warp == 0 || warp == 6) {
         if (lane == 0) {
-            // ---------------- TMA producer (both CTAs)
-            tma_prefetch_desc(&a_map);
+            // ---------------- TMA producers (both CTAs): warp 0 loads the matrix tiles (and, in the
+            // leader, arms each stage for the bytes of both CTAs), warp 6 the vector tiles; the two
+            // copy streams issue in parallel
+            const bool mat = warp == 0;
+            if (mat) tma_prefetch_desc(&a_map);
+            else {
 #pragma unroll
-            for (int u = 0; u < (PLANED ? 4 : 1); ++u) tma_prefetch_desc(&bm.m[u]);
-            uint32_t it = 0;
+                for (int u = 0; u < (PLANED ? 4 : 1); ++u) tma_prefetch_desc(&bm.m[u]);
+            }
+            const uint32_t kpp = PLANED ? ckb * plane_chunks : KB;   // k-steps per limb plane
+            uint32_t it = 0, st = 0, ph = 0;
             for (uint32_t t = cluster; t < tiles && !failed; t += nclusters) {
                 const int32_t m0 = static_cast<int32_t>((t / n_tiles) * 2 * kPM + rank * kPM);
                 const int32_t r0 = static_cast<int32_t>((t % n_tiles) * BN + rank * (BN / 2));
-                {
+                if (mat) {
                     const uint32_t v0 = (t % n_tiles) * QPT;
                     const uint32_t nv = v0 < NV ? (NV - v0 < (uint32_t)QPT ? NV - v0 : (uint32_t)QPT) : 0u;
                     if (static_cast<uint32_t>(m0) + kPM <= M) epi.prefetch(static_cast<uint64_t>(m0), v0, nv);
                 }
+                uint32_t u = 0, kin = 0;   // limb plane of k-step kb, and kb's place in it
                 for (uint32_t kb = 0; kb < KB; ++kb, ++it) {
-                    const uint32_t st = it % ST;
-                    const uint32_t ph = (it / ST) & 1u;
                     if (!mbar_wait(&empty[st], ph ^ 1u, abort)) {
                         fail_both();
                         break;
                     }
-                    const uint32_t u = PLANED ? (kb / kPChunkKB) / plane_chunks : 0u;
-                    const uint32_t brows = pair_b_box_rows(BN, PLANED, static_cast<int>(u));
                     uint8_t *sa = smem + st * Cfg::kStageBytes;
-                    if (leader) mbar_arrive_expect_tx(&full[st], 2u * (Cfg::kABytes + brows * kPK * 2u));
-                    tma_load_2d_pair(sa, &a_map, full_c + 8u * st, static_cast<int32_t>(kb * kPK), m0);
-                    tma_load_2d_pair(sa + Cfg::kABytes, &bm.m[u], full_c + 8u * st, static_cast<int32_t>(kb * kPK),
-                                     r0);
+                    if (mat) {
+                        if (leader) {
+                            const uint32_t brows = pair_b_box_rows(BN, PLANED, static_cast<int>(u));
+                            mbar_arrive_expect_tx(&full[st], 2u * (Cfg::kABytes + brows * kPK * 2u));
+                        }
+                        tma_load_2d_pair(sa, &a_map, full_c + 8u * st, static_cast<int32_t>(kb * kPK), m0);
+                    } else {
+                        tma_load_2d_pair(sa + Cfg::kABytes, &bm.m[u], full_c + 8u * st,
+                                         static_cast<int32_t>(kb * kPK), r0);
+                    }
+                    if (++st == (uint32_t)ST) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
+                    if (++kin == kpp) {
+                        kin = 0;
+                        ++u;
+                    }
                 }
             }
-            if (leader) {
-                // the stages still owed bytes (this CTA's and the peer's copies) must land before exit
+            if (leader && mat) {
+                // the stages still owed bytes (both producers' and the peer's copies) must land before exit
                 const uint32_t inflight = it < (uint32_t)ST ? it : (uint32_t)ST;
                 for (uint32_t j = it - inflight; j < it; ++j)
                     if (!drain_wait_p(&full[j % ST], (j / ST) & 1u)) failed = true;
@@ -192,12 +213,14 @@ __global__ void __launch_bounds__(kPThreads, 1)
     } else if (warp == 1) {
         if (leader) {
             // ---------------- MMA issuer (leader only): the whole warp walks the loop, one lane issues
-            uint32_t it = 0, ci = 0;
+            uint32_t ci = 0, st = 0, ph = 0;
+            const uint32_t kpp = PLANED ? ckb * plane_chunks : KB;
             bool issued = false;
             for (uint32_t t = cluster; t < tiles && !failed; t += nclusters) {
                 uint32_t d_tmem = tmem_base;
-                for (uint32_t kb = 0; kb < KB; ++kb, ++it) {
-                    if (kb % kPChunkKB == 0) {
+                uint32_t u = 0, kin = 0, kc = 0;   // limb plane, place in the plane, place in the chunk
+                for (uint32_t kb = 0; kb < KB; ++kb) {
+                    if (kc == 0) {
                         const uint32_t buf = ci & 1u;
                         const bool ok = mbar_wait(&acc_empty[buf], ((ci >> 1) & 1u) ^ 1u, abort);
                         if (__any_sync(0xffffffffu, !ok)) {
@@ -207,8 +230,6 @@ __global__ void __launch_bounds__(kPThreads, 1)
                         tc_fence_after();
                         d_tmem = tmem_base + buf * BN;
                     }
-                    const uint32_t st = it % ST;
-                    const uint32_t ph = (it / ST) & 1u;
                     const bool ok = mbar_wait(&full[st], ph, abort);
                     if (__any_sync(0xffffffffu, !ok)) {
                         fail_both();
@@ -218,20 +239,28 @@ __global__ void __launch_bounds__(kPThreads, 1)
                     const uint32_t sa = smem_addr(smem + st * Cfg::kStageBytes);
                     const uint64_t adesc = umma_desc_sw128(sa);
                     const uint64_t bdesc = umma_desc_sw128(sa + Cfg::kABytes);
-                    const uint32_t u = PLANED ? (kb / kPChunkKB) / plane_chunks : 0u;
                     const uint32_t idesc = umma_idesc_f16(2 * kPM, PLANED ? (4u - u) * (BN / 4) : BN);
-                    const bool last_of_chunk = kb % kPChunkKB == kPChunkKB - 1 || kb == KB - 1;
+                    const bool last_of_chunk = kc == ckb - 1 || kb == KB - 1;
                     if (elect_one()) {
 #pragma unroll
                         for (int k = 0; k < kPK / 16; ++k)
                             umma_f16_pair(d_tmem, adesc + 2u * k, bdesc + 2u * k, idesc,
-                                          (kb % kPChunkKB != 0 || k != 0) ? 1u : 0u);
+                                          (kc != 0 || k != 0) ? 1u : 0u);
                         umma_commit_pair(&empty[st], 3);
                         if (last_of_chunk) umma_commit_pair(&acc_full[ci & 1u], 3);
                     }
                     __syncwarp();
                     issued = true;
                     if (last_of_chunk) ++ci;
+                    if (++st == (uint32_t)ST) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
+                    if (++kc == ckb) kc = 0;
+                    if (++kin == kpp) {
+                        kin = 0;
+                        ++u;
+                    }
                 }
             }
             // every pair MMA must finish before TMEM is released
@@ -433,10 +462,16 @@ static int resident_pairs(int num_sms) {
     return n;
 }
 
+// k-steps (64 deep) per exact chunk: 8 for digits times limbs (StoreEpi), 16 for limbs times limbs.
+template <class Epi>
+constexpr uint32_t pair_chunk_kb() {
+    return std::is_same<Epi, StoreEpi>::value ? 8u : 16u;
+}
+
 template <int BN, class Epi, bool PLANED>
 static cudaError_t launch_pair_t(const CUtensorMap &a_map, const PairBMaps &bm, const Epi &epi, uint32_t M,
-                                 uint32_t NV, uint32_t KB, uint32_t plane_chunks, int num_sms, int *status,
-                                 cudaStream_t stream) {
+                                 uint32_t NV, uint32_t KB, uint32_t ckb, uint32_t plane_chunks, int num_sms,
+                                 int *status, cudaStream_t stream) {
     const uint64_t m_tiles = (M + 2ull * kPM - 1) / (2ull * kPM);
     const uint64_t n_tiles = (NV + PairCfg<BN>::kQPT - 1) / PairCfg<BN>::kQPT;
     const uint64_t tiles = m_tiles * n_tiles;
@@ -445,8 +480,8 @@ static cudaError_t launch_pair_t(const CUtensorMap &a_map, const PairBMaps &bm, 
     if (clusters == 0) return cudaSuccess;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = pair_config<BN>(static_cast<unsigned>(clusters), stream, attr);
-    return cudaLaunchKernelEx(&cfg, limb_gemm_pair_kernel<BN, Epi, PLANED>, a_map, bm, epi, M, NV, KB, plane_chunks,
-                              status);
+    return cudaLaunchKernelEx(&cfg, limb_gemm_pair_kernel<BN, Epi, PLANED>, a_map, bm, epi, M, NV, KB, ckb,
+                              plane_chunks, status);
 }
 
 template <class Epi>
@@ -456,22 +491,27 @@ static cudaError_t launch_pair_epi(int bn, const CUtensorMap &a_map, const PairB
     if (M == 0 || NV == 0 || K == 0 || num_sms < 2) return cudaErrorInvalidValue;
     const uint32_t KB = static_cast<uint32_t>((K + kPK - 1) / kPK);
     if (plane_chunks == 0) {
+        constexpr uint32_t ckb = pair_chunk_kb<Epi>();
         switch (bn) {
-            case 64: return launch_pair_t<64, Epi, false>(a_map, bm, epi, M, NV, KB, 0, num_sms, status, stream);
-            case 128: return launch_pair_t<128, Epi, false>(a_map, bm, epi, M, NV, KB, 0, num_sms, status, stream);
-            case 256: return launch_pair_t<256, Epi, false>(a_map, bm, epi, M, NV, KB, 0, num_sms, status, stream);
+            case 64: return launch_pair_t<64, Epi, false>(a_map, bm, epi, M, NV, KB, ckb, 0, num_sms, status, stream);
+            case 128: return launch_pair_t<128, Epi, false>(a_map, bm, epi, M, NV, KB, ckb, 0, num_sms, status, stream);
+            case 256: return launch_pair_t<256, Epi, false>(a_map, bm, epi, M, NV, KB, ckb, 0, num_sms, status, stream);
             default: return cudaErrorInvalidValue;
         }
     }
     if constexpr (std::is_same<Epi, StoreEpi>::value) {
         return cudaErrorInvalidValue;
     } else {
+        // every chunk lies inside one limb plane of n = K / 4 columns: 1024-deep chunks when n is a
+        // multiple of 1024, else 512-deep (plane_chunks = n / 512 then)
         if (K != 4ull * 512 * plane_chunks) return cudaErrorInvalidValue;
+        const uint32_t ckb = plane_chunks % 2 == 0 ? 16u : 8u;
+        const uint32_t pc = ckb == 16u ? plane_chunks / 2 : plane_chunks;
         switch (bn) {
             case 128:
-                return launch_pair_t<128, Epi, true>(a_map, bm, epi, M, NV, KB, plane_chunks, num_sms, status, stream);
+                return launch_pair_t<128, Epi, true>(a_map, bm, epi, M, NV, KB, ckb, pc, num_sms, status, stream);
             case 256:
-                return launch_pair_t<256, Epi, true>(a_map, bm, epi, M, NV, KB, plane_chunks, num_sms, status, stream);
+                return launch_pair_t<256, Epi, true>(a_map, bm, epi, M, NV, KB, ckb, pc, num_sms, status, stream);
             default: return cudaErrorInvalidValue;
         }
     }

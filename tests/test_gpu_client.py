@@ -101,13 +101,15 @@ def test_zero_block_skipping_on_and_off(cuda, R, C, n, B, max_batch, skip, pair)
     cl.close()
 
 
-@pytest.mark.parametrize("a_word,s_word", [(0xFFFFFFFF, 0xFFFFFFFF), (0x80808080, 0x80808080),
+@pytest.mark.parametrize("a_word,s_word", [(0x7F7F7F80, 0x7F7F7F80),   # every limb -128: chunks of 2^24 exactly
+                                           (0xFFFFFFFF, 0xFFFFFFFF), (0x80808080, 0x80808080),
                                            (0x7F7F7F7F, 0x80808080), (0x80808080, 0x7F7F7F7F),
                                            (0x7F7F7F7F, 0x7F7F7F7F), (0x00800080, 0xFF7FFF80)])
 @pytest.mark.parametrize("B", [16, 40])
 def test_limb_boundary_values(cuda, a_word, s_word, B):
-    # every limb at +-127/-128 pushes each 512-deep chunk to its exactness bound; B = 16 runs
-    # 64-wide pair tiles (plain), B = 40 planed 256-wide pair tiles
+    # every limb at +-127/-128 pushes each exact chunk to its bound (1024-deep chunks of limb
+    # products reach 2^24 when every limb is -128); B = 16 runs 64-wide pair tiles (plain), B = 40
+    # planed 256-wide pair tiles
     R, C, n = 256, 512, 1024
     A_np = np.full((C, n), a_word, dtype=np.uint32)
     S_np = np.full((B, n), s_word, dtype=np.uint32)
