@@ -24,8 +24,12 @@ int db_prepare_f16(qpadl_db *db, cudaStream_t stream);
 // Fills group slot `g` of a grouped u8 GEMM for NV vectors whose fp16 limbs
 // are at `limbs` (4 NV rows of db_limb_pitch elements); answers go to
 // out[v * R + i].  `unit_begin` is the group's first unit; returns its unit count.
+// pair: the group runs in the pair form of the GEMM (256-row tiles, half-height limb boxes).
 int db_fill_u8_group(qpadl_db *db, GroupedGemmArgs &args, int g, const __half *limbs, uint32_t NV, uint32_t *out,
-                     int bn, int ks, uint32_t unit_begin, uint32_t *units);
+                     int bn, int ks, uint32_t unit_begin, uint32_t *units, bool pair);
+
+// Whether this handle runs its batched GEMMs on CTA pairs (QPADL_OPT_PAIR_GEMM).
+bool db_pair_gemm(const qpadl_db *db);
 
 // Batched answer on the fp16 copy with the limbs in caller workspace (8 B pitch bytes).
 int db_answer_f16_ws(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, __half *limbs,

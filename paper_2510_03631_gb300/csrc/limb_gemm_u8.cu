@@ -30,6 +30,19 @@
 //   fp16 A slots in TMEM (freed when the MMA that reads them completes),
 // so the digit loads run ahead of the MMA instead of waiting for it.
 //
+// Pair form (PAIR = true): a tile is 256 rows over a cluster of two CTAs on
+// two SMs (tcgen05 cta_group::2).  Each CTA keeps its own digit ring and
+// converters and writes its own 128 rows of fp16 digits into its own TMEM A
+// slots; each loads half of the limb rows.  The leader CTA issues the pair
+// MMAs (M = 256, A from both CTAs' TMEM, B from both CTAs' shared memory):
+// one instruction drives both SMs' tensor cores, which halves the MMA issue
+// rate each stage needs (a 16-deep MMA costs about as much to issue as it
+// takes to run at these widths).  Both CTAs' converters arrive on the
+// leader's `aready`, both CTAs' limb copies complete on the leader's `lfull`,
+// both epilogues arrive on the leader's `acc_empty`; the leader's MMA commits
+// to `afree`, `lfree` and `acc_full` of both CTAs.  A cluster barrier keeps
+// either CTA from leaving while its peer may still reach its shared memory.
+//
 // Warp roles (480 threads, one CTA per SM):
 //   warp 0       TMA producer of the digit tiles (plus L2 prefetch ahead of them)
 //   warp 1       TMEM allocation; one thread issues the MMAs
@@ -56,12 +69,12 @@ constexpr int kPrefetch = 8;   // stages of digit tiles pulled into L2 ahead of 
 
 // BN: limb columns per tile; KS: digits per row per pipeline stage (a
 // multiple of 128: each digit tile is 128 rows x 128 bytes, 128-byte swizzle).
-template <int BN, int KS>
+template <int BN, int KS, bool PAIR = false>
 struct U8Cfg {
     static constexpr int kSubA = KS / 128;                          // digit boxes per stage
     static constexpr int kSubB = KS / 64;                           // limb boxes per stage
     static constexpr uint32_t kDigBytes = kBM * KS;                 // one digit slot
-    static constexpr uint32_t kBBoxBytes = BN * 128;
+    static constexpr uint32_t kBBoxBytes = (PAIR ? BN / 2 : BN) * 128;   // this CTA's limb rows
     static constexpr uint32_t kLimbBytes = kSubB * kBBoxBytes;      // one limb slot
     static constexpr uint32_t kSlotCols = KS / 2;                   // fp16 pairs per row per stage
     // Digit and A-slot counts are even: converter group g owns the stages with it % 2 == g and
@@ -98,7 +111,7 @@ struct Seg {
 
 // The next piece of this CTA's unit range [u, u_end); advances u.
 __device__ __forceinline__ bool next_seg(const GroupedGemmArgs &a, uint32_t &u, uint32_t u_end, uint32_t bn,
-                                         Seg &s) {
+                                         Seg &s, uint32_t tile_rows = kBM) {
     if (u >= u_end) return false;
     uint32_t g = 0;
     while (g + 1 < a.ngroups && u >= a.g[g + 1].unit_begin) ++g;
@@ -106,7 +119,7 @@ __device__ __forceinline__ bool next_seg(const GroupedGemmArgs &a, uint32_t &u, 
     const uint32_t local = u - a.g[g].unit_begin;
     const uint32_t tile = local / ns;
     s.g = g;
-    s.m0 = (tile / a.g[g].n_tiles) * kBM;
+    s.m0 = (tile / a.g[g].n_tiles) * tile_rows;
     s.n0 = (tile % a.g[g].n_tiles) * bn;
     s.ks0 = local % ns;
     s.ks1 = (ns - s.ks0 < u_end - u) ? ns : s.ks0 + (u_end - u);
@@ -120,10 +133,12 @@ __device__ __forceinline__ bool next_seg(const GroupedGemmArgs &a, uint32_t &u, 
 // LPV: vector-operand rows per vector.  4 = the four byte limbs of 32-bit vectors, recombined
 // mod 2^32; 1 = one row per vector (small signed integers, e.g. centred field elements), whose
 // exact 32-bit signed sums are stored.
-template <int BN, int KS, int LPV = 4>
+template <int BN, int KS, int LPV = 4, bool PAIR = false>
 __global__ void __launch_bounds__(kThreads, 1)
     limb_gemm_u8_kernel(const __grid_constant__ GroupedGemmArgs args, int *__restrict__ status) {
-    using Cfg = U8Cfg<BN, KS>;
+    using Cfg = U8Cfg<BN, KS, PAIR>;
+    static_assert(!PAIR || BN >= 32, "a pair MMA needs N >= 32 (16 limb rows per CTA)");
+    constexpr uint32_t TM = PAIR ? 2 * kBM : kBM;   // rows per tile
     static_assert(LPV == 4 || (LPV == 1 && BN <= 64), "one-row vectors: at most 64 running sums per thread");
     constexpr int QPT = BN / LPV;
     constexpr int SD = Cfg::kSD, SL = Cfg::kSL, SA = Cfg::kSA;
@@ -157,29 +172,50 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&lfree[s], 1);
         }
         for (int s = 0; s < SA; ++s) {
-            mbar_init(&aready[s], 4);
+            mbar_init(&aready[s], PAIR ? 8 : 4);   // the owning converter group (of both CTAs)
             mbar_init(&afree[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 4);
+            mbar_init(&acc_empty[b], PAIR ? 8 : 4);
         }
         mbar_init(mma_done, 1);
         *abort = 0;
         fence_barrier_init();
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, kTmemCols);
-        tmem_relinquish();
+        if constexpr (PAIR) {
+            tmem_alloc_pair(tmem_slot, kTmemCols);
+            tmem_relinquish_pair();
+        } else {
+            tmem_alloc(tmem_slot, kTmemCols);
+            tmem_relinquish();
+        }
     }
     tc_fence_before();
-    __syncthreads();
+    if constexpr (PAIR) cluster_sync();   // both CTAs' barriers exist before either touches the other's
+    else __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    // this CTA's share of the units, contiguous across tile boundaries
-    const uint32_t ubeg = static_cast<uint32_t>((uint64_t)blockIdx.x * args.total_units / gridDim.x);
-    const uint32_t uend = static_cast<uint32_t>((uint64_t)(blockIdx.x + 1) * args.total_units / gridDim.x);
+    const uint32_t rank = PAIR ? cluster_rank() : 0u;
+    const bool leader = rank == 0;
+    const uint32_t roff = rank * kBM;   // this CTA's first row within a tile
+    // shared::cluster addresses of the leader's barriers that both CTAs signal (pair form)
+    const uint32_t lfull_c = PAIR ? cluster_addr(lfull, 0) : 0u;
+    const uint32_t aready_c = PAIR ? cluster_addr(aready, 0) : 0u;
+    const uint32_t acc_empty_c = PAIR ? cluster_addr(acc_empty, 0) : 0u;
+    const uint32_t peer_abort = PAIR ? cluster_addr(const_cast<int *>(abort), rank ^ 1u) : 0u;
+    // this CTA's (pair: cluster's) share of the units, contiguous across tile boundaries
+    const uint32_t part = PAIR ? (blockIdx.x >> 1) : blockIdx.x;
+    const uint32_t nparts = PAIR ? (gridDim.x >> 1) : gridDim.x;
+    const uint32_t ubeg = static_cast<uint32_t>((uint64_t)part * args.total_units / nparts);
+    const uint32_t uend = static_cast<uint32_t>((uint64_t)(part + 1) * args.total_units / nparts);
     bool failed = false;
+    auto fail_here = [&]() {
+        failed = true;
+        *abort = 1;
+        if constexpr (PAIR) st_cluster_u32(peer_abort, 1u);
+    };
 
     // waits until every copy this thread issued into `ring` has landed (so the CTA can exit)
     auto drain_ring = [&](uint64_t *ring, int slots, uint32_t issued) {
@@ -195,33 +231,33 @@ __global__ void __launch_bounds__(kThreads, 1)
             // box into L2 before its load is issued.
             uint32_t pu = ubeg, pks = 0;
             Seg ps;
-            bool pvalid = next_seg(args, pu, uend, BN, ps);
+            bool pvalid = next_seg(args, pu, uend, BN, ps, TM);
             if (pvalid) pks = ps.ks0;
             auto prefetch_next = [&]() {
                 if (!pvalid) return;
                 tma_prefetch_l2_4d(&args.a[ps.g], 0, 0, static_cast<int32_t>(pks * KS / 128),
-                                   static_cast<int32_t>(ps.m0 / kBM));
+                                   static_cast<int32_t>((ps.m0 + roff) / kBM));
                 if (++pks >= ps.ks1) {
-                    pvalid = next_seg(args, pu, uend, BN, ps);
+                    pvalid = next_seg(args, pu, uend, BN, ps, TM);
                     if (pvalid) pks = ps.ks0;
                 }
             };
             for (int i = 0; i < kPrefetch; ++i) prefetch_next();
             uint32_t it = 0, u = ubeg;
             Seg tr;
-            while (!failed && next_seg(args, u, uend, BN, tr)) {
+            while (!failed && next_seg(args, u, uend, BN, tr, TM)) {
                 for (uint32_t ks = tr.ks0; ks < tr.ks1; ++ks, ++it) {
                     const uint32_t sd = it % SD;
                     prefetch_next();
                     if (!mbar_wait(&dfree[sd], ((it / SD) & 1u) ^ 1u, abort)) {
-                        failed = true;
+                        fail_here();
                         break;
                     }
                     mbar_arrive_expect_tx(&dfull[sd], Cfg::kDigBytes);
                     // the digits are stored blocked (128 x 128 tiles, each 16 KB contiguous), so the
                     // kSubA tiles of this stage are one contiguous read
                     tma_load_4d(dig + sd * Cfg::kDigBytes, &args.a[tr.g], &dfull[sd], 0, 0,
-                                static_cast<int32_t>(ks * KS / 128), static_cast<int32_t>(tr.m0 / kBM));
+                                static_cast<int32_t>(ks * KS / 128), static_cast<int32_t>((tr.m0 + roff) / kBM));
                 }
             }
             drain_ring(dfull, SD, it);
@@ -231,31 +267,45 @@ __global__ void __launch_bounds__(kThreads, 1)
             // ---------------- limb producer
             uint32_t it = 0, u = ubeg;
             Seg tr;
-            while (!failed && next_seg(args, u, uend, BN, tr)) {
+            while (!failed && next_seg(args, u, uend, BN, tr, TM)) {
                 for (uint32_t ks = tr.ks0; ks < tr.ks1; ++ks, ++it) {
                     const uint32_t sl = it % SL;
                     if (!mbar_wait(&lfree[sl], ((it / SL) & 1u) ^ 1u, abort)) {
-                        failed = true;
+                        fail_here();
                         break;
                     }
-                    mbar_arrive_expect_tx(&lfull[sl], Cfg::kLimbBytes);
                     const int32_t k0 = static_cast<int32_t>(ks * KS);
+                    if constexpr (PAIR) {
+                        // this CTA's half of the limb rows; both halves complete on the leader's barrier
+                        if (leader) mbar_arrive_expect_tx(&lfull[sl], 2u * Cfg::kLimbBytes);
 #pragma unroll
-                    for (int b = 0; b < Cfg::kSubB; ++b)
-                        tma_load_2d(limb + sl * Cfg::kLimbBytes + b * Cfg::kBBoxBytes, &args.b[tr.g], &lfull[sl],
-                                    k0 + 64 * b, static_cast<int32_t>(tr.n0));
+                        for (int b = 0; b < Cfg::kSubB; ++b)
+                            tma_load_2d_pair(limb + sl * Cfg::kLimbBytes + b * Cfg::kBBoxBytes, &args.b[tr.g],
+                                             lfull_c + 8u * sl, k0 + 64 * b,
+                                             static_cast<int32_t>(tr.n0 + rank * (BN / 2)));
+                    } else {
+                        mbar_arrive_expect_tx(&lfull[sl], Cfg::kLimbBytes);
+#pragma unroll
+                        for (int b = 0; b < Cfg::kSubB; ++b)
+                            tma_load_2d(limb + sl * Cfg::kLimbBytes + b * Cfg::kBBoxBytes, &args.b[tr.g], &lfull[sl],
+                                        k0 + 64 * b, static_cast<int32_t>(tr.n0));
+                    }
                 }
             }
-            drain_ring(lfull, SL, it);
+            // the leader's limb ring counts both CTAs' copies: it waits for them before exit
+            if (!PAIR || leader) drain_ring(lfull, SL, it);
         }
     } else if (warp == 1) {
+        if (PAIR && !leader) {
+            // the peer's MMA warp only holds TMEM with its leader
+        } else {
         // ---------------- MMA issuer: the whole warp walks the loop so the descriptors and
         // TMEM addresses stay warp-uniform; one elected lane issues each instruction
-        constexpr uint32_t idesc = umma_idesc_f16(kBM, BN);
+        constexpr uint32_t idesc = umma_idesc_f16(TM, BN);
         uint32_t it = 0, ci = 0, u = ubeg;
         bool issued = false;
         Seg sg;
-        while (!failed && next_seg(args, u, uend, BN, sg)) {
+        while (!failed && next_seg(args, u, uend, BN, sg, TM)) {
             uint32_t d_tmem = tmem_base;
             for (uint32_t ks = sg.ks0; ks < sg.ks1; ++ks, ++it) {
                 const uint32_t kr = ks - sg.ks0;   // exact chunks restart at every piece
@@ -264,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t buf = ci & 1u;
                     const bool ok = mbar_wait(&acc_empty[buf], ((ci >> 1) & 1u) ^ 1u, abort);
                     if (__any_sync(0xffffffffu, !ok)) {
-                        failed = true;
+                        fail_here();
                         break;
                     }
                     tc_fence_after();
@@ -274,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 bool ok = mbar_wait(&aready[sa], (it / SA) & 1u, abort);
                 ok = ok && mbar_wait(&lfull[sl], (it / SL) & 1u, abort);
                 if (__any_sync(0xffffffffu, !ok)) {
-                    failed = true;
+                    fail_here();
                     break;
                 }
                 tc_fence_after();
@@ -284,11 +334,21 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int kk = 0; kk < KS / 16; ++kk) {
                         const uint64_t bdesc = umma_desc_sw128(sb + (kk / 4) * Cfg::kBBoxBytes) + 2u * (kk % 4);
-                        umma_f16_ts(d_tmem, a_tmem + 8u * kk, bdesc, idesc, (kr % CS != 0 || kk != 0) ? 1u : 0u);
+                        if constexpr (PAIR)
+                            umma_f16_ts_pair(d_tmem, a_tmem + 8u * kk, bdesc, idesc,
+                                             (kr % CS != 0 || kk != 0) ? 1u : 0u);
+                        else
+                            umma_f16_ts(d_tmem, a_tmem + 8u * kk, bdesc, idesc, (kr % CS != 0 || kk != 0) ? 1u : 0u);
                     }
-                    umma_commit(&afree[sa]);   // the TMEM A slot and
-                    umma_commit(&lfree[sl]);   // the limb slot are free once these MMAs complete
-                    if (kr % CS == CS - 1 || ks == sg.ks1 - 1) umma_commit(&acc_full[ci & 1u]);
+                    if constexpr (PAIR) {
+                        umma_commit_pair(&afree[sa], 3);   // both CTAs' TMEM A slots and
+                        umma_commit_pair(&lfree[sl], 3);   // limb slots are free once these MMAs complete
+                        if (kr % CS == CS - 1 || ks == sg.ks1 - 1) umma_commit_pair(&acc_full[ci & 1u], 3);
+                    } else {
+                        umma_commit(&afree[sa]);   // the TMEM A slot and
+                        umma_commit(&lfree[sl]);   // the limb slot are free once these MMAs complete
+                        if (kr % CS == CS - 1 || ks == sg.ks1 - 1) umma_commit(&acc_full[ci & 1u]);
+                    }
                 }
                 __syncwarp();
                 issued = true;
@@ -296,9 +356,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
         if (issued) {
-            if (elect_one()) umma_commit(mma_done);
+            if (elect_one()) {
+                if constexpr (PAIR) umma_commit_pair(mma_done, 1);
+                else umma_commit(mma_done);
+            }
             __syncwarp();
             if (!drain_wait_u(mma_done, 0)) failed = true;
+        }
         }
     } else if (warp < 6) {
         // ---------------- epilogue (warps 2..5)
@@ -306,7 +370,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_addr = (quarter * 32u) << 16;
         uint32_t ci = 0, u = ubeg;
         Seg tr;
-        while (!failed && next_seg(args, u, uend, BN, tr)) {
+        while (!failed && next_seg(args, u, uend, BN, tr, TM)) {
             const GroupDesc &gd = args.g[tr.g];
             uint32_t run[QPT];
 #pragma unroll
@@ -314,8 +378,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t nchunks = (tr.ks1 - tr.ks0 + CS - 1) / CS;
             for (uint32_t c = 0; c < nchunks; ++c, ++ci) {
                 const uint32_t buf = ci & 1u;
-                if (!mbar_wait(&acc_full[buf], (ci >> 1) & 1u, abort)) {
-                    failed = true;
+                const bool ok = mbar_wait(&acc_full[buf], (ci >> 1) & 1u, abort);
+                if (__any_sync(0xffffffffu, !ok)) {   // the TMEM loads below are warp-collective
+                    fail_here();
                     break;
                 }
                 tc_fence_after();
@@ -341,10 +406,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&acc_empty[buf]);
+                if (lane == 0) {
+                    if constexpr (PAIR) mbar_arrive_cluster(acc_empty_c + 8u * buf);
+                    else mbar_arrive(&acc_empty[buf]);
+                }
             }
             if (failed) break;
-            const uint32_t row = tr.m0 + quarter * 32u + static_cast<uint32_t>(lane);
+            const uint32_t row = tr.m0 + roff + quarter * 32u + static_cast<uint32_t>(lane);
             const bool whole = tr.ks0 == 0 && tr.ks1 == tr.ns;   // no other CTA touches this tile
             if (row < gd.M) {
                 const uint32_t v0 = tr.n0 / LPV;
@@ -368,14 +436,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         const __half2 k1024 = __floats2half2_rn(1024.0f, 1024.0f);
         uint32_t it = 0, u = ubeg;
         Seg sg;
-        while (!failed && next_seg(args, u, uend, BN, sg)) {
+        while (!failed && next_seg(args, u, uend, BN, sg, TM)) {
             for (uint32_t ks = sg.ks0; ks < sg.ks1; ++ks, ++it) {
                 if (it % kConvGroups != group) continue;   // this group owns every phase of its slots
                 const uint32_t sd = it % SD, sa = it % SA;
                 bool ok = mbar_wait(&dfull[sd], (it / SD) & 1u, abort);
                 ok = ok && mbar_wait(&afree[sa], ((it / SA) & 1u) ^ 1u, abort);
                 if (__any_sync(0xffffffffu, !ok)) {
-                    failed = true;
+                    fail_here();
                     break;
                 }
                 tc_fence_after();   // the MMA that last read this A slot has completed
@@ -409,7 +477,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_wait_st();
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&aready[sa]);
+                if (lane == 0) {
+                    if constexpr (PAIR) mbar_arrive_cluster(aready_c + 8u * sa);   // the leader's MMA reads both slots
+                    else mbar_arrive(&aready[sa]);
+                }
             }
         }
     }
@@ -417,12 +488,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (failed) {
         *abort = 1;
         *status = kDevTimeout;
+        if constexpr (PAIR) {
+            // a copy this CTA issued may still be landing (after an abort its stage is never
+            // consumed): give it a bounded moment before the CTA can exit
+            const uint64_t t0 = global_ns();
+            while (global_ns() - t0 < 200000ull) {
+            }
+        }
     }
+    __syncwarp();
     tc_fence_before();
-    __syncthreads();
+    if constexpr (PAIR) cluster_sync();   // no CTA leaves while its peer may still reach it
+    else __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem_base, kTmemCols);
+        if constexpr (PAIR) tmem_dealloc_pair(tmem_base, kTmemCols);
+        else tmem_dealloc(tmem_base, kTmemCols);
     }
 }
 
@@ -458,10 +539,10 @@ cudaError_t launch_block_digits(const uint8_t *D, uint64_t R, uint64_t C, uint8_
 }
 
 // ------------------------------------------------------------------ host side
-template <int BN, int KS, int LPV = 4>
+template <int BN, int KS, int LPV = 4, bool PAIR = false>
 static cudaError_t set_attr() {
-    return cudaFuncSetAttribute(limb_gemm_u8_kernel<BN, KS, LPV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                U8Cfg<BN, KS>::kSmemBytes);
+    return cudaFuncSetAttribute(limb_gemm_u8_kernel<BN, KS, LPV, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                U8Cfg<BN, KS, PAIR>::kSmemBytes);
 }
 
 cudaError_t prepare_limb_gemm_u8_kernels() {
@@ -473,37 +554,86 @@ cudaError_t prepare_limb_gemm_u8_kernels() {
     if ((e = set_attr<128, 128>()) != cudaSuccess) return e;
     if ((e = set_attr<128, 256>()) != cudaSuccess) return e;
     if ((e = set_attr<32, 128, 1>()) != cudaSuccess) return e;
-    return set_attr<64, 128, 1>();
+    if ((e = set_attr<64, 128, 1>()) != cudaSuccess) return e;
+    if ((e = set_attr<32, 128, 4, true>()) != cudaSuccess) return e;
+    if ((e = set_attr<64, 128, 4, true>()) != cudaSuccess) return e;
+    if ((e = set_attr<128, 128, 4, true>()) != cudaSuccess) return e;
+    if ((e = set_attr<32, 128, 1, true>()) != cudaSuccess) return e;
+    return set_attr<64, 128, 1, true>();
 }
 
 // 128-digit stages for every tile width: with 256 the TMEM A slots allow only two stages in flight
 int limb_gemm_u8_default_ks(int) { return 128; }
 
+// Clusters of two CTAs (pair form), one CTA per SM.
+template <int BN, int KS, int LPV>
+static cudaLaunchConfig_t u8_pair_config(unsigned clusters, cudaStream_t stream, cudaLaunchAttribute *attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * clusters);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = U8Cfg<BN, KS, true>::kSmemBytes;
+    cfg.stream = stream;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// CTA pairs resident at once, per device (a GPC with an odd number of free SMs leaves one idle).
+template <int BN, int KS, int LPV>
+static int u8_resident_pairs(int num_sms) {
+    static int cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return num_sms / 2;
+    if (cache[dev] > 0) return cache[dev];
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = u8_pair_config<BN, KS, LPV>(static_cast<unsigned>(num_sms / 2), nullptr, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, limb_gemm_u8_kernel<BN, KS, LPV, true>, &cfg) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        return num_sms / 2;
+    }
+    n = n < num_sms / 2 ? n : num_sms / 2;
+    cache[dev] = n;
+    return n;
+}
+
 template <int BN, int KS, int LPV = 4>
-static cudaError_t launch_u8(const GroupedGemmArgs &args, int grid, int *status, cudaStream_t stream) {
+static cudaError_t launch_u8(const GroupedGemmArgs &args, int num_sms, bool pair, int *status, cudaStream_t stream) {
+    if (args.total_units == 0) return cudaSuccess;
+    if (pair) {
+        const uint32_t pairs = static_cast<uint32_t>(u8_resident_pairs<BN, KS, LPV>(num_sms));
+        const unsigned clusters = args.total_units < pairs ? args.total_units : pairs;
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = u8_pair_config<BN, KS, LPV>(clusters, stream, attr);
+        return cudaLaunchKernelEx(&cfg, limb_gemm_u8_kernel<BN, KS, LPV, true>, args, status);
+    }
+    const int grid = static_cast<int>(args.total_units < (uint32_t)num_sms ? args.total_units : (uint32_t)num_sms);
     limb_gemm_u8_kernel<BN, KS, LPV><<<grid, kThreads, U8Cfg<BN, KS>::kSmemBytes, stream>>>(args, status);
     return cudaGetLastError();
 }
 
+bool limb_gemm_u8_pair_ok(int bn, int ks) { return ks == 128 && bn >= 32 && bn <= 128; }
+
 cudaError_t launch_limb_gemm_u8(int bn, int ks, const GroupedGemmArgs &args, int num_sms, int *status,
-                                cudaStream_t stream) {
-    const int grid = static_cast<int>(args.total_units < (uint32_t)num_sms ? args.total_units : (uint32_t)num_sms);
-    if (grid <= 0) return cudaSuccess;
-    if (bn == 32 && ks == 128) return launch_u8<32, 128>(args, grid, status, stream);
-    if (bn == 32 && ks == 256) return launch_u8<32, 256>(args, grid, status, stream);
-    if (bn == 64 && ks == 128) return launch_u8<64, 128>(args, grid, status, stream);
-    if (bn == 64 && ks == 256) return launch_u8<64, 256>(args, grid, status, stream);
-    if (bn == 128 && ks == 128) return launch_u8<128, 128>(args, grid, status, stream);
-    if (bn == 128 && ks == 256) return launch_u8<128, 256>(args, grid, status, stream);
+                                cudaStream_t stream, bool pair) {
+    if (pair && !limb_gemm_u8_pair_ok(bn, ks)) return cudaErrorInvalidValue;
+    if (bn == 32 && ks == 128) return launch_u8<32, 128>(args, num_sms, pair, status, stream);
+    if (bn == 32 && ks == 256) return launch_u8<32, 256>(args, num_sms, false, status, stream);
+    if (bn == 64 && ks == 128) return launch_u8<64, 128>(args, num_sms, pair, status, stream);
+    if (bn == 64 && ks == 256) return launch_u8<64, 256>(args, num_sms, false, status, stream);
+    if (bn == 128 && ks == 128) return launch_u8<128, 128>(args, num_sms, pair, status, stream);
+    if (bn == 128 && ks == 256) return launch_u8<128, 256>(args, num_sms, false, status, stream);
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_limb_gemm_u8_rows(int bn, const GroupedGemmArgs &args, int num_sms, int *status,
-                                     cudaStream_t stream) {
-    const int grid = static_cast<int>(args.total_units < (uint32_t)num_sms ? args.total_units : (uint32_t)num_sms);
-    if (grid <= 0) return cudaSuccess;
-    if (bn == 32) return launch_u8<32, 128, 1>(args, grid, status, stream);
-    if (bn == 64) return launch_u8<64, 128, 1>(args, grid, status, stream);
+                                     cudaStream_t stream, bool pair) {
+    if (bn == 32) return launch_u8<32, 128, 1>(args, num_sms, pair, status, stream);
+    if (bn == 64) return launch_u8<64, 128, 1>(args, num_sms, pair, status, stream);
     return cudaErrorInvalidValue;
 }
 

@@ -40,8 +40,12 @@ cudaError_t launch_block_digits(const uint8_t *D, uint64_t R, uint64_t C, uint8_
 // bn in {32, 64, 128}, ks in {128, 256}: limb columns per
 // tile (the same for every group) and digits per row per pipeline stage.
 int limb_gemm_u8_default_ks(int bn);
+// Pair form (pair = true): tiles of 256 rows over clusters of two CTAs (tcgen05 cta_group::2),
+// each CTA loading half of the limb rows.  Then a group's units count 256-row tiles
+// (ceil(M / 256) x n_tiles x KB) and its b map has box {64, bn / 2}.  bn in {32, 64, 128}, ks = 128.
+bool limb_gemm_u8_pair_ok(int bn, int ks);
 cudaError_t launch_limb_gemm_u8(int bn, int ks, const GroupedGemmArgs &args, int num_sms, int *status,
-                                cudaStream_t stream);
+                                cudaStream_t stream, bool pair = false);
 
 // The same GEMM with one vector-operand row per vector (b maps {C, NV}): each
 // output is the exact signed sum sum_j D[i][j] x_b[j] stored as 32 bits, for
@@ -49,6 +53,6 @@ cudaError_t launch_limb_gemm_u8(int bn, int ks, const GroupedGemmArgs &args, int
 // whole sum below 2^31 for fewer than 65793 columns).  bn in {32, 64}, 128-digit
 // stages; output zeroed before the launch as above.
 cudaError_t launch_limb_gemm_u8_rows(int bn, const GroupedGemmArgs &args, int num_sms, int *status,
-                                     cudaStream_t stream);
+                                     cudaStream_t stream, bool pair = false);
 
 }  // namespace qpadl

@@ -367,11 +367,13 @@ int answer_tensor_u8(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans,
     QPADL_CU(launch_vec_limbs(Q, C, B, C, db->limbs, db->pitch, db->num_sms, stream));
     const int bn = limb_gemm_bn_for(B);
     const int ks = db->u8_kstep ? db->u8_kstep : limb_gemm_u8_default_ks(bn);
+    const bool pair = db->pair_gemm && db->num_sms >= 2 && limb_gemm_u8_pair_ok(bn, ks);
+    const uint32_t tile_rows = pair ? 2 * kLimbBoxM : kLimbBoxM;
     GroupedGemmArgs args;
     std::memset(&args, 0, sizeof(args));
     args.a[0] = db->u8_map[ks / 128 - 1];
     if (!encode_2d(&args.b[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, db->limbs, C, 4ull * B, db->pitch * 2, kLimbBoxK,
-                   static_cast<uint32_t>(bn), CU_TENSOR_MAP_SWIZZLE_128B))
+                   static_cast<uint32_t>(pair ? bn / 2 : bn), CU_TENSOR_MAP_SWIZZLE_128B))
         return QPADL_ECUDA;
     GroupDesc &g = args.g[0];
     g.out = ans;
@@ -383,10 +385,10 @@ int answer_tensor_u8(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans,
     g.unit_begin = 0;
     g.n_tiles = (4 * B + bn - 1) / bn;
     args.ngroups = 1;
-    args.total_units = static_cast<uint32_t>((R + kLimbBoxM - 1) / kLimbBoxM) * g.n_tiles * g.KB;
+    args.total_units = static_cast<uint32_t>((R + tile_rows - 1) / tile_rows) * g.n_tiles * g.KB;
     // tiles split between CTAs are accumulated with atomic adds into zeros
     QPADL_CU(cudaMemsetAsync(ans, 0, 4ull * B * R, stream));
-    QPADL_CU(launch_limb_gemm_u8(bn, ks, args, db->num_sms, db->d_status, stream));
+    QPADL_CU(launch_limb_gemm_u8(bn, ks, args, db->num_sms, db->d_status, stream, pair));
     return QPADL_OK;
 }
 
@@ -418,14 +420,16 @@ int db_num_sms(const qpadl_db *db) { return db->num_sms; }
 int *db_status_word(qpadl_db *db) { return db->d_status; }
 int db_prepare_u8(qpadl_db *db, cudaStream_t stream) { return ensure_blocked(db, stream); }
 int db_prepare_f16(qpadl_db *db, cudaStream_t stream) { return ensure_tensor_copy(db, stream); }
+bool db_pair_gemm(const qpadl_db *db) { return db->pair_gemm && db->num_sms >= 2; }
 
 int db_fill_u8_group(qpadl_db *db, GroupedGemmArgs &args, int g, const __half *limbs, uint32_t NV, uint32_t *out,
-                     int bn, int ks, uint32_t unit_begin, uint32_t *units) {
+                     int bn, int ks, uint32_t unit_begin, uint32_t *units, bool pair) {
     if (!db->blk || g < 0 || g >= kMaxGemmGroups) return QPADL_EINVAL;
     const uint64_t R = db->prm.rows, C = db->prm.cols;
+    const uint32_t tile_rows = pair ? 2 * kLimbBoxM : kLimbBoxM;
     args.a[g] = db->u8_map[ks / 128 - 1];
     if (!encode_2d(&args.b[g], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, limbs, C, 4ull * NV, db->pitch * 2, kLimbBoxK,
-                   static_cast<uint32_t>(bn), CU_TENSOR_MAP_SWIZZLE_128B))
+                   static_cast<uint32_t>(pair ? bn / 2 : bn), CU_TENSOR_MAP_SWIZZLE_128B))
         return QPADL_ECUDA;
     GroupDesc &gd = args.g[g];
     gd.out = out;
@@ -436,7 +440,7 @@ int db_fill_u8_group(qpadl_db *db, GroupedGemmArgs &args, int g, const __half *l
     gd.KB = static_cast<uint32_t>((C + ks - 1) / ks);
     gd.unit_begin = unit_begin;
     gd.n_tiles = (4 * NV + bn - 1) / bn;
-    *units = static_cast<uint32_t>((R + kLimbBoxM - 1) / kLimbBoxM) * gd.n_tiles * gd.KB;
+    *units = static_cast<uint32_t>((R + tile_rows - 1) / tile_rows) * gd.n_tiles * gd.KB;
     return QPADL_OK;
 }
 
@@ -1310,11 +1314,13 @@ int qpadl_goldberg_answer_batch(qpadl_goldberg *h, const uint32_t *Q_dev, uint32
         QPADL_CU(launch_centred_rows(Q_dev, B, C, h->p, db->limbs, db->pitch, db->num_sms, s));
         const int bn = B <= 32 ? 32 : 64;
         constexpr int ks = 128;
+        const bool pair = db->pair_gemm && db->num_sms >= 2;
+        const uint32_t tile_rows = pair ? 2 * kLimbBoxM : kLimbBoxM;
         GroupedGemmArgs args;
         std::memset(&args, 0, sizeof(args));
         args.a[0] = db->u8_map[ks / 128 - 1];
         if (!encode_2d(&args.b[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, db->limbs, C, B, db->pitch * 2, kLimbBoxK,
-                       static_cast<uint32_t>(bn), CU_TENSOR_MAP_SWIZZLE_128B))
+                       static_cast<uint32_t>(pair ? bn / 2 : bn), CU_TENSOR_MAP_SWIZZLE_128B))
             return QPADL_ECUDA;
         GroupDesc &g = args.g[0];
         g.out = out_dev;
@@ -1326,10 +1332,10 @@ int qpadl_goldberg_answer_batch(qpadl_goldberg *h, const uint32_t *Q_dev, uint32
         g.unit_begin = 0;
         g.n_tiles = (B + bn - 1) / bn;
         args.ngroups = 1;
-        args.total_units = static_cast<uint32_t>((R + kLimbBoxM - 1) / kLimbBoxM) * g.n_tiles * g.KB;
+        args.total_units = static_cast<uint32_t>((R + tile_rows - 1) / tile_rows) * g.n_tiles * g.KB;
         // tiles split between CTAs are accumulated with atomic adds into zeros
         QPADL_CU(cudaMemsetAsync(out_dev, 0, 4ull * B * R, s));
-        QPADL_CU(launch_limb_gemm_u8_rows(bn, args, db->num_sms, db->d_status, s));
+        QPADL_CU(launch_limb_gemm_u8_rows(bn, args, db->num_sms, db->d_status, s, pair));
         QPADL_CU(launch_mod_p_signed(out_dev, (uint64_t)B * R, h->p, db->num_sms, s));
         return QPADL_OK;
     }
@@ -1365,6 +1371,8 @@ int qpadl_goldberg_set_option(qpadl_goldberg *h, int option, int64_t value) {
             if (value < 0 || value > 64) return QPADL_EINVAL;
             h->u8_max_batch = static_cast<uint32_t>(value);
             return QPADL_OK;
+        case QPADL_GOLDBERG_OPT_PAIR_GEMM:
+            return qpadl_pir_set_option(h->db, QPADL_OPT_PAIR_GEMM, value);
         default: return QPADL_EINVAL;
     }
 }

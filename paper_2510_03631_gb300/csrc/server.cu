@@ -384,6 +384,9 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
         for (size_t k = k0; k < k1; ++k) maxb = std::max(maxb, small[k]->count);
         const int bn = qpadl::limb_gemm_bn_for(maxb);
         const int ks = qpadl::limb_gemm_u8_default_ks(bn);
+        // one launch takes one form: the pair form when every database in it allows it
+        bool pair = qpadl::limb_gemm_u8_pair_ok(bn, ks);
+        for (size_t k = k0; k < k1; ++k) pair = pair && qpadl::db_pair_gemm(dbs[small[k]->db].db);
         qpadl::GroupedGemmArgs args;
         std::memset(&args, 0, sizeof(args));
         uint32_t units = 0;
@@ -393,13 +396,15 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
             uint32_t u = 0;
             ok = qpadl::db_fill_u8_group(e.db, args, static_cast<int>(k - k0),
                                          reinterpret_cast<const __half *>(base + g.dl_off), g.count,
-                                         reinterpret_cast<uint32_t *>(base + g.da_off), bn, ks, units, &u) == QPADL_OK;
+                                         reinterpret_cast<uint32_t *>(base + g.da_off), bn, ks, units, &u,
+                                         pair) == QPADL_OK;
             units += u;
         }
         args.ngroups = static_cast<uint32_t>(k1 - k0);
         args.total_units = units;
         ok = ok && qpadl::launch_limb_gemm_u8(bn, ks, args, qpadl::db_num_sms(dbs[small[k0]->db].db),
-                                              qpadl::db_status_word(dbs[small[k0]->db].db), S.stream) == cudaSuccess;
+                                              qpadl::db_status_word(dbs[small[k0]->db].db), S.stream,
+                                              pair) == cudaSuccess;
         ++n_gemm_k;
     }
     if (ok) {

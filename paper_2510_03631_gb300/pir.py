@@ -476,6 +476,7 @@ class GoldbergDatabase:
 
 QPADL_GOLDBERG_OPT_GEMM_MIN_BATCH = 1
 QPADL_GOLDBERG_OPT_U8_MAX_BATCH = 2
+QPADL_GOLDBERG_OPT_PAIR_GEMM = 3
 
 
 def qpadl_goldberg_setup(rows: int, cols: int, p: int, db: torch.Tensor, stream=None) -> GoldbergDatabase:

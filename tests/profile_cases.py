@@ -78,6 +78,8 @@ def _goldberg_case(a):
     R, C, B, p = a.rows, a.cols, a.batch, 257
     D_np = inputs.db_digits(R, C, 256, seed=1)
     h = pir.qpadl_goldberg_setup(R, C, p, torch.from_numpy(D_np).cuda())
+    if a.pair >= 0:
+        pir.qpadl_goldberg_set_option(h, pir.QPADL_GOLDBERG_OPT_PAIR_GEMM, a.pair)
     Q_np = (inputs.uniform_u32(B * C, seed=2, tag=inputs.TAG_MISC) % p).reshape(B, C)
     Q = pir.from_u32(Q_np.reshape(-1))
     out = torch.empty(B * R, dtype=torch.int32, device="cuda")

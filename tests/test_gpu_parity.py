@@ -188,10 +188,11 @@ def test_answer_batch_u8_and_fp16_gemms_agree_with_oracle(R, C, B):
     prm, D, db = _setup(R, C, seed=R + B)
     Q = inputs.uniform_u32(B * C, seed=C + B, tag=inputs.TAG_MISC).reshape(B, C)
     exp = oracle.answer_batch(D, Q, threads=oracle.max_threads())
-    for u8max, kstep in ((32, 0), (32, 128), (32, 256), (0, 0)):
+    for u8max, kstep, pair in ((32, 0, 1), (32, 0, 0), (32, 128, 1), (32, 256, 1), (0, 0, 1), (0, 0, 0)):
         pir.qpadl_pir_set_option(db, pir.QPADL_OPT_U8_MAX_BATCH, u8max)
         pir.qpadl_pir_set_option(db, pir.QPADL_OPT_U8_KSTEP, kstep)
-        assert np.array_equal(_answers(db, Q, path=1), exp), f"u8 max batch {u8max}, k-step {kstep}"
+        pir.qpadl_pir_set_option(db, pir.QPADL_OPT_PAIR_GEMM, pair)
+        assert np.array_equal(_answers(db, Q, path=1), exp), f"u8 max batch {u8max}, k-step {kstep}, pair {pair}"
 
 
 @pytest.mark.parametrize("B,kstep", [(8, 0), (8, 128), (16, 0), (16, 128), (32, 0), (32, 256), (40, 0)])
@@ -202,8 +203,10 @@ def test_answer_batch_many_tiles_per_cta(B, kstep):
     prm, D, db = _setup(R, C, seed=B + 7)
     pir.qpadl_pir_set_option(db, pir.QPADL_OPT_U8_KSTEP, kstep)
     Q = inputs.uniform_u32(B * C, seed=B, tag=inputs.TAG_MISC).reshape(B, C)
-    got = _answers(db, Q, path=1)
-    assert np.array_equal(got, oracle.answer_batch(D, Q, threads=oracle.max_threads()))
+    exp = oracle.answer_batch(D, Q, threads=oracle.max_threads())
+    for pair in (1, 0):
+        pir.qpadl_pir_set_option(db, pir.QPADL_OPT_PAIR_GEMM, pair)
+        assert np.array_equal(_answers(db, Q, path=1), exp), f"pair {pair}"
 
 
 @pytest.mark.parametrize("R,C,B", [(40000, 2100, 70), (20000, 1100, 64), (128, 600, 1024)])
