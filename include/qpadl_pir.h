@@ -93,9 +93,12 @@ int qpadl_version(void);
                                         kernel (one launch, no scratch; two queries share one
                                         pass over D); 0 (default): a separate packing launch
                                         first */
-#define QPADL_OPT_U8_MAX_BATCH 4     /* batches of up to this many queries (0..32, default 32)
+#define QPADL_OPT_U8_MAX_BATCH 4     /* batches of up to this many queries (0..2^30, default 64)
                                         run the tensor-core GEMM on the uint8 digits as stored;
-                                        larger ones use the handle's fp16 operand copy */
+                                        larger ones use the handle's fp16 operand copy, and so
+                                        does the hint when n is larger.  A value at or above
+                                        every batch and n keeps no fp16 copy at all (the lean
+                                        layout: D plus one blocked copy of the same size) */
 #define QPADL_OPT_U8_KSTEP 5         /* digits per row per pipeline stage of that GEMM: 128 or 256;
                                         0 (default) = 128 */
 #define QPADL_OPT_PAIR_GEMM 6        /* batches on the fp16 operand copy and the hint: 1 (default)
@@ -164,8 +167,11 @@ int qpadl_pir_get_option(const qpadl_db *db, int option, int64_t *value);
  *  - if max_batch >= 2: QPADL_OPT_U8_KSTEP in {128, 256} at
  *    min(max(max_batch, 4), 16) queries (when that batch takes the uint8-
  *    digit GEMM), then QPADL_OPT_TENSOR_MIN_BATCH = the first B in 2..4 at
- *    which the tensor path beats the streaming kernel (5 if none does).
- * Allocates and frees scratch for 16 queries and answers, may build the
+ *    which the tensor path beats the streaming kernel (5 if none does);
+ *  - if max_batch > 32: QPADL_OPT_U8_MAX_BATCH = 128 if the uint8-digit GEMM
+ *    beats the fp16-copy GEMM at 128 queries, else 64 if it does at 64, else
+ *    32 (the two GEMMs, so the fp16 copy is built).
+ * Allocates and frees scratch for up to 128 queries and answers, may build the
  * blocked digit copy, and synchronises the stream.  report (may be NULL)
  * receives the times in ms (-1 where a choice does not apply). */
 typedef struct qpadl_tune_report {
@@ -176,6 +182,8 @@ typedef struct qpadl_tune_report {
     uint32_t tuned_batch;
     int32_t stream_chunk, stream_raw, u8_kstep;   /* the chosen settings */
     uint32_t tensor_min_batch;
+    double u8_vs_f16_ms[2][2];  /* [B = 64, 128][uint8-digit GEMM, fp16-copy GEMM] */
+    uint32_t u8_max_batch;      /* the chosen QPADL_OPT_U8_MAX_BATCH */
 } qpadl_tune_report;
 int qpadl_pir_autotune(qpadl_db *db, uint32_t max_batch, qpadl_stream_t stream, qpadl_tune_report *report);
 
@@ -530,9 +538,11 @@ int qpadl_selftest_bounded_wait(int arrive, int32_t *status_dev, uint64_t *waite
  * from up to max_batch queued requests of the database holding the oldest
  * request and of every other database within group_size_ratio of its size,
  * so new arrivals start while earlier launches are still on the GPU.  One
- * launch answers all its databases together: databases with 3..32 queued
- * queries share one grouped tensor-core GEMM, 1..2 queries use the
- * streaming kernel, more than 32 the fp16-copy GEMM.  Admission is by
+ * launch answers all its databases together in one grouped tensor-core GEMM
+ * over their uint8 digits, however uneven their counts (up to each handle's
+ * QPADL_OPT_U8_MAX_BATCH queries; a database with more takes the fp16-copy
+ * GEMM); a launch of a lone database with 1 or 2 queries uses the streaming
+ * kernel.  Admission is by
  * memory: each request's query and answer live in a mapped pinned host
  * arena of host_budget_bytes; each launch's workspace (queries, answers,
  * query limbs) comes from a device arena of device_budget_bytes, and a

@@ -128,6 +128,34 @@ __device__ __forceinline__ bool next_seg(const GroupedGemmArgs &a, uint32_t &u, 
     return true;
 }
 
+// A CTA's (pair form: a cluster's) pieces: whole tiles part, part + nparts, ... below
+// dp_tiles, then its even share of the units from dp_units on.
+struct SegIter {
+    uint32_t t, u, u_end;
+    __device__ __forceinline__ SegIter(const GroupedGemmArgs &a, uint32_t part, uint32_t nparts) {
+        t = part;
+        const uint32_t tail = a.total_units - a.dp_units;
+        u = a.dp_units + static_cast<uint32_t>((uint64_t)part * tail / nparts);
+        u_end = a.dp_units + static_cast<uint32_t>((uint64_t)(part + 1) * tail / nparts);
+    }
+    __device__ __forceinline__ bool next(const GroupedGemmArgs &a, uint32_t bn, uint32_t tile_rows, uint32_t nparts,
+                                         Seg &s) {
+        if (t < a.dp_tiles) {
+            uint32_t g = 0;
+            while (g + 1 < a.ngroups && t >= a.g[g + 1].tile_begin) ++g;
+            const uint32_t local = t - a.g[g].tile_begin;
+            s.g = g;
+            s.m0 = (local / a.g[g].n_tiles) * tile_rows;
+            s.n0 = (local % a.g[g].n_tiles) * bn;
+            s.ks0 = 0;
+            s.ks1 = s.ns = a.g[g].KB;
+            t += nparts;
+            return true;
+        }
+        return next_seg(a, u, u_end, bn, s, tile_rows);
+    }
+};
+
 }  // namespace
 
 // LPV: vector-operand rows per vector.  4 = the four byte limbs of 32-bit vectors, recombined
@@ -205,11 +233,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t aready_c = PAIR ? cluster_addr(aready, 0) : 0u;
     const uint32_t acc_empty_c = PAIR ? cluster_addr(acc_empty, 0) : 0u;
     const uint32_t peer_abort = PAIR ? cluster_addr(const_cast<int *>(abort), rank ^ 1u) : 0u;
-    // this CTA's (pair: cluster's) share of the units, contiguous across tile boundaries
+    // this CTA's (pair: cluster's) pieces: round-robin whole tiles, then a share of the rest
     const uint32_t part = PAIR ? (blockIdx.x >> 1) : blockIdx.x;
     const uint32_t nparts = PAIR ? (gridDim.x >> 1) : gridDim.x;
-    const uint32_t ubeg = static_cast<uint32_t>((uint64_t)part * args.total_units / nparts);
-    const uint32_t uend = static_cast<uint32_t>((uint64_t)(part + 1) * args.total_units / nparts);
     bool failed = false;
     auto fail_here = [&]() {
         failed = true;
@@ -229,23 +255,25 @@ __global__ void __launch_bounds__(kThreads, 1)
             // ---------------- digit producer
             // A second walker over the same stage sequence, kPrefetch stages ahead, pulls each digit
             // box into L2 before its load is issued.
-            uint32_t pu = ubeg, pks = 0;
+            uint32_t pks = 0;
             Seg ps;
-            bool pvalid = next_seg(args, pu, uend, BN, ps, TM);
+            SegIter pit(args, part, nparts);
+            bool pvalid = pit.next(args, BN, TM, nparts, ps);
             if (pvalid) pks = ps.ks0;
             auto prefetch_next = [&]() {
                 if (!pvalid) return;
                 tma_prefetch_l2_4d(&args.a[ps.g], 0, 0, static_cast<int32_t>(pks * KS / 128),
                                    static_cast<int32_t>((ps.m0 + roff) / kBM));
                 if (++pks >= ps.ks1) {
-                    pvalid = next_seg(args, pu, uend, BN, ps, TM);
+                    pvalid = pit.next(args, BN, TM, nparts, ps);
                     if (pvalid) pks = ps.ks0;
                 }
             };
             for (int i = 0; i < kPrefetch; ++i) prefetch_next();
-            uint32_t it = 0, u = ubeg;
+            uint32_t it = 0;
             Seg tr;
-            while (!failed && next_seg(args, u, uend, BN, tr, TM)) {
+            SegIter sit(args, part, nparts);
+            while (!failed && sit.next(args, BN, TM, nparts, tr)) {
                 for (uint32_t ks = tr.ks0; ks < tr.ks1; ++ks, ++it) {
                     const uint32_t sd = it % SD;
                     prefetch_next();
@@ -265,9 +293,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 14) {
         if (lane == 0) {
             // ---------------- limb producer
-            uint32_t it = 0, u = ubeg;
+            uint32_t it = 0;
             Seg tr;
-            while (!failed && next_seg(args, u, uend, BN, tr, TM)) {
+            SegIter sit(args, part, nparts);
+            while (!failed && sit.next(args, BN, TM, nparts, tr)) {
                 for (uint32_t ks = tr.ks0; ks < tr.ks1; ++ks, ++it) {
                     const uint32_t sl = it % SL;
                     if (!mbar_wait(&lfree[sl], ((it / SL) & 1u) ^ 1u, abort)) {
@@ -302,10 +331,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- MMA issuer: the whole warp walks the loop so the descriptors and
         // TMEM addresses stay warp-uniform; one elected lane issues each instruction
         constexpr uint32_t idesc = umma_idesc_f16(TM, BN);
-        uint32_t it = 0, ci = 0, u = ubeg;
+        uint32_t it = 0, ci = 0;
         bool issued = false;
         Seg sg;
-        while (!failed && next_seg(args, u, uend, BN, sg, TM)) {
+        SegIter sit(args, part, nparts);
+        while (!failed && sit.next(args, BN, TM, nparts, sg)) {
             uint32_t d_tmem = tmem_base;
             for (uint32_t ks = sg.ks0; ks < sg.ks1; ++ks, ++it) {
                 const uint32_t kr = ks - sg.ks0;   // exact chunks restart at every piece
@@ -368,9 +398,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- epilogue (warps 2..5)
         const uint32_t quarter = static_cast<uint32_t>(warp & 3);
         const uint32_t lane_addr = (quarter * 32u) << 16;
-        uint32_t ci = 0, u = ubeg;
+        uint32_t ci = 0;
         Seg tr;
-        while (!failed && next_seg(args, u, uend, BN, tr, TM)) {
+        SegIter sit(args, part, nparts);
+        while (!failed && sit.next(args, BN, TM, nparts, tr)) {
             const GroupDesc &gd = args.g[tr.g];
             uint32_t run[QPT];
 #pragma unroll
@@ -434,9 +465,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t row = quarter * 32u + static_cast<uint32_t>(lane);
         const uint32_t lane_addr = (quarter * 32u) << 16;
         const __half2 k1024 = __floats2half2_rn(1024.0f, 1024.0f);
-        uint32_t it = 0, u = ubeg;
+        uint32_t it = 0;
         Seg sg;
-        while (!failed && next_seg(args, u, uend, BN, sg, TM)) {
+        SegIter sit(args, part, nparts);
+        while (!failed && sit.next(args, BN, TM, nparts, sg)) {
             for (uint32_t ks = sg.ks0; ks < sg.ks1; ++ks, ++it) {
                 if (it % kConvGroups != group) continue;   // this group owns every phase of its slots
                 const uint32_t sd = it % SD, sa = it % SA;
@@ -601,17 +633,40 @@ static int u8_resident_pairs(int num_sms) {
     return n;
 }
 
+// Numbers the tiles across groups and chooses the schedule for `parts` CTAs (pair form:
+// clusters): whole tiles round-robin for every full wave but the last, so the CTAs on the
+// tiles of one row tile read its digits together; the last full wave and the remainder are
+// split evenly by units, so every CTA ends at about the same time.
+static void u8_schedule(GroupedGemmArgs &a, uint32_t tile_rows, uint32_t parts) {
+    uint32_t tiles = 0;
+    for (uint32_t g = 0; g < a.ngroups; ++g) {
+        a.g[g].tile_begin = tiles;
+        tiles += (a.g[g].M + tile_rows - 1) / tile_rows * a.g[g].n_tiles;
+    }
+    a.dp_tiles = tiles >= 2 * parts ? (tiles / parts - 1) * parts : 0;
+    a.dp_units = 0;
+    for (uint32_t g = 0; g < a.ngroups; ++g) {
+        const uint32_t t0 = a.g[g].tile_begin;
+        const uint32_t t1 = g + 1 < a.ngroups ? a.g[g + 1].tile_begin : tiles;
+        if (a.dp_tiles > t0) a.dp_units += ((a.dp_tiles < t1 ? a.dp_tiles : t1) - t0) * a.g[g].KB;
+    }
+}
+
 template <int BN, int KS, int LPV = 4>
-static cudaError_t launch_u8(const GroupedGemmArgs &args, int num_sms, bool pair, int *status, cudaStream_t stream) {
-    if (args.total_units == 0) return cudaSuccess;
+static cudaError_t launch_u8(const GroupedGemmArgs &args_in, int num_sms, bool pair, int *status,
+                             cudaStream_t stream) {
+    if (args_in.total_units == 0) return cudaSuccess;
+    GroupedGemmArgs args = args_in;
     if (pair) {
         const uint32_t pairs = static_cast<uint32_t>(u8_resident_pairs<BN, KS, LPV>(num_sms));
         const unsigned clusters = args.total_units < pairs ? args.total_units : pairs;
+        u8_schedule(args, 2 * kBM, clusters);
         cudaLaunchAttribute attr[1];
         cudaLaunchConfig_t cfg = u8_pair_config<BN, KS, LPV>(clusters, stream, attr);
         return cudaLaunchKernelEx(&cfg, limb_gemm_u8_kernel<BN, KS, LPV, true>, args, status);
     }
     const int grid = static_cast<int>(args.total_units < (uint32_t)num_sms ? args.total_units : (uint32_t)num_sms);
+    u8_schedule(args, kBM, static_cast<uint32_t>(grid));
     limb_gemm_u8_kernel<BN, KS, LPV><<<grid, kThreads, U8Cfg<BN, KS>::kSmemBytes, stream>>>(args, status);
     return cudaGetLastError();
 }

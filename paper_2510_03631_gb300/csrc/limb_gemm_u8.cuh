@@ -6,7 +6,7 @@
 
 namespace qpadl {
 
-constexpr int kMaxGemmGroups = 4;
+constexpr int kMaxGemmGroups = 8;
 
 // One group: a database (rows M, K columns) times NV vectors.
 struct GroupDesc {
@@ -14,8 +14,8 @@ struct GroupDesc {
     uint64_t ld_m, ld_b;
     uint32_t M, NV, KB;     // rows, vectors, pipeline stages per tile (ceil(K / ks))
     uint32_t unit_begin;    // first work unit (tile x stage) of this group in the launch
-    uint32_t n_tiles;       // BN-wide tiles per 128-row tile
-    uint32_t pad;
+    uint32_t n_tiles;       // BN-wide tiles per row tile (128 rows; 256 in the pair form)
+    uint32_t tile_begin;    // first tile of this group in the launch (set by the launch)
 };
 
 struct GroupedGemmArgs {
@@ -25,6 +25,11 @@ struct GroupedGemmArgs {
                                      // box {64, BN}, 128-byte swizzle
     GroupDesc g[kMaxGemmGroups];
     uint32_t ngroups, total_units;   // units = sum over groups of tiles x stages
+    // Schedule (set by the launch): tiles [0, dp_tiles) (numbered across groups, each group's
+    // tiles row tile by row tile) are dealt whole, round-robin, so the CTAs on the tiles of one
+    // row tile run together and share its digits through L2; the units from dp_units on are
+    // split evenly (stream-K).
+    uint32_t dp_tiles, dp_units;
 };
 
 cudaError_t prepare_limb_gemm_u8_kernels();
@@ -33,10 +38,11 @@ cudaError_t prepare_limb_gemm_u8_kernels();
 // blk holds ceil(R/128) * ceil(C/128) * 16384 bytes.
 cudaError_t launch_block_digits(const uint8_t *D, uint64_t R, uint64_t C, uint8_t *blk, cudaStream_t stream);
 
-// Work is split evenly over the CTAs by units (one tile's one pipeline stage),
-// across tile boundaries (stream-K): a tile wholly inside one CTA's share is
-// stored, a tile shared by CTAs is accumulated with atomic adds (exact mod
-// 2^32), so the output must be zeroed before the launch.
+// Whole tiles go round-robin to the CTAs for all but the last full wave; the
+// rest is split evenly by units (one tile's one pipeline stage), across tile
+// boundaries (stream-K): a tile wholly inside one CTA's share is stored, a
+// tile shared by CTAs is accumulated with atomic adds (exact mod 2^32), so the
+// output must be zeroed before the launch.
 // bn in {32, 64, 128}, ks in {128, 256}: limb columns per
 // tile (the same for every group) and digits per row per pipeline stage.
 int limb_gemm_u8_default_ks(int bn);

@@ -46,7 +46,7 @@ struct qpadl_db {
     uint8_t *blk = nullptr;          // blocked copy of the digits (128 x 128 tiles)
     uint64_t blk_bytes = 0;
     CUtensorMap u8_map[2];           // over blk: box {128, 128, ks/128, 1} for ks = 128, 256
-    uint32_t u8_max_batch = 32;      // QPADL_OPT_U8_MAX_BATCH
+    uint32_t u8_max_batch = 64;      // QPADL_OPT_U8_MAX_BATCH
     int u8_kstep = 0;                // QPADL_OPT_U8_KSTEP (0 = per tile width default)
     int pair_gemm = 1;               // QPADL_OPT_PAIR_GEMM
     __half *d16 = nullptr;           // digits as fp16, R x pitch
@@ -357,15 +357,13 @@ int ensure_blocked(qpadl_db *db, cudaStream_t stream) {
     return QPADL_OK;
 }
 
-// Batched answer on the u8 GEMM (blocked digits, fp16 made in TMEM): one group.
-int answer_tensor_u8(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, cudaStream_t stream) {
-    int rc = ensure_blocked(db, stream);
-    if (rc != QPADL_OK) return rc;
-    rc = ensure_limbs(db, 8ull * B * db->pitch);
-    if (rc != QPADL_OK) return rc;
+// Batched answer on the u8 GEMM (blocked digits, fp16 made in TMEM): one group of at most
+// 4096 queries (the limb scratch), in tiles of up to 128 limb columns.
+// out[i * ld_m + v * ld_b] = D * X[v] for B vectors whose fp16 limbs are in db->limbs, on the
+// uint8-digit GEMM (the output block must be dense: it is zeroed, split tiles add into it).
+int run_u8_gemm(qpadl_db *db, uint32_t B, uint32_t *ans, uint64_t ld_m, uint64_t ld_b, cudaStream_t stream) {
     const uint64_t R = db->prm.rows, C = db->prm.cols;
-    QPADL_CU(launch_vec_limbs(Q, C, B, C, db->limbs, db->pitch, db->num_sms, stream));
-    const int bn = limb_gemm_bn_for(B);
+    const int bn = std::min(limb_gemm_bn_for(B), 128);
     const int ks = db->u8_kstep ? db->u8_kstep : limb_gemm_u8_default_ks(bn);
     const bool pair = db->pair_gemm && db->num_sms >= 2 && limb_gemm_u8_pair_ok(bn, ks);
     const uint32_t tile_rows = pair ? 2 * kLimbBoxM : kLimbBoxM;
@@ -377,8 +375,8 @@ int answer_tensor_u8(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans,
         return QPADL_ECUDA;
     GroupDesc &g = args.g[0];
     g.out = ans;
-    g.ld_m = 1;
-    g.ld_b = R;
+    g.ld_m = ld_m;
+    g.ld_b = ld_b;
     g.M = static_cast<uint32_t>(R);
     g.NV = B;
     g.KB = static_cast<uint32_t>((C + ks - 1) / ks);
@@ -392,8 +390,29 @@ int answer_tensor_u8(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans,
     return QPADL_OK;
 }
 
+int answer_tensor_u8_chunk(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, cudaStream_t stream) {
+    const uint64_t R = db->prm.rows, C = db->prm.cols;
+    QPADL_CU(launch_vec_limbs(Q, C, B, C, db->limbs, db->pitch, db->num_sms, stream));
+    return run_u8_gemm(db, B, ans, 1, R, stream);
+}
+
+int answer_tensor_u8(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, cudaStream_t stream) {
+    int rc = ensure_blocked(db, stream);
+    if (rc != QPADL_OK) return rc;
+    constexpr uint32_t kChunk = 4096;
+    rc = ensure_limbs(db, 8ull * std::min(B, kChunk) * db->pitch);
+    if (rc != QPADL_OK) return rc;
+    const uint64_t R = db->prm.rows, C = db->prm.cols;
+    for (uint32_t b0 = 0; b0 < B; b0 += kChunk) {
+        rc = answer_tensor_u8_chunk(db, Q + (uint64_t)b0 * C, std::min(B - b0, kChunk), ans + (uint64_t)b0 * R,
+                                    stream);
+        if (rc != QPADL_OK) return rc;
+    }
+    return QPADL_OK;
+}
+
 int answer_tensor(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, cudaStream_t stream) {
-    if (db->u8_ok && B <= db->u8_max_batch && 4 * B <= 128) return answer_tensor_u8(db, Q, B, ans, stream);
+    if (db->u8_ok && B <= db->u8_max_batch) return answer_tensor_u8(db, Q, B, ans, stream);
     int rc = ensure_tensor_copy(db, stream);
     if (rc != QPADL_OK) return rc;
     // chunks of at most 4096 queries bound the limb scratch (8 bytes per query per column)
@@ -666,13 +685,14 @@ int qpadl_pir_hint(qpadl_db *db, const uint32_t *A_dev, uint32_t *H_dev, qpadl_s
     if (!db || !A_dev || !H_dev) return QPADL_EINVAL;
     if (set_device(db) != QPADL_OK) return QPADL_ECUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    int rc = ensure_tensor_copy(db, s);
-    if (rc != QPADL_OK) return rc;
     const uint32_t n = db->prm.n;
+    const bool u8 = db->u8_ok && n <= db->u8_max_batch;   // the lean layout keeps no fp16 copy
+    int rc = u8 ? ensure_blocked(db, s) : ensure_tensor_copy(db, s);
+    if (rc != QPADL_OK) return rc;
     rc = ensure_limbs(db, 8ull * n * db->pitch);
     if (rc != QPADL_OK) return rc;
     QPADL_CU(launch_mat_col_limbs(A_dev, db->prm.cols, n, db->limbs, db->pitch, s));
-    return run_limb_gemm(db, n, H_dev, n, 1, s);
+    return u8 ? run_u8_gemm(db, n, H_dev, n, 1, s) : run_limb_gemm(db, n, H_dev, n, 1, s);
 }
 
 int qpadl_pir_query(const qpadl_params *prm, const uint32_t *A_dev, const uint32_t *s_dev, const int32_t *e_dev,
@@ -744,7 +764,7 @@ int qpadl_pir_set_option(qpadl_db *db, int option, int64_t value) {
             db->stream_raw = static_cast<int>(value);
             return QPADL_OK;
         case QPADL_OPT_U8_MAX_BATCH:
-            if (value < 0 || value > 32) return QPADL_EINVAL;
+            if (value < 0 || value > (1ll << 30)) return QPADL_EINVAL;
             db->u8_max_batch = static_cast<uint32_t>(value);
             return QPADL_OK;
         case QPADL_OPT_U8_KSTEP:
@@ -780,9 +800,10 @@ int qpadl_pir_autotune(qpadl_db *db, uint32_t max_batch, qpadl_stream_t stream, 
     qpadl_tune_report rep;
     std::memset(&rep, 0, sizeof(rep));
     const uint32_t BT = std::min<uint32_t>(std::max<uint32_t>(max_batch, 4u), 16u);
+    const uint32_t BQ = max_batch > 32 ? 128u : BT;   // scratch: the GEMM comparison takes 128 queries
     uint32_t *Q = nullptr, *A = nullptr;
-    if (cudaMalloc(reinterpret_cast<void **>(&Q), 4ull * C * BT) != cudaSuccess ||
-        cudaMalloc(reinterpret_cast<void **>(&A), 4ull * R * BT) != cudaSuccess) {
+    if (cudaMalloc(reinterpret_cast<void **>(&Q), 4ull * C * BQ) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void **>(&A), 4ull * R * BQ) != cudaSuccess) {
         cudaGetLastError();
         if (Q) cudaFree(Q);
         return QPADL_ENOMEM;
@@ -795,7 +816,7 @@ int qpadl_pir_autotune(qpadl_db *db, uint32_t max_batch, qpadl_stream_t stream, 
         return rc;
     };
     // synthetic queries (uniform words); the answers are discarded
-    if (cuda_fail(launch_gen_a(0x9E3779B97F4A7C15ull, C * BT, 1, Q, db->num_sms, s), "tune queries") != QPADL_OK)
+    if (cuda_fail(launch_gen_a(0x9E3779B97F4A7C15ull, C * BQ, 1, Q, db->num_sms, s), "tune queries") != QPADL_OK)
         return done(QPADL_ECUDA);
     constexpr int kReps = 5;
     // 1. one query: chunk width x in-kernel packing
@@ -851,6 +872,24 @@ int qpadl_pir_autotune(qpadl_db *db, uint32_t max_batch, qpadl_stream_t stream, 
         }
         db->tensor_min_batch = threshold;
     }
+    // 3. larger batches: how far the uint8-digit GEMM stays ahead of the fp16-copy GEMM
+    rep.u8_vs_f16_ms[0][0] = rep.u8_vs_f16_ms[0][1] = rep.u8_vs_f16_ms[1][0] = rep.u8_vs_f16_ms[1][1] = -1.0;
+    if (max_batch > 32 && db->u8_ok) {
+        const uint32_t keep = db->u8_max_batch;
+        uint32_t pick = 32;
+        const uint32_t Bs[2] = {64, 128};
+        for (int i = 0; i < 2; ++i) {
+            db->u8_max_batch = 1u << 30;
+            const double mu = time_calls([&] { return answer_tensor(db, Q, Bs[i], A, s); }, s, kReps);
+            db->u8_max_batch = 0;
+            const double mf = time_calls([&] { return answer_tensor(db, Q, Bs[i], A, s); }, s, kReps);
+            rep.u8_vs_f16_ms[i][0] = mu;
+            rep.u8_vs_f16_ms[i][1] = mf;
+            if (mu > 0 && mf > 0 && mu <= mf) pick = Bs[i];
+        }
+        db->u8_max_batch = keep == 64 || keep == 32 || keep == 128 ? pick : keep;
+    }
+    rep.u8_max_batch = db->u8_max_batch;
     rep.stream_chunk = db->stream_chunk;
     rep.stream_raw = db->stream_raw;
     rep.u8_kstep = db->u8_kstep;

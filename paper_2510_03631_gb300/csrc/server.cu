@@ -11,11 +11,13 @@
 //    holding the oldest request and of every other database of about the
 //    same size (group_size_ratio), carves a workspace for them from a device
 //    arena, and enqueues on that stream one grouped cycle: a gather kernel that pulls every
-//    query straight from pinned host memory; one grouped exact byte-limb
-//    GEMM over all databases with 3..32 queued queries (the tiles of every
-//    database form one work list split evenly over the SMs); the streaming
-//    kernel for databases with 1 or 2 queries (two in one pass); the fp16-copy GEMM for
-//    batches above 32; and a scatter kernel that writes every answer
+//    query straight from pinned host memory; ONE grouped exact byte-limb
+//    GEMM over the uint8 digits of every database in the cycle, however
+//    uneven their counts (the tiles of every database form one work list
+//    dealt over the SMs); the streaming kernel when the cycle holds a lone
+//    database with 1 or 2 queries (two in one pass); the fp16-copy GEMM only
+//    for a database with more queries than its uint8-digit GEMM limit; and a
+//    scatter kernel that writes every answer
 //    straight into its request's pinned buffer.  A host callback at the end
 //    of the stream marks the requests done and frees the workspace.
 //  - each launch uses only its own workspace (the handles' operand copies
@@ -125,6 +127,7 @@ struct Request {
 struct DbEntry {
     qpadl_db *db = nullptr;
     uint64_t R = 0, C = 0, pitch = 0;
+    uint32_t u8_max = 0;     // largest group the uint8-digit GEMM takes (QPADL_OPT_U8_MAX_BATCH)
     std::deque<Request *> queue;
 };
 
@@ -249,10 +252,10 @@ namespace {
 constexpr uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 constexpr size_t kMaxGemmLaunches = 2;   // launches in flight at once while a GEMM is among them
 
-// Device workspace of one group of `take` requests: queries, answers and,
-// for the GEMM paths, the byte limbs of the queries.
+// Device workspace of one group of `take` requests: queries, answers and the byte limbs of the
+// queries (any group can join a grouped GEMM).
 uint64_t group_bytes(const DbEntry &e, uint32_t take) {
-    return align256(4ull * take * e.C) + align256(4ull * take * e.R) + (take >= 3 ? align256(8ull * take * e.pitch) : 0);
+    return align256(4ull * take * e.C) + align256(4ull * take * e.R) + align256(8ull * take * e.pitch);
 }
 }  // namespace
 
@@ -291,16 +294,18 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
         g.da_off = need;
         need += align256(4ull * take * e.R);
         g.dl_off = need;
-        if (take >= 3) need += align256(8ull * take * e.pitch);
+        need += align256(8ull * take * e.pitch);
         total += take;
         groups.push_back(g);
     }
     if (groups.empty()) return false;
-    // A batch of 3 or more runs a tensor-core GEMM whose grid fills every SM.  While one runs,
-    // at most kMaxGemmLaunches launches of any kind are in flight: more would only split the
-    // SMs and shrink each batch.  With no GEMM in flight, one- and two-query streaming
-    // launches may take every free stream, so a lone query does not queue behind another.
-    bool gemm = false;
+    // A launch over several databases, or with 3 or more queries, runs a tensor-core GEMM whose
+    // grid fills every SM.  While one runs, at most kMaxGemmLaunches launches of any kind are in
+    // flight: more would only split the SMs and shrink each batch.  With no GEMM in flight, a
+    // lone database's one- and two-query streaming launches may take every free stream, so a
+    // lone query does not queue behind another.
+    const bool lone = groups.size() == 1;
+    bool gemm = !lone;
     for (const Group &g : groups) gemm = gemm || g.count >= 3;
     if ((gemm || active_gemm > 0) && active.size() >= kMaxGemmLaunches) return false;
     uint64_t off = 0;
@@ -354,21 +359,25 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
     const unsigned gx = static_cast<unsigned>(std::min<uint64_t>((maxC + 1023) / 1024, 32));
     copy_jobs_kernel<<<dim3(gx, total), 256, 0, S.stream>>>(S.q_jobs);
     ok = ok && cudaGetLastError() == cudaSuccess;
-    // grouped GEMM over the databases with 3..32 queries (up to kMaxGemmGroups per launch)
+    // Response kernels.  A lone database with 1 or 2 queries takes the streaming kernel (one
+    // pass, lowest latency).  Otherwise every database whose queries the uint8-digit GEMM takes
+    // (up to its QPADL_OPT_U8_MAX_BATCH) joins one grouped GEMM launch (up to kMaxGemmGroups
+    // databases per launch), however uneven their counts; a database with more queries than
+    // that takes the fp16-copy GEMM.
     std::vector<const Group *> small;
     for (const Group &g : groups) {
         const DbEntry &e = dbs[g.db];
         uint32_t *dq = reinterpret_cast<uint32_t *>(base + g.dq_off);
         uint32_t *da = reinterpret_cast<uint32_t *>(base + g.da_off);
         __half *dl = reinterpret_cast<__half *>(base + g.dl_off);
-        if (g.count == 1) {
+        if (lone && g.count == 1) {
             ok = ok && qpadl::db_answer_one_noscratch(e.db, dq, da, S.stream) == QPADL_OK;
             ++n_stream_k;
-        } else if (g.count == 2) {
+        } else if (lone && g.count == 2) {
             // both queries in one pass over the database
             ok = ok && qpadl::db_answer_two_noscratch(e.db, dq, e.C, da, e.R, S.stream) == QPADL_OK;
             ++n_stream_k;
-        } else if (g.count <= 32) {
+        } else if (g.count <= e.u8_max) {
             ok = ok && qpadl::launch_vec_limbs(dq, e.C, g.count, e.C, dl, e.pitch, qpadl::db_num_sms(e.db),
                                                S.stream) == cudaSuccess;
             ok = ok && cudaMemsetAsync(da, 0, 4ull * g.count * e.R, S.stream) == cudaSuccess;
@@ -382,7 +391,8 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
         const size_t k1 = std::min(small.size(), k0 + qpadl::kMaxGemmGroups);
         uint32_t maxb = 0;
         for (size_t k = k0; k < k1; ++k) maxb = std::max(maxb, small[k]->count);
-        const int bn = qpadl::limb_gemm_bn_for(maxb);
+        // one tile width for the launch; a larger group takes several tiles of it
+        const int bn = std::min(qpadl::limb_gemm_bn_for(maxb), 128);
         const int ks = qpadl::limb_gemm_u8_default_ks(bn);
         // one launch takes one form: the pair form when every database in it allows it
         bool pair = qpadl::limb_gemm_u8_pair_ok(bn, ks);
@@ -538,14 +548,18 @@ int qpadl_server_add_db(qpadl_server *s, qpadl_db *db, int *db_id) {
     uint64_t R = 0, C = 0;
     if (qpadl_pir_shape(db, &R, &C) != QPADL_OK) return QPADL_EINVAL;
     // build the operand copies the launches read now, so launches never allocate
-    if (s->cfg.max_batch >= 3 && qpadl::db_prepare_u8(db, nullptr) != QPADL_OK) return QPADL_ENOMEM;
-    if (s->cfg.max_batch > 32 && qpadl::db_prepare_f16(db, nullptr) != QPADL_OK) return QPADL_ENOMEM;
+    int64_t u8_max = 0;
+    if (qpadl_pir_get_option(db, QPADL_OPT_U8_MAX_BATCH, &u8_max) != QPADL_OK) return QPADL_EINVAL;
+    if (qpadl::db_prepare_u8(db, nullptr) != QPADL_OK) return QPADL_ENOMEM;
+    if (s->cfg.max_batch > static_cast<uint64_t>(u8_max) && qpadl::db_prepare_f16(db, nullptr) != QPADL_OK)
+        return QPADL_ENOMEM;
     if (cudaDeviceSynchronize() != cudaSuccess) return QPADL_ECUDA;
     DbEntry e;
     e.db = db;
     e.R = R;
     e.C = C;
     e.pitch = qpadl::db_limb_pitch(db);
+    e.u8_max = static_cast<uint32_t>(std::min<int64_t>(u8_max, 1ll << 30));
     if (group_bytes(e, 1) > s->dev_alloc.size()) return QPADL_ENOMEM;   // not even one request fits
     s->dbs.push_back(e);
     *db_id = static_cast<int>(s->dbs.size() - 1);

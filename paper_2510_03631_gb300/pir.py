@@ -643,6 +643,7 @@ class qpadl_tune_report(ctypes.Structure):
         ("tuned_batch", ctypes.c_uint32),
         ("stream_chunk", ctypes.c_int32), ("stream_raw", ctypes.c_int32), ("u8_kstep", ctypes.c_int32),
         ("tensor_min_batch", ctypes.c_uint32),
+        ("u8_vs_f16_ms", (ctypes.c_double * 2) * 2), ("u8_max_batch", ctypes.c_uint32),
     ]
 
 
@@ -654,7 +655,9 @@ def qpadl_pir_autotune(db: Database, max_batch: int, stream=None) -> dict:
     return {"single_ms": [[rep.single_ms[c][r] for r in range(2)] for c in range(3)],
             "u8_kstep_ms": list(rep.u8_kstep_ms), "stream_ms": list(rep.stream_ms), "tensor_ms": list(rep.tensor_ms),
             "tuned_batch": rep.tuned_batch, "stream_chunk": rep.stream_chunk, "stream_raw": rep.stream_raw,
-            "u8_kstep": rep.u8_kstep, "tensor_min_batch": rep.tensor_min_batch}
+            "u8_kstep": rep.u8_kstep, "tensor_min_batch": rep.tensor_min_batch,
+            "u8_vs_f16_ms": [[rep.u8_vs_f16_ms[b][k] for k in range(2)] for b in range(2)],
+            "u8_max_batch": rep.u8_max_batch}
 
 
 def qpadl_pir_reserve(db: Database, max_batch: int, stream=None):

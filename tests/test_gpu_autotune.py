@@ -51,6 +51,20 @@ def test_autotune_picks_valid_options_and_keeps_answers_exact(cuda, R, C, max_ba
     db.close()
 
 
+def test_autotune_chooses_the_uint8_gemm_limit(cuda):
+    # max_batch above 32: the tuner times both batched GEMMs at 64 and 128 queries and keeps the
+    # largest batch the uint8-digit GEMM wins; answers on either side of the limit stay exact
+    R, C = 2048, 4096
+    D = inputs.db_digits(R, C, 256, seed=17)
+    db = pir.qpadl_pir_setup(pir.params(R, C, 16, seed=1), torch.from_numpy(D).cuda())
+    rep = pir.qpadl_pir_autotune(db, 256)
+    assert rep["u8_max_batch"] in (32, 64, 128)
+    assert pir.qpadl_pir_get_option(db, pir.QPADL_OPT_U8_MAX_BATCH) == rep["u8_max_batch"]
+    assert all(t > 0 for row in rep["u8_vs_f16_ms"] for t in row)
+    _check_answers(db, D, C, R, (33, 64, 65, 129))
+    db.close()
+
+
 def test_autotune_rejects_bad_arguments(cuda):
     D = torch.zeros(64 * 64, dtype=torch.uint8, device="cuda")
     db = pir.qpadl_pir_setup(pir.params(64, 64, 8), D)

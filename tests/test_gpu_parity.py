@@ -243,6 +243,25 @@ def test_answer_batch_pair_and_single_sm_gemms(R, C, B):
         assert np.array_equal(_answers(db, Q, path=1), exp), f"pair {pair}"
 
 
+@pytest.mark.parametrize("R,C,B", [
+    (300, 1000 + 8, 33),     # two vector tiles; the peer's rows partly past R
+    (1000, 2048, 100),       # four vector tiles, the last ragged
+    (4099, 1536, 200),       # round-robin whole tiles, then a split tail
+    (20000, 1100, 300),      # many tiles per CTA: several round-robin waves
+    (128, 64, 40),           # the peer holds no rows; K below one stage
+    (640, 512, 4096 + 40),   # crosses the 4096-query chunk of the limb scratch
+])
+def test_answer_batch_u8_gemm_large_batches(R, C, B):
+    # the uint8-digit GEMM for batches above 32 (tiles of 128 limb columns, several per row tile)
+    prm, D, db = _setup(R, C, seed=R + 5 * B)
+    pir.qpadl_pir_set_option(db, pir.QPADL_OPT_U8_MAX_BATCH, 1 << 20)
+    Q = inputs.uniform_u32(B * C, seed=C + 11 * B, tag=inputs.TAG_MISC).reshape(B, C)
+    exp = oracle.answer_batch(D, Q, threads=oracle.max_threads())
+    for pair in (1, 0):
+        pir.qpadl_pir_set_option(db, pir.QPADL_OPT_PAIR_GEMM, pair)
+        assert np.array_equal(_answers(db, Q, path=1), exp), f"pair {pair}"
+
+
 def test_answer_batch_pair_gemm_extreme_values():
     # every digit 255 against limb-extreme query words: each 512-deep chunk at its exactness bound
     R, C, B = 512, 2048, 64

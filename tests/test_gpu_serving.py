@@ -94,11 +94,11 @@ def test_answers_match_oracle(dbs):
     srv.close()
 
 
-@pytest.mark.parametrize("counts", [(2, 20, 45), (5, 17, 32), (1, 0, 3)])
+@pytest.mark.parametrize("counts", [(3, 20, 45), (2, 20, 45), (5, 17, 32), (1, 0, 3), (1, 1, 1), (0, 64, 0)])
 def test_one_launch_answers_every_database(dbs, counts):
-    # requests submitted before start form one launch over all databases:
-    # 1..2 queries take the streaming kernel, 3..32 share the grouped GEMM,
-    # more than 32 take the fp16-copy GEMM
+    # requests submitted before start form one launch over all databases, and that launch runs
+    # ONE grouped GEMM kernel however uneven the counts (the streaming kernel only for a lone
+    # database with one or two queries)
     srv = pir.qpadl_server_create(pir.server_config(max_batch=64, num_streams=1, group_size_ratio=1e9))
     ids = [pir.qpadl_server_add_db(srv, h) for _, h in dbs]
     tickets = []
@@ -115,7 +115,32 @@ def test_one_launch_answers_every_database(dbs, counts):
     st = pir.qpadl_server_stats(srv)
     assert st["launches"] == 1 and st["completed"] == sum(counts)
     assert st["grouped_launches"] == (1 if sum(c > 0 for c in counts) > 1 else 0)
+    assert st["gemm_kernels"] == 1 and st["stream_kernels"] == 0
     srv.close()
+
+
+def test_group_above_the_uint8_gemm_limit_takes_the_fp16_copy(dbs):
+    # a handle whose uint8-digit GEMM takes at most 8 queries: 20 queued queries of it run the
+    # fp16-copy GEMM, the other databases' queries the grouped uint8-digit GEMM, in one cycle
+    D1, h1 = dbs[1]
+    pir.qpadl_pir_set_option(h1, pir.QPADL_OPT_U8_MAX_BATCH, 8)
+    try:
+        srv = pir.qpadl_server_create(pir.server_config(max_batch=64, num_streams=1, group_size_ratio=1e9))
+        ids = [pir.qpadl_server_add_db(srv, h) for _, h in dbs]
+        tickets = []
+        for d, cnt in enumerate((4, 20, 6)):
+            for i in range(cnt):
+                q = inputs.uniform_u32(SHAPES[d][1], seed=9500 + 100 * d + i, tag=inputs.TAG_MISC)
+                tickets.append((d, q, pir.qpadl_server_submit(srv, ids[d], q)))
+        pir.qpadl_server_start(srv)
+        for d, q, t in tickets:
+            rc, ans, _ = _wait(srv, t, SHAPES[d][0])
+            assert rc == pir.QPADL_OK and np.array_equal(ans, oracle.answer(dbs[d][0], q))
+        st = pir.qpadl_server_stats(srv)
+        assert st["launches"] == 1 and st["gemm_kernels"] == 2 and st["stream_kernels"] == 0
+        srv.close()
+    finally:
+        pir.qpadl_pir_set_option(h1, pir.QPADL_OPT_U8_MAX_BATCH, 64)
 
 
 @pytest.mark.parametrize("ratio,grouped", [(0.0, False), (1.5, False), (2.5, True)])
