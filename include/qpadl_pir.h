@@ -503,6 +503,13 @@ int qpadl_chor_answer_batch(qpadl_chor *h, const uint32_t *Q_dev, uint32_t B, ui
  *   XOR tables in shared memory, looked up by 4 query bits); smaller ones the
  *   masked-XOR scan.  257 disables the four-Russians kernel. */
 #define QPADL_CHOR_OPT_M4RM_MIN_BATCH 1
+/* QPADL_CHOR_OPT_SCAN_FORM (-1..3, default -1): inner loop of the masked-XOR
+ * scan.  Bit 1: each thread covers 8 database words per row (at most 16
+ * queries) instead of 4 (at most 32), so one selector test serves twice the
+ * words; bit 0: a query's row words are XORed in under its selector bit
+ * instead of through an all-ones/all-zeros mask.  -1 picks by batch size:
+ * 0 up to 8 queries, 1 up to 16, 3 above.  Every form gives the same bits. */
+#define QPADL_CHOR_OPT_SCAN_FORM 2
 int qpadl_chor_set_option(qpadl_chor *h, int option, int64_t value);
 int qpadl_chor_get_option(qpadl_chor *h, int option, int64_t *value);
 

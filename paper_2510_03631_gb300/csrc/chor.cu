@@ -45,9 +45,11 @@ constexpr int kChorThreads = 256;          // consumer threads
 constexpr int kChorStages = 4;
 constexpr uint32_t kChorStageWords = 8192;  // 32 KB of database words per stage
 
-// Column tile width and band height for QG query groups per CTA.
-__host__ __device__ constexpr uint32_t chor_tw(int qg) { return 1024u / static_cast<uint32_t>(qg); }
-__host__ __device__ constexpr uint32_t chor_rb(int qg) { return kChorStageWords / chor_tw(qg); }
+// Column tile width and band height for QG query groups per CTA, WPT words per thread.
+__host__ __device__ constexpr uint32_t chor_tw(int qg, int wpt) {
+    return static_cast<uint32_t>(kChorThreads / qg * wpt);
+}
+__host__ __device__ constexpr uint32_t chor_rb(int qg, int wpt) { return kChorStageWords / chor_tw(qg, wpt); }
 
 // QT words per row as stored (at least 4, so a TMA box row is 16 bytes).
 __host__ __device__ constexpr uint32_t chor_qtw(uint32_t qbw) { return qbw < 4 ? 4u : qbw; }
@@ -75,17 +77,22 @@ __global__ void chor_transpose_kernel(const uint32_t *__restrict__ Q, uint64_t q
     }
 }
 
-template <int QB, int QG>
+// WPT: database words per thread per row (4 or 8: a mask or selector test serves WPT words).
+// PRED: per query, test its selector bit and XOR the row words in under that (warp-uniform)
+// condition, instead of building an all-ones/all-zeros mask and AND-ing it in.
+template <int QB, int QG, int WPT = 4, bool PRED = false>
 __global__ void __launch_bounds__(kChorThreads + 32, 1)
     chor_answer_kernel(const __grid_constant__ CUtensorMap db_map, const __grid_constant__ CUtensorMap qt_map,
                        uint64_t r, uint32_t W, uint32_t B, uint32_t qtw, uint32_t *__restrict__ out,
                        int *__restrict__ status) {
-    constexpr uint32_t TW = chor_tw(QG);
-    constexpr uint32_t RB = chor_rb(QG);
+    constexpr uint32_t TW = chor_tw(QG, WPT);
+    constexpr uint32_t RB = chor_rb(QG, WPT);
     constexpr uint32_t BOXW = TW < 256 ? TW : 256;   // words per TMA box row
     constexpr uint32_t NBOX = TW / BOXW;
-    constexpr uint32_t QUADS = TW / 4;               // threads per query group
-    static_assert(QUADS * QG == kChorThreads, "one thread per (word quad, query group)");
+    constexpr uint32_t QUADS = TW / WPT;             // threads per query group
+    static_assert(QUADS * QG == kChorThreads, "one thread per (WPT words, query group)");
+    static_assert(WPT == 4 || WPT == 8, "words per thread");
+    static_assert(QB <= 32 && 32 % QB == 0, "a query group lies inside one selector word");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t qt_stage_bytes = RB * qtw * 4u;
@@ -146,23 +153,28 @@ __global__ void __launch_bounds__(kChorThreads + 32, 1)
     } else {
         // ---------------- consumers
         const uint32_t quad = threadIdx.x % QUADS, g = threadIdx.x / QUADS;
-        const uint32_t bx = (quad * 4) / BOXW, wx = (quad * 4) % BOXW;
-        uint32_t acc[QB][4];
+        const uint32_t bx = (quad * WPT) / BOXW, wx = (quad * WPT) % BOXW;
+        // the group's QB selector bits: bits sh .. sh + QB - 1 of selector word g * QB / 32
+        const uint32_t sw = (g * QB) / 32, sh = (g * QB) % 32;
+        uint32_t acc[QB][WPT];
 #pragma unroll
-        for (int j = 0; j < QB; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0u;
+        for (int j = 0; j < QB; ++j)
+#pragma unroll
+            for (int k = 0; k < WPT; ++k) acc[j][k] = 0u;
         uint64_t cur_tile = u0 < u1 ? u0 / n_bands : 0;
         auto flush = [&](uint64_t tile) {
-            const uint64_t w0 = tile * TW + quad * 4;
+            const uint64_t w0 = tile * TW + quad * WPT;
 #pragma unroll
             for (int j = 0; j < QB; ++j) {
                 const uint32_t b = g * QB + j;
                 if (b < B) {
                     uint32_t *o = out + (uint64_t)b * W + w0;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
+                    for (int k = 0; k < WPT; ++k)
                         if (w0 + k < W && acc[j][k]) atomicXor(o + k, acc[j][k]);
                 }
-                acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0u;
+#pragma unroll
+                for (int k = 0; k < WPT; ++k) acc[j][k] = 0u;
             }
         };
         uint32_t it = 0;
@@ -179,19 +191,32 @@ __global__ void __launch_bounds__(kChorThreads + 32, 1)
                 break;
             }
             const uint32_t *rows = db_st + st * kChorStageWords + bx * RB * BOXW + wx;
-            const uint32_t *sel = qt_st + st * (2048 / 4) + g;
+            const uint32_t *sel = qt_st + st * (2048 / 4) + sw;
             const uint64_t row0 = band * RB;
             const uint32_t nrows = static_cast<uint32_t>(r - row0 < RB ? r - row0 : RB);
             for (uint32_t i = 0; i < nrows; ++i) {
-                const uint4 d = *reinterpret_cast<const uint4 *>(rows + i * BOXW);
-                const uint32_t s = sel[i * qtw];
+                uint32_t d[WPT];
+#pragma unroll
+                for (int k = 0; k < WPT; k += 4) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(rows + i * BOXW + k);
+                    d[k] = v.x;
+                    d[k + 1] = v.y;
+                    d[k + 2] = v.z;
+                    d[k + 3] = v.w;
+                }
+                const uint32_t s = sel[i * qtw] >> sh;
 #pragma unroll
                 for (int j = 0; j < QB; ++j) {
-                    const uint32_t m = static_cast<uint32_t>(static_cast<int32_t>(s << (31 - j)) >> 31);
-                    acc[j][0] ^= d.x & m;
-                    acc[j][1] ^= d.y & m;
-                    acc[j][2] ^= d.z & m;
-                    acc[j][3] ^= d.w & m;
+                    if constexpr (PRED) {
+                        if ((s >> j) & 1u) {
+#pragma unroll
+                            for (int k = 0; k < WPT; ++k) acc[j][k] ^= d[k];
+                        }
+                    } else {
+                        const uint32_t m = static_cast<uint32_t>(static_cast<int32_t>(s << (31 - j)) >> 31);
+#pragma unroll
+                        for (int k = 0; k < WPT; ++k) acc[j][k] ^= d[k] & m;
+                    }
                 }
             }
             __syncwarp();
@@ -394,8 +419,22 @@ __global__ void __launch_bounds__(kChorThreads + 32, 1)
 }
 
 // ------------------------------------------------------------------ host side
-static bool chor_pick(uint32_t B, int *qb, int *qg) {
-    if (B == 0 || B > kChorMaxBatch) return false;
+// Queries per thread (qb) and query groups per CTA (qg) for a batch; form bit 1 selects 8
+// words per thread (then at most 16 queries per thread, for the registers), bit 0 the
+// predicated XOR.
+static bool chor_pick(uint32_t B, int form, int *qb, int *qg, int *wpt) {
+    if (B == 0 || B > kChorMaxBatch || form < 0 || form > 3) return false;
+    *wpt = (form & 2) ? 8 : 4;
+    if (*wpt == 8) {
+        int q = 1;
+        while (q < static_cast<int>(B) && q < 16) q <<= 1;
+        *qb = q;
+        const uint32_t groups = (B + q - 1) / q;
+        int g = 1;
+        while (static_cast<uint32_t>(g) < groups) g <<= 1;
+        *qg = g;
+        return true;
+    }
     if (B <= 32) {
         int q = 1;
         while (q < static_cast<int>(B)) q <<= 1;
@@ -411,15 +450,28 @@ static bool chor_pick(uint32_t B, int *qb, int *qg) {
     return true;
 }
 
-template <int QB, int QG>
 static int chor_smem_bytes() {
     return kChorStages * (kChorStageWords * 4 + 2048) + 2 * kChorStages * 8 + 16 + 1024;
 }
 
+template <int QB, int QG, int WPT, bool PRED>
+static cudaError_t chor_attr1() {
+    return cudaFuncSetAttribute(chor_answer_kernel<QB, QG, WPT, PRED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                chor_smem_bytes());
+}
+
 template <int QB, int QG>
 static cudaError_t chor_attr() {
-    return cudaFuncSetAttribute(chor_answer_kernel<QB, QG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                chor_smem_bytes<QB, QG>());
+    cudaError_t e;
+    if ((e = chor_attr1<QB, QG, 4, false>()) != cudaSuccess) return e;
+    return chor_attr1<QB, QG, 4, true>();
+}
+
+template <int QB, int QG>
+static cudaError_t chor_attr8() {
+    cudaError_t e;
+    if ((e = chor_attr1<QB, QG, 8, false>()) != cudaSuccess) return e;
+    return chor_attr1<QB, QG, 8, true>();
 }
 
 static int chor_m4rm_smem_bytes() {
@@ -439,16 +491,25 @@ cudaError_t prepare_chor_kernels() {
     if ((e = chor_attr<32, 1>()) != cudaSuccess) return e;
     if ((e = chor_attr<32, 2>()) != cudaSuccess) return e;
     if ((e = chor_attr<32, 4>()) != cudaSuccess) return e;
-    return chor_attr<32, 8>();
+    if ((e = chor_attr<32, 8>()) != cudaSuccess) return e;
+    if ((e = chor_attr8<1, 1>()) != cudaSuccess) return e;
+    if ((e = chor_attr8<2, 1>()) != cudaSuccess) return e;
+    if ((e = chor_attr8<4, 1>()) != cudaSuccess) return e;
+    if ((e = chor_attr8<8, 1>()) != cudaSuccess) return e;
+    if ((e = chor_attr8<16, 1>()) != cudaSuccess) return e;
+    if ((e = chor_attr8<16, 2>()) != cudaSuccess) return e;
+    if ((e = chor_attr8<16, 4>()) != cudaSuccess) return e;
+    if ((e = chor_attr8<16, 8>()) != cudaSuccess) return e;
+    return chor_attr8<16, 16>();
 }
 
-bool chor_launch_shape(uint32_t B, uint32_t *tw, uint32_t *rb, uint32_t *box_words, uint32_t *qtw) {
-    int qb = 0, qg = 0;
-    if (!chor_pick(B, &qb, &qg)) return false;
-    *tw = chor_tw(qg);
-    *rb = chor_rb(qg);
+bool chor_launch_shape(uint32_t B, int form, uint32_t *tw, uint32_t *rb, uint32_t *box_words, uint32_t *qtw) {
+    int qb = 0, qg = 0, wpt = 0;
+    if (!chor_pick(B, form, &qb, &qg, &wpt)) return false;
+    *tw = chor_tw(qg, wpt);
+    *rb = chor_rb(qg, wpt);
     *box_words = *tw < 256 ? *tw : 256;
-    *qtw = chor_qtw(static_cast<uint32_t>(qg));
+    *qtw = chor_qtw(static_cast<uint32_t>((qg * qb + 31) / 32));
     return true;
 }
 
@@ -461,36 +522,67 @@ cudaError_t launch_chor_transpose(const uint32_t *Q, uint64_t qw, uint32_t B, ui
     return cudaGetLastError();
 }
 
-template <int QB, int QG>
-static cudaError_t launch_qbg(const CUtensorMap &db_map, const CUtensorMap &qt_map, uint64_t r, uint32_t W,
-                              uint32_t B, uint32_t qtw, uint32_t *out, int num_sms, int *status, cudaStream_t stream) {
-    const uint64_t units = ((W + chor_tw(QG) - 1) / chor_tw(QG)) * ((r + chor_rb(QG) - 1) / chor_rb(QG));
+template <int QB, int QG, int WPT, bool PRED>
+static cudaError_t launch_qbg1(const CUtensorMap &db_map, const CUtensorMap &qt_map, uint64_t r, uint32_t W,
+                               uint32_t B, uint32_t qtw, uint32_t *out, int num_sms, int *status,
+                               cudaStream_t stream) {
+    constexpr uint32_t TW = chor_tw(QG, WPT), RB = chor_rb(QG, WPT);
+    const uint64_t units = ((W + TW - 1) / TW) * ((r + RB - 1) / RB);
     const int grid = static_cast<int>(units < (uint64_t)num_sms ? units : (uint64_t)num_sms);
-    chor_answer_kernel<QB, QG><<<grid, kChorThreads + 32, chor_smem_bytes<QB, QG>(), stream>>>(db_map, qt_map, r, W, B,
-                                                                                              qtw, out, status);
+    chor_answer_kernel<QB, QG, WPT, PRED><<<grid, kChorThreads + 32, chor_smem_bytes(), stream>>>(
+        db_map, qt_map, r, W, B, qtw, out, status);
     return cudaGetLastError();
+}
+
+template <int QB, int QG, int WPT>
+static cudaError_t launch_qbg(bool pred, const CUtensorMap &db_map, const CUtensorMap &qt_map, uint64_t r,
+                              uint32_t W, uint32_t B, uint32_t qtw, uint32_t *out, int num_sms, int *status,
+                              cudaStream_t stream) {
+    return pred ? launch_qbg1<QB, QG, WPT, true>(db_map, qt_map, r, W, B, qtw, out, num_sms, status, stream)
+                : launch_qbg1<QB, QG, WPT, false>(db_map, qt_map, r, W, B, qtw, out, num_sms, status, stream);
 }
 
 cudaError_t launch_chor_answer(const CUtensorMap &db_map, const CUtensorMap &qt_map, uint64_t r, uint32_t W,
                                uint32_t B, uint32_t qtw, uint32_t *out, int num_sms, int *status,
-                               cudaStream_t stream) {
-    int qb = 0, qg = 0;
-    if (!chor_pick(B, &qb, &qg)) return cudaErrorInvalidValue;
+                               cudaStream_t stream, int form) {
+    int qb = 0, qg = 0, wpt = 0;
+    if (!chor_pick(B, form, &qb, &qg, &wpt)) return cudaErrorInvalidValue;
+    const bool pred = (form & 1) != 0;
+#define QPADL_CHOR_L(QB_, QG_, WPT_) \
+    launch_qbg<QB_, QG_, WPT_>(pred, db_map, qt_map, r, W, B, qtw, out, num_sms, status, stream)
+    if (wpt == 8) {
+        if (qg == 1) {
+            switch (qb) {
+                case 1: return QPADL_CHOR_L(1, 1, 8);
+                case 2: return QPADL_CHOR_L(2, 1, 8);
+                case 4: return QPADL_CHOR_L(4, 1, 8);
+                case 8: return QPADL_CHOR_L(8, 1, 8);
+                default: return QPADL_CHOR_L(16, 1, 8);
+            }
+        }
+        switch (qg) {
+            case 2: return QPADL_CHOR_L(16, 2, 8);
+            case 4: return QPADL_CHOR_L(16, 4, 8);
+            case 8: return QPADL_CHOR_L(16, 8, 8);
+            default: return QPADL_CHOR_L(16, 16, 8);
+        }
+    }
     if (qg == 1) {
         switch (qb) {
-            case 1: return launch_qbg<1, 1>(db_map, qt_map, r, W, B, qtw, out, num_sms, status, stream);
-            case 2: return launch_qbg<2, 1>(db_map, qt_map, r, W, B, qtw, out, num_sms, status, stream);
-            case 4: return launch_qbg<4, 1>(db_map, qt_map, r, W, B, qtw, out, num_sms, status, stream);
-            case 8: return launch_qbg<8, 1>(db_map, qt_map, r, W, B, qtw, out, num_sms, status, stream);
-            case 16: return launch_qbg<16, 1>(db_map, qt_map, r, W, B, qtw, out, num_sms, status, stream);
-            default: return launch_qbg<32, 1>(db_map, qt_map, r, W, B, qtw, out, num_sms, status, stream);
+            case 1: return QPADL_CHOR_L(1, 1, 4);
+            case 2: return QPADL_CHOR_L(2, 1, 4);
+            case 4: return QPADL_CHOR_L(4, 1, 4);
+            case 8: return QPADL_CHOR_L(8, 1, 4);
+            case 16: return QPADL_CHOR_L(16, 1, 4);
+            default: return QPADL_CHOR_L(32, 1, 4);
         }
     }
     switch (qg) {
-        case 2: return launch_qbg<32, 2>(db_map, qt_map, r, W, B, qtw, out, num_sms, status, stream);
-        case 4: return launch_qbg<32, 4>(db_map, qt_map, r, W, B, qtw, out, num_sms, status, stream);
-        default: return launch_qbg<32, 8>(db_map, qt_map, r, W, B, qtw, out, num_sms, status, stream);
+        case 2: return QPADL_CHOR_L(32, 2, 4);
+        case 4: return QPADL_CHOR_L(32, 4, 4);
+        default: return QPADL_CHOR_L(32, 8, 4);
     }
+#undef QPADL_CHOR_L
 }
 
 cudaError_t launch_chor_words(const uint32_t *Q, uint64_t qw, uint32_t B, uint64_t r, uint32_t *QS, int num_sms,

@@ -11,8 +11,9 @@ constexpr uint32_t kChorMaxBatch = 256;   // queries per launch; larger batches 
 cudaError_t prepare_chor_kernels();
 
 // Tile width (words), band height (rows), TMA box width (words) and QT words
-// per row that a launch for B queries uses; false if B is 0 or > kChorMaxBatch.
-bool chor_launch_shape(uint32_t B, uint32_t *tw, uint32_t *rb, uint32_t *box_words, uint32_t *qtw);
+// per row that a launch for B queries in scan form `form` (0..3: bit 1 = 8 words
+// per thread, bit 0 = predicated XOR) uses; false if B is 0 or > kChorMaxBatch.
+bool chor_launch_shape(uint32_t B, int form, uint32_t *tw, uint32_t *rb, uint32_t *box_words, uint32_t *qtw);
 
 // Q (B x qw words) -> QT (r x qtw words): bit j of QT[i][g] = bit i of query 32 g + j.
 cudaError_t launch_chor_transpose(const uint32_t *Q, uint64_t qw, uint32_t B, uint64_t r, uint32_t qtw, uint32_t *QT,
@@ -22,7 +23,7 @@ cudaError_t launch_chor_transpose(const uint32_t *Q, uint64_t qw, uint32_t B, ui
 // the database {W, r} words with box {box_words, rb}, qt_map QT {qtw, r} with box {qtw, rb}.
 cudaError_t launch_chor_answer(const CUtensorMap &db_map, const CUtensorMap &qt_map, uint64_t r, uint32_t W,
                                uint32_t B, uint32_t qtw, uint32_t *out, int num_sms, int *status,
-                               cudaStream_t stream);
+                               cudaStream_t stream, int form);
 
 // Four-Russians path (large batches): box shape of its database map.
 constexpr uint32_t kChorM4TileWords = 64;

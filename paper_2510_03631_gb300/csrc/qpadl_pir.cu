@@ -98,6 +98,7 @@ struct qpadl_chor {
     int *d_status = nullptr;
     uint64_t owned_bytes = 0;
     uint32_t m4rm_min_batch = 48;    // batches from this size take the four-Russians kernel
+    int scan_form = -1;              // QPADL_CHOR_OPT_SCAN_FORM (-1: by batch size)
 };
 
 namespace {
@@ -1235,7 +1236,10 @@ int qpadl_chor_answer_batch(qpadl_chor *h, const uint32_t *Q_dev, uint32_t B, ui
             continue;
         }
         uint32_t tw = 0, rb = 0, boxw = 0, qtw = 0;
-        if (!chor_launch_shape(Bc, &tw, &rb, &boxw, &qtw)) return QPADL_EINVAL;
+        // by batch size (measured on the 1 GiB database): the mask form up to 8 queries, the
+        // predicated XOR with 4 words per thread up to 16, with 8 words per thread above
+        const int form = h->scan_form >= 0 ? h->scan_form : (Bc <= 8 ? 0 : (Bc <= 16 ? 1 : 3));
+        if (!chor_launch_shape(Bc, form, &tw, &rb, &boxw, &qtw)) return QPADL_EINVAL;
         QPADL_CU(launch_chor_transpose(Q_dev + (uint64_t)b0 * h->qw, h->qw, Bc, h->rows, qtw, h->qt, h->num_sms, s));
         CUtensorMap db_map, qt_map;
         if (!encode_2d(&db_map, CU_TENSOR_MAP_DATA_TYPE_UINT32, h->db, W, h->rows, W * 4, boxw, rb,
@@ -1244,7 +1248,7 @@ int qpadl_chor_answer_batch(qpadl_chor *h, const uint32_t *Q_dev, uint32_t B, ui
                        CU_TENSOR_MAP_SWIZZLE_NONE))
             return QPADL_ECUDA;
         QPADL_CU(launch_chor_answer(db_map, qt_map, h->rows, static_cast<uint32_t>(W), Bc, qtw,
-                                    out_dev + (uint64_t)b0 * W, h->num_sms, h->d_status, s));
+                                    out_dev + (uint64_t)b0 * W, h->num_sms, h->d_status, s, form));
     }
     return QPADL_OK;
 }
@@ -1256,6 +1260,10 @@ int qpadl_chor_set_option(qpadl_chor *h, int option, int64_t value) {
             if (value < 1 || value > (int64_t)kChorMaxBatch + 1) return QPADL_EINVAL;
             h->m4rm_min_batch = static_cast<uint32_t>(value);
             return QPADL_OK;
+        case QPADL_CHOR_OPT_SCAN_FORM:
+            if (value < -1 || value > 3) return QPADL_EINVAL;
+            h->scan_form = static_cast<int>(value);
+            return QPADL_OK;
         default: return QPADL_EINVAL;
     }
 }
@@ -1264,6 +1272,7 @@ int qpadl_chor_get_option(qpadl_chor *h, int option, int64_t *value) {
     if (!h || !value) return QPADL_EINVAL;
     switch (option) {
         case QPADL_CHOR_OPT_M4RM_MIN_BATCH: *value = h->m4rm_min_batch; return QPADL_OK;
+        case QPADL_CHOR_OPT_SCAN_FORM: *value = h->scan_form; return QPADL_OK;
         default: return QPADL_EINVAL;
     }
 }

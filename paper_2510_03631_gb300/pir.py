@@ -556,6 +556,7 @@ def qpadl_chor_answer_batch(h: ChorDatabase, Q: torch.Tensor, out: torch.Tensor,
 
 
 QPADL_CHOR_OPT_M4RM_MIN_BATCH = 1
+QPADL_CHOR_OPT_SCAN_FORM = 2
 
 
 def qpadl_chor_set_option(h: ChorDatabase, option: int, value: int):

@@ -45,6 +45,8 @@ def _chor_case(a):
     h = pir.qpadl_chor_setup(rows, bits, torch.from_numpy(DB_np.view(np.int32).reshape(-1)).cuda())
     if a.m4rm >= 0:
         pir.qpadl_chor_set_option(h, pir.QPADL_CHOR_OPT_M4RM_MIN_BATCH, a.m4rm)
+    if a.form >= 0:
+        pir.qpadl_chor_set_option(h, pir.QPADL_CHOR_OPT_SCAN_FORM, a.form)
     Q = torch.from_numpy(Q_np.view(np.int32).reshape(-1)).cuda()
     out = torch.empty(B * W, dtype=torch.int32, device="cuda")
     fn = lambda: pir.qpadl_chor_answer_batch(h, Q, out)
@@ -153,6 +155,7 @@ def main():
     ap.add_argument("--cols", type=int, default=32768)
     ap.add_argument("--bits", type=int, default=262144, help="chor: bits per record")
     ap.add_argument("--m4rm", type=int, default=-1, help="chor: smallest batch on the four-Russians kernel")
+    ap.add_argument("--form", type=int, default=-1, help="chor: inner-loop form of the masked-XOR scan (0..3)")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--reps", type=int, default=3)

@@ -46,8 +46,12 @@ def test_chor_matches_oracle(cuda, rows, bits, B, m4rm_min):
     h = pir.qpadl_chor_setup(rows, bits, _dev(DB))
     pir.qpadl_chor_set_option(h, pir.QPADL_CHOR_OPT_M4RM_MIN_BATCH, m4rm_min)
     assert pir.qpadl_chor_get_option(h, pir.QPADL_CHOR_OPT_M4RM_MIN_BATCH) == m4rm_min
-    got = _answer(h, Q)
-    assert np.array_equal(got, oracle.chor_answer(DB, rows, Q, threads=oracle.max_threads()))
+    exp = oracle.chor_answer(DB, rows, Q, threads=oracle.max_threads())
+    # every inner-loop form of the masked-XOR scan (4 or 8 words per thread, mask or predicated)
+    for form in ((0, 1, 2, 3) if m4rm_min > 256 else (0,)):
+        pir.qpadl_chor_set_option(h, pir.QPADL_CHOR_OPT_SCAN_FORM, form)
+        assert pir.qpadl_chor_get_option(h, pir.QPADL_CHOR_OPT_SCAN_FORM) == form
+        assert np.array_equal(_answer(h, Q), exp), f"form {form}"
     h.close()
 
 
