@@ -88,13 +88,53 @@ __device__ __forceinline__ bool drain_wait_p(uint64_t *bar, uint32_t parity) {
     return true;
 }
 
+// One piece of a cluster's work: chunks [c0, c1) of pair tile t.  Tiles below dp_tiles are dealt
+// whole, round-robin (tile c, c + nclusters, ...), so the clusters on the n_tiles tiles of one row
+// tile run together and share its rows through L2.  The remaining tiles (whole row tiles) are
+// split by chunks (stream-K), so the last wave ends evenly: the first tail_parts * n_tiles
+// clusters form n_tiles groups, group n takes vector tile n of every tail row tile, and cluster p
+// of each group takes the same contiguous share of the (row tile, chunk) units, so the n_tiles
+// clusters that read one row tile's rows still read them together.
+struct PairPiece {
+    uint32_t t, c0, c1;
+};
+struct PairPieceIter {
+    uint32_t t, step, n, u, u_end;
+    __device__ __forceinline__ PairPieceIter(uint32_t tiles, uint32_t dp_tiles, uint32_t n_tiles, uint32_t nchunks,
+                                             uint32_t tail_parts, uint32_t part, uint32_t nparts) {
+        t = part;
+        step = nparts;
+        n = part % n_tiles;
+        u = u_end = 0;
+        const uint32_t p = part / n_tiles;
+        if (p < tail_parts) {
+            const uint64_t U = (uint64_t)((tiles - dp_tiles) / n_tiles) * nchunks;
+            u = static_cast<uint32_t>((uint64_t)p * U / tail_parts);
+            u_end = static_cast<uint32_t>((uint64_t)(p + 1) * U / tail_parts);
+        }
+    }
+    __device__ __forceinline__ bool next(PairPiece &pc, uint32_t dp_tiles, uint32_t n_tiles, uint32_t nchunks) {
+        if (t < dp_tiles) {
+            pc = PairPiece{t, 0u, nchunks};
+            t += step;
+            return true;
+        }
+        if (u >= u_end) return false;
+        const uint32_t c0 = u % nchunks;
+        const uint32_t c1 = nchunks - c0 < u_end - u ? nchunks : c0 + (u_end - u);
+        pc = PairPiece{dp_tiles + (u / nchunks) * n_tiles + n, c0, c1};
+        u += c1 - c0;
+        return true;
+    }
+};
+
 }  // namespace
 
 template <int BN, class Epi, bool PLANED>
 __global__ void __launch_bounds__(kPThreads, 1)
     limb_gemm_pair_kernel(const __grid_constant__ CUtensorMap a_map, const __grid_constant__ PairBMaps bm, Epi epi,
                           uint32_t M, uint32_t NV, uint32_t KB, uint32_t ckb, uint32_t plane_chunks,
-                          int *__restrict__ status) {
+                          uint32_t dp_tiles_arg, uint32_t tail_parts, int *__restrict__ status) {
     using Cfg = PairCfg<BN>;
     static_assert(Epi::kLimbs == 4, "four byte limbs per vector");
     static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
@@ -148,6 +188,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
     const uint32_t tiles = m_tiles * n_tiles;
     const uint32_t cluster = blockIdx.x >> 1, nclusters = gridDim.x >> 1;   // clusters are CTAs 2c, 2c + 1
     const uint32_t nchunks = (KB + ckb - 1) / ckb;
+    // only a plain store takes split tiles (their pieces add into a zeroed output)
+    constexpr bool kSplit = std::is_same<Epi, StoreEpi>::value;
+    const uint32_t dp_tiles = kSplit && dp_tiles_arg < tiles ? dp_tiles_arg : tiles;
+    const uint32_t tparts = dp_tiles < tiles ? tail_parts : 0u;
     bool failed = false;
     auto fail_both = [&]() {
         failed = true;
@@ -168,7 +212,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
             }
             const uint32_t kpp = PLANED ? ckb * plane_chunks : KB;   // k-steps per limb plane
             uint32_t it = 0, st = 0, ph = 0;
-            for (uint32_t t = cluster; t < tiles && !failed; t += nclusters) {
+            PairPieceIter pit(tiles, dp_tiles, n_tiles, nchunks, tparts, cluster, nclusters);
+            PairPiece pc;
+            while (!failed && pit.next(pc, dp_tiles, n_tiles, nchunks)) {
+                const uint32_t t = pc.t;
+                const uint32_t kb0 = pc.c0 * ckb, kb1 = pc.c1 * ckb < KB ? pc.c1 * ckb : KB;
                 const int32_t m0 = static_cast<int32_t>((t / n_tiles) * 2 * kPM + rank * kPM);
                 const int32_t r0 = static_cast<int32_t>((t % n_tiles) * BN + rank * (BN / 2));
                 if (mat) {
@@ -176,8 +224,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
                     const uint32_t nv = v0 < NV ? (NV - v0 < (uint32_t)QPT ? NV - v0 : (uint32_t)QPT) : 0u;
                     if (static_cast<uint32_t>(m0) + kPM <= M) epi.prefetch(static_cast<uint64_t>(m0), v0, nv);
                 }
-                uint32_t u = 0, kin = 0;   // limb plane of k-step kb, and kb's place in it
-                for (uint32_t kb = 0; kb < KB; ++kb, ++it) {
+                uint32_t u = 0, kin = 0;   // limb plane of k-step kb, and kb's place in it (planed: whole tiles)
+                for (uint32_t kb = kb0; kb < kb1; ++kb, ++it) {
                     if (!mbar_wait(&empty[st], ph ^ 1u, abort)) {
                         fail_both();
                         break;
@@ -216,10 +264,13 @@ __global__ void __launch_bounds__(kPThreads, 1)
             uint32_t ci = 0, st = 0, ph = 0;
             const uint32_t kpp = PLANED ? ckb * plane_chunks : KB;
             bool issued = false;
-            for (uint32_t t = cluster; t < tiles && !failed; t += nclusters) {
+            PairPieceIter pit(tiles, dp_tiles, n_tiles, nchunks, tparts, cluster, nclusters);
+            PairPiece pc;
+            while (!failed && pit.next(pc, dp_tiles, n_tiles, nchunks)) {
+                const uint32_t kb0 = pc.c0 * ckb, kb1 = pc.c1 * ckb < KB ? pc.c1 * ckb : KB;
                 uint32_t d_tmem = tmem_base;
                 uint32_t u = 0, kin = 0, kc = 0;   // limb plane, place in the plane, place in the chunk
-                for (uint32_t kb = 0; kb < KB; ++kb) {
+                for (uint32_t kb = kb0; kb < kb1; ++kb) {
                     if (kc == 0) {
                         const uint32_t buf = ci & 1u;
                         const bool ok = mbar_wait(&acc_empty[buf], ((ci >> 1) & 1u) ^ 1u, abort);
@@ -240,7 +291,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                     const uint64_t adesc = umma_desc_sw128(sa);
                     const uint64_t bdesc = umma_desc_sw128(sa + Cfg::kABytes);
                     const uint32_t idesc = umma_idesc_f16(2 * kPM, PLANED ? (4u - u) * (BN / 4) : BN);
-                    const bool last_of_chunk = kc == ckb - 1 || kb == KB - 1;
+                    const bool last_of_chunk = kc == ckb - 1 || kb == kb1 - 1;
                     if (elect_one()) {
 #pragma unroll
                         for (int k = 0; k < kPK / 16; ++k)
@@ -275,7 +326,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
         const uint32_t quarter = static_cast<uint32_t>(warp & 3);
         const uint32_t lane_addr = (quarter * 32u) << 16;
         uint32_t ci = 0;
-        for (uint32_t t = cluster; t < tiles && !failed; t += nclusters) {
+        PairPieceIter pit(tiles, dp_tiles, n_tiles, nchunks, tparts, cluster, nclusters);
+        PairPiece pc;
+        while (!failed && pit.next(pc, dp_tiles, n_tiles, nchunks)) {
+            const uint32_t t = pc.t;
             const uint32_t row = (t / n_tiles) * 2 * kPM + rank * kPM + quarter * 32u + static_cast<uint32_t>(lane);
             const uint32_t v0 = (t % n_tiles) * QPT;
             uint32_t run[QPT];
@@ -288,7 +342,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
 #pragma unroll
                 for (int q = 0; q < QPT; ++q) early[q] = (row < M && v0 + q < NV) ? epi.pre(row, v0 + q) : 0u;
             }
-            for (uint32_t c = 0; c < nchunks; ++c, ++ci) {
+            for (uint32_t c = pc.c0; c < pc.c1; ++c, ++ci) {
                 const uint32_t buf = ci & 1u;
                 const bool ok = mbar_wait(&acc_full[buf], (ci >> 1) & 1u, abort);
                 if (__any_sync(0xffffffffu, !ok)) {   // the TMEM loads below are warp-collective
@@ -353,6 +407,15 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 if (lane == 0) mbar_arrive_cluster(acc_empty_c + 8u * buf);
             }
             if (failed) break;
+            if constexpr (kSplit) {
+                if (row < M && !(pc.c0 == 0 && pc.c1 == nchunks)) {
+                    // part of a split tile: exact, since addition mod 2^32 commutes
+#pragma unroll
+                    for (int q = 0; q < QPT; ++q)
+                        if (v0 + q < NV) epi.add(row, v0 + q, run[q]);
+                    continue;
+                }
+            }
             if (row < M) {
                 if constexpr (PLANED) {
 #pragma unroll
@@ -468,6 +531,32 @@ constexpr uint32_t pair_chunk_kb() {
     return std::is_same<Epi, StoreEpi>::value ? 8u : 16u;
 }
 
+// Schedule of a plain-store launch over `tiles` pair tiles (n_tiles per row tile, nchunks exact
+// chunks each) on `pairs` resident clusters.  Measured in tile times, whole tiles take
+// ceil(tiles / pairs); a split keeps dp whole tiles (all waves but the last full one, rounded down
+// to whole row tiles) and cuts the rest over tail_parts * n_tiles clusters (the grouping of
+// PairPieceIter).  The split is taken when it saves at least 8% of that count, and never when
+// every cluster is busy on a one-tile-wide batch: that launch reads the fp16 copy of the database
+// at the HBM rate whatever the balance, and split pieces only add their atomics.  Returns false
+// when no tile is split; otherwise the cluster count, dp and tail_parts.
+static bool pair_split_schedule(uint64_t tiles, uint64_t n_tiles, uint32_t nchunks, uint64_t pairs,
+                                uint64_t *clusters, uint32_t *dp_tiles, uint32_t *tail_parts) {
+    if (pairs == 0 || nchunks < 2 || tiles % pairs == 0 || n_tiles > pairs) return false;
+    if (tiles > pairs && n_tiles == 1) return false;
+    uint64_t dp = 0;
+    if (tiles > pairs) dp = ((tiles / pairs - 1) * pairs) / n_tiles * n_tiles;
+    const uint64_t tail_units = (tiles - dp) / n_tiles * nchunks;
+    uint64_t P = pairs / n_tiles;
+    if (P > tail_units) P = tail_units;
+    const double whole = static_cast<double>((tiles + pairs - 1) / pairs);
+    const double split = static_cast<double>(dp) / pairs + static_cast<double>(tiles - dp) / (P * n_tiles);
+    if (split > 0.92 * whole) return false;
+    *clusters = dp > 0 ? pairs : P * n_tiles;
+    *dp_tiles = static_cast<uint32_t>(dp);
+    *tail_parts = static_cast<uint32_t>(P);
+    return true;
+}
+
 template <int BN, class Epi, bool PLANED>
 static cudaError_t launch_pair_t(const CUtensorMap &a_map, const PairBMaps &bm, const Epi &epi, uint32_t M,
                                  uint32_t NV, uint32_t KB, uint32_t ckb, uint32_t plane_chunks, int num_sms,
@@ -476,12 +565,27 @@ static cudaError_t launch_pair_t(const CUtensorMap &a_map, const PairBMaps &bm, 
     const uint64_t n_tiles = (NV + PairCfg<BN>::kQPT - 1) / PairCfg<BN>::kQPT;
     const uint64_t tiles = m_tiles * n_tiles;
     const uint64_t pairs = static_cast<uint64_t>(resident_pairs<BN, Epi, PLANED>(num_sms));
-    const uint64_t clusters = tiles < pairs ? tiles : pairs;
+    uint64_t clusters = tiles < pairs ? tiles : pairs;
+    uint32_t dp = 0xffffffffu, tail_parts = 0;
+    if constexpr (std::is_same<Epi, StoreEpi>::value) {
+        // split tiles add into the output, so it is zeroed first; only a dense output (every
+        // element of the M x NV block, in either order) can be zeroed in one piece
+        const bool dense = (epi.ld_m == 1 && epi.ld_b == M) || (epi.ld_b == 1 && epi.ld_m == NV);
+        uint64_t c2 = clusters;
+        uint32_t dp2 = 0, tp2 = 0;
+        if (dense && pair_split_schedule(tiles, n_tiles, (KB + ckb - 1) / ckb, pairs, &c2, &dp2, &tp2)) {
+            const cudaError_t e = cudaMemsetAsync(epi.out, 0, 4ull * M * NV, stream);
+            if (e != cudaSuccess) return e;
+            clusters = c2;
+            dp = dp2;
+            tail_parts = tp2;
+        }
+    }
     if (clusters == 0) return cudaSuccess;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = pair_config<BN>(static_cast<unsigned>(clusters), stream, attr);
     return cudaLaunchKernelEx(&cfg, limb_gemm_pair_kernel<BN, Epi, PLANED>, a_map, bm, epi, M, NV, KB, ckb,
-                              plane_chunks, status);
+                              plane_chunks, dp, tail_parts, status);
 }
 
 template <class Epi>
