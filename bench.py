@@ -190,7 +190,7 @@ def cpu_oracle_blocks(D, A_np, H_np, threads: int):
     out = {"cores": threads, "kind": "oracle"}
     # the batched Response, B queries (linear in the answered rows)
     sweep = {}
-    for B in (1, 8, 32, 128, 256, 1024):
+    for B in (1, 8, 16, 32, 64, 128, 256, 1024):
         Q = inputs.uniform_u32(B * C, seed=900 + B, tag=inputs.TAG_MISC).reshape(B, C)
         r0 = max(2 * threads, 4096 // B)
         full_s, r = _time_rows(lambda r: oracle.answer_batch(np.ascontiguousarray(D[:r]), Q, threads=threads), R, r0)
@@ -802,7 +802,7 @@ def run_ours(args):
     one_qps = 1e3 / resp_ms_avg
     sweep = {}
     if extras:
-        for B in (1, 8, 32, 128, 256, 1024):
+        for B in (1, 8, 16, 32, 64, 128, 256, 1024):
             QB = torch.randint(-2**31, 2**31 - 1, (B * C,), dtype=torch.int32, device="cuda")
             AB = torch.empty(B * R, dtype=torch.int32, device="cuda")
             # back-to-back launches within a graph, as for the one-at-a-time rate above

@@ -533,7 +533,16 @@ __device__ __forceinline__ void balanced_limbs(uint32_t x, float (&c)[4]) {
 // X (uint32, NV x C, vector v in row v) -> limbs (fp16, 4*NV x pitch),
 // limb k of vector v in row 4v + k.  One block per vector at a time.
 __global__ void vec_limbs_kernel(const uint32_t *__restrict__ X, uint64_t x_ld, uint32_t NV, uint64_t C,
-                                 __half *__restrict__ L, uint64_t pitch) {
+                                 __half *__restrict__ L, uint64_t pitch, uint32_t *__restrict__ Z, uint64_t z_words) {
+    // a GEMM launched as this kernel's programmatic dependent may start now: it waits for this
+    // grid's completion (griddepcontrol.wait) before it reads the limbs or writes its output
+    griddep_launch_dependents();
+    if (Z != nullptr) {   // zero the dependent GEMM's output block (its split tiles add into it)
+        const uint64_t nthreads = (uint64_t)gridDim.x * gridDim.y * blockDim.x;
+        for (uint64_t i = ((uint64_t)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x; i < z_words;
+             i += nthreads)
+            Z[i] = 0u;
+    }
     // block (x, y): vector y, columns [2048 x, 2048 x + 2048), 8 consecutive columns per thread,
     // so even a handful of vectors spreads over the whole GPU
     constexpr uint32_t kCols = 8;
@@ -840,14 +849,17 @@ cudaError_t launch_db_to_f16(const uint8_t *D, uint64_t R, uint64_t C, __half *D
 }
 
 cudaError_t launch_vec_limbs(const uint32_t *X, uint64_t x_ld, uint32_t NV, uint64_t C, __half *L, uint64_t pitch,
-                             int num_sms, cudaStream_t stream) {
+                             int num_sms, cudaStream_t stream, uint32_t *zero, uint64_t zero_words) {
     (void)num_sms;
-    if (NV == 0 || C == 0) return cudaSuccess;
+    if (NV == 0 || C == 0) {
+        if (zero != nullptr && zero_words > 0) return cudaMemsetAsync(zero, 0, 4ull * zero_words, stream);
+        return cudaSuccess;
+    }
     for (uint32_t v0 = 0; v0 < NV; v0 += 65535) {   // grid.y limit
         const uint32_t nv = NV - v0 < 65535 ? NV - v0 : 65535;
         const dim3 grid(static_cast<unsigned>((C + 2047) / 2048), nv);
         vec_limbs_kernel<<<grid, 256, 0, stream>>>(X + (uint64_t)v0 * x_ld, x_ld, nv, C, L + 4ull * v0 * pitch,
-                                                    pitch);
+                                                    pitch, v0 == 0 ? zero : nullptr, v0 == 0 ? zero_words : 0);
     }
     return cudaGetLastError();
 }

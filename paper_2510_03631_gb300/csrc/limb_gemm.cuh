@@ -50,8 +50,11 @@ cudaError_t launch_mod_p_signed(uint32_t *x, uint64_t n, uint32_t p, int num_sms
 
 cudaError_t launch_db_to_f16(const uint8_t *D, uint64_t R, uint64_t C, __half *D16, uint64_t pitch, int num_sms,
                              cudaStream_t stream);
+// Limbs of NV vectors (vector v at X + v * x_ld) into L (limb k of vector v in row 4 v + k).
+// When `zero` is given, the same launch also zeroes zero_words words there (the output block of a
+// uint8-digit GEMM launched right after it as its programmatic dependent).
 cudaError_t launch_vec_limbs(const uint32_t *X, uint64_t x_ld, uint32_t NV, uint64_t C, __half *L, uint64_t pitch,
-                             int num_sms, cudaStream_t stream);
+                             int num_sms, cudaStream_t stream, uint32_t *zero = nullptr, uint64_t zero_words = 0);
 cudaError_t launch_mat_col_limbs(const uint32_t *A, uint64_t C, uint32_t n, __half *L, uint64_t pitch,
                                  cudaStream_t stream);
 cudaError_t launch_mat_row_limbs(const uint32_t *X, uint64_t rows, uint32_t n, __half *L, uint64_t pitch, int num_sms,

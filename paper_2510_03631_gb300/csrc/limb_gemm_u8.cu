@@ -11,7 +11,8 @@
 // tiles (128 or 256 digits per row) into shared memory from a blocked copy of
 // the digits (128 x 128 tiles stored contiguously, so each stage is one
 // contiguous 16-32 KB read), converter warps turn each row
-// into fp16 (byte-permute next to 0x64 gives 1024 + d exactly, minus 1024)
+// into fp16 (one byte permute per two digits: the byte under a zero exponent
+// is the subnormal d * 2^-24, exact; the epilogue scales sums back by 2^24)
 // and store it into tensor memory, and the MMA reads A from tensor memory
 // (tcgen05.mma with A in TMEM).  Half the HBM traffic of the fp16 copy, and
 // shared memory carries only the digit tile (128-byte swizzled, so the row-
@@ -35,9 +36,8 @@
 // converters and writes its own 128 rows of fp16 digits into its own TMEM A
 // slots; each loads half of the limb rows.  The leader CTA issues the pair
 // MMAs (M = 256, A from both CTAs' TMEM, B from both CTAs' shared memory):
-// one instruction drives both SMs' tensor cores, which halves the MMA issue
-// rate each stage needs (a 16-deep MMA costs about as much to issue as it
-// takes to run at these widths).  Both CTAs' converters arrive on the
+// one instruction drives both SMs' tensor cores, and each SM loads only half
+// of every limb tile.  Both CTAs' converters arrive on the
 // leader's `aready`, both CTAs' limb copies complete on the leader's `lfull`,
 // both epilogues arrive on the leader's `acc_empty`; the leader's MMA commits
 // to `afree`, `lfree` and `acc_full` of both CTAs.  A cluster barrier keeps
@@ -66,6 +66,10 @@ constexpr int kThreads = 480;
 constexpr int kConvGroups = 2;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kPrefetch = 8;   // stages of digit tiles pulled into L2 ahead of their loads
+// The A operand holds each digit d as the fp16 subnormal d * 2^-24, so an accumulator holds
+// 2^-24 times an exact integer sum (|sum| <= 2^24: the fp32 significand keeps it exact); the
+// epilogue scales it back by 2^24 (exact) before rounding to an integer.
+constexpr float kUnscale = 16777216.0f;
 
 // BN: limb columns per tile; KS: digits per row per pipeline stage (a
 // multiple of 128: each digit tile is 128 rows x 128 bytes, 128-byte swizzle).
@@ -80,8 +84,10 @@ struct U8Cfg {
     // Digit and A-slot counts are even: converter group g owns the stages with it % 2 == g and
     // so every phase of the slots with index % 2 == g (a parity wait never falls two phases behind).
     static constexpr int kSA = (((kTmemCols - 2 * BN) / kSlotCols) / 2) * 2;
-    static constexpr int kSD = KS == 128 ? (BN == 128 ? 6 : 8) : (BN == 128 ? 2 : 4);
-    static constexpr int kSLfit = (192 * 1024 - kSD * kDigBytes) / kLimbBytes;
+    // pair tiles halve a CTA's limb slots, which leaves room for a deeper digit ring
+    static constexpr int kSD = KS == 128 ? (PAIR ? (BN == 128 ? 8 : 10) : (BN == 128 ? 6 : 8)) : (BN == 128 ? 2 : 4);
+    static constexpr int kRingBytes = PAIR ? 224 * 1024 : 192 * 1024;
+    static constexpr int kSLfit = (kRingBytes - kSD * kDigBytes) / kLimbBytes;
     static constexpr int kSL = kSLfit < 8 ? kSLfit : 8;
     static constexpr uint32_t kAColBase = 2 * BN;                   // A slots after the accumulators
     static constexpr int kChunkStages = 512 / KS;                   // stages per exact 512-deep K-chunk
@@ -293,6 +299,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 14) {
         if (lane == 0) {
             // ---------------- limb producer
+            griddep_wait();   // the limbs may come from the kernel this one overlaps (programmatic launch)
             uint32_t it = 0;
             Seg tr;
             SegIter sit(args, part, nparts);
@@ -396,6 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp < 6) {
         // ---------------- epilogue (warps 2..5)
+        griddep_wait();   // the output may be zeroed by the kernel this one overlaps
         const uint32_t quarter = static_cast<uint32_t>(warp & 3);
         const uint32_t lane_addr = (quarter * 32u) << 16;
         uint32_t ci = 0;
@@ -423,14 +431,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if constexpr (LPV == 1) {
 #pragma unroll
                         for (int q = 0; q < 16; ++q)
-                            run[16 * j + q] += static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[q])));
+                            run[16 * j + q] += static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[q]) * kUnscale));
                     } else {
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            const uint32_t s0 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 0])));
-                            const uint32_t s1 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 1])));
-                            const uint32_t s2 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 2])));
-                            const uint32_t s3 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 3])));
+                            const uint32_t s0 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 0]) * kUnscale));
+                            const uint32_t s1 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 1]) * kUnscale));
+                            const uint32_t s2 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 2]) * kUnscale));
+                            const uint32_t s3 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[4 * q + 3]) * kUnscale));
                             run[4 * j + q] += s0 + (s1 << 8) + (s2 << 16) + (s3 << 24);
                         }
                     }
@@ -464,7 +472,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t group = static_cast<uint32_t>(warp - 6) / 4;   // owns the stages it % 2 == group
         const uint32_t row = quarter * 32u + static_cast<uint32_t>(lane);
         const uint32_t lane_addr = (quarter * 32u) << 16;
-        const __half2 k1024 = __floats2half2_rn(1024.0f, 1024.0f);
         uint32_t it = 0;
         Seg sg;
         SegIter sit(args, part, nparts);
@@ -493,13 +500,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         uint32_t o[8];
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            // [d0, 0x64, d1, 0x64] is the fp16 pair (1024 + d0, 1024 + d1)
-                            uint32_t lo = __byte_perm(x[q], 0x64646464u, 0x4140);
-                            uint32_t hi = __byte_perm(x[q], 0x64646464u, 0x4342);
-                            __half2 hl = __hsub2(*reinterpret_cast<__half2 *>(&lo), k1024);
-                            __half2 hh = __hsub2(*reinterpret_cast<__half2 *>(&hi), k1024);
-                            o[2 * q] = *reinterpret_cast<uint32_t *>(&hl);
-                            o[2 * q + 1] = *reinterpret_cast<uint32_t *>(&hh);
+                            // [d0, 0, d1, 0]: a byte under a zero exponent is the fp16 subnormal
+                            // d * 2^-24, exact, so each pair of digits is one byte permute
+                            o[2 * q] = __byte_perm(x[q], 0u, 0x4140);
+                            o[2 * q + 1] = __byte_perm(x[q], 0u, 0x4342);
                         }
                         tmem_st8(a_tmem + 64u * b + 8u * j, o);   // warp-uniform TMEM address
                     }
@@ -614,6 +618,14 @@ static cudaLaunchConfig_t u8_pair_config(unsigned clusters, cudaStream_t stream,
     return cfg;
 }
 
+// Adds the programmatic-dependent-launch attribute to a launch configuration (attr has room).
+static void add_pdl(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *attr) {
+    attr[cfg.numAttrs].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[cfg.numAttrs].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    ++cfg.numAttrs;
+}
+
 // CTA pairs resident at once, per device (a GPC with an odd number of free SMs leaves one idle).
 template <int BN, int KS, int LPV>
 static int u8_resident_pairs(int num_sms) {
@@ -654,41 +666,47 @@ static void u8_schedule(GroupedGemmArgs &a, uint32_t tile_rows, uint32_t parts) 
 
 template <int BN, int KS, int LPV = 4>
 static cudaError_t launch_u8(const GroupedGemmArgs &args_in, int num_sms, bool pair, int *status,
-                             cudaStream_t stream) {
+                             cudaStream_t stream, bool pdl) {
     if (args_in.total_units == 0) return cudaSuccess;
     GroupedGemmArgs args = args_in;
+    cudaLaunchAttribute attr[2];
     if (pair) {
         const uint32_t pairs = static_cast<uint32_t>(u8_resident_pairs<BN, KS, LPV>(num_sms));
         const unsigned clusters = args.total_units < pairs ? args.total_units : pairs;
         u8_schedule(args, 2 * kBM, clusters);
-        cudaLaunchAttribute attr[1];
         cudaLaunchConfig_t cfg = u8_pair_config<BN, KS, LPV>(clusters, stream, attr);
+        if (pdl) add_pdl(cfg, attr);
         return cudaLaunchKernelEx(&cfg, limb_gemm_u8_kernel<BN, KS, LPV, true>, args, status);
     }
     const int grid = static_cast<int>(args.total_units < (uint32_t)num_sms ? args.total_units : (uint32_t)num_sms);
     u8_schedule(args, kBM, static_cast<uint32_t>(grid));
-    limb_gemm_u8_kernel<BN, KS, LPV><<<grid, kThreads, U8Cfg<BN, KS>::kSmemBytes, stream>>>(args, status);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = U8Cfg<BN, KS>::kSmemBytes;
+    cfg.stream = stream;
+    if (pdl) add_pdl(cfg, attr);
+    return cudaLaunchKernelEx(&cfg, limb_gemm_u8_kernel<BN, KS, LPV, false>, args, status);
 }
 
 bool limb_gemm_u8_pair_ok(int bn, int ks) { return ks == 128 && bn >= 32 && bn <= 128; }
 
 cudaError_t launch_limb_gemm_u8(int bn, int ks, const GroupedGemmArgs &args, int num_sms, int *status,
-                                cudaStream_t stream, bool pair) {
+                                cudaStream_t stream, bool pair, bool pdl) {
     if (pair && !limb_gemm_u8_pair_ok(bn, ks)) return cudaErrorInvalidValue;
-    if (bn == 32 && ks == 128) return launch_u8<32, 128>(args, num_sms, pair, status, stream);
-    if (bn == 32 && ks == 256) return launch_u8<32, 256>(args, num_sms, false, status, stream);
-    if (bn == 64 && ks == 128) return launch_u8<64, 128>(args, num_sms, pair, status, stream);
-    if (bn == 64 && ks == 256) return launch_u8<64, 256>(args, num_sms, false, status, stream);
-    if (bn == 128 && ks == 128) return launch_u8<128, 128>(args, num_sms, pair, status, stream);
-    if (bn == 128 && ks == 256) return launch_u8<128, 256>(args, num_sms, false, status, stream);
+    if (bn == 32 && ks == 128) return launch_u8<32, 128>(args, num_sms, pair, status, stream, pdl);
+    if (bn == 32 && ks == 256) return launch_u8<32, 256>(args, num_sms, false, status, stream, pdl);
+    if (bn == 64 && ks == 128) return launch_u8<64, 128>(args, num_sms, pair, status, stream, pdl);
+    if (bn == 64 && ks == 256) return launch_u8<64, 256>(args, num_sms, false, status, stream, pdl);
+    if (bn == 128 && ks == 128) return launch_u8<128, 128>(args, num_sms, pair, status, stream, pdl);
+    if (bn == 128 && ks == 256) return launch_u8<128, 256>(args, num_sms, false, status, stream, pdl);
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_limb_gemm_u8_rows(int bn, const GroupedGemmArgs &args, int num_sms, int *status,
                                      cudaStream_t stream, bool pair) {
-    if (bn == 32) return launch_u8<32, 128, 1>(args, num_sms, pair, status, stream);
-    if (bn == 64) return launch_u8<64, 128, 1>(args, num_sms, pair, status, stream);
+    if (bn == 32) return launch_u8<32, 128, 1>(args, num_sms, pair, status, stream, false);
+    if (bn == 64) return launch_u8<64, 128, 1>(args, num_sms, pair, status, stream, false);
     return cudaErrorInvalidValue;
 }
 

@@ -50,8 +50,11 @@ int limb_gemm_u8_default_ks(int bn);
 // each CTA loading half of the limb rows.  Then a group's units count 256-row tiles
 // (ceil(M / 256) x n_tiles x KB) and its b map has box {64, bn / 2}.  bn in {32, 64, 128}, ks = 128.
 bool limb_gemm_u8_pair_ok(int bn, int ks);
+// pdl: launch as the programmatic dependent of the kernel just before it in the stream.  Only the
+// limb loads and the output stores wait for that kernel (every kernel before it has completed when
+// this one starts); the digit loads start at once, so that kernel must not write the digits.
 cudaError_t launch_limb_gemm_u8(int bn, int ks, const GroupedGemmArgs &args, int num_sms, int *status,
-                                cudaStream_t stream, bool pair = false);
+                                cudaStream_t stream, bool pair = false, bool pdl = false);
 
 // The same GEMM with one vector-operand row per vector (b maps {C, NV}): each
 // output is the exact signed sum sum_j D[i][j] x_b[j] stored as 32 bits, for

@@ -362,7 +362,11 @@ int ensure_blocked(qpadl_db *db, cudaStream_t stream) {
 // 4096 queries (the limb scratch), in tiles of up to 128 limb columns.
 // out[i * ld_m + v * ld_b] = D * X[v] for B vectors whose fp16 limbs are in db->limbs, on the
 // uint8-digit GEMM (the output block must be dense: it is zeroed, split tiles add into it).
-int run_u8_gemm(qpadl_db *db, uint32_t B, uint32_t *ans, uint64_t ld_m, uint64_t ld_b, cudaStream_t stream) {
+// after_prep: the kernel just before this launch in the stream made the limbs and zeroed the
+// output block (launch_vec_limbs with `zero`), so the GEMM skips the memset and overlaps that
+// kernel as its programmatic dependent.
+int run_u8_gemm(qpadl_db *db, uint32_t B, uint32_t *ans, uint64_t ld_m, uint64_t ld_b, cudaStream_t stream,
+                bool after_prep = false) {
     const uint64_t R = db->prm.rows, C = db->prm.cols;
     const int bn = std::min(limb_gemm_bn_for(B), 128);
     const int ks = db->u8_kstep ? db->u8_kstep : limb_gemm_u8_default_ks(bn);
@@ -386,15 +390,16 @@ int run_u8_gemm(qpadl_db *db, uint32_t B, uint32_t *ans, uint64_t ld_m, uint64_t
     args.ngroups = 1;
     args.total_units = static_cast<uint32_t>((R + tile_rows - 1) / tile_rows) * g.n_tiles * g.KB;
     // tiles split between CTAs are accumulated with atomic adds into zeros
-    QPADL_CU(cudaMemsetAsync(ans, 0, 4ull * B * R, stream));
-    QPADL_CU(launch_limb_gemm_u8(bn, ks, args, db->num_sms, db->d_status, stream, pair));
+    if (!after_prep) QPADL_CU(cudaMemsetAsync(ans, 0, 4ull * B * R, stream));
+    QPADL_CU(launch_limb_gemm_u8(bn, ks, args, db->num_sms, db->d_status, stream, pair, after_prep));
     return QPADL_OK;
 }
 
 int answer_tensor_u8_chunk(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, cudaStream_t stream) {
     const uint64_t R = db->prm.rows, C = db->prm.cols;
-    QPADL_CU(launch_vec_limbs(Q, C, B, C, db->limbs, db->pitch, db->num_sms, stream));
-    return run_u8_gemm(db, B, ans, 1, R, stream);
+    // one launch makes the limbs and zeroes the answers; the GEMM overlaps its start with it
+    QPADL_CU(launch_vec_limbs(Q, C, B, C, db->limbs, db->pitch, db->num_sms, stream, ans, (uint64_t)B * R));
+    return run_u8_gemm(db, B, ans, 1, R, stream, true);
 }
 
 int answer_tensor_u8(qpadl_db *db, const uint32_t *Q, uint32_t B, uint32_t *ans, cudaStream_t stream) {

@@ -378,9 +378,9 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
             ok = ok && qpadl::db_answer_two_noscratch(e.db, dq, e.C, da, e.R, S.stream) == QPADL_OK;
             ++n_stream_k;
         } else if (g.count <= e.u8_max) {
+            // the limbs, and zeroed answers for the tiles the GEMM splits between CTAs
             ok = ok && qpadl::launch_vec_limbs(dq, e.C, g.count, e.C, dl, e.pitch, qpadl::db_num_sms(e.db),
-                                               S.stream) == cudaSuccess;
-            ok = ok && cudaMemsetAsync(da, 0, 4ull * g.count * e.R, S.stream) == cudaSuccess;
+                                               S.stream, da, (uint64_t)g.count * e.R) == cudaSuccess;
             small.push_back(&g);
         } else {
             ok = ok && qpadl::db_answer_f16_ws(e.db, dq, g.count, da, dl, S.stream) == QPADL_OK;
@@ -412,9 +412,12 @@ bool qpadl_server::form_launch(int si, std::unique_lock<std::mutex> &lk) {
         }
         args.ngroups = static_cast<uint32_t>(k1 - k0);
         args.total_units = units;
+        // a programmatic dependent of the kernel before it: every earlier kernel (the limb
+        // kernels of this launch's groups among them) has completed when it starts, and it waits
+        // for that kernel before its limb loads and output stores
         ok = ok && qpadl::launch_limb_gemm_u8(bn, ks, args, qpadl::db_num_sms(dbs[small[k0]->db].db),
-                                              qpadl::db_status_word(dbs[small[k0]->db].db), S.stream,
-                                              pair) == cudaSuccess;
+                                              qpadl::db_status_word(dbs[small[k0]->db].db), S.stream, pair,
+                                              true) == cudaSuccess;
         ++n_gemm_k;
     }
     if (ok) {

@@ -277,6 +277,24 @@ def test_answer_batch_pair_gemm_extreme_values():
         assert np.all(got[b] == exp[b]), hex(int(Q[b, 0]))
 
 
+@pytest.mark.parametrize("R,C,B", [(512, 2048, 16), (1000, 2048 + 128, 40), (3000, 1024, 32)])
+def test_answer_batch_u8_gemm_extreme_values(R, C, B):
+    # the uint8-digit GEMM holds digits as fp16 subnormals (d * 2^-24): every digit 255 against
+    # limb-extreme words puts each 512-deep chunk at its exactness bound, on tiles split between
+    # CTAs (the answers start at -1: the zeroing before the split tiles' adds is part of the call)
+    D = np.full((R, C), 255, dtype=np.uint8)
+    prm, D, db = _setup(R, C, D=D)
+    pir.qpadl_pir_set_option(db, pir.QPADL_OPT_U8_MAX_BATCH, 1 << 20)
+    words = np.array([0x7F7F7F80, 0x7F7F7F7F, 0xFFFFFFFF, 0x80808080], dtype=np.uint32)
+    Q = np.resize(words, B)[:, None].repeat(C, axis=1)
+    exp = ((255 * C * Q[:, 0].astype(np.uint64)) & M32).astype(np.uint32)
+    for pair in (1, 0):
+        pir.qpadl_pir_set_option(db, pir.QPADL_OPT_PAIR_GEMM, pair)
+        got = _answers(db, Q, path=1)
+        for b in range(B):
+            assert np.all(got[b] == exp[b]), (pair, hex(int(Q[b, 0])))
+
+
 def test_answer_batch_linearity_on_device():
     R, C, B = 256, 2048, 8
     prm, D, db = _setup(R, C, seed=3)
