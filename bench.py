@@ -482,7 +482,7 @@ def goldberg_measure(torch, pir, inputs, seed=41):
     res = {"workload": f"{C} records x {R} bytes (1 GiB), p = {p}", "batches": {}}
     one_qps = None
     rows = np.array([0, R // 3, R - 1])
-    for B in (1, 8, 32, 64, 256, 1024):
+    for B in (1, 8, 32, 64, 128, 256, 1024):
         Q_np = (inputs.uniform_u32(B * C, seed=seed + B, tag=inputs.TAG_MISC) % p).reshape(B, C)
         Q = pir.from_u32(Q_np.reshape(-1))
         out = torch.empty(B * R, dtype=torch.int32, device="cuda")
@@ -503,8 +503,8 @@ def goldberg_measure(torch, pir, inputs, seed=41):
         qps = B / (ms * 1e-3)
         one_qps = one_qps or qps
         # the handle's defaults: streaming below 3 queries, the uint8-digit GEMM (one centred row
-        # per query) up to 64, the one-limb fp16-copy GEMM above
-        path = "streaming + mod p" if B < 3 else ("uint8-digit GEMM + mod p" if B <= 64 else "one-limb fp16 GEMM")
+        # per query) up to 128, the one-limb fp16-copy GEMM above
+        path = "streaming + mod p" if B < 3 else ("uint8-digit GEMM + mod p" if B <= 128 else "one-limb fp16 GEMM")
         ent = {"ms": round(ms, 4), "queries_per_s": round(qps, 1),
                "db_scan_gbs": round(B * R * C / (ms * 1e-3) / 1e9, 1), "x_vs_one_at_a_time": round(qps / one_qps, 2),
                "path": path}

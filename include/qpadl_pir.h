@@ -452,9 +452,10 @@ int qpadl_goldberg_answer_batch(qpadl_goldberg *h, const uint32_t *Q_dev, uint32
                                 qpadl_stream_t stream);
 
 /* QPADL_GOLDBERG_OPT_GEMM_MIN_BATCH (default 3): smallest batch on a GEMM.
- * QPADL_GOLDBERG_OPT_U8_MAX_BATCH (0..64, default 64): largest batch on the
+ * QPADL_GOLDBERG_OPT_U8_MAX_BATCH (0..256, default 128): largest batch on the
  *   uint8-digit GEMM (one centred fp16 row per query, exact signed sums, then
- *   mod p); larger batches take the one-limb fp16 GEMM. */
+ *   mod p; 64-wide tiles, several per row tile above 64 queries); larger batches
+ *   take the one-limb fp16 GEMM.  EINVAL outside the range. */
 #define QPADL_GOLDBERG_OPT_GEMM_MIN_BATCH 1
 #define QPADL_GOLDBERG_OPT_U8_MAX_BATCH 2
 /* QPADL_GOLDBERG_OPT_PAIR_GEMM (0/1, default 1): the uint8-digit GEMM on tiles of

@@ -894,7 +894,16 @@ cudaError_t launch_secret_limbs_planed(const uint32_t *S, uint32_t B, uint32_t n
 // Goldberg queries (B x C field elements < p) -> one fp16 row per query,
 // centred: q if q <= p / 2, else q - p (|value| <= 128 for p <= 257).
 __global__ void centred_rows_kernel(const uint32_t *__restrict__ Q, uint32_t B, uint64_t C, uint32_t p,
-                                    __half *__restrict__ L, uint64_t pitch) {
+                                    __half *__restrict__ L, uint64_t pitch, uint32_t *__restrict__ Z,
+                                    uint64_t z_words) {
+    // as in vec_limbs_kernel: a GEMM launched as this kernel's programmatic dependent may start now,
+    // and its output block is zeroed here
+    griddep_launch_dependents();
+    if (Z != nullptr) {
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < z_words;
+             i += (uint64_t)gridDim.x * blockDim.x)
+            Z[i] = 0u;
+    }
     const uint64_t total = (uint64_t)B * C;
     for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (uint64_t)gridDim.x * blockDim.x) {
@@ -926,8 +935,8 @@ cudaError_t launch_mod_p_signed(uint32_t *x, uint64_t n, uint32_t p, int num_sms
 }
 
 cudaError_t launch_centred_rows(const uint32_t *Q, uint32_t B, uint64_t C, uint32_t p, __half *L, uint64_t pitch,
-                                int num_sms, cudaStream_t stream) {
-    centred_rows_kernel<<<num_sms * 4, 256, 0, stream>>>(Q, B, C, p, L, pitch);
+                                int num_sms, cudaStream_t stream, uint32_t *zero, uint64_t zero_words) {
+    centred_rows_kernel<<<num_sms * 4, 256, 0, stream>>>(Q, B, C, p, L, pitch, zero, zero_words);
     return cudaGetLastError();
 }
 

@@ -42,8 +42,10 @@ cudaError_t launch_limb_gemm_recover(int bn, const CUtensorMap &a_map, const CUt
 // 256 keeps them in TMEM, reduced mod p after every chunk), through ModPEpi.
 cudaError_t launch_limb_gemm_modp(int bn, const CUtensorMap &a_map, const CUtensorMap &b_map, const ModPEpi &epi,
                                   uint32_t M, uint32_t NV, uint64_t K, int num_sms, int *status, cudaStream_t stream);
+// Z_p vectors q -> one centred fp16 row each (q or q - p).  When `zero` is given, the same launch
+// zeroes zero_words words there (as launch_vec_limbs does for a dependent uint8-digit GEMM).
 cudaError_t launch_centred_rows(const uint32_t *Q, uint32_t B, uint64_t C, uint32_t p, __half *L, uint64_t pitch,
-                                int num_sms, cudaStream_t stream);
+                                int num_sms, cudaStream_t stream, uint32_t *zero = nullptr, uint64_t zero_words = 0);
 cudaError_t launch_mod_p(uint32_t *x, uint64_t n, uint32_t p, int num_sms, cudaStream_t stream);
 // x[i] = (x[i] as a signed 32-bit integer) mod p, in [0, p).
 cudaError_t launch_mod_p_signed(uint32_t *x, uint64_t n, uint32_t p, int num_sms, cudaStream_t stream);

@@ -704,9 +704,9 @@ cudaError_t launch_limb_gemm_u8(int bn, int ks, const GroupedGemmArgs &args, int
 }
 
 cudaError_t launch_limb_gemm_u8_rows(int bn, const GroupedGemmArgs &args, int num_sms, int *status,
-                                     cudaStream_t stream, bool pair) {
-    if (bn == 32) return launch_u8<32, 128, 1>(args, num_sms, pair, status, stream, false);
-    if (bn == 64) return launch_u8<64, 128, 1>(args, num_sms, pair, status, stream, false);
+                                     cudaStream_t stream, bool pair, bool pdl) {
+    if (bn == 32) return launch_u8<32, 128, 1>(args, num_sms, pair, status, stream, pdl);
+    if (bn == 64) return launch_u8<64, 128, 1>(args, num_sms, pair, status, stream, pdl);
     return cudaErrorInvalidValue;
 }
 

@@ -60,8 +60,8 @@ cudaError_t launch_limb_gemm_u8(int bn, int ks, const GroupedGemmArgs &args, int
 // output is the exact signed sum sum_j D[i][j] x_b[j] stored as 32 bits, for
 // |x_b[j]| <= 128 (so every 512-deep chunk stays below 2^24 in fp32 and the
 // whole sum below 2^31 for fewer than 65793 columns).  bn in {32, 64}, 128-digit
-// stages; output zeroed before the launch as above.
+// stages; output zeroed before the launch as above; pdl as above.
 cudaError_t launch_limb_gemm_u8_rows(int bn, const GroupedGemmArgs &args, int num_sms, int *status,
-                                     cudaStream_t stream, bool pair = false);
+                                     cudaStream_t stream, bool pair = false, bool pdl = false);
 
 }  // namespace qpadl

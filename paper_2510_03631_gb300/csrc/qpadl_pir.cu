@@ -83,7 +83,7 @@ struct qpadl_goldberg {
     qpadl_db *db = nullptr;
     uint32_t p = 0;
     uint32_t gemm_min_batch = 3;     // batches from this size take a tensor-core GEMM
-    uint32_t u8_max_batch = 64;      // ... the uint8-digit one up to this size, the one-limb fp16 one above
+    uint32_t u8_max_batch = 128;     // ... the uint8-digit one up to this size, the one-limb fp16 one above
 };
 
 // Chor-style GF(2) database handle.
@@ -1358,13 +1358,17 @@ int qpadl_goldberg_answer_batch(qpadl_goldberg *h, const uint32_t *Q_dev, uint32
         QPADL_CU(launch_mod_p(out_dev, (uint64_t)B * R, h->p, db->num_sms, s));
         return QPADL_OK;
     }
-    if (B <= h->u8_max_batch && db->u8_ok && B <= 64) {
+    if (B <= h->u8_max_batch && db->u8_ok) {
         // the uint8-digit GEMM with one centred row per query gives the exact signed sums
-        // (below 2^31 in magnitude for at most kGoldbergMaxCols columns), then mod p
+        // (below 2^31 in magnitude for at most kGoldbergMaxCols columns), then mod p; above 64
+        // queries a row tile takes several 64-wide tiles (one read of the digits, converted once
+        // per tile), which beats the fp16 copy's one-limb GEMM up to about 128-192 queries
         int rc = ensure_blocked(db, s);
         if (rc != QPADL_OK) return rc;
         if ((rc = ensure_limbs(db, 2ull * B * db->pitch)) != QPADL_OK) return rc;
-        QPADL_CU(launch_centred_rows(Q_dev, B, C, h->p, db->limbs, db->pitch, db->num_sms, s));
+        // one launch makes the rows and zeroes the sums; the GEMM overlaps its start with it
+        QPADL_CU(launch_centred_rows(Q_dev, B, C, h->p, db->limbs, db->pitch, db->num_sms, s, out_dev,
+                                     (uint64_t)B * R));
         const int bn = B <= 32 ? 32 : 64;
         constexpr int ks = 128;
         const bool pair = db->pair_gemm && db->num_sms >= 2;
@@ -1386,9 +1390,8 @@ int qpadl_goldberg_answer_batch(qpadl_goldberg *h, const uint32_t *Q_dev, uint32
         g.n_tiles = (B + bn - 1) / bn;
         args.ngroups = 1;
         args.total_units = static_cast<uint32_t>((R + tile_rows - 1) / tile_rows) * g.n_tiles * g.KB;
-        // tiles split between CTAs are accumulated with atomic adds into zeros
-        QPADL_CU(cudaMemsetAsync(out_dev, 0, 4ull * B * R, s));
-        QPADL_CU(launch_limb_gemm_u8_rows(bn, args, db->num_sms, db->d_status, s, pair));
+        // tiles split between CTAs are accumulated with atomic adds into the zeros
+        QPADL_CU(launch_limb_gemm_u8_rows(bn, args, db->num_sms, db->d_status, s, pair, true));
         QPADL_CU(launch_mod_p_signed(out_dev, (uint64_t)B * R, h->p, db->num_sms, s));
         return QPADL_OK;
     }
@@ -1421,7 +1424,7 @@ int qpadl_goldberg_set_option(qpadl_goldberg *h, int option, int64_t value) {
             h->gemm_min_batch = static_cast<uint32_t>(value);
             return QPADL_OK;
         case QPADL_GOLDBERG_OPT_U8_MAX_BATCH:
-            if (value < 0 || value > 64) return QPADL_EINVAL;
+            if (value < 0 || value > 256) return QPADL_EINVAL;
             h->u8_max_batch = static_cast<uint32_t>(value);
             return QPADL_OK;
         case QPADL_GOLDBERG_OPT_PAIR_GEMM:

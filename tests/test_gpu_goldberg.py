@@ -43,8 +43,10 @@ CASES = [(300, 1000, 257, 1), (257, 513, 251, 4), (1000, 2048, 257, 5), (700, 40
 
 
 @pytest.mark.parametrize("R,C,p,B", CASES)
-# uint8-digit GEMM up to 32 or 64 queries (on SM pairs or single SMs) / fp16-copy GEMM / streaming
-@pytest.mark.parametrize("gemm_min,u8max,pair", [(1, 32, 1), (1, 64, 1), (1, 64, 0), (1, 0, 1), (1 << 30, 32, 1)])
+# uint8-digit GEMM up to 32, 64 or 256 queries (on SM pairs or single SMs; above 64 several tiles
+# per row tile) / fp16-copy GEMM / streaming
+@pytest.mark.parametrize("gemm_min,u8max,pair", [(1, 32, 1), (1, 64, 1), (1, 64, 0), (1, 256, 1), (1, 256, 0),
+                                                 (1, 0, 1), (1 << 30, 32, 1)])
 def test_goldberg_matches_oracle(cuda, R, C, p, B, gemm_min, u8max, pair):
     D = _db(R, C, p, seed=R + C)
     Q = (inputs.uniform_u32(B * C, seed=B + p, tag=inputs.TAG_MISC) % p).reshape(B, C)
