@@ -458,8 +458,9 @@ int qpadl_goldberg_answer_batch(qpadl_goldberg *h, const uint32_t *Q_dev, uint32
  *   take the one-limb fp16 GEMM.  EINVAL outside the range. */
 #define QPADL_GOLDBERG_OPT_GEMM_MIN_BATCH 1
 #define QPADL_GOLDBERG_OPT_U8_MAX_BATCH 2
-/* QPADL_GOLDBERG_OPT_PAIR_GEMM (0/1, default 1): the uint8-digit GEMM on tiles of
- * 256 rows over pairs of SMs (see QPADL_OPT_PAIR_GEMM). */
+/* QPADL_GOLDBERG_OPT_PAIR_GEMM (0/1, default 1): the uint8-digit GEMM, and the
+ * one-limb fp16 GEMM's 256-wide tiles, on tiles of 256 rows over pairs of SMs
+ * (see QPADL_OPT_PAIR_GEMM). */
 #define QPADL_GOLDBERG_OPT_PAIR_GEMM 3
 int qpadl_goldberg_set_option(qpadl_goldberg *h, int option, int64_t value);
 

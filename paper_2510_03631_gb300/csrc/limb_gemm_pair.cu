@@ -136,11 +136,16 @@ __global__ void __launch_bounds__(kPThreads, 1)
                           uint32_t M, uint32_t NV, uint32_t KB, uint32_t ckb, uint32_t plane_chunks,
                           uint32_t dp_tiles_arg, uint32_t tail_parts, int *__restrict__ status) {
     using Cfg = PairCfg<BN>;
-    static_assert(Epi::kLimbs == 4, "four byte limbs per vector");
     static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
     static_assert(!PLANED || BN >= 128, "a planed shift group needs N/2 >= 16 rows per CTA");
     constexpr int ST = Cfg::kStages;
-    constexpr int QPT = Cfg::kQPT;
+    constexpr int LPV = Epi::kLimbs;   // vector-operand rows per vector
+    static_assert(LPV == 4 || (LPV == 1 && BN == 256 && !PLANED), "one-row vectors: 256-wide plain tiles");
+    constexpr int QPT = BN / LPV;      // vectors per pair tile
+    // one-row tiles (Z_p vectors, ModPEpi) keep their running sums in TMEM, reduced mod p after
+    // every chunk: a representative |r| <= 1.5 p plus one chunk (digits times centred entries,
+    // |product| <= 255 * 128, 512 deep) stays below 2^24, so fp32 stays exact
+    constexpr bool TMEMSUM = LPV == 1;
     constexpr int HQ = QPT / 2;   // planed: secrets per CTA block
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -296,7 +301,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
 #pragma unroll
                         for (int k = 0; k < kPK / 16; ++k)
                             umma_f16_pair(d_tmem, adesc + 2u * k, bdesc + 2u * k, idesc,
-                                          (kc != 0 || k != 0) ? 1u : 0u);
+                                          (kc != 0 || k != 0 || (TMEMSUM && kb >= 2u * ckb)) ? 1u : 0u);
                         umma_commit_pair(&empty[st], 3);
                         if (last_of_chunk) umma_commit_pair(&acc_full[ci & 1u], 3);
                     }
@@ -332,9 +337,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
             const uint32_t t = pc.t;
             const uint32_t row = (t / n_tiles) * 2 * kPM + rank * kPM + quarter * 32u + static_cast<uint32_t>(lane);
             const uint32_t v0 = (t % n_tiles) * QPT;
-            uint32_t run[QPT];
+            constexpr int RUN = TMEMSUM ? 1 : QPT;   // running sums kept in registers
+            uint32_t run[RUN];
 #pragma unroll
-            for (int q = 0; q < QPT; ++q) run[q] = 0u;
+            for (int q = 0; q < RUN; ++q) run[q] = 0u;
             // client tiles are short in K: their epilogue inputs are loaded as the tile starts
             constexpr int EARLY = PLANED ? QPT : 1;
             uint32_t early[EARLY];
@@ -351,7 +357,68 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t acc = tmem_base + lane_addr + buf * BN;
-                if constexpr (PLANED) {
+                if constexpr (TMEMSUM) {
+                    const float pf = static_cast<float>(epi.p), inv = 1.0f / pf;
+                    if (c + 1 < nchunks) {
+                        // replace this buffer's running sums by small representatives of their
+                        // residues mod p: q = x / p rounded to an integer through the 1.5 * 2^23
+                        // rounding constant, r = x - q p with |r| <= 1.5 p; q p and r are integers
+                        // below 2^24, so the fused multiply-add is exact.  Four 32-column loads per
+                        // wait; the next MMAs into this buffer accumulate on top.
+                        constexpr float kRound = 12582912.0f;
+#pragma unroll 1
+                        for (int j0 = 0; j0 < BN / 32; j0 += 4) {
+                            uint32_t v[4][32];
+#pragma unroll
+                            for (int g = 0; g < 4; ++g) tmem_ld32(acc + 32u * (j0 + g), v[g]);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int g = 0; g < 4; ++g) {
+#pragma unroll
+                                for (int q = 0; q < 32; ++q) {
+                                    const float x = __uint_as_float(v[g][q]);
+                                    const float qf = __fsub_rn(__fmaf_rn(x, inv, kRound), kRound);
+                                    v[g][q] = __float_as_uint(__fmaf_rn(-qf, pf, x));
+                                }
+                                tmem_st32(acc + 32u * (j0 + g), v[g]);
+                            }
+                        }
+                        tmem_wait_st();
+                        if (c + 2 < nchunks) {
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive_cluster(acc_empty_c + 8u * buf);
+                        }
+                        // the second-to-last chunk's buffer is held for the final combine
+                        continue;
+                    }
+                    // last chunk: its buffer plus the other buffer's residue, mod p, to the output
+                    const uint32_t oth = tmem_base + lane_addr + (buf ^ 1u) * BN;
+                    const int32_t ip = epi.p;
+#pragma unroll 1
+                    for (int j = 0; j < BN / 32; ++j) {
+                        uint32_t v[32], w[32];
+                        tmem_ld32(acc + 32u * j, v);
+                        if (nchunks >= 2) tmem_ld32(oth + 32u * j, w);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            int32_t x = __float2int_rn(__uint_as_float(v[q]));
+                            if (nchunks >= 2) x += __float2int_rn(__uint_as_float(w[q]));
+                            int32_t r = x % ip;
+                            if (r < 0) r += ip;
+                            const uint32_t vi = v0 + 32u * j + q;
+                            if (row < M && vi < NV) epi.put(row, vi, static_cast<uint32_t>(r), 0u);
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        mbar_arrive_cluster(acc_empty_c + 8u * buf);
+                        if (nchunks >= 2) mbar_arrive_cluster(acc_empty_c + 8u * (buf ^ 1u));
+                    }
+                    continue;
+                } else if constexpr (PLANED) {
                     const uint32_t u = c / plane_chunks;
                     const uint32_t half = (4u - u) * HQ;   // N / 2
                     for (uint32_t s = u; s < 4; ++s) {
@@ -407,6 +474,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 if (lane == 0) mbar_arrive_cluster(acc_empty_c + 8u * buf);
             }
             if (failed) break;
+            if constexpr (TMEMSUM) continue;   // the last chunk already wrote the tile
             if constexpr (kSplit) {
                 if (row < M && !(pc.c0 == 0 && pc.c1 == nchunks)) {
                     // part of a split tile: exact, since addition mod 2^32 commutes
@@ -478,7 +546,8 @@ cudaError_t prepare_limb_gemm_pair_kernels() {
     if ((e = set_pair_attr<128, QueryNoiseEpi, true>()) != cudaSuccess) return e;
     if ((e = set_pair_attr<256, QueryNoiseEpi, true>()) != cudaSuccess) return e;
     if ((e = set_pair_attr<128, RecoverEpi, true>()) != cudaSuccess) return e;
-    return set_pair_attr<256, RecoverEpi, true>();
+    if ((e = set_pair_attr<256, RecoverEpi, true>()) != cudaSuccess) return e;
+    return set_pair_attr<256, ModPEpi, false>();
 }
 
 int limb_gemm_pair_bn_for(uint32_t nv) {
@@ -528,7 +597,7 @@ static int resident_pairs(int num_sms) {
 // k-steps (64 deep) per exact chunk: 8 for digits times limbs (StoreEpi), 16 for limbs times limbs.
 template <class Epi>
 constexpr uint32_t pair_chunk_kb() {
-    return std::is_same<Epi, StoreEpi>::value ? 8u : 16u;
+    return (std::is_same<Epi, StoreEpi>::value || std::is_same<Epi, ModPEpi>::value) ? 8u : 16u;
 }
 
 // Schedule of a plain-store launch over `tiles` pair tiles (n_tiles per row tile, nchunks exact
@@ -567,7 +636,8 @@ static cudaError_t launch_pair_t(const CUtensorMap &a_map, const PairBMaps &bm, 
                                  uint32_t NV, uint32_t KB, uint32_t ckb, uint32_t plane_chunks, int num_sms,
                                  int *status, cudaStream_t stream) {
     const uint64_t m_tiles = (M + 2ull * kPM - 1) / (2ull * kPM);
-    const uint64_t n_tiles = (NV + PairCfg<BN>::kQPT - 1) / PairCfg<BN>::kQPT;
+    constexpr uint64_t qpt = BN / Epi::kLimbs;   // vectors per pair tile
+    const uint64_t n_tiles = (NV + qpt - 1) / qpt;
     const uint64_t tiles = m_tiles * n_tiles;
     const uint64_t pairs = static_cast<uint64_t>(resident_pairs<BN, Epi, PLANED>(num_sms));
     uint64_t clusters = tiles < pairs ? tiles : pairs;
@@ -599,29 +669,38 @@ static cudaError_t launch_pair_epi(int bn, const CUtensorMap &a_map, const PairB
                                    cudaStream_t stream) {
     if (M == 0 || NV == 0 || K == 0 || num_sms < 2) return cudaErrorInvalidValue;
     const uint32_t KB = static_cast<uint32_t>((K + kPK - 1) / kPK);
-    if (plane_chunks == 0) {
-        constexpr uint32_t ckb = pair_chunk_kb<Epi>();
-        switch (bn) {
-            case 64: return launch_pair_t<64, Epi, false>(a_map, bm, epi, M, NV, KB, ckb, 0, num_sms, status, stream);
-            case 128: return launch_pair_t<128, Epi, false>(a_map, bm, epi, M, NV, KB, ckb, 0, num_sms, status, stream);
-            case 256: return launch_pair_t<256, Epi, false>(a_map, bm, epi, M, NV, KB, ckb, 0, num_sms, status, stream);
-            default: return cudaErrorInvalidValue;
-        }
-    }
-    if constexpr (std::is_same<Epi, StoreEpi>::value) {
-        return cudaErrorInvalidValue;
+    if constexpr (Epi::kLimbs == 1) {   // one row per vector: 256-wide plain tiles only
+        if (bn != 256 || plane_chunks != 0) return cudaErrorInvalidValue;
+        return launch_pair_t<256, Epi, false>(a_map, bm, epi, M, NV, KB, pair_chunk_kb<Epi>(), 0, num_sms, status,
+                                             stream);
     } else {
-        // every chunk lies inside one limb plane of n = K / 4 columns: 1024-deep chunks when n is a
-        // multiple of 1024, else 512-deep (plane_chunks = n / 512 then)
-        if (K != 4ull * 512 * plane_chunks) return cudaErrorInvalidValue;
-        const uint32_t ckb = plane_chunks % 2 == 0 ? 16u : 8u;
-        const uint32_t pc = ckb == 16u ? plane_chunks / 2 : plane_chunks;
-        switch (bn) {
-            case 128:
-                return launch_pair_t<128, Epi, true>(a_map, bm, epi, M, NV, KB, ckb, pc, num_sms, status, stream);
-            case 256:
-                return launch_pair_t<256, Epi, true>(a_map, bm, epi, M, NV, KB, ckb, pc, num_sms, status, stream);
-            default: return cudaErrorInvalidValue;
+        if (plane_chunks == 0) {
+            constexpr uint32_t ckb = pair_chunk_kb<Epi>();
+            switch (bn) {
+                case 64:
+                    return launch_pair_t<64, Epi, false>(a_map, bm, epi, M, NV, KB, ckb, 0, num_sms, status, stream);
+                case 128:
+                    return launch_pair_t<128, Epi, false>(a_map, bm, epi, M, NV, KB, ckb, 0, num_sms, status, stream);
+                case 256:
+                    return launch_pair_t<256, Epi, false>(a_map, bm, epi, M, NV, KB, ckb, 0, num_sms, status, stream);
+                default: return cudaErrorInvalidValue;
+            }
+        }
+        if constexpr (std::is_same<Epi, StoreEpi>::value) {
+            return cudaErrorInvalidValue;
+        } else {
+            // every chunk lies inside one limb plane of n = K / 4 columns: 1024-deep chunks when n is a
+            // multiple of 1024, else 512-deep (plane_chunks = n / 512 then)
+            if (K != 4ull * 512 * plane_chunks) return cudaErrorInvalidValue;
+            const uint32_t ckb = plane_chunks % 2 == 0 ? 16u : 8u;
+            const uint32_t pc = ckb == 16u ? plane_chunks / 2 : plane_chunks;
+            switch (bn) {
+                case 128:
+                    return launch_pair_t<128, Epi, true>(a_map, bm, epi, M, NV, KB, ckb, pc, num_sms, status, stream);
+                case 256:
+                    return launch_pair_t<256, Epi, true>(a_map, bm, epi, M, NV, KB, ckb, pc, num_sms, status, stream);
+                default: return cudaErrorInvalidValue;
+            }
         }
     }
 }
@@ -643,6 +722,11 @@ cudaError_t launch_limb_gemm_pair_recover(int bn, const CUtensorMap &a_map, cons
                                           const RecoverEpi &epi, uint32_t M, uint32_t NV, uint64_t K,
                                           uint32_t plane_chunks, int num_sms, int *status, cudaStream_t stream) {
     return launch_pair_epi(bn, a_map, bm, epi, M, NV, K, plane_chunks, num_sms, status, stream);
+}
+
+cudaError_t launch_limb_gemm_pair_modp(const CUtensorMap &a_map, const PairBMaps &bm, const ModPEpi &epi, uint32_t M,
+                                       uint32_t NV, uint64_t K, int num_sms, int *status, cudaStream_t stream) {
+    return launch_pair_epi(256, a_map, bm, epi, M, NV, K, 0, num_sms, status, stream);
 }
 
 }  // namespace qpadl

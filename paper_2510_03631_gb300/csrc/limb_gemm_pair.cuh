@@ -41,4 +41,10 @@ cudaError_t launch_limb_gemm_pair_recover(int bn, const CUtensorMap &a_map, cons
                                           const RecoverEpi &epi, uint32_t M, uint32_t NV, uint64_t K,
                                           uint32_t plane_chunks, int num_sms, int *status, cudaStream_t stream);
 
+// One centred fp16 row per Z_p vector (Goldberg Response): out[i * ld_m + v * ld_b] =
+// (sum_j D[i][j] X[v][j]) mod p in [0, p), on 256-wide pair tiles whose running sums stay in TMEM
+// (reduced mod p after every 512-deep chunk); bm.m[0] has box 64 x 128 over the NV rows.
+cudaError_t launch_limb_gemm_pair_modp(const CUtensorMap &a_map, const PairBMaps &bm, const ModPEpi &epi, uint32_t M,
+                                       uint32_t NV, uint64_t K, int num_sms, int *status, cudaStream_t stream);
+
 }  // namespace qpadl

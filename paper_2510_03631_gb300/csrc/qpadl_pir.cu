@@ -1405,11 +1405,22 @@ int qpadl_goldberg_answer_batch(qpadl_goldberg *h, const uint32_t *Q_dev, uint32
         QPADL_CU(launch_centred_rows(Q_dev + (uint64_t)b0 * C, Bc, C, h->p, db->limbs, db->pitch, db->num_sms, s));
         // up to 64 queries: running sums in registers; more: 256-wide tiles with the sums in TMEM
         const int bn = Bc <= 32 ? 32 : (Bc <= 64 ? 64 : 256);
+        const ModPEpi epi{out_dev + (uint64_t)b0 * R, 1, R, static_cast<int32_t>(h->p)};
+        if (bn == 256 && db->pair_gemm && db->num_sms >= 2) {
+            // 256-row tiles over pairs of SMs, each SM loading half of every vector tile
+            PairBMaps bm;
+            std::memset(&bm, 0, sizeof(bm));
+            if (!encode_2d(&bm.m[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, db->limbs, C, Bc, db->pitch * 2, kLimbBoxK,
+                           pair_b_box_rows(256, false, 0), CU_TENSOR_MAP_SWIZZLE_128B))
+                return QPADL_ECUDA;
+            QPADL_CU(launch_limb_gemm_pair_modp(db->a_map, bm, epi, static_cast<uint32_t>(R), Bc, C, db->num_sms,
+                                                db->d_status, s));
+            continue;
+        }
         CUtensorMap b_map;
         if (!encode_2d(&b_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, db->limbs, C, Bc, db->pitch * 2, kLimbBoxK,
                        static_cast<uint32_t>(bn), CU_TENSOR_MAP_SWIZZLE_128B))
             return QPADL_ECUDA;
-        const ModPEpi epi{out_dev + (uint64_t)b0 * R, 1, R, static_cast<int32_t>(h->p)};
         QPADL_CU(launch_limb_gemm_modp(bn, db->a_map, b_map, epi, static_cast<uint32_t>(R), Bc, C, db->num_sms,
                                        db->d_status, s));
     }
