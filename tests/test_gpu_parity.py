@@ -229,6 +229,8 @@ def test_answer_batch_split_tiles(R, C, B):
     (128, 64, 40),           # the peer holds no rows at all; K below one k-step
     (20000, 1100, 300),      # several tiles per CTA pair, rings wrapping
     (20000, 2048 + 8, 100),  # two vector tiles per row tile: a whole wave, then a split tail (ragged K)
+    (20000, 1100, 160),      # three vector tiles per row tile (the last half full): whole waves, split tail
+    (1000, 2048, 256),       # four vector tiles per row tile, tiles filling few clusters: all split
     (600, 512, 17),          # 68 limb columns: 128-wide pair tiles (u8 GEMM off)
     (600, 512, 9),           # 36 limb columns: 64-wide pair tiles (u8 GEMM off)
 ])
