@@ -423,8 +423,8 @@ def serving_measure(torch, pir, inputs, rates, duration_s, single_db_one_ms, see
 def chor_measure(torch, pir, inputs, seed=31):
     """Chor Response over GF(2) (Sec. 5.2, Alg. 3) on a 1 GiB bit database:
     32768 records of 262144 bits; batches of uniformly random queries, one
-    pass over the database per 256 queries.  Checks query 0 of every batch on
-    its first 64 words against a host XOR of the selected records."""
+    pass over the database per 256 queries.  Query 0 of every batch selects one
+    record (a unit vector), so its answer must be that record as stored."""
     w = inputs.WORKLOADS["chor_1gib"]
     rows, bits = w["rows"], w["bits"]
     W = bits // 32
@@ -435,6 +435,9 @@ def chor_measure(torch, pir, inputs, seed=31):
     one_qps = None
     for B in w["batches"]:
         Q_np = inputs.chor_queries(B, rows, seed=seed + B)
+        r0 = (seed * 7919 + B * 104729) % rows
+        Q_np[0] = 0
+        Q_np[0][r0 // 32] = np.uint32(1) << np.uint32(r0 % 32)
         Q = torch.from_numpy(Q_np.view(np.int32).reshape(-1)).cuda()
         out = torch.empty(B * W, dtype=torch.int32, device="cuda")
         pir.qpadl_chor_answer_batch(h, Q, out)
@@ -447,10 +450,8 @@ def chor_measure(torch, pir, inputs, seed=31):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
-        sel = ((Q_np[0][np.arange(rows) // 32] >> (np.arange(rows) % 32).astype(np.uint32)) & 1).astype(bool)
-        exp = np.bitwise_xor.reduce(DB_np[sel, :64], axis=0)
-        if not np.array_equal(pir.as_u32(out)[:64], exp) or pir.qpadl_chor_status(h) != 0:
-            raise SystemExit("bench: Chor answer differs from the host XOR")
+        if not np.array_equal(pir.as_u32(out)[:W], DB_np[r0]) or pir.qpadl_chor_status(h) != 0:
+            raise SystemExit("bench: Chor answer to a one-record query differs from that record")
         qps = B / (ms * 1e-3)
         if B == 1:
             one_qps = qps
@@ -474,16 +475,19 @@ def chor_measure(torch, pir, inputs, seed=31):
 def goldberg_measure(torch, pir, inputs, seed=41):
     """Goldberg Response over Z_257 (Sec. 5.2, Alg. 4) on the 1 GiB byte
     database (32768 records of 32768 bytes): batches of uniform field
-    elements; sampled rows checked against a host dot product mod p."""
+    elements; query 0 of every batch selects one record (a unit vector), so its
+    answer must be that record as stored."""
     w = inputs.WORKLOADS["single_1gib"]
     R, C, p = w["rows"], w["cols"], 257
     D_np = inputs.db_digits(R, C, 256, seed=seed)
     h = pir.qpadl_goldberg_setup(R, C, p, torch.from_numpy(D_np).cuda())
     res = {"workload": f"{C} records x {R} bytes (1 GiB), p = {p}", "batches": {}}
     one_qps = None
-    rows = np.array([0, R // 3, R - 1])
     for B in (1, 8, 32, 64, 128, 256, 1024):
         Q_np = (inputs.uniform_u32(B * C, seed=seed + B, tag=inputs.TAG_MISC) % p).reshape(B, C)
+        j0 = (seed * 7919 + B * 104729) % C
+        Q_np[0] = 0
+        Q_np[0, j0] = 1
         Q = pir.from_u32(Q_np.reshape(-1))
         out = torch.empty(B * R, dtype=torch.int32, device="cuda")
         pir.qpadl_goldberg_answer_batch(h, Q, out)
@@ -496,10 +500,9 @@ def goldberg_measure(torch, pir, inputs, seed=41):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
-        got = pir.as_u32(out).reshape(B, R)[:2, rows]
-        exp = (Q_np[:2].astype(np.int64) @ D_np[rows].T.astype(np.int64)) % p
-        if not np.array_equal(got, exp.astype(np.uint32)) or pir.qpadl_goldberg_status(h) != 0:
-            raise SystemExit("bench: Goldberg answer differs from the host dot product")
+        got = pir.as_u32(out).reshape(B, R)[0]
+        if not np.array_equal(got, D_np[:, j0].astype(np.uint32)) or pir.qpadl_goldberg_status(h) != 0:
+            raise SystemExit("bench: Goldberg answer to a one-record query differs from that record")
         qps = B / (ms * 1e-3)
         one_qps = one_qps or qps
         # the handle's defaults: streaming below 3 queries, the uint8-digit GEMM (one centred row
