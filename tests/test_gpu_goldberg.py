@@ -39,7 +39,8 @@ def _answer(h, Q_np, gemm_min=None, u8max=None):
 
 CASES = [(300, 1000, 257, 1), (257, 513, 251, 4), (1000, 2048, 257, 5), (700, 4096 + 48, 101, 33),
          (129, 300, 257, 64), (2000, 1024, 257, 200), (384, 512, 2, 7), (50, 777, 257, 1100),
-         (640, 512, 257, 65), (333, 1500, 101, 300)]
+         (640, 512, 257, 65), (333, 1500, 101, 300),
+         (600, 2048, 2, 100), (520, 1100, 3, 257)]   # p < 4 on the 256-wide one-limb tiles
 
 
 @pytest.mark.parametrize("R,C,p,B", CASES)
