@@ -44,7 +44,8 @@
 // either CTA from leaving while its peer may still reach its shared memory.
 //
 // Warp roles (480 threads, one CTA per SM):
-//   warp 0       TMA producer of the digit tiles (plus L2 prefetch ahead of them)
+//   warp 0       TMA producer of the digit tiles (wider tiles: the first ring's worth issued before
+//                setup ends; 32-column tiles: the digits pulled into L2 a few stages ahead)
 //   warp 1       TMEM allocation; one thread issues the MMAs
 //   warps 2..5   epilogue: drain one of two BN-column accumulators per chunk
 //   warps 6..13  converters, two groups of four, each owning every other stage:
@@ -65,7 +66,6 @@ constexpr int kBM = 128;
 constexpr int kThreads = 480;
 constexpr int kConvGroups = 2;
 constexpr uint32_t kTmemCols = 512;
-constexpr int kPrefetch = 8;   // stages of digit tiles pulled into L2 ahead of their loads
 // The A operand holds each digit d as the fp16 subnormal d * 2^-24, so an accumulator holds
 // 2^-24 times an exact integer sum (|sum| <= 2^24: the fp32 significand keeps it exact); the
 // epilogue scales it back by 2^24 (exact) before rounding to an integer.
@@ -195,6 +195,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    const uint32_t rank = PAIR ? cluster_rank() : 0u;
+    const uint32_t roff = rank * kBM;   // this CTA's first row within a tile
+    // this CTA's (pair: cluster's) pieces: round-robin whole tiles, then a share of the rest
+    const uint32_t part = PAIR ? (blockIdx.x >> 1) : blockIdx.x;
+    const uint32_t nparts = PAIR ? (gridDim.x >> 1) : gridDim.x;
+    uint32_t early = 0;   // digit stages the producer (thread 0) issued before the setup barrier
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < SD; ++s) {
@@ -216,6 +222,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_init(mma_done, 1);
         *abort = 0;
         fence_barrier_init();
+        // the first ring's digit loads need only this CTA's own barriers and shared memory: they
+        // go out now, while TMEM is allocated and the CTAs meet at the setup barrier (tiles wider
+        // than 32 columns; the narrowest ones measured faster with their L2 prefetch prologue first)
+        if constexpr (BN > 32) {
+            Seg tr;
+            SegIter sit(args, part, nparts);
+            while (early < static_cast<uint32_t>(SD) && sit.next(args, BN, TM, nparts, tr)) {
+                for (uint32_t ks = tr.ks0; ks < tr.ks1 && early < static_cast<uint32_t>(SD); ++ks, ++early) {
+                    mbar_arrive_expect_tx(&dfull[early], Cfg::kDigBytes);
+                    tma_load_4d(dig + early * Cfg::kDigBytes, &args.a[tr.g], &dfull[early], 0, 0,
+                                static_cast<int32_t>(ks * KS / 128), static_cast<int32_t>((tr.m0 + roff) / kBM));
+                }
+            }
+        }
     }
     if (warp == 1) {
         if constexpr (PAIR) {
@@ -231,17 +251,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     else __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const uint32_t rank = PAIR ? cluster_rank() : 0u;
     const bool leader = rank == 0;
-    const uint32_t roff = rank * kBM;   // this CTA's first row within a tile
     // shared::cluster addresses of the leader's barriers that both CTAs signal (pair form)
     const uint32_t lfull_c = PAIR ? cluster_addr(lfull, 0) : 0u;
     const uint32_t aready_c = PAIR ? cluster_addr(aready, 0) : 0u;
     const uint32_t acc_empty_c = PAIR ? cluster_addr(acc_empty, 0) : 0u;
     const uint32_t peer_abort = PAIR ? cluster_addr(const_cast<int *>(abort), rank ^ 1u) : 0u;
-    // this CTA's (pair: cluster's) pieces: round-robin whole tiles, then a share of the rest
-    const uint32_t part = PAIR ? (blockIdx.x >> 1) : blockIdx.x;
-    const uint32_t nparts = PAIR ? (gridDim.x >> 1) : gridDim.x;
     bool failed = false;
     auto fail_here = [&]() {
         failed = true;
@@ -258,31 +273,38 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- digit producer
-            // A second walker over the same stage sequence, kPrefetch stages ahead, pulls each digit
-            // box into L2 before its load is issued.
+            // ---------------- digit producer (thread 0; stages below `early` are already issued)
+            // For the narrowest tiles, whose stages stream fastest, a second walker over the same
+            // stage sequence pulls each digit box into L2 kPrefetch stages before its load; wider
+            // tiles measured faster without it (each prefetch costs the issuing thread ~0.1 us).
+            constexpr int kPrefetch = BN <= 32 ? 8 : 0;
             uint32_t pks = 0;
             Seg ps;
             SegIter pit(args, part, nparts);
-            bool pvalid = pit.next(args, BN, TM, nparts, ps);
+            bool pvalid = kPrefetch > 0 && pit.next(args, BN, TM, nparts, ps);
             if (pvalid) pks = ps.ks0;
-            auto prefetch_next = [&]() {
+            auto walk = [&](bool issue) {
                 if (!pvalid) return;
-                tma_prefetch_l2_4d(&args.a[ps.g], 0, 0, static_cast<int32_t>(pks * KS / 128),
-                                   static_cast<int32_t>((ps.m0 + roff) / kBM));
+                if (issue)
+                    tma_prefetch_l2_4d(&args.a[ps.g], 0, 0, static_cast<int32_t>(pks * KS / 128),
+                                       static_cast<int32_t>((ps.m0 + roff) / kBM));
                 if (++pks >= ps.ks1) {
                     pvalid = pit.next(args, BN, TM, nparts, ps);
                     if (pvalid) pks = ps.ks0;
                 }
             };
-            for (int i = 0; i < kPrefetch; ++i) prefetch_next();
+            if constexpr (kPrefetch > 0) {
+                for (uint32_t i = 0; i < early; ++i) walk(false);
+                for (int i = 0; i < kPrefetch; ++i) walk(true);
+            }
             uint32_t it = 0;
             Seg tr;
             SegIter sit(args, part, nparts);
             while (!failed && sit.next(args, BN, TM, nparts, tr)) {
                 for (uint32_t ks = tr.ks0; ks < tr.ks1; ++ks, ++it) {
+                    if (it < early) continue;
                     const uint32_t sd = it % SD;
-                    prefetch_next();
+                    if constexpr (kPrefetch > 0) walk(true);
                     if (!mbar_wait(&dfree[sd], ((it / SD) & 1u) ^ 1u, abort)) {
                         fail_here();
                         break;
@@ -294,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 static_cast<int32_t>(ks * KS / 128), static_cast<int32_t>((tr.m0 + roff) / kBM));
                 }
             }
-            drain_ring(dfull, SD, it);
+            drain_ring(dfull, SD, it > early ? it : early);
         }
     } else if (warp == 14) {
         if (lane == 0) {
