@@ -166,7 +166,9 @@ int qpadl_pir_get_option(const qpadl_db *db, int option, int64_t *value);
  *    QPADL_OPT_STREAM_RAW in {0, 1};
  *  - if max_batch >= 2: QPADL_OPT_U8_KSTEP in {128, 256} at
  *    min(max(max_batch, 4), 16) queries (when that batch takes the uint8-
- *    digit GEMM), then QPADL_OPT_TENSOR_MIN_BATCH = the first B in 2..4 at
+ *    digit GEMM; both are timed, but with QPADL_OPT_PAIR_GEMM on the depth
+ *    stays 128, the only one the pair tiles take), then
+ *    QPADL_OPT_TENSOR_MIN_BATCH = the first B in 2..4 at
  *    which the tensor path beats the streaming kernel (5 if none does);
  *  - if max_batch > 32: QPADL_OPT_U8_MAX_BATCH = 128 if the uint8-digit GEMM
  *    beats the fp16-copy GEMM at 128 queries, else 64 if it does at 64, else

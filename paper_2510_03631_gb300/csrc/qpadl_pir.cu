@@ -862,7 +862,10 @@ int qpadl_pir_autotune(qpadl_db *db, uint32_t max_batch, qpadl_stream_t stream, 
                     kpick = ks[k];
                 }
             }
-            db->u8_kstep = kpick;
+            // the pair form exists only with 128-digit stages: while it is on, a deeper stage would
+            // also move every batch onto single-SM tiles, which one probe size cannot weigh (both
+            // depths are timed and reported; the depth stays 128)
+            db->u8_kstep = (db->pair_gemm && db->num_sms >= 2) ? 128 : kpick;
         }
         uint32_t threshold = db->tensor_min_batch;
         for (uint32_t B = 2; B <= 4; ++B) {

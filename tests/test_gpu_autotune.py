@@ -45,6 +45,12 @@ def test_autotune_picks_valid_options_and_keeps_answers_exact(cuda, R, C, max_ba
         assert 2 <= rep["tensor_min_batch"] <= 5
         assert pir.qpadl_pir_get_option(db, pir.QPADL_OPT_TENSOR_MIN_BATCH) == rep["tensor_min_batch"]
         assert all(t > 0 for t in rep["stream_ms"][:1])
+        if rep["u8_kstep_ms"][0] > 0:
+            # both stage depths were timed; with the pair tiles on (the default) the depth stays at
+            # 128, the only one they take
+            assert rep["u8_kstep_ms"][1] > 0
+            assert pir.qpadl_pir_get_option(db, pir.QPADL_OPT_PAIR_GEMM) == 1
+            assert pir.qpadl_pir_get_option(db, pir.QPADL_OPT_U8_KSTEP) == 128 == rep["u8_kstep"]
     else:
         assert pir.qpadl_pir_get_option(db, pir.QPADL_OPT_TENSOR_MIN_BATCH) == before
     _check_answers(db, D, C, R, (1, 2, 3, 5, 16))
