@@ -127,6 +127,10 @@ struct ModPEpi {
         if (r < 0) r += p;
         out[i * ld_m + (uint64_t)b * ld_b] = static_cast<uint32_t>(r);
     }
+    // a residue already in [0, p)
+    __device__ __forceinline__ void store(uint64_t i, uint32_t b, uint32_t r) const {
+        out[i * ld_m + (uint64_t)b * ld_b] = r;
+    }
     __device__ __forceinline__ void operator()(uint64_t i, uint32_t b, uint32_t dot) const { put(i, b, dot, 0u); }
 };
 

@@ -392,9 +392,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
                         // the second-to-last chunk's buffer is held for the final combine
                         continue;
                     }
-                    // last chunk: its buffer plus the other buffer's residue, mod p, to the output
+                    // last chunk: its buffer plus the other buffer's residue, mod p, to the output.  Each
+                    // buffer is first cut to a representative |r| <= 1.5 p as in the pass above, so
+                    // their sum is an exact float of at most 3 p; q = floor(sum / p) is then off by at
+                    // most one, which the two compares put right, and the residue stays exact.
                     const uint32_t oth = tmem_base + lane_addr + (buf ^ 1u) * BN;
-                    const int32_t ip = epi.p;
+                    constexpr float kRound = 12582912.0f;
 #pragma unroll 1
                     for (int j = 0; j < BN / 32; ++j) {
                         uint32_t v[32], w[32];
@@ -403,12 +406,18 @@ __global__ void __launch_bounds__(kPThreads, 1)
                         tmem_wait_ld();
 #pragma unroll
                         for (int q = 0; q < 32; ++q) {
-                            int32_t x = __float2int_rn(__uint_as_float(v[q]));
-                            if (nchunks >= 2) x += __float2int_rn(__uint_as_float(w[q]));
-                            int32_t r = x % ip;
-                            if (r < 0) r += ip;
+                            float x = __uint_as_float(v[q]);
+                            x = __fmaf_rn(-__fsub_rn(__fmaf_rn(x, inv, kRound), kRound), pf, x);
+                            if (nchunks >= 2) {
+                                float y = __uint_as_float(w[q]);
+                                y = __fmaf_rn(-__fsub_rn(__fmaf_rn(y, inv, kRound), kRound), pf, y);
+                                x = __fadd_rn(x, y);
+                            }
+                            float r = __fmaf_rn(-floorf(x * inv), pf, x);
+                            if (r < 0.0f) r = __fadd_rn(r, pf);
+                            if (r >= pf) r = __fsub_rn(r, pf);
                             const uint32_t vi = v0 + 32u * j + q;
-                            if (row < M && vi < NV) epi.put(row, vi, static_cast<uint32_t>(r), 0u);
+                            if (row < M && vi < NV) epi.store(row, vi, static_cast<uint32_t>(r));
                         }
                     }
                     tc_fence_before();
