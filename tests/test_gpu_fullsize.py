@@ -95,7 +95,9 @@ def test_query_matches_oracle_sampled(big):
         assert np.array_equal(Q_np[b], oracle.query(A_np, S_np[b], E_np[b], int(cols[b]), 1 << 24))
 
 
-@pytest.mark.parametrize("B", [256, 1024])
+# 16: uint8-digit GEMM, 64-column tiles; 64: two 128-column tiles per row tile; 128: the fp16-copy
+# pair GEMM with a split tail; 256, 1024: whole tiles
+@pytest.mark.parametrize("B", [16, 64, 128, 256, 1024])
 def test_batched_response_full_size(big, B):
     S_np, E_np, cols, Q = _queries(big, B, seed=300 + B)
     ans = torch.empty(B * R, dtype=torch.int32, device="cuda")
