@@ -46,6 +46,15 @@
 // (4 - u) QPT/2 rows of its block and the MMA runs N = (4 - u) QPT; column
 // (3 - t) QPT/2 + q is shift t of leader secret q and column N/2 + (3 - t)
 // QPT/2 + q shift t of peer secret q.
+//
+// Schedule.  Whole pair tiles go round-robin to the clusters.  A plain store may split its last
+// wave stream-K style (PairPieceIter: clusters grouped by vector tile so the clusters on one row
+// tile read its rows together), the split pieces adding into a zeroed output.
+//
+// One-row mode (ModPEpi: Z_p vectors as single centred fp16 rows, 256-wide tiles).  The running
+// sums stay in TMEM: after every 512-deep chunk the epilogue replaces its accumulator buffer by
+// small representatives of the sums mod p, and the MMA accumulates the chunk after next on top;
+// the last two buffers are combined mod p at the end of the tile.
 #include <cstdint>
 #include <type_traits>
 #include <cuda_fp16.h>
