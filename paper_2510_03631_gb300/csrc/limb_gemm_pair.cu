@@ -83,7 +83,6 @@ struct PairCfg {
     static constexpr int kStages = kFit < 8 ? kFit : 8;
     static constexpr uint32_t kTmemCols = 2 * BN;                 // two accumulators
     static constexpr int kSmemBytes = kStages * kStageBytes + 256 + 1024;
-    static constexpr int kQPT = BN / 4;                           // vectors per pair tile
     static_assert(kSmemBytes <= 227 * 1024, "shared memory");
     static_assert(kStages >= 4, "pipeline depth");
 };
