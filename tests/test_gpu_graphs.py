@@ -1,4 +1,4 @@
-"""Batched Responses captured in a CUDA graph and replayed with new queries.
+"""Batched Responses (LWE, Goldberg, Chor) captured in a CUDA graph and replayed with new queries.
 
 The uint8-digit GEMM is launched as the programmatic dependent of the kernel
 that makes its limbs and zeroes its output; under stream capture that launch
@@ -88,5 +88,31 @@ def test_goldberg_answers_replayed_in_a_cuda_graph(cuda, B):
         assert pir.qpadl_goldberg_status(h) == pir.QPADL_OK
         got = pir.as_u32(out).reshape(B, R)
         assert np.array_equal(got, oracle.goldberg_answer(D, Q_np, p, threads=oracle.max_threads())), seed
+    del g
+    h.close()
+
+
+@pytest.mark.parametrize("B,m4rm_min", [(1, 257), (8, 257), (32, 257), (100, 64)])   # scans / four-Russians
+def test_chor_answers_replayed_in_a_cuda_graph(cuda, B, m4rm_min):
+    rows, bits = 3000, 4096
+    DB = inputs.chor_db(rows, bits, seed=B + 3)
+    h = pir.qpadl_chor_setup(rows, bits, torch.from_numpy(DB.view(np.int32).reshape(-1)).cuda())
+    pir.qpadl_chor_set_option(h, pir.QPADL_CHOR_OPT_M4RM_MIN_BATCH, m4rm_min)
+    Q0 = inputs.chor_queries(B, rows, seed=B)
+    Q = torch.from_numpy(np.ascontiguousarray(Q0).view(np.int32).reshape(-1)).cuda()
+    out = torch.empty(B * h.words, dtype=torch.int32, device="cuda")
+    call = lambda: pir.qpadl_chor_answer_batch(h, Q, out)
+    call()
+    torch.cuda.synchronize()
+    g = _capture(call)
+    for seed in (B + 11, B + 12):
+        Q_np = inputs.chor_queries(B, rows, seed=seed)
+        Q.copy_(torch.from_numpy(np.ascontiguousarray(Q_np).view(np.int32).reshape(-1)))
+        out.fill_(-1)
+        g.replay()
+        torch.cuda.synchronize()
+        assert pir.qpadl_chor_status(h) == pir.QPADL_OK
+        got = pir.as_u32(out).reshape(B, h.words)
+        assert np.array_equal(got, oracle.chor_answer(DB, rows, Q_np, threads=oracle.max_threads())), seed
     del g
     h.close()
