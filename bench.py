@@ -309,6 +309,33 @@ def run_reference(args, budget_s: float = 150.0):
 
 
 # ----------------------------------------------------------------------------- serving
+def _graph_ms(torch, fn, B):
+    """Device time of one call of fn: calls captured back to back in a CUDA graph (4 per replay
+    up to 256 queries, else 1), as the batch sweep times them; CUDA events around the replays."""
+    per = 4 if B <= 256 else 1
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(per):
+            fn()
+    g.replay()
+    torch.cuda.synchronize()
+    reps = 10 if B <= 256 else 4
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    del g
+    return e0.elapsed_time(e1) / (reps * per)
+
+
 def _pct(a, q):
     return float(np.percentile(a, q)) if len(a) else None
 
@@ -431,7 +458,8 @@ def chor_measure(torch, pir, inputs, seed=31):
     DB_np = inputs.chor_db(rows, bits, seed=seed)
     h = pir.qpadl_chor_setup(rows, bits, torch.from_numpy(DB_np.view(np.int32).reshape(-1)).cuda())
     peak, peak_kind = _peaks()
-    res = {"workload": f"{rows} records x {bits} bits (1 GiB)", "batches": {}}
+    res = {"workload": f"{rows} records x {bits} bits (1 GiB)", "batches": {},
+           "timing": "CUDA events over graph replays of back-to-back calls (4 per replay up to 256 queries)"}
     one_qps = None
     for B in w["batches"]:
         Q_np = inputs.chor_queries(B, rows, seed=seed + B)
@@ -442,14 +470,7 @@ def chor_measure(torch, pir, inputs, seed=31):
         out = torch.empty(B * W, dtype=torch.int32, device="cuda")
         pir.qpadl_chor_answer_batch(h, Q, out)
         torch.cuda.synchronize()
-        reps = 20 if B <= 32 else 5
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            pir.qpadl_chor_answer_batch(h, Q, out)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
+        ms = _graph_ms(torch, lambda: pir.qpadl_chor_answer_batch(h, Q, out), B)
         if not np.array_equal(pir.as_u32(out)[:W], DB_np[r0]) or pir.qpadl_chor_status(h) != 0:
             raise SystemExit("bench: Chor answer to a one-record query differs from that record")
         qps = B / (ms * 1e-3)
@@ -481,7 +502,8 @@ def goldberg_measure(torch, pir, inputs, seed=41):
     R, C, p = w["rows"], w["cols"], 257
     D_np = inputs.db_digits(R, C, 256, seed=seed)
     h = pir.qpadl_goldberg_setup(R, C, p, torch.from_numpy(D_np).cuda())
-    res = {"workload": f"{C} records x {R} bytes (1 GiB), p = {p}", "batches": {}}
+    res = {"workload": f"{C} records x {R} bytes (1 GiB), p = {p}", "batches": {},
+           "timing": "CUDA events over graph replays of back-to-back calls (4 per replay up to 256 queries)"}
     one_qps = None
     for B in (1, 8, 32, 64, 128, 256, 1024):
         Q_np = (inputs.uniform_u32(B * C, seed=seed + B, tag=inputs.TAG_MISC) % p).reshape(B, C)
@@ -492,14 +514,7 @@ def goldberg_measure(torch, pir, inputs, seed=41):
         out = torch.empty(B * R, dtype=torch.int32, device="cuda")
         pir.qpadl_goldberg_answer_batch(h, Q, out)
         torch.cuda.synchronize()
-        reps = 20 if B <= 32 else 5
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            pir.qpadl_goldberg_answer_batch(h, Q, out)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
+        ms = _graph_ms(torch, lambda: pir.qpadl_goldberg_answer_batch(h, Q, out), B)
         got = pir.as_u32(out).reshape(B, R)[0]
         if not np.array_equal(got, D_np[:, j0].astype(np.uint32)) or pir.qpadl_goldberg_status(h) != 0:
             raise SystemExit("bench: Goldberg answer to a one-record query differs from that record")
